@@ -1,0 +1,422 @@
+/*
+ * srng_oracle.c -- plain, slow, obviously correct CPU oracle for the bulk
+ * uniform-generation path of arXiv 1412.8266 (ShoveRand).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline / reference leg load this file's library.  It shares
+ * no code, header, table or constant generator with the CUDA library, and the
+ * CUDA library never loads it.
+ *
+ * Every function is the plain definition of what it computes, written for a
+ * reader who checks it against the paper by eye:
+ *
+ *   - MRG32k3a (paper Sec. 4.1, which cites L'Ecuyer 1999 for the generator):
+ *     two order-3 multiple recursive components modulo m1 = 2^32-209 and
+ *     m2 = 2^32-22853, a state of six integers, a period of about 2^191, and
+ *     sequence splitting (Sec. 2.3) into 2^64 streams of 2^127 draws, each cut
+ *     into substreams of 2^76 draws.  The recurrence coefficients are those of
+ *     the cited publication; the paper itself does not print them.
+ *   - Philox4x32-10 (paper Sec. 4.3, which cites Salmon et al. 2011): a
+ *     counter-based generator whose parameter is a key; ten rounds of a
+ *     multiply/xor network on a 4 x 32-bit counter with a 2 x 32-bit key.
+ *   - The integer -> uniform conversions, the Monte Carlo quarter-circle hit
+ *     test and the SplitMix64 seed expansion, which the paper leaves open; the
+ *     readings taken are stated beside each function.
+ *
+ * Arithmetic: exact 64-bit (and, for the hit test, 128-bit) integers; the one
+ * floating-point rounding (MRG32k3a -> double) is a single IEEE-754
+ * round-to-nearest-even multiply, so the file is built with
+ * -ffp-contract=off and without fast-math.
+ *
+ * Parallelism: the *_bulk and *_batch entry points split independent streams
+ * or instances over OpenMP threads; each stream is still stepped one draw at a
+ * time, in order.
+ */
+#include <stdint.h>
+#include <string.h>
+#include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------------------------------------------------------------- */
+/* MRG32k3a definition (Sec. 4.1; coefficients of L'Ecuyer 1999)           */
+/* ---------------------------------------------------------------------- */
+
+#define ORC_M1 4294967087ULL /* 2^32 - 209   */
+#define ORC_M2 4294944443ULL /* 2^32 - 22853 */
+#define ORC_A12 1403580LL    /* x1[n] =  a12 x1[n-2] - a13 x1[n-3]  mod m1 */
+#define ORC_A13 810728LL
+#define ORC_A21 527612LL     /* x2[n] =  a21 x2[n-1] - a23 x2[n-3]  mod m2 */
+#define ORC_A23 1370589LL
+
+enum { ORC_OUT_U32 = 0, ORC_OUT_F32 = 1, ORC_OUT_F64 = 2 };
+
+/* State layout: s[0..2] = (x1[n-3], x1[n-2], x1[n-1]),
+ *               s[3..5] = (x2[n-3], x2[n-2], x2[n-1]).
+ * One step computes x1[n], x2[n], shifts them in, and returns the combined
+ * value z = (x1[n] - x2[n]) mod m1, taken in [1, m1] (z = m1 when the two
+ * components are equal).  Draw k of a stream is the value returned by step
+ * k+1 from the stream's start state ("step, then output"). */
+uint32_t oracle_mrg_step(uint32_t s[6])
+{
+    int64_t p1 = (ORC_A12 * (int64_t)s[1] - ORC_A13 * (int64_t)s[0]) % (int64_t)ORC_M1;
+    if (p1 < 0) p1 += (int64_t)ORC_M1;
+    s[0] = s[1]; s[1] = s[2]; s[2] = (uint32_t)p1;
+
+    int64_t p2 = (ORC_A21 * (int64_t)s[5] - ORC_A23 * (int64_t)s[3]) % (int64_t)ORC_M2;
+    if (p2 < 0) p2 += (int64_t)ORC_M2;
+    s[3] = s[4]; s[4] = s[5]; s[5] = (uint32_t)p2;
+
+    if (p1 > p2) return (uint32_t)(p1 - p2);
+    return (uint32_t)(p1 - p2 + (int64_t)ORC_M1);
+}
+
+/* The one-step transition of each component as a 3x3 matrix acting on the
+ * column (x[n-3], x[n-2], x[n-1]); entries reduced into [0, m). */
+void oracle_mrg_matrix(int comp, uint64_t a[9])
+{
+    uint64_t m = comp == 0 ? ORC_M1 : ORC_M2;
+    memset(a, 0, 9 * sizeof(uint64_t));
+    a[0 * 3 + 1] = 1;
+    a[1 * 3 + 2] = 1;
+    if (comp == 0) {
+        a[2 * 3 + 0] = m - (uint64_t)ORC_A13;
+        a[2 * 3 + 1] = (uint64_t)ORC_A12;
+    } else {
+        a[2 * 3 + 0] = m - (uint64_t)ORC_A23;
+        a[2 * 3 + 2] = (uint64_t)ORC_A21;
+    }
+}
+
+/* c = a * b mod m for 3x3 matrices with entries in [0, m), m < 2^32. */
+static void mat_mul(const uint64_t a[9], const uint64_t b[9], uint64_t m, uint64_t c[9])
+{
+    uint64_t t[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            uint64_t acc = 0;
+            for (int k = 0; k < 3; ++k)
+                acc = (acc + (a[i * 3 + k] * b[k * 3 + j]) % m) % m;
+            t[i * 3 + j] = acc;
+        }
+    memcpy(c, t, sizeof t);
+}
+
+/* out = A_comp^e mod m, e = e_hi * 2^64 + e_lo, by square-and-multiply. */
+void oracle_mrg_matpow(int comp, uint64_t e_hi, uint64_t e_lo, uint64_t out[9])
+{
+    uint64_t m = comp == 0 ? ORC_M1 : ORC_M2;
+    uint64_t base[9], r[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    oracle_mrg_matrix(comp, base);
+    for (int bit = 0; bit < 128; ++bit) {
+        uint64_t word = bit < 64 ? e_lo : e_hi;
+        if ((word >> (bit & 63)) & 1) mat_mul(r, base, m, r);
+        mat_mul(base, base, m, base);
+    }
+    memcpy(out, r, sizeof r);
+}
+
+/* v = a * v mod m for one component (3 entries). */
+static void mat_vec(const uint64_t a[9], uint32_t v[3], uint64_t m)
+{
+    uint64_t t[3];
+    for (int i = 0; i < 3; ++i) {
+        uint64_t acc = 0;
+        for (int k = 0; k < 3; ++k) acc = (acc + (a[i * 3 + k] * (uint64_t)v[k]) % m) % m;
+        t[i] = acc;
+    }
+    for (int i = 0; i < 3; ++i) v[i] = (uint32_t)t[i];
+}
+
+/* Advance a state by n = n_hi * 2^64 + n_lo draws: s <- A^n s (Sec. 2.3,
+ * sequence splitting; the jump is the n-th matrix power). */
+void oracle_mrg_jump(uint32_t s[6], uint64_t n_hi, uint64_t n_lo)
+{
+    uint64_t a1[9], a2[9];
+    oracle_mrg_matpow(0, n_hi, n_lo, a1);
+    oracle_mrg_matpow(1, n_hi, n_lo, a2);
+    mat_vec(a1, s, ORC_M1);
+    mat_vec(a2, s + 3, ORC_M2);
+}
+
+/* Start states of `count` consecutive streams (Sec. 4.1: streams of 2^127
+ * draws, substreams of 2^76).  Stream i starts 2^e draws after stream i-1;
+ * stream 0 is the seed state.  Written out as the definition: step from the
+ * seed state to stream `first`, then one jump of 2^e per following stream.
+ * out holds 6 words per stream (same order as the state layout above). */
+void oracle_mrg_stream_starts(const uint32_t seed_state[6], int e, uint64_t first, uint64_t count,
+                              uint32_t *out)
+{
+    uint64_t j1[9], j2[9], f1[9], f2[9];
+    uint64_t e_hi = e >= 64 ? (1ULL << (e - 64)) : 0;
+    uint64_t e_lo = e >= 64 ? 0 : (1ULL << e);
+    oracle_mrg_matpow(0, e_hi, e_lo, j1);           /* A1^(2^e) */
+    oracle_mrg_matpow(1, e_hi, e_lo, j2);           /* A2^(2^e) */
+    uint32_t y[6];
+    memcpy(y, seed_state, sizeof y);
+    /* stream `first` = (A^(2^e))^first applied to the seed state */
+    uint64_t p1[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, p2[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    memcpy(f1, j1, sizeof f1);
+    memcpy(f2, j2, sizeof f2);
+    for (uint64_t k = first; k; k >>= 1) {
+        if (k & 1) { mat_mul(p1, f1, ORC_M1, p1); mat_mul(p2, f2, ORC_M2, p2); }
+        mat_mul(f1, f1, ORC_M1, f1);
+        mat_mul(f2, f2, ORC_M2, f2);
+    }
+    mat_vec(p1, y, ORC_M1);
+    mat_vec(p2, y + 3, ORC_M2);
+    for (uint64_t i = 0; i < count; ++i) {
+        memcpy(out + 6 * i, y, sizeof y);
+        mat_vec(j1, y, ORC_M1);
+        mat_vec(j2, y + 3, ORC_M2);
+    }
+}
+
+/* A state is valid when every word of component c is below m_c and no
+ * component is all zero (the all-zero component is a fixed point). */
+int oracle_mrg_state_valid(const uint32_t s[6])
+{
+    for (int i = 0; i < 3; ++i) if (s[i] >= ORC_M1) return 0;
+    for (int i = 3; i < 6; ++i) if (s[i] >= ORC_M2) return 0;
+    if (s[0] == 0 && s[1] == 0 && s[2] == 0) return 0;
+    if (s[3] == 0 && s[4] == 0 && s[5] == 0) return 0;
+    return 1;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Seed expansion (the paper gives none; Sec. 2.3 only names seeding by     */
+/* random statuses).  Reading: SplitMix64 (Steele, Lea & Flood, OOPSLA      */
+/* 2014) seeded with the 64-bit seed; six successive outputs r0..r5 give    */
+/* x1[i] = r_i mod m1 and x2[i] = r_(i+3) mod m2; a component that comes    */
+/* out all zero is replaced by (12345, 12345, 12345).                       */
+/* ---------------------------------------------------------------------- */
+
+uint64_t oracle_splitmix64_next(uint64_t *state)
+{
+    *state += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = *state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+void oracle_seed_expand(uint64_t seed, uint32_t out[6])
+{
+    uint64_t st = seed;
+    uint64_t r[6];
+    for (int i = 0; i < 6; ++i) r[i] = oracle_splitmix64_next(&st);
+    for (int i = 0; i < 3; ++i) out[i] = (uint32_t)(r[i] % ORC_M1);
+    for (int i = 0; i < 3; ++i) out[3 + i] = (uint32_t)(r[3 + i] % ORC_M2);
+    if (out[0] == 0 && out[1] == 0 && out[2] == 0) out[0] = out[1] = out[2] = 12345;
+    if (out[3] == 0 && out[4] == 0 && out[5] == 0) out[3] = out[4] = out[5] = 12345;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Philox4x32-10 (Sec. 4.3; definition of Salmon et al. 2011)              */
+/* ---------------------------------------------------------------------- */
+
+#define ORC_PHILOX_M0 0xD2511F53U
+#define ORC_PHILOX_M1 0xCD9E8D57U
+#define ORC_PHILOX_W0 0x9E3779B9U /* floor(2^32 / golden ratio)   */
+#define ORC_PHILOX_W1 0xBB67AE85U /* floor(2^32 * (sqrt(3) - 1))  */
+
+/* One round: the two multiplies give (hi, lo) halves; the outputs are
+ * (hi1 ^ x1 ^ k0, lo1, hi0 ^ x3 ^ k1, lo0) with (hi0,lo0) = M0 * x0 and
+ * (hi1,lo1) = M1 * x2.  Ten rounds, the key bumped by (W0, W1) between them. */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += ORC_PHILOX_W0; k1 += ORC_PHILOX_W1; }
+        uint64_t p0 = (uint64_t)ORC_PHILOX_M0 * x0;
+        uint64_t p1 = (uint64_t)ORC_PHILOX_M1 * x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Word `p` of Philox stream `s` under key (k0, k1).  Reading of the paper's
+ * "one key per thread" parameterisation as a counter split: the stream index
+ * fills counter words 2-3, the block index q = p / 4 fills counter words
+ * 0-1, and the draw is word p mod 4 of that block. */
+uint32_t oracle_philox_word(uint32_t k0, uint32_t k1, uint64_t s, uint64_t p)
+{
+    uint64_t q = p / 4;
+    uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), (uint32_t)s, (uint32_t)(s >> 32)};
+    uint32_t key[2] = {k0, k1};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    return out[p % 4];
+}
+
+/* ---------------------------------------------------------------------- */
+/* Integer -> uniform conversions (fixed readings)                          */
+/* ---------------------------------------------------------------------- */
+
+/* 24-bit single: the top 24 bits of the word times 2^-24, in [0, 1). */
+float oracle_to_f32(uint32_t v)
+{
+    return ldexpf((float)(v >> 8), -24);
+}
+
+/* MRG32k3a double: z * norm rounded once to nearest even, norm being the
+ * double nearest 1/(m1+1); z in [1, m1] gives a value in (0, 1). */
+double oracle_mrg_to_f64(uint32_t z)
+{
+    const double norm = 1.0 / 4294967088.0; /* 1 / (m1 + 1), one IEEE division */
+    return (double)z * norm;
+}
+
+/* Philox double: (w + 1/2) * 2^-32, exact, in (0, 1). */
+double oracle_philox_to_f64(uint32_t w)
+{
+    return ((double)w + 0.5) / 4294967296.0;
+}
+
+static void store_value(int out_type, void *out, uint64_t i, uint32_t v, int is_mrg)
+{
+    if (out_type == ORC_OUT_U32) ((uint32_t *)out)[i] = v;
+    else if (out_type == ORC_OUT_F32) ((float *)out)[i] = oracle_to_f32(v);
+    else ((double *)out)[i] = is_mrg ? oracle_mrg_to_f64(v) : oracle_philox_to_f64(v);
+}
+
+/* n draws of one MRG32k3a stream from state s (advanced in place). */
+void oracle_mrg_generate(uint32_t s[6], uint64_t n, int out_type, void *out)
+{
+    for (uint64_t k = 0; k < n; ++k) store_value(out_type, out, k, oracle_mrg_step(s), 1);
+}
+
+/* n words of Philox stream s starting at position p. */
+void oracle_philox_generate(uint32_t k0, uint32_t k1, uint64_t s, uint64_t p, uint64_t n,
+                            int out_type, void *out)
+{
+    for (uint64_t k = 0; k < n; ++k) store_value(out_type, out, k, oracle_philox_word(k0, k1, s, p + k), 0);
+}
+
+/* Stream-major bulk output of many streams:
+ * out[i * n + k] = draw k of stream i.  MRG: states holds 6 words per stream
+ * and is advanced in place.  Philox: positions[i] is the start position of
+ * stream (stream0 + i) and is advanced by n. */
+void oracle_mrg_bulk(uint32_t *states, uint64_t n_streams, uint64_t n, int out_type, void *out,
+                     int threads)
+{
+    size_t esz = out_type == ORC_OUT_F64 ? 8 : 4;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t i = 0; i < (int64_t)n_streams; ++i)
+        oracle_mrg_generate(states + 6 * i, n, out_type, (char *)out + (size_t)i * n * esz);
+}
+
+void oracle_philox_bulk(uint32_t k0, uint32_t k1, uint64_t stream0, uint64_t *positions,
+                        uint64_t n_streams, uint64_t n, int out_type, void *out, int threads)
+{
+    size_t esz = out_type == ORC_OUT_F64 ? 8 : 4;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t i = 0; i < (int64_t)n_streams; ++i) {
+        oracle_philox_generate(k0, k1, stream0 + (uint64_t)i, positions[i], n, out_type,
+                               (char *)out + (size_t)i * n * esz);
+        positions[i] += n;
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Monte Carlo quarter-circle hit count (fused consumer reading).          */
+/* Draws are taken in pairs (2k, 2k+1), k < floor(L/2); a pair hits when    */
+/* the point lies strictly inside the quarter disc, tested exactly on the   */
+/* defined uniforms:                                                        */
+/*   Philox: u = (w >> 8) 2^-24   ->  a^2 + b^2 < 2^48                      */
+/*   MRG   : u = z / (m1 + 1)     ->  z1^2 + z2^2 < (m1 + 1)^2              */
+/* ---------------------------------------------------------------------- */
+
+int oracle_pi_hit_philox(uint32_t w0, uint32_t w1)
+{
+    unsigned __int128 a = w0 >> 8, b = w1 >> 8;
+    return a * a + b * b < ((unsigned __int128)1 << 48);
+}
+
+int oracle_pi_hit_mrg(uint32_t z0, uint32_t z1)
+{
+    unsigned __int128 a = z0, b = z1, r = ORC_M1 + 1;
+    return a * a + b * b < r * r;
+}
+
+int64_t oracle_mrg_pi_count(uint32_t s[6], uint64_t length)
+{
+    int64_t hits = 0;
+    for (uint64_t k = 0; k + 1 < length; k += 2) {
+        uint32_t z0 = oracle_mrg_step(s);
+        uint32_t z1 = oracle_mrg_step(s);
+        hits += oracle_pi_hit_mrg(z0, z1);
+    }
+    if (length & 1) (void)oracle_mrg_step(s); /* the unpaired last draw is consumed, not used */
+    return hits;
+}
+
+int64_t oracle_philox_pi_count(uint32_t k0, uint32_t k1, uint64_t s, uint64_t p, uint64_t length)
+{
+    int64_t hits = 0;
+    for (uint64_t k = 0; k + 1 < length; k += 2)
+        hits += oracle_pi_hit_philox(oracle_philox_word(k0, k1, s, p + k),
+                                     oracle_philox_word(k0, k1, s, p + k + 1));
+    return hits;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Batched instances: instance i draws `lengths[i]` values from its own     */
+/* stream.  gens[i] = 0 for MRG32k3a (start state in mrg_states, 6 words    */
+/* per instance, not modified), 1 for Philox (stream philox_streams[i] from */
+/* position philox_pos[i] under key (k0, k1)).                              */
+/* mode 0: u32 output written at out_offsets[i]; mode 1: hit counts.        */
+/* ---------------------------------------------------------------------- */
+
+void oracle_batch(uint64_t n_inst, const int32_t *gens, const uint32_t *mrg_states,
+                  uint32_t k0, uint32_t k1, const uint64_t *philox_streams,
+                  const uint64_t *philox_pos, const uint64_t *lengths,
+                  const uint64_t *out_offsets, int mode, int out_type, void *out,
+                  int64_t *counts, int threads)
+{
+    size_t esz = out_type == ORC_OUT_F64 ? 8 : 4;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t i = 0; i < (int64_t)n_inst; ++i) {
+        if (gens[i] == 0) {
+            uint32_t s[6];
+            memcpy(s, mrg_states + 6 * i, sizeof s);
+            if (mode == 0)
+                oracle_mrg_generate(s, lengths[i], out_type, (char *)out + out_offsets[i] * esz);
+            else
+                counts[i] = oracle_mrg_pi_count(s, lengths[i]);
+        } else {
+            if (mode == 0)
+                oracle_philox_generate(k0, k1, philox_streams[i], philox_pos[i], lengths[i],
+                                       out_type, (char *)out + out_offsets[i] * esz);
+            else
+                counts[i] = oracle_philox_pi_count(k0, k1, philox_streams[i], philox_pos[i],
+                                                   lengths[i]);
+        }
+    }
+}
+
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

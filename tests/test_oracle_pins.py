@@ -1,0 +1,408 @@
+"""Pins of the CPU oracle to things other than itself (no GPU needed).
+
+Each test states what it pins and to what: the period the paper gives for
+MRG32k3a (Sec. 4.1), its stream/substream spacing (Sec. 4.1), number theory
+(primality, primitivity, exact rational arithmetic), brute-force stepping on
+small inputs, statistics, and an independent third-party implementation
+(NVIDIA cuRAND's host-side generators, run as a library) for the generator
+definitions the paper cites but does not print.
+"""
+import ctypes
+import math
+import random
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import sympy
+
+from oracle import oracle as O
+
+M1, M2 = O.M1, O.M2
+
+
+def _pymatmul(a, b, m):
+    return [[sum(int(a[i][k]) * int(b[k][j]) for k in range(3)) % m for j in range(3)] for i in range(3)]
+
+
+def _pymatpow(a, e, m):
+    r = [[int(i == j) for j in range(3)] for i in range(3)]
+    a = [[int(x) for x in row] for row in a]
+    while e:
+        if e & 1:
+            r = _pymatmul(r, a, m)
+        a = _pymatmul(a, a, m)
+        e >>= 1
+    return r
+
+
+def _rand_state(rng):
+    return [rng.randrange(M1) for _ in range(3)] + [rng.randrange(M2) for _ in range(3)]
+
+
+# ------------------------------------------------------------------ MRG32k3a
+def test_moduli_are_prime():
+    """m1 = 2^32-209 and m2 = 2^32-22853 are prime (number theory)."""
+    assert M1 == 2**32 - 209 and M2 == 2**32 - 22853
+    assert sympy.isprime(M1) and sympy.isprime(M2)
+
+
+def test_step_matches_transition_matrix():
+    """The recurrence the step function applies equals the transition matrix:
+    stepping the unit states yields the matrix columns (linear algebra)."""
+    for comp, m in ((0, M1), (1, M2)):
+        a = O.mrg_matrix(comp)
+        for j in range(3):
+            e = [0, 0, 0]
+            e[j] = 1
+            st = [0] * 6
+            st[3 * comp: 3 * comp + 3] = e
+            other = 3 * (1 - comp)
+            st[other: other + 3] = [1, 2, 3]  # keep the other component non-zero
+            _, s = O.mrg_step(st)
+            col = [int(x) for x in s[3 * comp: 3 * comp + 3]]
+            assert col == [int(a[i][j]) for i in range(3)]
+
+
+def test_step_is_linear_mod_m():
+    """A wrong modular reduction breaks linearity: step(a u + b v) = a step(u) + b step(v)."""
+    rng = random.Random(7)
+    for _ in range(200):
+        u, v = _rand_state(rng), _rand_state(rng)
+        a, b = rng.randrange(1, 1 << 20), rng.randrange(1, 1 << 20)
+        w = [(a * u[i] + b * v[i]) % (M1 if i < 3 else M2) for i in range(6)]
+        if not O.mrg_state_valid(w):
+            continue
+        _, su = O.mrg_step(u)
+        _, sv = O.mrg_step(v)
+        _, sw = O.mrg_step(w)
+        for i in range(6):
+            m = M1 if i < 3 else M2
+            assert int(sw[i]) == (a * int(su[i]) + b * int(sv[i])) % m
+
+
+def _prime_factors(n):
+    return list(sympy.factorint(n).keys())
+
+
+@pytest.mark.parametrize("comp", [0, 1])
+def test_components_have_full_period(comp):
+    """Each component matrix has multiplicative order exactly m^3-1 (a primitive
+    characteristic polynomial).  This is what makes the combined period about
+    2^191 (Sec. 4.1); a mistyped coefficient almost never keeps it."""
+    m = M1 if comp == 0 else M2
+    order = m**3 - 1
+    ident = np.eye(3, dtype=np.uint64)
+    assert np.array_equal(O.mrg_matpow(comp, order), ident)
+    a = O.mrg_matrix(comp)
+    assert _pymatpow(a, order, m) == [[int(i == j) for j in range(3)] for i in range(3)]
+    for q in _prime_factors(order):
+        assert not np.array_equal(O.mrg_matpow(comp, order // q), ident), q
+
+
+def test_combined_period_is_2_pow_191():
+    """Sec. 4.1 gives a period of about 2^191: lcm(m1^3-1, m2^3-1) = product/2."""
+    p1, p2 = M1**3 - 1, M2**3 - 1
+    assert math.gcd(p1, p2) == 2
+    period = p1 * p2 // 2
+    assert abs(math.log2(period) - 191) < 0.01
+
+
+def test_jump_equals_brute_force_stepping():
+    """Jump-ahead by A^n equals n single steps (brute force, small n)."""
+    rng = random.Random(11)
+    start = [12345] * 6
+    for n in list(range(0, 40)) + [rng.randrange(1, 1 << 14) for _ in range(8)]:
+        _, stepped = O.mrg_generate(start, n)
+        assert list(O.mrg_jump(start, n)) == list(stepped), n
+    s = _rand_state(rng)
+    _, stepped = O.mrg_generate(s, 100000)
+    assert list(O.mrg_jump(s, 100000)) == list(stepped)
+
+
+def test_matpow_agrees_with_python_bigint():
+    """The oracle's 128-bit exponent square-and-multiply equals an
+    independent Python big-integer power, for the stream/substream spacings."""
+    for comp, m in ((0, M1), (1, M2)):
+        a = O.mrg_matrix(comp)
+        for e in (1 << 76, 1 << 127, (1 << 127) + (1 << 76) + 12345, 3 << 100):
+            assert O.mrg_matpow(comp, e).tolist() == _pymatpow(a, e, m)
+
+
+def test_stream_spacing_composes():
+    """Stream spacing 2^127 = 2^51 substreams of 2^76 (Sec. 4.1): stream i of a
+    stream set is substream i * 2^51 of a substream set."""
+    y0 = [12345] * 6
+    streams = O.mrg_stream_starts(y0, 127, 0, 4)
+    for i in range(4):
+        sub = O.mrg_stream_starts(y0, 76, i << 51, 1)[0]
+        assert list(streams[i]) == list(sub)
+    # and explicit powers: stream 1 = A^(2^127) y0, stream 3 = A^(2^127) applied three times
+    assert list(streams[1]) == list(O.mrg_jump(y0, 1 << 127))
+    y = list(y0)
+    for _ in range(3):
+        y = list(O.mrg_jump(y, 1 << 127))
+    assert list(streams[3]) == y
+
+
+def test_stream_starts_iterative_equals_power():
+    """Starting mid-set (by power) equals stepping stream by stream."""
+    y0 = O.seed_expand(0x5EED5EED5EED5EED)
+    all_ = O.mrg_stream_starts(y0, 76, 0, 40)
+    mid = O.mrg_stream_starts(y0, 76, 25, 15)
+    assert np.array_equal(all_[25:], mid)
+
+
+def test_state_range_invariant_and_output_range():
+    """Every state word stays in [0, m) and z in [1, m1] (definition)."""
+    rng = random.Random(3)
+    for _ in range(20):
+        s = _rand_state(rng)
+        z, st = O.mrg_generate(s, 5000)
+        assert z.min() >= 1 and int(z.max()) <= M1
+        assert O.mrg_state_valid(st)
+
+
+def test_mrg_matches_curand_host_generator(curand_path):
+    """Independent implementation: NVIDIA cuRAND's host MRG32k3a generator,
+    seeded with 0, starts from the all-12345 state and emits draws of
+    substreams spaced 2^76 apart.  Its uniform doubles are z/m1, so z is
+    recovered exactly by rounding u*m1.  The layout (which output index holds
+    which substream/draw) is discovered from the data, not assumed."""
+    lib = ctypes.CDLL(curand_path)
+    gen = ctypes.c_void_p()
+    assert lib.curandCreateGeneratorHost(ctypes.byref(gen), 121) == 0  # CURAND_RNG_PSEUDO_MRG32K3A
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(0)) == 0
+        n = 1 << 19
+        buf = (ctypes.c_double * n)()
+        assert lib.curandGenerateUniformDouble(gen, buf, ctypes.c_size_t(n)) == 0
+    finally:
+        lib.curandDestroyGenerator(gen)
+    z = np.rint(np.frombuffer(buf, dtype=np.float64) * M1).astype(np.uint64)
+    starts = O.mrg_stream_starts([12345] * 6, 76, 0, 256)
+    first = np.array([O.mrg_generate(st, 1)[0][0] for st in starts], dtype=np.uint64)
+    assert np.array_equal(z[:256], first)
+    # draws 0..5 of substreams 0..63: find the stride T of the layout, then compare
+    draws = np.stack([O.mrg_generate(st, 6)[0] for st in starts[:64]]).astype(np.uint64)
+    t = int(np.nonzero(z == draws[0, 1])[0][0])
+    assert t >= 256
+    for k in range(6):
+        if (k + 1) * t > n:
+            break
+        assert np.array_equal(z[k * t: k * t + 64], draws[:, k]), k
+
+
+# ------------------------------------------------------------------ Philox4x32-10
+@pytest.mark.parametrize("seed", [0xC0FFEE, 0x0123456789ABCDEF])
+def test_philox_matches_curand_host_generator(curand_path, seed):
+    """Independent implementation: cuRAND's host Philox4_32_10 with a 64-bit
+    seed uses key = (seed low word, seed high word); its output starts with
+    the blocks of counters (0, 0, s, 0), s = 0, 1, 2, ...  This pins the
+    round function, both multipliers, the key schedule and the word order."""
+    lib = ctypes.CDLL(curand_path)
+    gen = ctypes.c_void_p()
+    assert lib.curandCreateGeneratorHost(ctypes.byref(gen), 161) == 0  # CURAND_RNG_PSEUDO_PHILOX4_32_10
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        n = 1 << 19
+        buf = (ctypes.c_uint32 * n)()
+        assert lib.curandGenerate(gen, buf, ctypes.c_size_t(n)) == 0
+    finally:
+        lib.curandDestroyGenerator(gen)
+    w = np.frombuffer(buf, dtype=np.uint32)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for s in range(256):
+        assert list(O.philox4x32_10([0, 0, s, 0], key)) == list(w[4 * s: 4 * s + 4]), s
+    # blocks of counter word 0 = 1 follow further on, at a stride found from the data
+    blk1 = O.philox4x32_10([1, 0, 0, 0], key)
+    hits = [int(h) for h in np.nonzero(w == blk1[0])[0] if h + 4 <= n and list(w[h: h + 4]) == list(blk1)]
+    assert hits
+    t = hits[0]
+    for s in range(64):
+        assert list(O.philox4x32_10([1, 0, s, 0], key)) == list(w[t + 4 * s: t + 4 * s + 4]), s
+    # the stream/position split reads the same blocks
+    assert O.philox_word(key, 7, 2) == int(w[4 * 7 + 2])
+
+
+def test_philox_is_a_bijection_on_small_counter_sets():
+    """Counter-based generators are bijections of the counter (Salmon et al.):
+    2^16 distinct counters give 2^16 distinct blocks, and changing any single
+    counter or key bit changes the block."""
+    key = (0xC0FFEE, 0)
+    blocks = {tuple(O.philox4x32_10([c, 0x1234, 0, 7], key)) for c in range(1 << 12)}
+    assert len(blocks) == 1 << 12
+    base = O.philox4x32_10([5, 6, 7, 8], key)
+    for word in range(4):
+        for bit in (0, 13, 31):
+            c = [5, 6, 7, 8]
+            c[word] ^= 1 << bit
+            assert list(O.philox4x32_10(c, key)) != list(base)
+    assert list(O.philox4x32_10([5, 6, 7, 8], (key[0], 1))) != list(base)
+
+
+def test_philox_weyl_constants_closed_form():
+    """The key-schedule increments are floor(2^32/phi) and floor(2^32 (sqrt3-1));
+    the cuRAND comparison above shows the oracle uses exactly these."""
+    phi = (1 + sympy.sqrt(5)) / 2
+    assert int(sympy.floor(sympy.Integer(2**32) / phi)) == 0x9E3779B9
+    assert int(sympy.floor(sympy.Integer(2**32) * (sympy.sqrt(3) - 1))) == 0xBB67AE85
+
+
+# ------------------------------------------------------------------ conversions
+_EDGE_WORDS = [0, 1, 2, 255, 256, 257, (1 << 24) - 1, 1 << 24, (1 << 31) - 1, 1 << 31,
+               M2, M1 - 1, M1, M1 + 1, 2**32 - 257, 2**32 - 256, 2**32 - 2, 2**32 - 1]
+
+
+def test_f32_conversion_is_exact_24_bit():
+    """FP32 = (v >> 8) * 2^-24 exactly, in [0, 1)."""
+    rng = random.Random(5)
+    for v in _EDGE_WORDS + [rng.randrange(1 << 32) for _ in range(2000)]:
+        f = O.to_f32(v)
+        assert Fraction(f) == Fraction(v >> 8, 1 << 24)
+        assert 0.0 <= f < 1.0
+
+
+def test_mrg_f64_is_one_correctly_rounded_multiply():
+    """norm is the double nearest 1/(m1+1); the conversion is z*norm rounded
+    once to nearest even (checked in exact rational arithmetic), in (0, 1)."""
+    norm = O.mrg_to_f64(1)
+    exact = Fraction(1, M1 + 1)
+    assert Fraction(norm) == Fraction(float(exact))  # float(Fraction) rounds to nearest even
+    assert norm.hex() == "0x1.000000d00000bp-32"
+    rng = random.Random(9)
+    zs = [1, 2, 3, M1, M1 - 1, M1 - 2, 1 << 24, (1 << 25) - 1, 1 << 31, M2] + \
+         [rng.randrange(1, M1 + 1) for _ in range(5000)]
+    for z in zs:
+        assert O.mrg_to_f64(z) == float(Fraction(z) * Fraction(norm)), z
+    assert 0.0 < O.mrg_to_f64(1) and O.mrg_to_f64(M1) < 1.0
+
+
+def test_philox_f64_is_exact_midpoint():
+    """Philox FP64 = (2w+1) 2^-33 exactly, in (0, 1)."""
+    for w in _EDGE_WORDS:
+        assert Fraction(O.philox_to_f64(w)) == Fraction(2 * w + 1, 1 << 33)
+    assert 0.0 < O.philox_to_f64(0) and O.philox_to_f64(2**32 - 1) < 1.0
+
+
+def test_vector_conversion_equals_scalar():
+    v = np.array(_EDGE_WORDS[:-4] + [5, 77], dtype=np.uint32)
+    assert np.array_equal(O.convert(v, 1, O.OUT_F32), np.array([O.to_f32(int(x)) for x in v], np.float32))
+    zs = np.array([1, 2, 999, M1], dtype=np.uint32)
+    assert np.array_equal(O.convert(zs, 0, O.OUT_F64), np.array([O.mrg_to_f64(int(x)) for x in zs]))
+
+
+# ------------------------------------------------------------------ Monte Carlo pi
+def test_pi_hit_tests_equal_exact_rational_geometry():
+    """The integer hit tests equal u0^2 + u1^2 < 1 on the defined uniforms
+    (exact fractions), including points on or next to the circle."""
+    rng = random.Random(13)
+    for _ in range(3000):
+        w0, w1 = rng.randrange(1 << 32), rng.randrange(1 << 32)
+        u0, u1 = Fraction(w0 >> 8, 1 << 24), Fraction(w1 >> 8, 1 << 24)
+        assert O.pi_hit_philox(w0, w1) == (u0 * u0 + u1 * u1 < 1)
+        z0, z1 = rng.randrange(1, M1 + 1), rng.randrange(1, M1 + 1)
+        v0, v1 = Fraction(z0, M1 + 1), Fraction(z1, M1 + 1)
+        assert O.pi_hit_mrg(z0, z1) == (v0 * v0 + v1 * v1 < 1)
+    # near the circle: a^2 + b^2 just below / above 2^48
+    a = 11863283  # ~ 2^24 / sqrt 2
+    for b in range(a - 3, a + 4):
+        lhs = a * a + b * b
+        assert O.pi_hit_philox(a << 8, b << 8) == (lhs < 1 << 48)
+    r = M1 + 1
+    z0 = 3037000000
+    z1 = math.isqrt(r * r - z0 * z0)
+    for d in (-1, 0, 1, 2):
+        zz = z1 + d
+        assert O.pi_hit_mrg(z0, zz) == (z0 * z0 + zz * zz < r * r)
+    # corners
+    assert O.pi_hit_philox(0, 0) and not O.pi_hit_philox(2**32 - 1, 2**32 - 1)
+    assert O.pi_hit_mrg(1, 1) and not O.pi_hit_mrg(M1, M1)
+
+
+def test_pi_counts_match_brute_force_and_pi():
+    """Counts equal a brute-force loop over the oracle's draws, ignore the odd
+    last draw, and estimate pi/4 within 5 sigma."""
+    s = [12345] * 6
+    for L in (0, 1, 2, 3, 10, 11, 1001):
+        z, _ = O.mrg_generate(s, L)
+        brute = sum(O.pi_hit_mrg(int(z[2 * k]), int(z[2 * k + 1])) for k in range(L // 2))
+        assert O.mrg_pi_count(s, L) == brute
+        w = O.philox_generate((1, 2), 3, 5, L)
+        brute = sum(O.pi_hit_philox(int(w[2 * k]), int(w[2 * k + 1])) for k in range(L // 2))
+        assert O.philox_pi_count((1, 2), 3, 5, L) == brute
+    L = 1 << 20
+    npairs = L // 2
+    sigma = math.sqrt(npairs * (math.pi / 4) * (1 - math.pi / 4))
+    assert abs(O.mrg_pi_count(s, L) - npairs * math.pi / 4) < 5 * sigma
+    assert abs(O.philox_pi_count((0xC0FFEE, 0), 0, 0, L) - npairs * math.pi / 4) < 5 * sigma
+
+
+# ------------------------------------------------------------------ seeding
+def test_seed_expansion_structure():
+    """SplitMix64 steps its state by the odd integer nearest 2^64/phi, and
+    the expanded state obeys the range invariant (0 <= x < m, no all-zero
+    component).  The two mixing multipliers themselves are parity unpinned."""
+    st = (ctypes.c_uint64 * 1)(0)
+    lib = O._load()
+    lib.oracle_splitmix64_next(ctypes.cast(st, ctypes.POINTER(ctypes.c_uint64)))
+    gamma = int(st[0])
+    phi = (1 + sympy.sqrt(5)) / 2
+    g = int(sympy.floor(sympy.Integer(2**64) / phi))
+    assert gamma in (g, g + 1) and gamma % 2 == 1
+    outs = O.splitmix64(0x5EED, 1 << 12)
+    assert len(set(outs)) == len(outs)
+    for seed in [0, 1, 0xC0FFEE, 0x5EED5EED5EED5EED, 2**64 - 1]:
+        s = O.seed_expand(seed)
+        assert O.mrg_state_valid(s)
+        r = O.splitmix64(seed, 6)
+        assert [int(x) for x in s[:3]] == [x % M1 for x in r[:3]]
+        assert [int(x) for x in s[3:]] == [x % M2 for x in r[3:]]
+
+
+# ------------------------------------------------------------------ statistics
+def _chi2_p(counts):
+    from scipy.stats import chisquare
+    return chisquare(counts).pvalue
+
+
+@pytest.mark.parametrize("gen", ["mrg", "philox"])
+def test_chi_square_uniformity(gen):
+    """Gross-bug sanity: 2^20 draws in 256 bins, and 2^19 pairs in 16x16 cells."""
+    n = 1 << 20
+    if gen == "mrg":
+        v, _ = O.mrg_generate(O.seed_expand(0x5EED5EED5EED5EED), n)
+    else:
+        v = O.philox_generate((0xC0FFEE, 0), 0, 0, n)
+    v = v.astype(np.uint64)
+    c1 = np.bincount((v >> np.uint64(24)).astype(np.int64), minlength=256)
+    p = _chi2_p(c1)
+    assert 1e-4 < p < 1 - 1e-4, p
+    pairs = (v[0::2] >> np.uint64(28)) * np.uint64(16) + (v[1::2] >> np.uint64(28))
+    c2 = np.bincount(pairs.astype(np.int64), minlength=256)
+    p2 = _chi2_p(c2)
+    assert 1e-4 < p2 < 1 - 1e-4, p2
+
+
+# ------------------------------------------------------------------ batch oracle consistency
+def test_batch_oracle_equals_per_instance_calls():
+    rng = random.Random(17)
+    n = 9
+    lengths = [rng.randrange(0, 300) for _ in range(n)]
+    offs = np.concatenate([[0], np.cumsum(lengths)[:-1]]).astype(np.uint64)
+    gens = [i % 2 for i in range(n)]
+    states = O.mrg_stream_starts(O.seed_expand(42), 127, 0, n)
+    key = (0xC0FFEE, 0)
+    streams = list(range(n))
+    pos = [rng.randrange(0, 50) for _ in range(n)]
+    flat = O.batch(gens, states, key, streams, pos, lengths, offs, 0, total=int(sum(lengths)))
+    counts = O.batch(gens, states, key, streams, pos, lengths, offs, 1)
+    for i in range(n):
+        seg = flat[int(offs[i]): int(offs[i]) + lengths[i]]
+        if gens[i] == 0:
+            ref, _ = O.mrg_generate(states[i], lengths[i])
+            assert counts[i] == O.mrg_pi_count(states[i], lengths[i])
+        else:
+            ref = O.philox_generate(key, streams[i], pos[i], lengths[i])
+            assert counts[i] == O.philox_pi_count(key, streams[i], pos[i], lengths[i])
+        assert np.array_equal(seg, ref)
