@@ -1,0 +1,432 @@
+#!/usr/bin/env python
+"""Benchmark of the bulk uniform-generation hot path on GB300.
+
+One step = one pass of the MRG32k3a bulk workload through the C ABI:
+  srng_reset (stream placement by jump-ahead, K1) of 2^18 streams 2^127 apart
+  from the expanded seed 0x5EED5EED5EED5EED, then srng_generate of 4096 draws
+  per stream as uint32 (2^30 values), then -- after moving on -- another 4096
+  draws per stream as FP64 (2^30 values).  Metric: uniforms per second
+  (2^31 per step), with every output resident in HBM (12.9 GB per step,
+  100x the L2, so no flush is needed between steps).
+
+Other workloads (MRG32k3a plain 64 x 2^16 FP64, Philox4x32-10 bulk 2^30
+words, the 10^4-instance batched launch with its fused Monte Carlo consumer
+and the serving loop) are reported under "workloads" in the same JSON line.
+
+--impl reference times the CPU oracle (the plain definition, OpenMP over
+streams) on the host cores on a bounded sample of the same workload.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run (one process per GPU, independent replicas: rank r
+generates streams [r S, (r+1) S) of one set; no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+S_STREAMS, N_DRAWS, SEED = 1 << 18, 4096, 0x5EED5EED5EED5EED
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-extras", action="store_true", help="skip the other workloads")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = ["paper_1412_8266_gb300/csrc/generate.cu", "include/srng_device.cuh"]
+
+
+def ncu_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    sources are unchanged since it was taken (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    e = d.get(kernel_key)
+    if not e or e.get("source_hash") != source_hash(KERNEL_SOURCES):
+        return None
+    return e.get("bytes_per_launch")
+
+
+# --------------------------------------------------------------------- CPU oracle
+def oracle_sample(target_s: float):
+    """Time the oracle on a bounded sample of the MRG32k3a bulk workload:
+    the first s streams of the same set, 4096 draws each as uint32, then 4096
+    more as FP64 (the shape of one step), s chosen so the run takes about
+    target_s seconds.  Returns (Guniforms/s, cores used, description)."""
+    from oracle import oracle as O
+    y0 = O.seed_expand(SEED)
+    threads = O.max_threads()
+
+    def run(s):
+        starts = O.mrg_stream_starts(y0, 127, 0, s)
+        t0 = time.perf_counter()
+        _, st = O.mrg_bulk(starts, N_DRAWS, O.OUT_U32, threads)
+        O.mrg_bulk(st, N_DRAWS, O.OUT_F64, threads)
+        return time.perf_counter() - t0
+
+    probe = 64 * threads
+    dt = run(probe)
+    s = int(min(S_STREAMS, max(probe, probe * target_s / max(dt, 1e-6))))
+    dt = run(s)
+    nums = 2 * s * N_DRAWS
+    return nums / dt / 1e9, threads, (f"{s} of {S_STREAMS} streams x {N_DRAWS} draws, uint32 then FP64 "
+                                      f"({nums} values in {dt:.1f} s on {threads} threads)")
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    vals = []
+    cores = 0
+    desc = ""
+    for _ in range(args.warmup):
+        oracle_sample(args.cpu_seconds / 4)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, cores, desc = oracle_sample(args.cpu_seconds / max(1, args.steps))
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": "Guniforms/s (MRG32k3a bulk, uint32 + FP64, bit-exact)", "value": value,
+        "unit": "Guniforms/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "MRG32k3a bulk: 2^18 streams x 4096 draws, uint32 + FP64 (CPU sample)",
+                   "streams": S_STREAMS, "draws_per_stream": N_DRAWS, "seed": hex(SEED)},
+        "cpu_baseline": {"value": value, "unit": "Guniforms/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "Guniforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1412_8266_gb300 as srng
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_kind = measured_peaks()
+
+    h = srng.srng_create(srng.SRNG_MRG32K3A, SEED, S_STREAMS * world, srng.SRNG_SPACING_STREAM, stream)
+    b = rank * S_STREAMS
+    out_u = torch.empty(S_STREAMS * N_DRAWS, dtype=torch.int32, device=dev)
+    out_f = torch.empty(S_STREAMS * N_DRAWS, dtype=torch.float64, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+
+    def step(k=None):
+        srng.srng_reset(h, stream)
+        if k is not None:
+            ev[k][0].record(stream)
+        srng.srng_generate(h, b, S_STREAMS, N_DRAWS, srng.SRNG_OUT_U32, out_u, stream)
+        if k is not None:
+            ev[k][1].record(stream)
+            ev[k][2].record(stream)
+        srng.srng_generate(h, b, S_STREAMS, N_DRAWS, srng.SRNG_OUT_F64, out_f, stream)
+        if k is not None:
+            ev[k][3].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(k)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    numbers = 2 * S_STREAMS * N_DRAWS
+    value = world * numbers / (ms_step / 1e3) / 1e9
+    ms_u = statistics.mean(ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps))
+    ms_f = statistics.mean(ev[k][2].elapsed_time(ev[k][3]) for k in range(args.steps))
+    bytes_u, bytes_f = S_STREAMS * N_DRAWS * 4, S_STREAMS * N_DRAWS * 8
+    dom = "mrg_f64" if ms_f * 1 >= ms_u else "mrg_u32"
+    dom_bytes, dom_ms = (bytes_f, ms_f) if dom == "mrg_f64" else (bytes_u, ms_u)
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+
+    # end to end through the host-buffer entry point (device -> pinned host inside the timed region)
+    e2e = None
+    if True:
+        host_u = torch.empty(S_STREAMS * N_DRAWS, dtype=torch.int32, pin_memory=True)
+        host_f = torch.empty(S_STREAMS * N_DRAWS, dtype=torch.float64, pin_memory=True)
+
+        def e2e_step():
+            srng.srng_reset(h, stream)
+            srng.srng_generate_host(h, b, S_STREAMS, N_DRAWS, srng.SRNG_OUT_U32, host_u, stream)
+            srng.srng_generate_host(h, b, S_STREAMS, N_DRAWS, srng.SRNG_OUT_F64, host_f, stream)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        if world > 1:
+            tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        # the host copy must equal the device output of the same step
+        same = bool(np.array_equal(host_u[:1 << 20].numpy(), out_u[:1 << 20].cpu().numpy()))
+        e2e = {"value": world * numbers / e2e_s / 1e9, "unit": "Guniforms/s", "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": bytes_u + bytes_f, "ms_per_step": e2e_s * 1e3, "matches_device_output": same}
+        del host_u, host_f
+
+    srng.srng_destroy(h)
+    del out_u, out_f
+    torch.cuda.empty_cache()
+
+    line = {
+        "metric": "Guniforms/s (MRG32k3a bulk, uint32 + FP64, bit-exact)", "value": value, "unit": "Guniforms/s",
+        "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": "MRG32k3a bulk: 2^18 streams x 4096 draws, uint32 + FP64 per step",
+                   "streams_per_gpu": S_STREAMS, "draws_per_stream": N_DRAWS, "seed": hex(SEED),
+                   "spacing": "2^127", "outputs_bytes_per_step": bytes_u + bytes_f,
+                   "l2": "no flush: 12.9 GB of outputs per step, 100x the L2",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "traffic": ncu_traffic(dom), "algorithmic_bytes_per_launch": dom_bytes,
+                     "ms_per_launch": dom_ms},
+        "kernels": {"mrg_u32": {"ms": ms_u, "GB_s": bytes_u / (ms_u / 1e3) / 1e9,
+                                "Guniforms_s": S_STREAMS * N_DRAWS / (ms_u / 1e3) / 1e9},
+                    "mrg_f64": {"ms": ms_f, "GB_s": bytes_f / (ms_f / 1e3) / 1e9,
+                                "Guniforms_s": S_STREAMS * N_DRAWS / (ms_f / 1e3) / 1e9}},
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": 5 * args.steps,
+    }
+
+    if rank == 0 and not args.no_extras:
+        try:
+            line["workloads"] = extras(torch, srng, dev, stream, peak)
+        except Exception as ex:  # report, do not hide
+            line["workloads"] = {"error": repr(ex)}
+    if rank == 0:
+        v, cores, desc = oracle_sample(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "Guniforms/s", "cores": cores, "kind": "oracle", "sample": desc}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def _time(torch, stream, fn, reps=5, warm=2):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(reps):
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return min(ts), statistics.median(ts)
+
+
+def extras(torch, srng, dev, stream, peak):
+    import numpy as np
+    from paper_1412_8266_gb300 import workload as W
+    res = {}
+    # MRG32k3a plain: 64 streams x 2^16 FP64
+    h = srng.srng_create_from_state([12345] * 6, 64, srng.SRNG_SPACING_STREAM, stream)
+    o = torch.empty(64 << 16, dtype=torch.float64, device=dev)
+    best, med = _time(torch, stream, lambda: (srng.srng_reset(h, stream),
+                                              srng.srng_generate(h, 0, 64, 1 << 16, srng.SRNG_OUT_F64, o, stream)))
+    res["mrg_plain_64x65536_f64"] = {"ms_best": best, "ms_median": med, "Guniforms_s": (64 << 16) / best / 1e6,
+                                     "GB_s": (64 << 16) * 8 / best / 1e6}
+    srng.srng_destroy(h)
+    del o
+    # Philox bulk: 2^30 words u32 and f32
+    h = srng.srng_create(srng.SRNG_PHILOX4X32_10, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
+    n = 1 << 30
+    ph = {}
+    for name, t, dt in (("u32", srng.SRNG_OUT_U32, torch.int32), ("f32", srng.SRNG_OUT_F32, torch.float32)):
+        o = torch.empty(n, dtype=dt, device=dev)
+        best, med = _time(torch, stream, lambda: (srng.srng_reset(h, stream),
+                                                  srng.srng_generate(h, 0, 1, n, t, o, stream)))
+        ph[name] = {"ms_best": best, "ms_median": med, "Guniforms_s": n / best / 1e6, "GB_s": n * 4 / best / 1e6,
+                    "frac_of_copy_peak": n * 4 / best / 1e6 / peak}
+        del o
+    srng.srng_destroy(h)
+    res["philox_bulk_2^30"] = ph
+    # Batched: 10^4 instances, plain per-instance launches vs one graph launch; fused pi
+    gens, lengths, outoff = W.batched_instances()
+    ni = len(gens)
+    total = int(outoff[-1] + lengths[-1])
+    hm = srng.srng_create(srng.SRNG_MRG32K3A, SEED, ni, srng.SRNG_SPACING_STREAM, stream)
+    hp = srng.srng_create(srng.SRNG_PHILOX4X32_10, 0xC0FFEE, ni, srng.SRNG_SPACING_STREAM, stream)
+    inst = [srng.Instance(set_index=int(gens[i]), stream=i, offset=0, length=int(lengths[i]),
+                          out_offset=int(outoff[i])) for i in range(ni)]
+    out = torch.empty(total, dtype=torch.int32, device=dev)
+    plan = srng.srng_batch_plan_create([hm, hp], inst, srng.SRNG_BATCH_WRITE, srng.SRNG_OUT_U32, out, None, stream)
+    bb, bm = _time(torch, stream, lambda: srng.srng_batch_plan_launch(plan, stream), reps=5)
+    items, _ = srng.srng_batch_plan_info(plan)
+    srng.srng_batch_plan_destroy(plan)
+    views = [out[int(outoff[i]):int(outoff[i]) + int(lengths[i])] for i in range(ni)]
+
+    def plain():
+        for i in range(ni):
+            srng.srng_generate(hm if gens[i] == 0 else hp, i, 1, int(lengths[i]), srng.SRNG_OUT_U32, views[i], stream)
+
+    pb, pm = _time(torch, stream, plain, reps=2, warm=1)
+    counts = torch.empty(ni, dtype=torch.int64, device=dev)
+    plan = srng.srng_batch_plan_create([hm, hp], inst, srng.SRNG_BATCH_FUSED_PI, srng.SRNG_OUT_U32, counts, None,
+                                       stream)
+    fb, fm = _time(torch, stream, lambda: srng.srng_batch_plan_launch(plan, stream), reps=5)
+    srng.srng_batch_plan_destroy(plan)
+    c = counts.cpu().numpy()
+    pairs = int(np.sum(lengths // 2))
+    res["batched_10k_u32"] = {
+        "draws": total, "work_items": items,
+        "batched_ms": bb, "batched_Guniforms_s": total / bb / 1e6, "batched_GB_s": total * 4 / bb / 1e6,
+        "batched_frac_of_copy_peak": total * 4 / bb / 1e6 / peak,
+        "plain_per_instance_ms": pb, "plain_Guniforms_s": total / pb / 1e6, "plain_launches": 2 * ni,
+        "speedup_batched_vs_plain": pb / bb,
+        "fused_pi_ms": fb, "fused_pi_Guniforms_s": total / fb / 1e6, "pi_estimate": 4.0 * c.sum() / pairs,
+    }
+    srng.srng_destroy(hm)
+    srng.srng_destroy(hp)
+    del out, views, counts
+    torch.cuda.empty_cache()
+    return res
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

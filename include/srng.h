@@ -1,0 +1,298 @@
+/*
+ * srng.h -- C ABI of the GB300 bulk uniform-generation library.
+ *
+ * The library implements the hot path of arXiv 1412.8266 (Passerat-Palmbach &
+ * Hill, "How to correctly deal with pseudorandom numbers in manycore
+ * environments", ShoveRand): many independent, reproducible streams of
+ * uniform pseudorandom numbers on the GPU, one stream per processing element.
+ *
+ *   - MRG32k3a (paper Sec. 4.1): 2^64 streams of 2^127 draws, each cut into
+ *     substreams of 2^76 draws, placed by sequence splitting (Sec. 2.3) with
+ *     3x3 jump-ahead matrix powers modulo m1 = 2^32-209 and m2 = 2^32-22853.
+ *   - Philox4x32-10 (paper Sec. 4.3): counter-based; the parameter is a key.
+ *
+ * Host set-up (paper Sec. 5.1: one host call allocates and places the streams
+ * before the kernels run) maps to srng_create; release (Sec. 5, Listing 1)
+ * maps to srng_destroy; the device-side constructor + next() (Sec. 5.2) is the
+ * device header srng_device.cuh.
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named *_dev are device pointers (cudaMalloc, torch, or any
+ *     allocation the current device can address).  Pointers named *_host are
+ *     host pointers (pinned memory gives the fastest copies).
+ *   - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued asynchronously on it unless the entry point
+ *     says it synchronises.
+ *   - Every call returns an srng_status; on failure srng_last_error() returns a
+ *     message (per host thread) and nothing was enqueued unless stated.
+ *   - Output layout of every generate call is stream-major and contiguous:
+ *     out[(s - stream_begin) * n_per_stream + k] = draw k of stream s, counted
+ *     from the stream's position when the call is made.  Values never depend
+ *     on launch configuration or tuning.
+ *   - Output of the three types (fixed conversions):
+ *       SRNG_OUT_U32: MRG32k3a z = (x1 - x2) mod m1 taken in [1, m1]
+ *                     (0 and values above m1 never occur); Philox: the word.
+ *       SRNG_OUT_F32: (v >> 8) * 2^-24, exact, in [0, 1) (both generators).
+ *       SRNG_OUT_F64: MRG32k3a: z * norm rounded to nearest even, norm the
+ *                     double nearest 1/(m1+1), in (0, 1);
+ *                     Philox: (2w + 1) * 2^-33, exact, in (0, 1).
+ */
+#ifndef SRNG_H
+#define SRNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SRNG_ABI_VERSION 1
+
+typedef enum srng_status {
+    SRNG_OK = 0,
+    SRNG_ERR_ARG = 1,      /* invalid argument: NULL pointer, zero/too large count, bad enum   */
+    SRNG_ERR_OOM = 2,      /* a device or host allocation failed                              */
+    SRNG_ERR_STATE = 3,    /* an explicit MRG32k3a state violates 0 <= x < m / non-zero rule   */
+    SRNG_ERR_CUDA = 4,     /* a CUDA runtime call failed; srng_last_error() has its message    */
+    SRNG_ERR_BUDGET = 5,   /* a request is larger than the server's whole memory budget        */
+    SRNG_ERR_TIMEOUT = 6,  /* a bounded wait expired                                           */
+    SRNG_ERR_RANGE = 7,    /* stream range outside the set, or a position would overflow       */
+    SRNG_ERR_CLOSED = 8,   /* the server is stopped / the ticket is unknown                    */
+    SRNG_ERR_UNSUPPORTED = 9 /* operation not defined for this generator                       */
+} srng_status;
+
+typedef enum srng_gen {
+    SRNG_MRG32K3A = 0,
+    SRNG_PHILOX4X32_10 = 1
+} srng_gen;
+
+typedef enum srng_out {
+    SRNG_OUT_U32 = 0,
+    SRNG_OUT_F32 = 1,
+    SRNG_OUT_F64 = 2
+} srng_out;
+
+/* Spacing of consecutive streams of an MRG32k3a set (paper Sec. 4.1). */
+typedef enum srng_spacing {
+    SRNG_SPACING_STREAM = 0,    /* 2^127 draws apart */
+    SRNG_SPACING_SUBSTREAM = 1  /* 2^76 draws apart  */
+} srng_spacing;
+
+/* Unit of a jump distance. */
+typedef enum srng_jump_unit {
+    SRNG_JUMP_DRAWS = 0,       /* n draws                      */
+    SRNG_JUMP_SUBSTREAMS = 1,  /* n * 2^76 draws (MRG32k3a)    */
+    SRNG_JUMP_STREAMS = 2      /* n * 2^127 draws (MRG32k3a)   */
+} srng_jump_unit;
+
+typedef struct srng_set srng_set;
+
+/* Launch shape of the generation kernels.  Any zero field takes the
+ * library's default (or the value set by srng_set_tune).  Values never change
+ * the output, only the speed.
+ *   block_threads : threads per block (multiple of 32, 32..1024)
+ *   blocks_per_sm : resident blocks per SM the grid is sized for (grid =
+ *                   SM count x blocks_per_sm, work taken by grid stride)
+ *   chunk         : MRG32k3a draws per thread item (a stream longer than this
+ *                   is split into chunks whose start states are reached by
+ *                   jump-ahead); multiple of 32
+ *   unroll        : Philox blocks per thread per loop trip (1, 2 or 4)
+ *   vector_store  : 1 = 16-byte stores where the output alignment allows,
+ *                   2 = never (element stores, always coalesced)
+ *   lane_blocks   : batched launches only: Philox blocks each lane computes
+ *                   per work item (a Philox work item covers 32 x lane_blocks
+ *                   blocks of one instance); MRG32k3a work items are 32
+ *                   chunks of `chunk` draws of one instance                  */
+typedef struct srng_tune {
+    uint32_t block_threads;
+    uint32_t blocks_per_sm;
+    uint32_t chunk;
+    uint32_t unroll;
+    uint32_t vector_store;
+    uint32_t lane_blocks;
+    uint32_t reserved[2];
+} srng_tune;
+
+/* ------------------------------------------------------------------ errors */
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *srng_last_error(void);
+/* Static name of a status code. */
+const char *srng_status_string(srng_status status);
+/* SRNG_ABI_VERSION of the loaded library. */
+int srng_abi_version(void);
+
+/* ---------------------------------------------------------- stream sets */
+
+/* Create a set of n_streams streams of generator `gen` (paper Sec. 5.1: one
+ * host call places every stream before any kernel runs).
+ *   MRG32k3a: the seed is expanded into the six state words by SplitMix64
+ *     (Steele, Lea & Flood 2014): six successive outputs r0..r5 give
+ *     x1[i] = r_i mod m1, x2[i] = r_(i+3) mod m2, an all-zero component being
+ *     replaced by (12345, 12345, 12345).  Stream i starts at A^(i * 2^e) y0
+ *     with e = 127 (SRNG_SPACING_STREAM) or 76 (SRNG_SPACING_SUBSTREAM); the
+ *     start states are computed on the device by the jump-ahead kernel.
+ *   Philox4x32-10: key = (seed & 0xffffffff, seed >> 32); stream s uses
+ *     counter words 2-3 = s and counter words 0-1 = position / 4, draw =
+ *     word position % 4; every position starts at 0.  `spacing` is ignored.
+ * n_streams: 1 .. 2^40 (MRG32k3a with SRNG_SPACING_STREAM: at most 2^64 by
+ * the paper, here limited by device memory: 24 bytes per stream; Philox: 8).
+ * The set owns its device memory until srng_destroy.  Synchronises
+ * cuda_stream before returning (the set is ready to use on any stream). */
+srng_status srng_create(srng_set **out, srng_gen gen, uint64_t seed, uint64_t n_streams,
+                        srng_spacing spacing, void *cuda_stream);
+
+/* Same, MRG32k3a only, from an explicit seed state y0 = (x1[n-3], x1[n-2],
+ * x1[n-1], x2[n-3], x2[n-2], x2[n-1]).  SRNG_ERR_STATE unless every x1 word
+ * is < m1, every x2 word < m2 and neither component is all zero. */
+srng_status srng_create_from_state(srng_set **out, const uint32_t state[6], uint64_t n_streams,
+                                   srng_spacing spacing, void *cuda_stream);
+
+/* Free the set and its device memory (after the device is done with it:
+ * synchronises the device first).  NULL is accepted. */
+srng_status srng_destroy(srng_set *set);
+
+/* Put every stream of the set back at its start (re-runs the placement). */
+srng_status srng_reset(srng_set *set, void *cuda_stream);
+
+/* Description of a set. */
+typedef struct srng_set_desc {
+    srng_gen gen;
+    srng_spacing spacing;
+    uint64_t n_streams;
+    uint64_t seed;
+    uint32_t seed_state[6]; /* MRG32k3a y0; Philox: key in [0], [1] */
+} srng_set_desc;
+srng_status srng_describe(const srng_set *set, srng_set_desc *out);
+
+/* Move streams [stream_begin, stream_begin + count) forward by
+ * n = n_hi * 2^64 + n_lo units (paper Sec. 2.3 sequence splitting).
+ *   MRG32k3a: state <- A^(n * 2^u) state, u = 0, 76 or 127 by `unit`; the
+ *     3x3 power is computed exactly on the host, its product with each state
+ *     on the device.
+ *   Philox: only SRNG_JUMP_DRAWS with n_hi = 0; position += n_lo
+ *     (SRNG_ERR_RANGE if a position would pass 2^64 - 1).           */
+srng_status srng_jump(srng_set *set, uint64_t stream_begin, uint64_t count, srng_jump_unit unit,
+                      uint64_t n_hi, uint64_t n_lo, void *cuda_stream);
+
+/* Generate n_per_stream values of type `type` from each of streams
+ * [stream_begin, stream_begin + stream_count) into out_dev (stream-major, see
+ * above; needs stream_count * n_per_stream * sizeof(type) bytes, any
+ * alignment of the element size; 16-byte alignment is fastest) and move the
+ * streams forward by n_per_stream draws.  Asynchronous on cuda_stream. */
+srng_status srng_generate(srng_set *set, uint64_t stream_begin, uint64_t stream_count,
+                          uint64_t n_per_stream, srng_out type, void *out_dev, void *cuda_stream);
+
+/* Same, with an explicit launch shape (NULL = defaults).  Output identical. */
+srng_status srng_generate_tuned(srng_set *set, uint64_t stream_begin, uint64_t stream_count,
+                                uint64_t n_per_stream, srng_out type, void *out_dev,
+                                const srng_tune *tune, void *cuda_stream);
+
+/* Same result as srng_generate, written to a HOST buffer: the library
+ * generates into an internal device staging ring (allocated on first use,
+ * kept by the set, at most 2 x 256 MiB) and overlaps generation of one piece
+ * with the device-to-host copy of the previous one.  Synchronises
+ * cuda_stream before returning. */
+srng_status srng_generate_host(srng_set *set, uint64_t stream_begin, uint64_t stream_count,
+                               uint64_t n_per_stream, srng_out type, void *out_host,
+                               void *cuda_stream);
+
+/* Copy per-stream state to / from the host (checkpoint / resume; paper
+ * Sec. 1 asks for reproducible streams).  MRG32k3a: 6 uint32 per stream in
+ * the order of srng_create_from_state; Philox: one uint64 position per
+ * stream.  srng_set_state validates MRG32k3a states (SRNG_ERR_STATE).
+ * Both synchronise cuda_stream. */
+srng_status srng_get_state(const srng_set *set, uint64_t stream_begin, uint64_t count,
+                           void *state_host, void *cuda_stream);
+srng_status srng_set_state(srng_set *set, uint64_t stream_begin, uint64_t count,
+                           const void *state_host, void *cuda_stream);
+
+/* Default launch shape used by srng_generate for (gen, type); NULL resets
+ * it to the built-in default.  Process-wide. */
+srng_status srng_set_tune(srng_gen gen, srng_out type, const srng_tune *tune);
+srng_status srng_get_tune(srng_gen gen, srng_out type, srng_tune *out);
+
+/* Integer -> uniform conversion alone: out_dev[i] = convert(in_dev[i]) with
+ * the generator's fixed rule for `type` (see the header comment).  For
+ * SRNG_MRG32K3A the inputs must be combined values in [1, m1]
+ * (SRNG_OUT_F64 assumes it; other values give the same formula's result). */
+srng_status srng_convert(srng_gen gen, srng_out type, const uint32_t *in_dev, uint64_t n,
+                         void *out_dev, void *cuda_stream);
+
+/* Device view of a set for use inside user kernels with srng_device.cuh
+ * (the paper's in-kernel constructor + next(), Sec. 5.2).  The pointers stay
+ * owned by the set and valid until srng_destroy. */
+typedef struct srng_dev_view {
+    int32_t gen;            /* SRNG_MRG32K3A or SRNG_PHILOX4X32_10              */
+    uint32_t key0, key1;    /* Philox key                                      */
+    uint32_t pad;
+    uint64_t n_streams;
+    uint32_t *mrg_state;    /* MRG32k3a, SoA: word j of stream i at
+                             * [j * n_streams + i], j in the srng_create_from_state order */
+    uint64_t *philox_pos;   /* Philox: current position of each stream          */
+} srng_dev_view;
+srng_status srng_get_device_view(const srng_set *set, srng_dev_view *out);
+
+/* ------------------------------------------------------------ host maths */
+
+/* The SplitMix64 seed expansion used by srng_create (pure host function). */
+srng_status srng_seed_expand(uint64_t seed, uint32_t state[6]);
+
+/* The jump matrices A1^d mod m1 and A2^d mod m2, d = n * 2^u (u by `unit`),
+ * row-major 3x3, acting on (x[n-3], x[n-2], x[n-1]).  Pure host function. */
+srng_status srng_jump_matrix(srng_jump_unit unit, uint64_t n_hi, uint64_t n_lo, uint32_t a1[9],
+                             uint32_t a2[9]);
+
+/* ----------------------------------------------- batched instances (K4/K5) */
+
+/* One simulation instance of a batch: `length` draws of stream `stream` of
+ * set sets[set_index], starting `offset` draws after that stream's current
+ * position (the batch reads the set, it does not move it). */
+typedef struct srng_instance {
+    uint32_t set_index;
+    uint32_t reserved;
+    uint64_t stream;
+    uint64_t offset;
+    uint64_t length;
+    uint64_t out_offset; /* element offset of the instance's output (WRITE mode) */
+} srng_instance;
+
+typedef enum srng_batch_mode {
+    SRNG_BATCH_WRITE = 0,    /* write the values (type `type`) at out_offset            */
+    SRNG_BATCH_FUSED_PI = 1  /* no values written: count, per instance, the pairs
+                              * (draw 2k, draw 2k+1), k < length/2, inside the quarter
+                              * disc, tested exactly on the uniforms (Philox:
+                              * a^2 + b^2 < 2^48 with a = w >> 8; MRG32k3a:
+                              * z0^2 + z1^2 < (m1+1)^2); int64 per instance          */
+} srng_batch_mode;
+
+typedef struct srng_batch_plan srng_batch_plan;
+
+/* Build a batch plan: instance start states (jump-ahead kernel), the flat work
+ * list (fixed-size chunks of every instance, mixed generators) and a CUDA
+ * graph of {reset work counter, zero counts, persistent kernel}.  `out_dev`
+ * is where launches write: WRITE mode -> values; FUSED_PI -> n_inst int64
+ * counts.  The plan keeps pointers to `sets` (they must outlive it) but
+ * copies `inst`.  Synchronises cuda_stream. */
+srng_status srng_batch_plan_create(srng_batch_plan **out, srng_set *const *sets, uint32_t n_sets,
+                                   const srng_instance *inst, uint64_t n_inst, srng_batch_mode mode,
+                                   srng_out type, void *out_dev, const srng_tune *tune,
+                                   void *cuda_stream);
+/* Launch the captured graph once on cuda_stream (asynchronous). */
+srng_status srng_batch_plan_launch(srng_batch_plan *plan, void *cuda_stream);
+/* Number of kernel launches one srng_batch_plan_launch performs. */
+srng_status srng_batch_plan_info(const srng_batch_plan *plan, uint64_t *n_work_items,
+                                 uint32_t *kernels_per_launch);
+srng_status srng_batch_plan_destroy(srng_batch_plan *plan);
+
+/* One-shot batch: create a plan, launch it, wait, destroy it. */
+srng_status srng_batch_run(srng_set *const *sets, uint32_t n_sets, const srng_instance *inst,
+                           uint64_t n_inst, srng_batch_mode mode, srng_out type, void *out_dev,
+                           void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRNG_H */

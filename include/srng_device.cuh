@@ -1,0 +1,259 @@
+/*
+ * srng_device.cuh -- device-side draws for CUDA kernels (sm_103a).
+ *
+ * The paper's device layer (arXiv 1412.8266, Sec. 5.2) constructs a generator
+ * object inside the kernel, which picks up the calling thread's stream, and
+ * calls next() on it.  Here the stream set's device view (srng_dev_view,
+ * filled by srng_get_device_view in srng.h) is passed explicitly instead of
+ * through hidden globals, so kernels stay pure functions of
+ * (set, stream, position):
+ *
+ *     __global__ void foo(float* out, srng_dev_view v) {
+ *         uint64_t s = blockIdx.x * blockDim.x + threadIdx.x;
+ *         srng::Mrg32k3a g(v, s);            // loads stream s's state
+ *         out[s] = g.next_f32();             // the paper's Listing 1
+ *     }
+ *
+ * All arithmetic is exact integer arithmetic: MRG32k3a products are formed
+ * with 32x32->64-bit multiplies and reduced modulo m = 2^32 - c by folding
+ * (2^32 = c mod m), Philox uses the 32x32->64-bit products of its round
+ * function, and the floating-point outputs are assembled from integer bits
+ * (no FP64 pipe, no rounding other than the defined one).
+ *
+ * This header holds no allocation and no host code; it is the device math of
+ * the library's own kernels too.
+ */
+#ifndef SRNG_DEVICE_CUH
+#define SRNG_DEVICE_CUH
+
+#include <stdint.h>
+
+#include "srng.h"
+
+namespace srng {
+
+/* ---------------------------------------------------------- MRG32k3a maths */
+namespace mrg {
+/* Moduli and recurrence coefficients (L'Ecuyer 1999, the generator of the
+ * paper's Sec. 4.1):  x1[n] = (a12 x1[n-2] - a13 x1[n-3]) mod m1,
+ *                     x2[n] = (a21 x2[n-1] - a23 x2[n-3]) mod m2. */
+constexpr uint32_t kM1 = 4294967087u;  /* 2^32 - 209   */
+constexpr uint32_t kM2 = 4294944443u;  /* 2^32 - 22853 */
+constexpr uint32_t kC1 = 209u;
+constexpr uint32_t kC2 = 22853u;
+constexpr uint32_t kA12 = 1403580u;
+constexpr uint32_t kA13 = 810728u;
+constexpr uint32_t kA21 = 527612u;
+constexpr uint32_t kA23 = 1370589u;
+
+/* One step.  s0..s2 = (x1[n-3], x1[n-2], x1[n-1]), s3..s5 likewise for x2.
+ * Returns z = (x1[n] - x2[n]) mod m1 in [1, m1].
+ *
+ * Component 1: t = a12 s1 + a13 (m1 - s0) = a12 s1 - a13 s0 (mod m1), and
+ *   t < 2^21 2^32 + 2^20 2^32 < 2^54.  Fold 1: u = (t >> 32) c1 + (t mod 2^32)
+ *   < 2^30 + 2^32.  Fold 2: v = (u mod 2^32) + (u >> 32) c1, where u >> 32 is
+ *   0 or 1 (and when it is 1, u mod 2^32 < 2^30, so v < m1); v < 2^32, and one
+ *   conditional subtraction of m1 leaves v in [0, m1).
+ * Component 2: t < 2^20 2^32 + 2^21 2^32 < 2^54.  Fold 1: u < 2^22 c2 + 2^32,
+ *   so u >> 32 <= 23.  Fold 2: v = (u >> 32) c2 + (u mod 2^32) < 2^32 + 525619.
+ *   Fold 3: w = (v mod 2^32) + (v >> 32) c2 < 2^32 (v >> 32 is 0 or 1, and when
+ *   1, v mod 2^32 < 525619).  One conditional subtraction of m2 finishes. */
+__device__ __forceinline__ uint32_t step(uint32_t &s0, uint32_t &s1, uint32_t &s2, uint32_t &s3,
+                                         uint32_t &s4, uint32_t &s5)
+{
+    uint64_t t1 = (uint64_t)kA12 * s1 + (uint64_t)kA13 * (kM1 - s0);
+    uint64_t u1 = (t1 >> 32) * kC1 + (uint32_t)t1;
+    uint32_t v1 = (uint32_t)u1 + (uint32_t)(u1 >> 32) * kC1;
+    v1 = min(v1, v1 - kM1);               /* v1 >= m1 ? v1 - m1 : v1 (unsigned wrap) */
+
+    uint64_t t2 = (uint64_t)kA21 * s5 + (uint64_t)kA23 * (kM2 - s3);
+    uint64_t u2 = (t2 >> 32) * kC2 + (uint32_t)t2;
+    uint64_t v2 = (u2 >> 32) * kC2 + (uint32_t)u2;
+    uint32_t w2 = (uint32_t)v2 + (uint32_t)(v2 >> 32) * kC2;
+    w2 = min(w2, w2 - kM2);
+
+    s0 = s1; s1 = s2; s2 = v1;
+    s3 = s4; s4 = s5; s5 = w2;
+    uint32_t d = v1 - w2;
+    return v1 > w2 ? d : d + kM1;
+}
+
+/* x mod (2^32 - c) for any 64-bit x, c < 2^15 (three folds and one
+ * conditional subtraction; used by the jump-ahead products). */
+__device__ __forceinline__ uint32_t reduce64(uint64_t x, uint32_t c, uint32_t m)
+{
+    x = (x >> 32) * c + (uint32_t)x;  /* < 2^47 + 2^32         */
+    x = (x >> 32) * c + (uint32_t)x;  /* < 2^30 + 2^32         */
+    x = (x >> 32) * c + (uint32_t)x;  /* < 2^32 (see step())   */
+    uint32_t r = (uint32_t)x;
+    return min(r, r - m);
+}
+
+/* (y0, y1, y2) <- M (y0, y1, y2) mod m for a row-major 3x3 matrix M with
+ * entries below m.  Each product is reduced before the three are summed. */
+__device__ __forceinline__ void matvec(const uint32_t *M, uint32_t &y0, uint32_t &y1, uint32_t &y2,
+                                       uint32_t c, uint32_t m)
+{
+    uint32_t r[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        uint64_t acc = (uint64_t)reduce64((uint64_t)M[3 * i] * y0, c, m) +
+                       (uint64_t)reduce64((uint64_t)M[3 * i + 1] * y1, c, m) +
+                       (uint64_t)reduce64((uint64_t)M[3 * i + 2] * y2, c, m);
+        r[i] = reduce64(acc, c, m);
+    }
+    y0 = r[0]; y1 = r[1]; y2 = r[2];
+}
+
+/* Apply a pair of jump matrices (A1^d, A2^d), 18 words: 9 for m1 then 9 for m2. */
+__device__ __forceinline__ void jump(const uint32_t *M18, uint32_t &s0, uint32_t &s1, uint32_t &s2,
+                                     uint32_t &s3, uint32_t &s4, uint32_t &s5)
+{
+    matvec(M18, s0, s1, s2, kC1, kM1);
+    matvec(M18 + 9, s3, s4, s5, kC2, kM2);
+}
+
+/* double nearest to z * norm, norm = 0x1.000000d00000bp-32 (the double nearest
+ * 1/(m1+1)), built from integers, for z in [1, m1].  norm = M 2^-84 with
+ * M = 2^52 + 0xd00000b, so the exact product is P = z 2^52 + z 0xd00000b
+ * (< 2^85).  Keep its top 53 bits, round the rest to nearest, ties to even,
+ * and place the exponent: value = mant 2^(s-84) with s = bitlength(P) - 53. */
+__device__ __forceinline__ double to_f64(uint32_t z)
+{
+    uint64_t w = (uint64_t)z * 0xd00000bu;
+    uint64_t lo = ((uint64_t)z << 52) + w;
+    uint64_t hi = (uint64_t)(z >> 12) + (lo < w ? 1u : 0u);
+    int b = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+    int s = b - 53;                                    /* 0 .. 32 */
+    uint64_t mant, rem, half;
+    if (s == 0) {
+        mant = lo; rem = 0; half = 1;                  /* exact: nothing to round */
+    } else {
+        mant = (lo >> s) | (hi << (64 - s));
+        rem = lo & ((1ull << s) - 1);
+        half = 1ull << (s - 1);
+    }
+    mant += (rem > half || (rem == half && (mant & 1))) ? 1 : 0;
+    uint64_t bits = ((uint64_t)(s + 990) << 52) + mant; /* biased exponent s + 991 */
+    return __longlong_as_double((long long)bits);
+}
+
+/* The same value through the FP64 multiply (IEEE round to nearest even). */
+__device__ __forceinline__ double to_f64_dmul(uint32_t z)
+{
+    return __dmul_rn((double)z, 0x1.000000d00000bp-32);
+}
+}  // namespace mrg
+
+/* ------------------------------------------------------ Philox4x32-10 maths */
+namespace philox {
+/* Multipliers and key increments of Philox4x32 (Salmon et al. 2011, the
+ * generator of the paper's Sec. 4.3). */
+constexpr uint32_t kM0 = 0xD2511F53u;
+constexpr uint32_t kM1 = 0xCD9E8D57u;
+constexpr uint32_t kW0 = 0x9E3779B9u;
+constexpr uint32_t kW1 = 0xBB67AE85u;
+
+/* Ten rounds on counter (c0..c3) with key (k0, k1), in place. */
+__device__ __forceinline__ void block(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3,
+                                      uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint64_t p0 = (uint64_t)kM0 * c0;
+        uint64_t p1 = (uint64_t)kM1 * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+        k0 += kW0;
+        k1 += kW1;
+    }
+}
+
+/* (2w + 1) 2^-33 as a double, exact, built from integers. */
+__device__ __forceinline__ double to_f64(uint32_t w)
+{
+    uint64_t v = 2ull * w + 1;                          /* odd, < 2^33 */
+    int b = 64 - __clzll((long long)v);                 /* 1 .. 33     */
+    uint64_t mant = v << (53 - b);                      /* [2^52, 2^53) */
+    uint64_t bits = ((uint64_t)(b + 988) << 52) + mant; /* biased exponent b + 989 */
+    return __longlong_as_double((long long)bits);
+}
+}  // namespace philox
+
+/* (v >> 8) 2^-24 as a float, exact. */
+__device__ __forceinline__ float to_f32(uint32_t v)
+{
+    return __uint2float_rn(v >> 8) * 0x1p-24f;
+}
+
+/* ------------------------------------------------------- generator objects */
+
+/* MRG32k3a stream handle: the paper's device RNG object with next(). */
+class Mrg32k3a {
+  public:
+    __device__ Mrg32k3a(const srng_dev_view &v, uint64_t stream)
+    {
+        const uint64_t n = v.n_streams;
+        s0 = v.mrg_state[0 * n + stream]; s1 = v.mrg_state[1 * n + stream];
+        s2 = v.mrg_state[2 * n + stream]; s3 = v.mrg_state[3 * n + stream];
+        s4 = v.mrg_state[4 * n + stream]; s5 = v.mrg_state[5 * n + stream];
+    }
+    __device__ explicit Mrg32k3a(const uint32_t st[6])
+        : s0(st[0]), s1(st[1]), s2(st[2]), s3(st[3]), s4(st[4]), s5(st[5]) {}
+
+    __device__ __forceinline__ uint32_t next_u32() { return mrg::step(s0, s1, s2, s3, s4, s5); }
+    __device__ __forceinline__ float next_f32() { return to_f32(next_u32()); }
+    __device__ __forceinline__ double next_f64() { return mrg::to_f64(next_u32()); }
+    /* Jump by a precomputed matrix pair (A1^d, A2^d) (srng_jump_matrix). */
+    __device__ __forceinline__ void jump(const uint32_t *M18) { mrg::jump(M18, s0, s1, s2, s3, s4, s5); }
+    /* Write the current state back (so a later launch continues from here). */
+    __device__ void store(const srng_dev_view &v, uint64_t stream) const
+    {
+        const uint64_t n = v.n_streams;
+        v.mrg_state[0 * n + stream] = s0; v.mrg_state[1 * n + stream] = s1;
+        v.mrg_state[2 * n + stream] = s2; v.mrg_state[3 * n + stream] = s3;
+        v.mrg_state[4 * n + stream] = s4; v.mrg_state[5 * n + stream] = s5;
+    }
+
+    uint32_t s0, s1, s2, s3, s4, s5;
+};
+
+/* Philox4x32-10 stream handle: counter words 2-3 = stream, 0-1 = block index. */
+class Philox4x32_10 {
+  public:
+    __device__ Philox4x32_10(const srng_dev_view &v, uint64_t stream)
+        : k0(v.key0), k1(v.key1), stream_(stream), pos_(v.philox_pos[stream]) {}
+    __device__ Philox4x32_10(uint32_t key0, uint32_t key1, uint64_t stream, uint64_t position)
+        : k0(key0), k1(key1), stream_(stream), pos_(position) {}
+
+    /* The four words of block q of this stream. */
+    __device__ __forceinline__ uint4 block(uint64_t q) const
+    {
+        uint32_t c0 = (uint32_t)q, c1 = (uint32_t)(q >> 32);
+        uint32_t c2 = (uint32_t)stream_, c3 = (uint32_t)(stream_ >> 32);
+        philox::block(c0, c1, c2, c3, k0, k1);
+        return make_uint4(c0, c1, c2, c3);
+    }
+    __device__ __forceinline__ uint32_t next_u32()
+    {
+        uint4 b = block(pos_ >> 2);
+        uint32_t j = (uint32_t)pos_ & 3u;
+        ++pos_;
+        return j == 0 ? b.x : j == 1 ? b.y : j == 2 ? b.z : b.w;
+    }
+    __device__ __forceinline__ float next_f32() { return to_f32(next_u32()); }
+    __device__ __forceinline__ double next_f64() { return philox::to_f64(next_u32()); }
+    __device__ void store(const srng_dev_view &v) const { v.philox_pos[stream_] = pos_; }
+    __device__ uint64_t position() const { return pos_; }
+
+    uint32_t k0, k1;
+    uint64_t stream_, pos_;
+};
+
+}  // namespace srng
+
+#endif /* SRNG_DEVICE_CUH */

@@ -1,0 +1,332 @@
+"""Python binding of the GB300 bulk uniform-generation library (include/srng.h).
+
+Argument marshalling only: every function here has the name of the C entry
+point it calls, passes plain pointers and sizes through ``ctypes``, and raises
+``SrngError`` when the call returns a non-zero status.  All generation runs in
+the CUDA kernels of ``libsrng.so``; there is no fallback of any kind -- if the
+library is missing or cannot be loaded, every call raises.
+
+Pointers may be given as integers, ``torch.Tensor`` (its ``data_ptr()``) or
+numpy arrays (host pointers).  ``stream`` may be ``None`` (torch's current
+stream when torch is imported and CUDA is initialised, else the legacy
+default stream), an integer ``cudaStream_t`` or a ``torch.cuda.Stream``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import sys
+import threading
+
+__all__ = [
+    "SrngError", "Tune", "Instance", "SetDesc", "DevView", "lib_path", "load",
+    "SRNG_MRG32K3A", "SRNG_PHILOX4X32_10", "SRNG_OUT_U32", "SRNG_OUT_F32", "SRNG_OUT_F64",
+    "SRNG_SPACING_STREAM", "SRNG_SPACING_SUBSTREAM", "SRNG_JUMP_DRAWS", "SRNG_JUMP_SUBSTREAMS",
+    "SRNG_JUMP_STREAMS", "SRNG_BATCH_WRITE", "SRNG_BATCH_FUSED_PI",
+]
+
+SRNG_MRG32K3A, SRNG_PHILOX4X32_10 = 0, 1
+SRNG_OUT_U32, SRNG_OUT_F32, SRNG_OUT_F64 = 0, 1, 2
+SRNG_SPACING_STREAM, SRNG_SPACING_SUBSTREAM = 0, 1
+SRNG_JUMP_DRAWS, SRNG_JUMP_SUBSTREAMS, SRNG_JUMP_STREAMS = 0, 1, 2
+SRNG_BATCH_WRITE, SRNG_BATCH_FUSED_PI = 0, 1
+OUT_ITEMSIZE = {SRNG_OUT_U32: 4, SRNG_OUT_F32: 4, SRNG_OUT_F64: 8}
+
+STATUS_NAMES = {0: "SRNG_OK", 1: "SRNG_ERR_ARG", 2: "SRNG_ERR_OOM", 3: "SRNG_ERR_STATE", 4: "SRNG_ERR_CUDA",
+                5: "SRNG_ERR_BUDGET", 6: "SRNG_ERR_TIMEOUT", 7: "SRNG_ERR_RANGE", 8: "SRNG_ERR_CLOSED",
+                9: "SRNG_ERR_UNSUPPORTED"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lock = threading.Lock()
+_lib = None
+
+
+class SrngError(RuntimeError):
+    def __init__(self, status: int, message: str, func: str):
+        self.status = status
+        self.name = STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{func}: {self.name}: {message}")
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("chunk", ctypes.c_uint32), ("unroll", ctypes.c_uint32), ("vector_store", ctypes.c_uint32),
+                ("lane_blocks", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("set_index", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("stream", ctypes.c_uint64),
+                ("offset", ctypes.c_uint64), ("length", ctypes.c_uint64), ("out_offset", ctypes.c_uint64)]
+
+
+class SetDesc(ctypes.Structure):
+    _fields_ = [("gen", ctypes.c_int), ("spacing", ctypes.c_int), ("n_streams", ctypes.c_uint64),
+                ("seed", ctypes.c_uint64), ("seed_state", ctypes.c_uint32 * 6)]
+
+
+class DevView(ctypes.Structure):
+    _fields_ = [("gen", ctypes.c_int32), ("key0", ctypes.c_uint32), ("key1", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32), ("n_streams", ctypes.c_uint64), ("mrg_state", ctypes.c_void_p),
+                ("philox_pos", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("draws_completed", ctypes.c_uint64), ("steps", ctypes.c_uint64), ("kernels", ctypes.c_uint64),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("max_us", ctypes.c_double), ("busy_s", ctypes.c_double), ("peak_bytes", ctypes.c_uint64)]
+
+
+_vp, _u64, _u32, _int = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+_SIGS = {
+    "srng_last_error": (ctypes.c_char_p, []),
+    "srng_status_string": (ctypes.c_char_p, [_int]),
+    "srng_abi_version": (_int, []),
+    "srng_create": (_int, [ctypes.POINTER(_vp), _int, _u64, _u64, _int, _vp]),
+    "srng_create_from_state": (_int, [ctypes.POINTER(_vp), _vp, _u64, _int, _vp]),
+    "srng_destroy": (_int, [_vp]),
+    "srng_reset": (_int, [_vp, _vp]),
+    "srng_describe": (_int, [_vp, ctypes.POINTER(SetDesc)]),
+    "srng_get_device_view": (_int, [_vp, ctypes.POINTER(DevView)]),
+    "srng_jump": (_int, [_vp, _u64, _u64, _int, _u64, _u64, _vp]),
+    "srng_generate": (_int, [_vp, _u64, _u64, _u64, _int, _vp, _vp]),
+    "srng_generate_tuned": (_int, [_vp, _u64, _u64, _u64, _int, _vp, ctypes.POINTER(Tune), _vp]),
+    "srng_generate_host": (_int, [_vp, _u64, _u64, _u64, _int, _vp, _vp]),
+    "srng_get_state": (_int, [_vp, _u64, _u64, _vp, _vp]),
+    "srng_set_state": (_int, [_vp, _u64, _u64, _vp, _vp]),
+    "srng_set_tune": (_int, [_int, _int, ctypes.POINTER(Tune)]),
+    "srng_get_tune": (_int, [_int, _int, ctypes.POINTER(Tune)]),
+    "srng_convert": (_int, [_int, _int, _vp, _u64, _vp, _vp]),
+    "srng_seed_expand": (_int, [_u64, _vp]),
+    "srng_jump_matrix": (_int, [_int, _u64, _u64, _vp, _vp]),
+    "srng_batch_plan_create": (_int, [ctypes.POINTER(_vp), _vp, _u32, _vp, _u64, _int, _int, _vp,
+                                      ctypes.POINTER(Tune), _vp]),
+    "srng_batch_plan_launch": (_int, [_vp, _vp]),
+    "srng_batch_plan_info": (_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
+    "srng_batch_plan_destroy": (_int, [_vp]),
+    "srng_batch_run": (_int, [_vp, _u32, _vp, _u64, _int, _int, _vp, _vp]),
+}
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "libsrng.so")
+
+
+def load():
+    """Load libsrng.so (built by ``__graft_entry__.build()``).  Raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libsrng.so not found at {path}: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name, None)
+            if fn is None:
+                continue
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(st: int, func: str):
+    if st != 0:
+        msg = load().srng_last_error()
+        raise SrngError(st, msg.decode() if msg else "", func)
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if hasattr(x, "ctypes"):
+        return int(x.ctypes.data)
+    if isinstance(x, ctypes.Array):
+        return ctypes.addressof(x)
+    raise TypeError(f"cannot take a pointer of {type(x)!r}")
+
+
+def _stream(s) -> int:
+    if s is None:
+        torch = sys.modules.get("torch")
+        if torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():
+            return int(torch.cuda.current_stream().cuda_stream)
+        return 0
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return int(s.cuda_stream)
+    raise TypeError(f"not a stream: {type(s)!r}")
+
+
+def _tune(t):
+    if t is None:
+        return None
+    if isinstance(t, Tune):
+        return ctypes.byref(t)
+    if isinstance(t, dict):
+        return ctypes.byref(Tune(**t))
+    raise TypeError("tune must be a Tune or a dict")
+
+
+# ---------------------------------------------------------------- errors / info
+def srng_last_error() -> str:
+    return load().srng_last_error().decode()
+
+
+def srng_status_string(status: int) -> str:
+    return load().srng_status_string(status).decode()
+
+
+def srng_abi_version() -> int:
+    return load().srng_abi_version()
+
+
+# ---------------------------------------------------------------- stream sets
+def srng_create(gen: int, seed: int, n_streams: int, spacing: int = SRNG_SPACING_STREAM, stream=None) -> int:
+    h = _vp()
+    _check(load().srng_create(ctypes.byref(h), gen, seed, n_streams, spacing, _stream(stream)), "srng_create")
+    return h.value
+
+
+def srng_create_from_state(state, n_streams: int, spacing: int = SRNG_SPACING_STREAM, stream=None) -> int:
+    st = (ctypes.c_uint32 * 6)(*[int(x) for x in state])
+    h = _vp()
+    _check(load().srng_create_from_state(ctypes.byref(h), ctypes.addressof(st), n_streams, spacing,
+                                         _stream(stream)), "srng_create_from_state")
+    return h.value
+
+
+def srng_destroy(handle: int) -> None:
+    _check(load().srng_destroy(handle), "srng_destroy")
+
+
+def srng_reset(handle: int, stream=None) -> None:
+    _check(load().srng_reset(handle, _stream(stream)), "srng_reset")
+
+
+def srng_describe(handle: int) -> SetDesc:
+    d = SetDesc()
+    _check(load().srng_describe(handle, ctypes.byref(d)), "srng_describe")
+    return d
+
+
+def srng_get_device_view(handle: int) -> DevView:
+    v = DevView()
+    _check(load().srng_get_device_view(handle, ctypes.byref(v)), "srng_get_device_view")
+    return v
+
+
+def srng_jump(handle: int, stream_begin: int, count: int, unit: int, n: int, stream=None) -> None:
+    _check(load().srng_jump(handle, stream_begin, count, unit, (n >> 64) & (2**64 - 1), n & (2**64 - 1),
+                            _stream(stream)), "srng_jump")
+
+
+def srng_generate(handle: int, stream_begin: int, stream_count: int, n_per_stream: int, out_type: int, out,
+                  stream=None) -> None:
+    _check(load().srng_generate(handle, stream_begin, stream_count, n_per_stream, out_type, _ptr(out),
+                                _stream(stream)), "srng_generate")
+
+
+def srng_generate_tuned(handle: int, stream_begin: int, stream_count: int, n_per_stream: int, out_type: int, out,
+                        tune=None, stream=None) -> None:
+    _check(load().srng_generate_tuned(handle, stream_begin, stream_count, n_per_stream, out_type, _ptr(out),
+                                      _tune(tune), _stream(stream)), "srng_generate_tuned")
+
+
+def srng_generate_host(handle: int, stream_begin: int, stream_count: int, n_per_stream: int, out_type: int,
+                       out_host, stream=None) -> None:
+    _check(load().srng_generate_host(handle, stream_begin, stream_count, n_per_stream, out_type, _ptr(out_host),
+                                     _stream(stream)), "srng_generate_host")
+
+
+def srng_get_state(handle: int, stream_begin: int, count: int, state_host, stream=None) -> None:
+    _check(load().srng_get_state(handle, stream_begin, count, _ptr(state_host), _stream(stream)), "srng_get_state")
+
+
+def srng_set_state(handle: int, stream_begin: int, count: int, state_host, stream=None) -> None:
+    _check(load().srng_set_state(handle, stream_begin, count, _ptr(state_host), _stream(stream)), "srng_set_state")
+
+
+def srng_set_tune(gen: int, out_type: int, tune=None) -> None:
+    _check(load().srng_set_tune(gen, out_type, _tune(tune)), "srng_set_tune")
+
+
+def srng_get_tune(gen: int, out_type: int) -> Tune:
+    t = Tune()
+    _check(load().srng_get_tune(gen, out_type, ctypes.byref(t)), "srng_get_tune")
+    return t
+
+
+def srng_convert(gen: int, out_type: int, in_dev, n: int, out_dev, stream=None) -> None:
+    _check(load().srng_convert(gen, out_type, _ptr(in_dev), n, _ptr(out_dev), _stream(stream)), "srng_convert")
+
+
+def srng_seed_expand(seed: int) -> list:
+    st = (ctypes.c_uint32 * 6)()
+    _check(load().srng_seed_expand(seed, ctypes.addressof(st)), "srng_seed_expand")
+    return list(st)
+
+
+def srng_jump_matrix(unit: int, n: int):
+    a1 = (ctypes.c_uint32 * 9)()
+    a2 = (ctypes.c_uint32 * 9)()
+    _check(load().srng_jump_matrix(unit, (n >> 64) & (2**64 - 1), n & (2**64 - 1), ctypes.addressof(a1),
+                                   ctypes.addressof(a2)), "srng_jump_matrix")
+    return [list(a1[3 * i:3 * i + 3]) for i in range(3)], [list(a2[3 * i:3 * i + 3]) for i in range(3)]
+
+
+# ---------------------------------------------------------------- batches
+def _instances(inst):
+    if isinstance(inst, ctypes.Array):
+        return inst, len(inst)
+    arr = (Instance * len(inst))()
+    for i, x in enumerate(inst):
+        if isinstance(x, Instance):
+            arr[i] = x
+        else:
+            arr[i] = Instance(**x) if isinstance(x, dict) else Instance(*x)
+    return arr, len(inst)
+
+
+def _sets(sets):
+    arr = (_vp * len(sets))(*sets)
+    return arr, len(sets)
+
+
+def srng_batch_plan_create(sets, inst, mode: int, out_type: int, out_dev, tune=None, stream=None):
+    """Returns (plan handle, keep-alive tuple)."""
+    sa, ns = _sets(sets)
+    ia, ni = _instances(inst)
+    h = _vp()
+    _check(load().srng_batch_plan_create(ctypes.byref(h), sa, ns, ia, ni, mode, out_type, _ptr(out_dev),
+                                         _tune(tune), _stream(stream)), "srng_batch_plan_create")
+    return h.value
+
+
+def srng_batch_plan_launch(plan: int, stream=None) -> None:
+    _check(load().srng_batch_plan_launch(plan, _stream(stream)), "srng_batch_plan_launch")
+
+
+def srng_batch_plan_info(plan: int):
+    n = _u64()
+    k = _u32()
+    _check(load().srng_batch_plan_info(plan, ctypes.byref(n), ctypes.byref(k)), "srng_batch_plan_info")
+    return n.value, k.value
+
+
+def srng_batch_plan_destroy(plan: int) -> None:
+    _check(load().srng_batch_plan_destroy(plan), "srng_batch_plan_destroy")
+
+
+def srng_batch_run(sets, inst, mode: int, out_type: int, out_dev, stream=None) -> None:
+    sa, ns = _sets(sets)
+    ia, ni = _instances(inst)
+    _check(load().srng_batch_run(sa, ns, ia, ni, mode, out_type, _ptr(out_dev), _stream(stream)), "srng_batch_run")

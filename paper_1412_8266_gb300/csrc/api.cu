@@ -1,0 +1,627 @@
+// C ABI entry points (srng.h): stream sets, jumps, generation, state I/O.
+//
+// Host side of the paper's initialisation layer (arXiv 1412.8266 Sec. 5.1):
+// one call allocates the device state and places every stream before any
+// user kernel runs; the device never sees host-only concepts.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "srng.h"
+
+namespace srng_impl {
+
+// ------------------------------------------------------------------ errors
+namespace {
+thread_local std::string t_last_error;
+}
+
+srng_status fail(srng_status st, const std::string &msg)
+{
+    t_last_error = msg;
+    return st;
+}
+
+srng_status cuda_fail(cudaError_t e, const char *what)
+{
+    t_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? SRNG_ERR_OOM : SRNG_ERR_CUDA;
+}
+
+void clear_error() { t_last_error.clear(); }
+
+// ------------------------------------------------------------------ devices
+srng_status current_device(DeviceInfo *out)
+{
+    static std::mutex mu;
+    static std::map<int, int> sm_counts;
+    int dev = 0;
+    SRNG_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = sm_counts.find(dev);
+    if (it == sm_counts.end()) {
+        int sms = 0;
+        SRNG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        it = sm_counts.emplace(dev, sms).first;
+    }
+    out->device = dev;
+    out->sm_count = it->second;
+    return SRNG_OK;
+}
+
+// ------------------------------------------------------------------ tuning
+namespace {
+std::mutex g_tune_mu;
+srng_tune g_tune[2][3];
+bool g_tune_set[2][3];
+
+srng_tune builtin_tune(srng_gen gen, srng_out)
+{
+    srng_tune t;
+    memset(&t, 0, sizeof t);
+    t.block_threads = gen == SRNG_MRG32K3A ? 256 : 256;
+    t.blocks_per_sm = gen == SRNG_MRG32K3A ? 5 : 8;
+    t.chunk = 0;  // chosen from the problem shape
+    t.unroll = 2;
+    t.vector_store = 1;
+    t.lane_blocks = 64;
+    return t;
+}
+}  // namespace
+
+srng_tune effective_tune(srng_gen gen, srng_out type, const srng_tune *user)
+{
+    srng_tune t = builtin_tune(gen, type);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (g_tune_set[gen][type]) {
+            const srng_tune &d = g_tune[gen][type];
+            if (d.block_threads) t.block_threads = d.block_threads;
+            if (d.blocks_per_sm) t.blocks_per_sm = d.blocks_per_sm;
+            if (d.chunk) t.chunk = d.chunk;
+            if (d.unroll) t.unroll = d.unroll;
+            if (d.vector_store) t.vector_store = d.vector_store;
+            if (d.lane_blocks) t.lane_blocks = d.lane_blocks;
+        }
+    }
+    if (user) {
+        if (user->block_threads) t.block_threads = user->block_threads;
+        if (user->blocks_per_sm) t.blocks_per_sm = user->blocks_per_sm;
+        if (user->chunk) t.chunk = user->chunk;
+        if (user->unroll) t.unroll = user->unroll;
+        if (user->vector_store) t.vector_store = user->vector_store;
+        if (user->lane_blocks) t.lane_blocks = user->lane_blocks;
+    }
+    return t;
+}
+
+srng_status check_tune(const srng_tune *t)
+{
+    if (!t) return SRNG_OK;
+    if (t->block_threads && (t->block_threads % 32 || t->block_threads > 256 || t->block_threads < 64))
+        return fail(SRNG_ERR_ARG, "tune.block_threads must be a multiple of 32 in [64, 256]");
+    if (t->blocks_per_sm > 64) return fail(SRNG_ERR_ARG, "tune.blocks_per_sm must be <= 64");
+    if (t->chunk && t->chunk % 32) return fail(SRNG_ERR_ARG, "tune.chunk must be a multiple of 32");
+    if (t->unroll && t->unroll != 1 && t->unroll != 2 && t->unroll != 4)
+        return fail(SRNG_ERR_ARG, "tune.unroll must be 1, 2 or 4");
+    if (t->vector_store > 2) return fail(SRNG_ERR_ARG, "tune.vector_store must be 0, 1 or 2");
+    if (t->lane_blocks > 4096) return fail(SRNG_ERR_ARG, "tune.lane_blocks must be <= 4096");
+    return SRNG_OK;
+}
+
+// --------------------------------------------------------- jump tables
+namespace {
+std::mutex g_tab_mu;
+std::map<std::pair<int, uint64_t>, JumpTable> g_tabs;  // (shift, chunk) -> J_k = A^(chunk 2^(shift+k))
+
+// J_k = (A^(base * 2^shift))^(2^k), k < 64.
+const JumpTable &jump_table(int shift, uint64_t base)
+{
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    auto key = std::make_pair(shift, base);
+    auto it = g_tabs.find(key);
+    if (it != g_tabs.end()) return it->second;
+    JumpTable t;
+    MatPair m = mat_pow_shifted(0, base, shift);
+    for (int k = 0; k < 64; ++k) {
+        memcpy(t.m[k], m.a, sizeof m.a);
+        m = mat_mul(m, m);
+    }
+    return g_tabs.emplace(key, t).first->second;
+}
+
+int bit_length(uint64_t x)
+{
+    int b = 0;
+    while (x) { ++b; x >>= 1; }
+    return b;
+}
+
+size_t out_size(srng_out t) { return t == SRNG_OUT_F64 ? 8 : 4; }
+
+bool valid_gen(int g) { return g == SRNG_MRG32K3A || g == SRNG_PHILOX4X32_10; }
+bool valid_out(int t) { return t == SRNG_OUT_U32 || t == SRNG_OUT_F32 || t == SRNG_OUT_F64; }
+
+int spacing_shift(srng_spacing sp) { return sp == SRNG_SPACING_SUBSTREAM ? 76 : 127; }
+
+}  // namespace
+
+// Placement of streams [first, first + count) of an MRG32k3a set.
+static srng_status place_streams(srng_set *s, uint64_t first, uint64_t count, cudaStream_t stream)
+{
+    DeviceInfo dev;
+    srng_status st = current_device(&dev);
+    if (st) return st;
+    const int nbits = bit_length(first + count - 1);
+    const JumpTable &tab = jump_table(spacing_shift(s->spacing), 1);
+    SRNG_CUDA_TRY(launch_mrg_place(s->d_state, s->n_streams, first, count, s->y0, tab, nbits, stream, dev));
+    return SRNG_OK;
+}
+
+static srng_status create_common(srng_set **out, srng_gen gen, uint64_t seed, const uint32_t *state,
+                                 uint64_t n_streams, srng_spacing spacing, void *cuda_stream)
+{
+    if (!out) return fail(SRNG_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!valid_gen(gen)) return fail(SRNG_ERR_ARG, "unknown generator");
+    if (spacing != SRNG_SPACING_STREAM && spacing != SRNG_SPACING_SUBSTREAM)
+        return fail(SRNG_ERR_ARG, "unknown spacing");
+    if (n_streams == 0 || n_streams > (1ull << 40)) return fail(SRNG_ERR_ARG, "n_streams must be in [1, 2^40]");
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    srng_set *s = new (std::nothrow) srng_set();
+    if (!s) return fail(SRNG_ERR_OOM, "host allocation failed");
+    s->gen = gen;
+    s->spacing = spacing;
+    s->n_streams = n_streams;
+    s->seed = seed;
+    s->d_state = nullptr;
+    s->d_pos = nullptr;
+    s->max_pos = 0;
+    s->d_stage[0] = s->d_stage[1] = nullptr;
+    s->stage_bytes = 0;
+    s->copy_stream = nullptr;
+    memset(s->y0, 0, sizeof s->y0);
+    cudaGetDevice(&s->device);
+    srng_status st = SRNG_OK;
+    cudaError_t e;
+    if (gen == SRNG_MRG32K3A) {
+        if (state) memcpy(s->y0, state, sizeof s->y0);
+        else seed_expand(seed, s->y0);
+        e = cudaMalloc(&s->d_state, 6 * n_streams * sizeof(uint32_t));
+        if (e != cudaSuccess) { st = cuda_fail(e, "cudaMalloc(stream states)"); goto bad; }
+        st = place_streams(s, 0, n_streams, stream);
+        if (st) goto bad;
+    } else {
+        s->key0 = (uint32_t)seed;
+        s->key1 = (uint32_t)(seed >> 32);
+        e = cudaMalloc(&s->d_pos, n_streams * sizeof(uint64_t));
+        if (e != cudaSuccess) { st = cuda_fail(e, "cudaMalloc(positions)"); goto bad; }
+        e = cudaMemsetAsync(s->d_pos, 0, n_streams * sizeof(uint64_t), stream);
+        if (e != cudaSuccess) { st = cuda_fail(e, "cudaMemsetAsync(positions)"); goto bad; }
+    }
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) { st = cuda_fail(e, "cudaStreamSynchronize(create)"); goto bad; }
+    *out = s;
+    return SRNG_OK;
+bad:
+    if (s->d_state) cudaFree(s->d_state);
+    if (s->d_pos) cudaFree(s->d_pos);
+    delete s;
+    return st;
+}
+
+static srng_status check_range(const srng_set *s, uint64_t begin, uint64_t count)
+{
+    if (!s) return fail(SRNG_ERR_ARG, "set is NULL");
+    if (begin > s->n_streams || count > s->n_streams - begin)
+        return fail(SRNG_ERR_RANGE, "stream range [" + std::to_string(begin) + ", +" + std::to_string(count) +
+                                        ") outside the set of " + std::to_string(s->n_streams));
+    return SRNG_OK;
+}
+
+// Generation into a device buffer (shared by srng_generate* and the host path).
+static srng_status generate_dev(srng_set *s, uint64_t b, uint64_t c, uint64_t n, srng_out type, void *out,
+                                const srng_tune &t, cudaStream_t stream, const DeviceInfo &dev)
+{
+    if (s->gen == SRNG_MRG32K3A) {
+        MrgGenArgs a;
+        a.state = s->d_state;
+        a.n_streams = s->n_streams;
+        a.s_begin = b;
+        a.s_count = c;
+        a.n = n;
+        uint64_t chunk = t.chunk;
+        if (!chunk) {
+            // enough items for about four waves of resident threads
+            const uint64_t resident = (uint64_t)dev.sm_count * t.blocks_per_sm * t.block_threads;
+            const uint64_t want = 4 * resident;
+            const uint64_t splits = c >= want ? 1 : (want + c - 1) / c;
+            chunk = (n + splits - 1) / splits;
+            chunk = ((chunk + 31) / 32) * 32;
+            if (chunk < 256) chunk = 256;
+        }
+        if (chunk > n) chunk = n;
+        a.chunk = chunk;
+        a.cps = (n + chunk - 1) / chunk;
+        a.nbits = bit_length(a.cps - 1);
+        a.out = out;
+        const JumpTable &tab = jump_table(0, chunk);
+        SRNG_CUDA_TRY(launch_mrg_generate(a, type, tab, t, stream, dev));
+        SRNG_CUDA_TRY(launch_mrg_apply(s->d_state, s->n_streams, b, c, mat_pow_shifted(0, n, 0), stream, dev));
+    } else {
+        PhiloxGenArgs a;
+        a.k0 = s->key0;
+        a.k1 = s->key1;
+        a.pos = s->d_pos;
+        a.s_begin = b;
+        a.s_count = c;
+        a.n = n;
+        a.out = out;
+        SRNG_CUDA_TRY(launch_philox_generate(a, type, t, stream, dev));
+        SRNG_CUDA_TRY(launch_philox_advance(s->d_pos, b, c, n, stream, dev));
+        s->max_pos += n;
+    }
+    return SRNG_OK;
+}
+
+static srng_status generate_checks(srng_set *s, uint64_t b, uint64_t c, uint64_t n, srng_out type,
+                                   const void *out)
+{
+    srng_status st = check_range(s, b, c);
+    if (st) return st;
+    if (!valid_out(type)) return fail(SRNG_ERR_ARG, "unknown output type");
+    if (c == 0 || n == 0) return SRNG_OK;
+    if (!out) return fail(SRNG_ERR_ARG, "output pointer is NULL");
+    if (reinterpret_cast<uintptr_t>(out) % out_size(type))
+        return fail(SRNG_ERR_ARG, "output pointer not aligned to the element size");
+    if (n > (1ull << 62) || c > (1ull << 62) / n || c * n > (1ull << 62) / out_size(type))
+        return fail(SRNG_ERR_ARG, "output size overflows");
+    if (s->gen == SRNG_PHILOX4X32_10 && n > UINT64_MAX - s->max_pos)
+        return fail(SRNG_ERR_RANGE, "a Philox position would pass 2^64 - 1");
+    return SRNG_OK;
+}
+
+}  // namespace srng_impl
+
+using namespace srng_impl;
+
+extern "C" {
+
+const char *srng_last_error(void) { return t_last_error.c_str(); }
+
+const char *srng_status_string(srng_status status)
+{
+    switch (status) {
+    case SRNG_OK: return "SRNG_OK";
+    case SRNG_ERR_ARG: return "SRNG_ERR_ARG";
+    case SRNG_ERR_OOM: return "SRNG_ERR_OOM";
+    case SRNG_ERR_STATE: return "SRNG_ERR_STATE";
+    case SRNG_ERR_CUDA: return "SRNG_ERR_CUDA";
+    case SRNG_ERR_BUDGET: return "SRNG_ERR_BUDGET";
+    case SRNG_ERR_TIMEOUT: return "SRNG_ERR_TIMEOUT";
+    case SRNG_ERR_RANGE: return "SRNG_ERR_RANGE";
+    case SRNG_ERR_CLOSED: return "SRNG_ERR_CLOSED";
+    case SRNG_ERR_UNSUPPORTED: return "SRNG_ERR_UNSUPPORTED";
+    }
+    return "SRNG_UNKNOWN_STATUS";
+}
+
+int srng_abi_version(void) { return SRNG_ABI_VERSION; }
+
+srng_status srng_create(srng_set **out, srng_gen gen, uint64_t seed, uint64_t n_streams, srng_spacing spacing,
+                        void *cuda_stream)
+{
+    clear_error();
+    return create_common(out, gen, seed, nullptr, n_streams, spacing, cuda_stream);
+}
+
+srng_status srng_create_from_state(srng_set **out, const uint32_t state[6], uint64_t n_streams,
+                                   srng_spacing spacing, void *cuda_stream)
+{
+    clear_error();
+    if (!state) return fail(SRNG_ERR_ARG, "state is NULL");
+    if (!state_valid(state))
+        return fail(SRNG_ERR_STATE, "seed state must have x1 words < m1, x2 words < m2, no all-zero component");
+    return create_common(out, SRNG_MRG32K3A, 0, state, n_streams, spacing, cuda_stream);
+}
+
+srng_status srng_destroy(srng_set *set)
+{
+    clear_error();
+    if (!set) return SRNG_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(set->device);
+    cudaDeviceSynchronize();
+    if (set->d_state) cudaFree(set->d_state);
+    if (set->d_pos) cudaFree(set->d_pos);
+    for (int i = 0; i < 2; ++i) {
+        if (set->d_stage[i]) cudaFree(set->d_stage[i]);
+    }
+    if (set->copy_stream) {
+        cudaStreamDestroy(set->copy_stream);
+        for (int i = 0; i < 2; ++i) {
+            cudaEventDestroy(set->ev_gen[i]);
+            cudaEventDestroy(set->ev_copy[i]);
+        }
+    }
+    cudaSetDevice(prev);
+    delete set;
+    return SRNG_OK;
+}
+
+srng_status srng_reset(srng_set *set, void *cuda_stream)
+{
+    clear_error();
+    if (!set) return fail(SRNG_ERR_ARG, "set is NULL");
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    if (set->gen == SRNG_MRG32K3A) return place_streams(set, 0, set->n_streams, stream);
+    SRNG_CUDA_TRY(cudaMemsetAsync(set->d_pos, 0, set->n_streams * sizeof(uint64_t), stream));
+    set->max_pos = 0;
+    return SRNG_OK;
+}
+
+srng_status srng_describe(const srng_set *set, srng_set_desc *out)
+{
+    clear_error();
+    if (!set || !out) return fail(SRNG_ERR_ARG, "NULL argument");
+    memset(out, 0, sizeof *out);
+    out->gen = set->gen;
+    out->spacing = set->spacing;
+    out->n_streams = set->n_streams;
+    out->seed = set->seed;
+    if (set->gen == SRNG_MRG32K3A) memcpy(out->seed_state, set->y0, sizeof set->y0);
+    else { out->seed_state[0] = set->key0; out->seed_state[1] = set->key1; }
+    return SRNG_OK;
+}
+
+srng_status srng_get_device_view(const srng_set *set, srng_dev_view *out)
+{
+    clear_error();
+    if (!set || !out) return fail(SRNG_ERR_ARG, "NULL argument");
+    memset(out, 0, sizeof *out);
+    out->gen = set->gen;
+    out->key0 = set->key0;
+    out->key1 = set->key1;
+    out->n_streams = set->n_streams;
+    out->mrg_state = set->d_state;
+    out->philox_pos = set->d_pos;
+    return SRNG_OK;
+}
+
+srng_status srng_jump(srng_set *set, uint64_t stream_begin, uint64_t count, srng_jump_unit unit, uint64_t n_hi,
+                      uint64_t n_lo, void *cuda_stream)
+{
+    clear_error();
+    srng_status st = check_range(set, stream_begin, count);
+    if (st) return st;
+    if (unit != SRNG_JUMP_DRAWS && unit != SRNG_JUMP_SUBSTREAMS && unit != SRNG_JUMP_STREAMS)
+        return fail(SRNG_ERR_ARG, "unknown jump unit");
+    if (count == 0) return SRNG_OK;
+    DeviceInfo dev;
+    if ((st = current_device(&dev))) return st;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    if (set->gen == SRNG_MRG32K3A) {
+        const int shift = unit == SRNG_JUMP_DRAWS ? 0 : unit == SRNG_JUMP_SUBSTREAMS ? 76 : 127;
+        SRNG_CUDA_TRY(launch_mrg_apply(set->d_state, set->n_streams, stream_begin, count,
+                                       mat_pow_shifted(n_hi, n_lo, shift), stream, dev));
+        return SRNG_OK;
+    }
+    if (unit != SRNG_JUMP_DRAWS) return fail(SRNG_ERR_UNSUPPORTED, "Philox streams jump by draws only");
+    if (n_hi || n_lo > UINT64_MAX - set->max_pos) return fail(SRNG_ERR_RANGE, "a Philox position would pass 2^64 - 1");
+    SRNG_CUDA_TRY(launch_philox_advance(set->d_pos, stream_begin, count, n_lo, stream, dev));
+    set->max_pos += n_lo;
+    return SRNG_OK;
+}
+
+srng_status srng_generate_tuned(srng_set *set, uint64_t stream_begin, uint64_t stream_count, uint64_t n_per_stream,
+                                srng_out type, void *out_dev, const srng_tune *tune, void *cuda_stream)
+{
+    clear_error();
+    srng_status st = generate_checks(set, stream_begin, stream_count, n_per_stream, type, out_dev);
+    if (st) return st;
+    if ((st = check_tune(tune))) return st;
+    if (stream_count == 0 || n_per_stream == 0) return SRNG_OK;
+    DeviceInfo dev;
+    if ((st = current_device(&dev))) return st;
+    const srng_tune t = effective_tune(set->gen, type, tune);
+    return generate_dev(set, stream_begin, stream_count, n_per_stream, type, out_dev, t,
+                        static_cast<cudaStream_t>(cuda_stream), dev);
+}
+
+srng_status srng_generate(srng_set *set, uint64_t stream_begin, uint64_t stream_count, uint64_t n_per_stream,
+                          srng_out type, void *out_dev, void *cuda_stream)
+{
+    return srng_generate_tuned(set, stream_begin, stream_count, n_per_stream, type, out_dev, nullptr, cuda_stream);
+}
+
+srng_status srng_generate_host(srng_set *set, uint64_t stream_begin, uint64_t stream_count, uint64_t n_per_stream,
+                               srng_out type, void *out_host, void *cuda_stream)
+{
+    clear_error();
+    srng_status st = generate_checks(set, stream_begin, stream_count, n_per_stream, type, out_host);
+    if (st) return st;
+    if (stream_count == 0 || n_per_stream == 0) return SRNG_OK;
+    DeviceInfo dev;
+    if ((st = current_device(&dev))) return st;
+    std::lock_guard<std::mutex> lk(set->mu);
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    const size_t kStage = 256ull << 20;
+    if (!set->d_stage[0]) {
+        for (int i = 0; i < 2; ++i) SRNG_CUDA_TRY(cudaMalloc(&set->d_stage[i], kStage));
+        SRNG_CUDA_TRY(cudaStreamCreateWithFlags(&set->copy_stream, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            SRNG_CUDA_TRY(cudaEventCreateWithFlags(&set->ev_gen[i], cudaEventDisableTiming));
+            SRNG_CUDA_TRY(cudaEventCreateWithFlags(&set->ev_copy[i], cudaEventDisableTiming));
+        }
+        set->stage_bytes = kStage;
+    }
+    const srng_tune t = effective_tune(set->gen, type, nullptr);
+    const size_t esz = out_size(type);
+    const uint64_t stage_elems = set->stage_bytes / esz;
+    // Pieces: whole streams when a stream fits the stage, else consecutive
+    // parts of one stream (generation of part k moves the stream to part k+1).
+    struct Piece { uint64_t s, cnt, n, host_off; };
+    std::vector<Piece> pieces;
+    if (n_per_stream <= stage_elems) {
+        const uint64_t per = stage_elems / n_per_stream;
+        for (uint64_t s = 0; s < stream_count; s += per) {
+            const uint64_t cnt = std::min(per, stream_count - s);
+            pieces.push_back({stream_begin + s, cnt, n_per_stream, s * n_per_stream});
+        }
+    } else {
+        for (uint64_t s = 0; s < stream_count; ++s)
+            for (uint64_t k = 0; k < n_per_stream; k += stage_elems)
+                pieces.push_back({stream_begin + s, 1, std::min(stage_elems, n_per_stream - k), s * n_per_stream + k});
+    }
+    bool used[2] = {false, false};
+    for (size_t i = 0; i < pieces.size(); ++i) {
+        const int slot = (int)(i & 1);
+        const Piece &p = pieces[i];
+        if (used[slot]) SRNG_CUDA_TRY(cudaStreamWaitEvent(stream, set->ev_copy[slot], 0));
+        st = generate_dev(set, p.s, p.cnt, p.n, type, set->d_stage[slot], t, stream, dev);
+        if (st) return st;
+        SRNG_CUDA_TRY(cudaEventRecord(set->ev_gen[slot], stream));
+        SRNG_CUDA_TRY(cudaStreamWaitEvent(set->copy_stream, set->ev_gen[slot], 0));
+        SRNG_CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(out_host) + p.host_off * esz, set->d_stage[slot],
+                                      p.cnt * p.n * esz, cudaMemcpyDeviceToHost, set->copy_stream));
+        SRNG_CUDA_TRY(cudaEventRecord(set->ev_copy[slot], set->copy_stream));
+        used[slot] = true;
+    }
+    SRNG_CUDA_TRY(cudaStreamSynchronize(set->copy_stream));
+    SRNG_CUDA_TRY(cudaStreamSynchronize(stream));
+    return SRNG_OK;
+}
+
+srng_status srng_get_state(const srng_set *set, uint64_t stream_begin, uint64_t count, void *state_host,
+                           void *cuda_stream)
+{
+    clear_error();
+    srng_status st = check_range(set, stream_begin, count);
+    if (st) return st;
+    if (count == 0) return SRNG_OK;
+    if (!state_host) return fail(SRNG_ERR_ARG, "state_host is NULL");
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    if (set->gen == SRNG_PHILOX4X32_10) {
+        SRNG_CUDA_TRY(cudaMemcpyAsync(state_host, set->d_pos + stream_begin, count * sizeof(uint64_t),
+                                      cudaMemcpyDeviceToHost, stream));
+        SRNG_CUDA_TRY(cudaStreamSynchronize(stream));
+        return SRNG_OK;
+    }
+    std::vector<uint32_t> soa;
+    try { soa.resize(6 * count); } catch (...) { return fail(SRNG_ERR_OOM, "host allocation failed"); }
+    SRNG_CUDA_TRY(cudaMemcpy2DAsync(soa.data(), count * sizeof(uint32_t), set->d_state + stream_begin,
+                                    set->n_streams * sizeof(uint32_t), count * sizeof(uint32_t), 6,
+                                    cudaMemcpyDeviceToHost, stream));
+    SRNG_CUDA_TRY(cudaStreamSynchronize(stream));
+    uint32_t *h = static_cast<uint32_t *>(state_host);
+    for (uint64_t i = 0; i < count; ++i)
+        for (int j = 0; j < 6; ++j) h[6 * i + j] = soa[j * count + i];
+    return SRNG_OK;
+}
+
+srng_status srng_set_state(srng_set *set, uint64_t stream_begin, uint64_t count, const void *state_host,
+                           void *cuda_stream)
+{
+    clear_error();
+    srng_status st = check_range(set, stream_begin, count);
+    if (st) return st;
+    if (count == 0) return SRNG_OK;
+    if (!state_host) return fail(SRNG_ERR_ARG, "state_host is NULL");
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    if (set->gen == SRNG_PHILOX4X32_10) {
+        const uint64_t *p = static_cast<const uint64_t *>(state_host);
+        uint64_t mx = 0;
+        for (uint64_t i = 0; i < count; ++i) mx = std::max(mx, p[i]);
+        SRNG_CUDA_TRY(cudaMemcpyAsync(set->d_pos + stream_begin, state_host, count * sizeof(uint64_t),
+                                      cudaMemcpyHostToDevice, stream));
+        SRNG_CUDA_TRY(cudaStreamSynchronize(stream));
+        set->max_pos = std::max(set->max_pos, mx);
+        return SRNG_OK;
+    }
+    const uint32_t *h = static_cast<const uint32_t *>(state_host);
+    for (uint64_t i = 0; i < count; ++i)
+        if (!state_valid(h + 6 * i))
+            return fail(SRNG_ERR_STATE, "state of stream " + std::to_string(stream_begin + i) + " is invalid");
+    std::vector<uint32_t> soa;
+    try { soa.resize(6 * count); } catch (...) { return fail(SRNG_ERR_OOM, "host allocation failed"); }
+    for (uint64_t i = 0; i < count; ++i)
+        for (int j = 0; j < 6; ++j) soa[j * count + i] = h[6 * i + j];
+    SRNG_CUDA_TRY(cudaMemcpy2DAsync(set->d_state + stream_begin, set->n_streams * sizeof(uint32_t), soa.data(),
+                                    count * sizeof(uint32_t), count * sizeof(uint32_t), 6, cudaMemcpyHostToDevice,
+                                    stream));
+    SRNG_CUDA_TRY(cudaStreamSynchronize(stream));
+    return SRNG_OK;
+}
+
+srng_status srng_set_tune(srng_gen gen, srng_out type, const srng_tune *tune)
+{
+    clear_error();
+    if (!valid_gen(gen) || !valid_out(type)) return fail(SRNG_ERR_ARG, "unknown generator or output type");
+    srng_status st = check_tune(tune);
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (tune) {
+        g_tune[gen][type] = *tune;
+        g_tune_set[gen][type] = true;
+    } else {
+        g_tune_set[gen][type] = false;
+    }
+    return SRNG_OK;
+}
+
+srng_status srng_get_tune(srng_gen gen, srng_out type, srng_tune *out)
+{
+    clear_error();
+    if (!valid_gen(gen) || !valid_out(type) || !out) return fail(SRNG_ERR_ARG, "bad argument");
+    *out = effective_tune(gen, type, nullptr);
+    return SRNG_OK;
+}
+
+srng_status srng_convert(srng_gen gen, srng_out type, const uint32_t *in_dev, uint64_t n, void *out_dev,
+                         void *cuda_stream)
+{
+    clear_error();
+    if (!valid_gen(gen) || !valid_out(type)) return fail(SRNG_ERR_ARG, "unknown generator or output type");
+    if (n == 0) return SRNG_OK;
+    if (!in_dev || !out_dev) return fail(SRNG_ERR_ARG, "NULL pointer");
+    if (reinterpret_cast<uintptr_t>(in_dev) % 4 || reinterpret_cast<uintptr_t>(out_dev) % out_size(type))
+        return fail(SRNG_ERR_ARG, "misaligned pointer");
+    DeviceInfo dev;
+    srng_status st = current_device(&dev);
+    if (st) return st;
+    SRNG_CUDA_TRY(launch_convert(gen, type, in_dev, n, out_dev, static_cast<cudaStream_t>(cuda_stream), dev));
+    return SRNG_OK;
+}
+
+srng_status srng_seed_expand(uint64_t seed, uint32_t state[6])
+{
+    clear_error();
+    if (!state) return fail(SRNG_ERR_ARG, "state is NULL");
+    seed_expand(seed, state);
+    return SRNG_OK;
+}
+
+srng_status srng_jump_matrix(srng_jump_unit unit, uint64_t n_hi, uint64_t n_lo, uint32_t a1[9], uint32_t a2[9])
+{
+    clear_error();
+    if (!a1 || !a2) return fail(SRNG_ERR_ARG, "NULL output");
+    if (unit != SRNG_JUMP_DRAWS && unit != SRNG_JUMP_SUBSTREAMS && unit != SRNG_JUMP_STREAMS)
+        return fail(SRNG_ERR_ARG, "unknown jump unit");
+    const int shift = unit == SRNG_JUMP_DRAWS ? 0 : unit == SRNG_JUMP_SUBSTREAMS ? 76 : 127;
+    MatPair m = mat_pow_shifted(n_hi, n_lo, shift);
+    memcpy(a1, m.a, 9 * sizeof(uint32_t));
+    memcpy(a2, m.a + 9, 9 * sizeof(uint32_t));
+    return SRNG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,555 @@
+// K4 / K5 -- batched instances in one persistent, graph-captured launch.
+//
+// Thousands of simulation instances, each with its own stream (paper Sec. 4.1
+// / 4.3: one stream per processing element) and its own length, mixed
+// MRG32k3a and Philox4x32-10, are cut into equal-sized work items:
+//   - MRG32k3a item: 32 consecutive chunks of `chunk` draws of one instance,
+//     one chunk per lane; a lane reaches its chunk's start by jump-ahead
+//     ((A^chunk)^t applied to the instance's start state, Sec. 2.3);
+//   - Philox item: 32 x lane_blocks consecutive Philox blocks of one instance.
+// A persistent grid (one wave of resident blocks) takes items from a global
+// counter with one atomicAdd per warp and item, so instance lengths spread
+// over five decades still load every SM evenly, and one launch serves them
+// all.  The plan captures {zero counter, zero counts, kernel} in a CUDA graph.
+//
+// Modes:
+//   WRITE     values go to out[out_offset + k] (staged through shared memory
+//             for MRG32k3a exactly as in the plain kernel);
+//   FUSED_PI  nothing is written: draws stay in registers, pairs
+//             (2k, 2k+1) are tested exactly against the quarter disc and the
+//             per-lane counts are reduced (warp shuffle for Philox items, one
+//             64-bit atomicAdd per lane-chunk for MRG32k3a items).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "srng_device.cuh"
+
+namespace srng_impl {
+
+// Per-instance descriptor on the device.
+struct BatchInst {
+    uint32_t gen;
+    uint32_t key0, key1;
+    uint32_t st[6];           // MRG32k3a start state (written by the set-up kernel)
+    uint64_t stream;          // stream index in its set
+    uint64_t offset;          // draws after the stream's current position
+    uint64_t pos;             // Philox start position (written by the set-up kernel)
+    uint64_t length;
+    uint64_t out_offset;
+    const uint32_t *src_state;  // MRG32k3a set states (SoA) and their stride
+    uint64_t src_ns;
+    const uint64_t *src_pos;    // Philox set positions
+};
+
+struct BatchArgs {
+    const BatchInst *inst;
+    const uint2 *items;       // {instance, first chunk (MRG32k3a) or segment (Philox)}
+    uint32_t *counter;
+    uint64_t n_items;
+    uint64_t chunk;           // MRG32k3a draws per lane-chunk
+    uint32_t lane_blocks;     // Philox blocks per lane per item
+    int32_t mode;             // srng_batch_mode
+    void *out;                // values (WRITE) or int64 counts (FUSED_PI)
+};
+
+namespace {
+
+template <int OUT> struct OutT;
+template <> struct OutT<SRNG_OUT_U32> { using T = uint32_t; };
+template <> struct OutT<SRNG_OUT_F32> { using T = float; };
+template <> struct OutT<SRNG_OUT_F64> { using T = double; };
+
+template <int GEN, int OUT>
+__device__ __forceinline__ typename OutT<OUT>::T bconvert(uint32_t v)
+{
+    if constexpr (OUT == SRNG_OUT_U32) return v;
+    else if constexpr (OUT == SRNG_OUT_F32) return srng::to_f32(v);
+    else if constexpr (GEN == SRNG_MRG32K3A) return srng::mrg::to_f64(v);
+    else return srng::philox::to_f64(v);
+}
+
+// Exact quarter-disc tests on the defined uniforms.
+__device__ __forceinline__ uint32_t hit_mrg(uint32_t z0, uint32_t z1)
+{
+    // z0^2 + z1^2 < (m1 + 1)^2; the sum can pass 2^64, in which case it is a miss.
+    const uint64_t a = (uint64_t)z0 * z0, s = a + (uint64_t)z1 * z1;
+    const uint64_t r = (uint64_t)srng::mrg::kM1 + 1;
+    return (s >= a && s < r * r) ? 1u : 0u;
+}
+
+__device__ __forceinline__ uint32_t hit_philox(uint32_t w0, uint32_t w1)
+{
+    const uint64_t a = w0 >> 8, b = w1 >> 8;
+    return a * a + b * b < (1ull << 48) ? 1u : 0u;
+}
+
+constexpr int kWarps = 8;
+
+template <int OUT>
+struct Smem {
+    using T = typename OutT<OUT>::T;
+    static constexpr int G = 128 / sizeof(T);
+    static constexpr int VPL = 16 / sizeof(T);
+    static constexpr int RS = G + VPL;
+    T tile[kWarps][32 * RS];
+    uint32_t row_len[kWarps][32];
+};
+
+// ---------------------------------------------------- MRG32k3a work item
+template <int OUT>
+__device__ void mrg_item(const BatchArgs &a, const JumpTable &tab, uint32_t ii, uint32_t first_chunk,
+                         Smem<OUT> &sm, int warp, int lane)
+{
+    using T = typename OutT<OUT>::T;
+    constexpr int G = Smem<OUT>::G, VPL = Smem<OUT>::VPL, RS = Smem<OUT>::RS;
+    const BatchInst &in = a.inst[ii];
+    const uint64_t t = (uint64_t)first_chunk + lane;
+    const uint64_t start = t * a.chunk;
+    const uint64_t len = start < in.length ? min(a.chunk, in.length - start) : 0;
+    uint32_t s0 = in.st[0], s1 = in.st[1], s2 = in.st[2], s3 = in.st[3], s4 = in.st[4], s5 = in.st[5];
+    if (len) {
+        for (int k = 0; k < 40; ++k) {
+            if ((t >> k) == 0) break;
+            if ((t >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
+        }
+    }
+    if (a.mode == SRNG_BATCH_FUSED_PI) {
+        uint32_t hits = 0;
+        for (uint64_t k = 0; k + 1 < len; k += 2) {
+            const uint32_t z0 = srng::mrg::step(s0, s1, s2, s3, s4, s5);
+            const uint32_t z1 = srng::mrg::step(s0, s1, s2, s3, s4, s5);
+            hits += hit_mrg(z0, z1);
+        }
+        if (hits) atomicAdd(reinterpret_cast<unsigned long long *>(a.out) + ii, (unsigned long long)hits);
+        return;
+    }
+    T *out = static_cast<T *>(a.out);
+    T *my = &sm.tile[warp][lane * RS];
+    const uint64_t row0 = in.out_offset + (uint64_t)first_chunk * a.chunk;  // row r starts at row0 + r * chunk
+    const bool vec = ((reinterpret_cast<uintptr_t>(out + row0) & 15) == 0) && (a.chunk % VPL == 0);
+    const uint32_t ntiles = (uint32_t)((len + G - 1) / G);
+    const uint32_t max_tiles = __reduce_max_sync(0xffffffffu, ntiles);
+    for (uint32_t g = 0; g < max_tiles; ++g) {
+        const uint64_t done = (uint64_t)g * G;
+        const uint32_t rl = len > done ? (uint32_t)min((uint64_t)G, len - done) : 0u;
+        sm.row_len[warp][lane] = rl;
+        for (uint32_t j = 0; j < rl; j += VPL) {
+            if constexpr (sizeof(T) == 4) {
+                T x[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) x[e] = bconvert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+                *reinterpret_cast<uint4 *>(&my[j]) = *reinterpret_cast<uint4 *>(x);
+            } else {
+                double2 v;
+                v.x = bconvert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+                v.y = bconvert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+                *reinterpret_cast<double2 *>(&my[j]) = v;
+            }
+        }
+        __syncwarp();
+        if (vec) {
+            constexpr int LPR = G / VPL, RPI = 32 / LPR;
+            const int q = lane % LPR, rsub = lane / LPR;
+            for (int r0 = 0; r0 < 32; r0 += RPI) {
+                const int r = r0 + rsub;
+                const uint32_t rlen = sm.row_len[warp][r];
+                const uint32_t e = q * VPL;
+                T *dst = out + row0 + (uint64_t)r * a.chunk + done + e;
+                if (e + VPL <= rlen) {
+                    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(&sm.tile[warp][r * RS + e]);
+                } else {
+                    for (uint32_t x = e; x < rlen; ++x) out[row0 + (uint64_t)r * a.chunk + done + x] = sm.tile[warp][r * RS + x];
+                }
+            }
+        } else {
+            constexpr int LPR = G, RPI = 32 / LPR;
+            const int q = lane % LPR, rsub = lane / LPR;
+            for (int r0 = 0; r0 < 32; r0 += RPI) {
+                const int r = r0 + rsub;
+                if ((uint32_t)q < sm.row_len[warp][r])
+                    out[row0 + (uint64_t)r * a.chunk + done + q] = sm.tile[warp][r * RS + q];
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------- Philox work item
+template <int OUT>
+__device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int lane)
+{
+    using T = typename OutT<OUT>::T;
+    const BatchInst &in = a.inst[ii];
+    const uint64_t p0 = in.pos;
+    const uint32_t al = (uint32_t)p0 & 3u;
+    const uint64_t q0 = p0 >> 2;
+    const uint64_t nb = (al + in.length + 3) >> 2;
+    const uint64_t b0 = (uint64_t)seg * 32 * a.lane_blocks;
+    const uint32_t c2 = (uint32_t)in.stream, c3 = (uint32_t)(in.stream >> 32);
+    const uint64_t L = in.length;
+    if (a.mode == SRNG_BATCH_FUSED_PI) {
+        uint32_t hits = 0;
+        for (uint32_t u = 0; u < a.lane_blocks; ++u) {
+            const uint64_t b = b0 + (uint64_t)u * 32 + lane;
+            if (b >= nb) break;
+            const uint64_t q = q0 + b;
+            uint32_t x0 = (uint32_t)q, x1 = (uint32_t)(q >> 32), x2 = c2, x3 = c3;
+            srng::philox::block(x0, x1, x2, x3, in.key0, in.key1);
+            const int64_t k0 = (int64_t)(b * 4) - al;  // draw index of word 0
+            if ((al & 1) == 0) {
+                // pairs are (word 0, word 1) and (word 2, word 3)
+                if (k0 >= 0 && (uint64_t)k0 + 1 < L) hits += hit_philox(x0, x1);
+                if (k0 + 2 >= 0 && (uint64_t)(k0 + 2) + 1 < L) hits += hit_philox(x2, x3);
+            } else {
+                // odd start: pairs (word 1, word 2) and (word 3, next block's word 0)
+                if (k0 + 1 >= 0 && (uint64_t)(k0 + 1) + 1 < L) hits += hit_philox(x1, x2);
+                if (k0 + 3 >= 0 && (uint64_t)(k0 + 3) + 1 < L) {
+                    const uint64_t qn = q + 1;
+                    uint32_t y0 = (uint32_t)qn, y1 = (uint32_t)(qn >> 32), y2 = c2, y3 = c3;
+                    srng::philox::block(y0, y1, y2, y3, in.key0, in.key1);
+                    hits += hit_philox(x3, y0);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) hits += __shfl_down_sync(0xffffffffu, hits, o);
+        if (lane == 0 && hits) atomicAdd(reinterpret_cast<unsigned long long *>(a.out) + ii, (unsigned long long)hits);
+        return;
+    }
+    T *row = static_cast<T *>(a.out) + in.out_offset;
+    for (uint32_t u = 0; u < a.lane_blocks; ++u) {
+        const uint64_t b = b0 + (uint64_t)u * 32 + lane;
+        if (b >= nb) break;
+        const uint64_t q = q0 + b;
+        uint32_t x0 = (uint32_t)q, x1 = (uint32_t)(q >> 32), x2 = c2, x3 = c3;
+        srng::philox::block(x0, x1, x2, x3, in.key0, in.key1);
+        const int64_t k0 = (int64_t)(b * 4) - al;
+        const T v[4] = {bconvert<SRNG_PHILOX4X32_10, OUT>(x0), bconvert<SRNG_PHILOX4X32_10, OUT>(x1),
+                        bconvert<SRNG_PHILOX4X32_10, OUT>(x2), bconvert<SRNG_PHILOX4X32_10, OUT>(x3)};
+        if (k0 >= 0 && (uint64_t)k0 + 4 <= L && ((reinterpret_cast<uintptr_t>(row + k0) & 15) == 0)) {
+            if constexpr (sizeof(T) == 4) {
+                *reinterpret_cast<uint4 *>(row + k0) = *reinterpret_cast<const uint4 *>(v);
+            } else {
+                *reinterpret_cast<double2 *>(row + k0) = make_double2(v[0], v[1]);
+                *reinterpret_cast<double2 *>(row + k0 + 2) = make_double2(v[2], v[3]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t k = k0 + j;
+                if (k >= 0 && (uint64_t)k < L) row[k] = v[j];
+            }
+        }
+    }
+}
+
+template <int OUT>
+__global__ void __launch_bounds__(kWarps * 32) k_batch(const BatchArgs a, const __grid_constant__ JumpTable tab)
+{
+    __shared__ __align__(16) Smem<OUT> sm;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(a.counter, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= a.n_items) break;
+        const uint2 item = a.items[it];
+        if (a.inst[item.x].gen == SRNG_MRG32K3A) mrg_item<OUT>(a, tab, item.x, item.y, sm, warp, lane);
+        else philox_item<OUT>(a, item.x, item.y, lane);
+    }
+}
+
+// Instance start states: MRG32k3a = A^offset applied to the stream's state
+// (J_k = A^(2^k)); Philox = stream position + offset.
+__global__ void __launch_bounds__(256) k_batch_setup(BatchInst *inst, uint64_t n, const __grid_constant__ JumpTable tab)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    BatchInst &in = inst[i];
+    if (in.gen == SRNG_MRG32K3A) {
+        const uint64_t ns = in.src_ns, s = in.stream;
+        uint32_t s0 = in.src_state[s], s1 = in.src_state[ns + s], s2 = in.src_state[2 * ns + s];
+        uint32_t s3 = in.src_state[3 * ns + s], s4 = in.src_state[4 * ns + s], s5 = in.src_state[5 * ns + s];
+        for (int k = 0; k < 64; ++k)
+            if ((in.offset >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
+        in.st[0] = s0; in.st[1] = s1; in.st[2] = s2; in.st[3] = s3; in.st[4] = s4; in.st[5] = s5;
+    } else {
+        in.pos = in.src_pos[in.stream] + in.offset;
+    }
+}
+
+}  // namespace
+
+// Host-side plan.
+struct BatchPlanImpl {
+    int device;
+    srng_batch_mode mode;
+    srng_out type;
+    uint64_t n_inst, n_items;
+    BatchInst *d_inst = nullptr;
+    uint2 *d_items = nullptr;
+    uint32_t *d_counter = nullptr;
+    void *out = nullptr;
+    BatchArgs args;
+    JumpTable chunk_tab;
+    unsigned grid = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace srng_impl
+
+struct srng_batch_plan {
+    srng_impl::BatchPlanImpl p;
+};
+
+using namespace srng_impl;
+
+namespace srng_impl {
+
+static void plan_free(srng_batch_plan *pl)
+{
+    if (!pl) return;
+    BatchPlanImpl &p = pl->p;
+    if (p.exec) cudaGraphExecDestroy(p.exec);
+    if (p.graph) cudaGraphDestroy(p.graph);
+    if (p.d_inst) cudaFree(p.d_inst);
+    if (p.d_items) cudaFree(p.d_items);
+    if (p.d_counter) cudaFree(p.d_counter);
+    delete pl;
+}
+
+static cudaError_t enqueue_batch(const BatchPlanImpl &p, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(p.d_counter, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    if (p.mode == SRNG_BATCH_FUSED_PI && p.n_inst) {
+        e = cudaMemsetAsync(p.out, 0, p.n_inst * sizeof(int64_t), s);
+        if (e != cudaSuccess) return e;
+    }
+    if (p.n_items == 0) return cudaSuccess;
+    switch (p.type) {
+    case SRNG_OUT_U32: k_batch<SRNG_OUT_U32><<<p.grid, kWarps * 32, 0, s>>>(p.args, p.chunk_tab); break;
+    case SRNG_OUT_F32: k_batch<SRNG_OUT_F32><<<p.grid, kWarps * 32, 0, s>>>(p.args, p.chunk_tab); break;
+    default: k_batch<SRNG_OUT_F64><<<p.grid, kWarps * 32, 0, s>>>(p.args, p.chunk_tab); break;
+    }
+    return cudaGetLastError();
+}
+
+static int occupancy_blocks(srng_out type)
+{
+    int nb = 0;
+    switch (type) {
+    case SRNG_OUT_U32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<SRNG_OUT_U32>, kWarps * 32, 0); break;
+    case SRNG_OUT_F32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<SRNG_OUT_F32>, kWarps * 32, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<SRNG_OUT_F64>, kWarps * 32, 0); break;
+    }
+    return nb > 0 ? nb : 1;
+}
+
+// Validate, build instance descriptors and the item list on the host.
+srng_status batch_build(srng_set *const *sets, uint32_t n_sets, const srng_instance *inst, uint64_t n_inst,
+                        srng_batch_mode mode, srng_out type, void *out_dev, const srng_tune &t,
+                        std::vector<BatchInst> &hin, std::vector<uint2> &items, uint64_t &chunk)
+{
+    if (mode != SRNG_BATCH_WRITE && mode != SRNG_BATCH_FUSED_PI) return fail(SRNG_ERR_ARG, "unknown batch mode");
+    if (type != SRNG_OUT_U32 && type != SRNG_OUT_F32 && type != SRNG_OUT_F64)
+        return fail(SRNG_ERR_ARG, "unknown output type");
+    if (n_inst && (!inst || !sets || n_sets == 0)) return fail(SRNG_ERR_ARG, "NULL instances or sets");
+    if (n_inst >= (1ull << 32)) return fail(SRNG_ERR_ARG, "at most 2^32 - 1 instances");
+    if (n_inst && !out_dev) return fail(SRNG_ERR_ARG, "output pointer is NULL");
+    const size_t esz = type == SRNG_OUT_F64 ? 8 : 4;
+    if (mode == SRNG_BATCH_WRITE && reinterpret_cast<uintptr_t>(out_dev) % esz)
+        return fail(SRNG_ERR_ARG, "output pointer not aligned to the element size");
+    if (mode == SRNG_BATCH_FUSED_PI && reinterpret_cast<uintptr_t>(out_dev) % 8)
+        return fail(SRNG_ERR_ARG, "counts pointer not 8-byte aligned");
+    chunk = t.chunk ? t.chunk : 512;
+    const uint64_t lane_blocks = t.lane_blocks ? t.lane_blocks : 64;
+    hin.resize(n_inst);
+    for (uint64_t i = 0; i < n_inst; ++i) {
+        const srng_instance &x = inst[i];
+        if (x.set_index >= n_sets || !sets[x.set_index])
+            return fail(SRNG_ERR_ARG, "instance " + std::to_string(i) + ": bad set index");
+        const srng_set *s = sets[x.set_index];
+        if (x.stream >= s->n_streams) return fail(SRNG_ERR_RANGE, "instance " + std::to_string(i) + ": stream outside its set");
+        if (x.length > (1ull << 48)) return fail(SRNG_ERR_ARG, "instance " + std::to_string(i) + ": length above 2^48");
+        if (s->gen == SRNG_PHILOX4X32_10 && (x.offset > UINT64_MAX - s->max_pos ||
+                                             x.length > UINT64_MAX - s->max_pos - x.offset))
+            return fail(SRNG_ERR_RANGE, "instance " + std::to_string(i) + ": Philox position would pass 2^64 - 1");
+        BatchInst b;
+        memset(&b, 0, sizeof b);
+        b.gen = s->gen;
+        b.key0 = s->key0;
+        b.key1 = s->key1;
+        b.stream = x.stream;
+        b.offset = x.offset;
+        b.length = x.length;
+        b.out_offset = x.out_offset;
+        b.src_state = s->d_state;
+        b.src_ns = s->n_streams;
+        b.src_pos = s->d_pos;
+        hin[i] = b;
+        if (x.length == 0) continue;
+        if (s->gen == SRNG_MRG32K3A) {
+            const uint64_t nch = (x.length + chunk - 1) / chunk;
+            if (nch > (1ull << 32)) return fail(SRNG_ERR_ARG, "instance too long for the chunk size");
+            for (uint64_t c = 0; c < nch; c += 32) items.push_back(make_uint2((uint32_t)i, (uint32_t)c));
+        } else {
+            const uint64_t nb = (x.length + 3) / 4 + 1;
+            const uint64_t per = 32 * lane_blocks;
+            const uint64_t nseg = (nb + per - 1) / per;
+            if (nseg > (1ull << 32)) return fail(SRNG_ERR_ARG, "instance too long");
+            for (uint64_t g = 0; g < nseg; ++g) items.push_back(make_uint2((uint32_t)i, (uint32_t)g));
+        }
+    }
+    if (items.size() >= (1ull << 32)) return fail(SRNG_ERR_ARG, "too many work items");
+    return SRNG_OK;
+}
+
+}  // namespace srng_impl
+
+extern "C" {
+
+srng_status srng_batch_plan_create(srng_batch_plan **out, srng_set *const *sets, uint32_t n_sets,
+                                   const srng_instance *inst, uint64_t n_inst, srng_batch_mode mode, srng_out type,
+                                   void *out_dev, const srng_tune *tune, void *cuda_stream)
+{
+    clear_error();
+    if (!out) return fail(SRNG_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    srng_status st = check_tune(tune);
+    if (st) return st;
+    DeviceInfo dev;
+    if ((st = current_device(&dev))) return st;
+    const srng_tune t = effective_tune(SRNG_MRG32K3A, type == SRNG_OUT_F64 ? SRNG_OUT_F64 : type, tune);
+    std::vector<BatchInst> hin;
+    std::vector<uint2> items;
+    uint64_t chunk = 0;
+    if ((st = batch_build(sets, n_sets, inst, n_inst, mode, type, out_dev, t, hin, items, chunk))) return st;
+
+    srng_batch_plan *pl = new (std::nothrow) srng_batch_plan();
+    if (!pl) return fail(SRNG_ERR_OOM, "host allocation failed");
+    BatchPlanImpl &p = pl->p;
+    p.device = dev.device;
+    p.mode = mode;
+    p.type = type;
+    p.n_inst = n_inst;
+    p.n_items = items.size();
+    p.out = out_dev;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaStream_t cap = nullptr;
+    cudaError_t e;
+#define PLAN_TRY(expr)                                                   \
+    do {                                                                 \
+        e = (expr);                                                      \
+        if (e != cudaSuccess) { st = cuda_fail(e, #expr); goto bad; }    \
+    } while (0)
+    PLAN_TRY(cudaMalloc(&p.d_counter, sizeof(uint32_t)));
+    if (n_inst) {
+        PLAN_TRY(cudaMalloc(&p.d_inst, n_inst * sizeof(BatchInst)));
+        PLAN_TRY(cudaMemcpyAsync(p.d_inst, hin.data(), n_inst * sizeof(BatchInst), cudaMemcpyHostToDevice, stream));
+        {
+            JumpTable unit_tab;  // J_k = A^(2^k)
+            for (int k = 0; k < 64; ++k) memcpy(unit_tab.m[k], mat_pow2(k).a, sizeof unit_tab.m[k]);
+            const unsigned g = (unsigned)((n_inst + 255) / 256);
+            k_batch_setup<<<g, 256, 0, stream>>>(p.d_inst, n_inst, unit_tab);
+            PLAN_TRY(cudaGetLastError());
+        }
+    }
+    if (p.n_items) {
+        PLAN_TRY(cudaMalloc(&p.d_items, p.n_items * sizeof(uint2)));
+        PLAN_TRY(cudaMemcpyAsync(p.d_items, items.data(), p.n_items * sizeof(uint2), cudaMemcpyHostToDevice, stream));
+    }
+    {
+        MatPair m = mat_pow_shifted(0, chunk, 0);  // J_k = A^(chunk 2^k)
+        for (int k = 0; k < 64; ++k) {
+            memcpy(p.chunk_tab.m[k], m.a, sizeof m.a);
+            m = mat_mul(m, m);
+        }
+    }
+    p.args.inst = p.d_inst;
+    p.args.items = p.d_items;
+    p.args.counter = p.d_counter;
+    p.args.n_items = p.n_items;
+    p.args.chunk = chunk;
+    p.args.lane_blocks = t.lane_blocks ? t.lane_blocks : 64;
+    p.args.mode = mode;
+    p.args.out = out_dev;
+    {
+        int per_sm = occupancy_blocks(type);
+        if (tune && tune->blocks_per_sm) per_sm = std::min<int>(per_sm, (int)tune->blocks_per_sm);
+        const uint64_t want = (p.n_items + kWarps - 1) / kWarps;
+        uint64_t g = (uint64_t)dev.sm_count * per_sm;
+        if (g > want) g = want;
+        p.grid = (unsigned)std::max<uint64_t>(1, g);
+    }
+    PLAN_TRY(cudaStreamSynchronize(stream));
+    // Capture {reset counter, zero counts, persistent kernel} once.
+    PLAN_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    PLAN_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    e = enqueue_batch(p, cap);
+    {
+        cudaError_t e2 = cudaStreamEndCapture(cap, &p.graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e != cudaSuccess) { st = cuda_fail(e, "graph capture of the batch launch"); goto bad; }
+    PLAN_TRY(cudaGraphInstantiate(&p.exec, p.graph, 0));
+    cudaStreamDestroy(cap);
+    *out = pl;
+    return SRNG_OK;
+bad:
+    if (cap) cudaStreamDestroy(cap);
+    plan_free(pl);
+    return st;
+#undef PLAN_TRY
+}
+
+srng_status srng_batch_plan_launch(srng_batch_plan *plan, void *cuda_stream)
+{
+    clear_error();
+    if (!plan) return fail(SRNG_ERR_ARG, "plan is NULL");
+    SRNG_CUDA_TRY(cudaGraphLaunch(plan->p.exec, static_cast<cudaStream_t>(cuda_stream)));
+    return SRNG_OK;
+}
+
+srng_status srng_batch_plan_info(const srng_batch_plan *plan, uint64_t *n_work_items, uint32_t *kernels_per_launch)
+{
+    clear_error();
+    if (!plan) return fail(SRNG_ERR_ARG, "plan is NULL");
+    if (n_work_items) *n_work_items = plan->p.n_items;
+    if (kernels_per_launch) *kernels_per_launch = plan->p.n_items ? 1u : 0u;
+    return SRNG_OK;
+}
+
+srng_status srng_batch_plan_destroy(srng_batch_plan *plan)
+{
+    clear_error();
+    if (!plan) return SRNG_OK;
+    cudaDeviceSynchronize();
+    plan_free(plan);
+    return SRNG_OK;
+}
+
+srng_status srng_batch_run(srng_set *const *sets, uint32_t n_sets, const srng_instance *inst, uint64_t n_inst,
+                           srng_batch_mode mode, srng_out type, void *out_dev, void *cuda_stream)
+{
+    srng_batch_plan *plan = nullptr;
+    srng_status st = srng_batch_plan_create(&plan, sets, n_sets, inst, n_inst, mode, type, out_dev, nullptr, cuda_stream);
+    if (st) return st;
+    st = srng_batch_plan_launch(plan, cuda_stream);
+    if (st == SRNG_OK) {
+        cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize(batch)");
+    }
+    srng_batch_plan_destroy(plan);
+    return st;
+}
+
+}  // extern "C"

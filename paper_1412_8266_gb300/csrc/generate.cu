@@ -1,0 +1,305 @@
+// K2 / K3 -- bulk generation with register-resident generator state, the
+// fixed integer -> uniform conversion, and the output writer.
+//
+// K2 (MRG32k3a, paper Sec. 4.1): one thread owns a (stream, chunk) item.  It
+// reaches the chunk's start state from the stream's state by jump-ahead
+// (Sec. 2.3: chunk t starts at (A^C)^t y), then steps the recurrence in
+// registers.  Because a thread's draws are contiguous in the stream-major
+// output but 32 threads of a warp own 32 different rows, the warp stages a
+// 32-row tile of 128-byte rows in shared memory and writes it back row by row:
+// eight lanes cover one 128-byte row with 16-byte stores (or 32/16 lanes with
+// element stores when the output alignment does not allow vectors), so every
+// warp store instruction fills whole 128-byte lines.
+//
+// K3 (Philox4x32-10, Sec. 4.3): counter-based, so any position is computed
+// directly.  A block of threads covers a contiguous run of Philox blocks of
+// one stream; lane-consecutive blocks are 16 bytes apart in the output, so a
+// warp writes 512 contiguous bytes per store (u32 / f32).
+//
+// Algorithmic HBM bytes per output value: the value's size (4 or 8); states
+// and positions add 24 and 8 bytes per stream per call.
+#include <stdint.h>
+
+#include "internal.h"
+#include "srng_device.cuh"
+
+namespace srng_impl {
+
+namespace {
+
+template <int OUT> struct OutType;
+template <> struct OutType<SRNG_OUT_U32> { using T = uint32_t; };
+template <> struct OutType<SRNG_OUT_F32> { using T = float; };
+template <> struct OutType<SRNG_OUT_F64> { using T = double; };
+
+template <int GEN, int OUT>
+__device__ __forceinline__ typename OutType<OUT>::T convert(uint32_t v)
+{
+    if constexpr (OUT == SRNG_OUT_U32) return v;
+    else if constexpr (OUT == SRNG_OUT_F32) return srng::to_f32(v);
+    else if constexpr (GEN == SRNG_MRG32K3A) return srng::mrg::to_f64(v);
+    else return srng::philox::to_f64(v);
+}
+
+// ------------------------------------------------------------------ K2
+template <int OUT, bool VEC, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_mrg_generate(const MrgGenArgs a, const __grid_constant__ JumpTable tab)
+{
+    using T = typename OutType<OUT>::T;
+    constexpr int G = 128 / sizeof(T);    // elements per 128-byte row (32 or 16)
+    constexpr int VPL = 16 / sizeof(T);   // elements per 16-byte vector (4 or 2)
+    constexpr int RS = G + VPL;           // row stride: 144 bytes, keeps 16-byte stores conflict-free
+    __shared__ __align__(16) T tile[WARPS][32 * RS];
+    __shared__ uint64_t row_off[WARPS][32];
+    __shared__ uint32_t row_len[WARPS][32];
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T *my = &tile[warp][lane * RS];
+    T *out = static_cast<T *>(a.out);
+    const uint64_t n_items = a.s_count * a.cps;
+    const uint64_t wstride = (uint64_t)gridDim.x * WARPS * 32;
+
+    for (uint64_t base = ((uint64_t)blockIdx.x * WARPS + warp) * 32; base < n_items; base += wstride) {
+        const uint64_t item = base + lane;
+        uint64_t len = 0;
+        uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
+        if (item < n_items) {
+            const uint64_t s_rel = item / a.cps;
+            const uint64_t t = item - s_rel * a.cps;
+            const uint64_t start = t * a.chunk;
+            len = min(a.chunk, a.n - start);
+            const uint64_t s = a.s_begin + s_rel;
+            const uint64_t ns = a.n_streams;
+            s0 = a.state[s]; s1 = a.state[ns + s]; s2 = a.state[2 * ns + s];
+            s3 = a.state[3 * ns + s]; s4 = a.state[4 * ns + s]; s5 = a.state[5 * ns + s];
+            for (int k = 0; k < a.nbits; ++k)
+                if ((t >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
+            row_off[warp][lane] = s_rel * a.n + start;
+        }
+        const uint32_t ntiles = (uint32_t)((len + G - 1) / G);
+        const uint32_t max_tiles = __reduce_max_sync(0xffffffffu, ntiles);
+
+        for (uint32_t g = 0; g < max_tiles; ++g) {
+            const uint64_t done = (uint64_t)g * G;
+            const uint32_t rl = len > done ? (uint32_t)min((uint64_t)G, len - done) : 0u;
+            row_len[warp][lane] = rl;
+            for (uint32_t j = 0; j < rl; j += VPL) {
+                if constexpr (sizeof(T) == 4) {
+                    uint4 v;
+                    T x0 = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+                    T x1 = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+                    T x2 = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+                    T x3 = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+                    v.x = *reinterpret_cast<uint32_t *>(&x0);
+                    v.y = *reinterpret_cast<uint32_t *>(&x1);
+                    v.z = *reinterpret_cast<uint32_t *>(&x2);
+                    v.w = *reinterpret_cast<uint32_t *>(&x3);
+                    *reinterpret_cast<uint4 *>(&my[j]) = v;
+                } else {
+                    double2 v;
+                    v.x = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+                    v.y = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+                    *reinterpret_cast<double2 *>(&my[j]) = v;
+                }
+            }
+            __syncwarp();
+            constexpr int LPR = VEC ? G / VPL : G;  // lanes per row
+            constexpr int RPI = 32 / LPR;           // rows per warp instruction
+            const int q = lane % LPR, rsub = lane / LPR;
+#pragma unroll 4
+            for (int r0 = 0; r0 < 32; r0 += RPI) {
+                const int r = r0 + rsub;
+                const uint32_t rlen = row_len[warp][r];
+                if constexpr (VEC) {
+                    const uint32_t e = q * VPL;
+                    if (e < rlen)
+                        *reinterpret_cast<uint4 *>(out + row_off[warp][r] + done + e) =
+                            *reinterpret_cast<const uint4 *>(&tile[warp][r * RS + e]);
+                } else {
+                    const uint32_t e = q;
+                    if (e < rlen) out[row_off[warp][r] + done + e] = tile[warp][r * RS + e];
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// ------------------------------------------------------------------ K3
+template <int GEN, int OUT, bool VEC>
+__device__ __forceinline__ void store4(typename OutType<OUT>::T *row, int64_t k0, uint64_t n, uint32_t w0,
+                                       uint32_t w1, uint32_t w2, uint32_t w3)
+{
+    using T = typename OutType<OUT>::T;
+    const T v0 = convert<GEN, OUT>(w0), v1 = convert<GEN, OUT>(w1);
+    const T v2 = convert<GEN, OUT>(w2), v3 = convert<GEN, OUT>(w3);
+    if (VEC && k0 >= 0 && (uint64_t)k0 + 4 <= n && ((reinterpret_cast<uintptr_t>(row + k0) & 15) == 0)) {
+        if constexpr (sizeof(T) == 4) {
+            uint4 v;
+            v.x = *reinterpret_cast<const uint32_t *>(&v0);
+            v.y = *reinterpret_cast<const uint32_t *>(&v1);
+            v.z = *reinterpret_cast<const uint32_t *>(&v2);
+            v.w = *reinterpret_cast<const uint32_t *>(&v3);
+            *reinterpret_cast<uint4 *>(row + k0) = v;
+        } else {
+            *reinterpret_cast<double2 *>(row + k0) = make_double2(v0, v1);
+            *reinterpret_cast<double2 *>(row + k0 + 2) = make_double2(v2, v3);
+        }
+    } else {
+        const T v[4] = {v0, v1, v2, v3};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t k = k0 + j;
+            if (k >= 0 && (uint64_t)k < n) row[k] = v[j];
+        }
+    }
+}
+
+// Tiles of blockDim.x * U Philox blocks; tps tiles per stream; the grid takes
+// tiles by a stride of gridDim.x, tracked as (stream, tile) with the host's
+// quotient / remainder of gridDim.x by tps.
+template <int OUT, int U, bool VEC>
+__global__ void __launch_bounds__(256)
+    k_philox_generate(const PhiloxGenArgs a, uint64_t tps, uint64_t q_grid, uint64_t r_grid)
+{
+    using T = typename OutType<OUT>::T;
+    const uint64_t tb = (uint64_t)blockDim.x * U;
+    const uint64_t n_tiles = a.s_count * tps;
+    uint64_t s_rel = blockIdx.x / tps;
+    uint64_t tt = blockIdx.x - s_rel * tps;
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const uint64_t s = a.s_begin + s_rel;
+        const uint64_t p0 = a.pos[s];
+        const uint32_t al = (uint32_t)p0 & 3u;
+        const uint64_t q0 = p0 >> 2;
+        const uint64_t nb = (al + a.n + 3) >> 2;
+        T *row = static_cast<T *>(a.out) + s_rel * a.n;
+        const uint32_t c2 = (uint32_t)s, c3 = (uint32_t)(s >> 32);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t b = tt * tb + (uint64_t)u * blockDim.x + threadIdx.x;
+            if (b < nb) {
+                const uint64_t q = q0 + b;
+                uint32_t x0 = (uint32_t)q, x1 = (uint32_t)(q >> 32), x2 = c2, x3 = c3;
+                srng::philox::block(x0, x1, x2, x3, a.k0, a.k1);
+                store4<SRNG_PHILOX4X32_10, OUT, VEC>(row, (int64_t)(b * 4) - al, a.n, x0, x1, x2, x3);
+            }
+        }
+        tt += r_grid;
+        s_rel += q_grid;
+        if (tt >= tps) { tt -= tps; ++s_rel; }
+    }
+}
+
+// ---------------------------------------------------------- conversion
+template <int GEN, int OUT>
+__global__ void __launch_bounds__(256) k_convert(const uint32_t *__restrict__ in, uint64_t n,
+                                                 typename OutType<OUT>::T *__restrict__ out)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = convert<GEN, OUT>(in[i]);
+}
+
+template <int OUT, bool VEC>
+cudaError_t mrg_dispatch_warps(const MrgGenArgs &a, const JumpTable &tab, const srng_tune &t,
+                               cudaStream_t stream, const DeviceInfo &dev)
+{
+    const uint64_t items = a.s_count * a.cps;
+    const int warps = t.block_threads >= 256 ? 8 : 4;
+    uint64_t blocks = (items + warps * 32 - 1) / (warps * 32);
+    uint64_t cap = (uint64_t)dev.sm_count * (t.blocks_per_sm ? t.blocks_per_sm : 5);
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) blocks = 1;
+    if (warps == 8) k_mrg_generate<OUT, VEC, 8><<<(unsigned)blocks, 256, 0, stream>>>(a, tab);
+    else k_mrg_generate<OUT, VEC, 4><<<(unsigned)blocks, 128, 0, stream>>>(a, tab);
+    return cudaGetLastError();
+}
+
+template <int OUT>
+cudaError_t mrg_dispatch(const MrgGenArgs &a, const JumpTable &tab, const srng_tune &t, cudaStream_t stream,
+                         const DeviceInfo &dev)
+{
+    using T = typename OutType<OUT>::T;
+    constexpr uint64_t VPL = 16 / sizeof(T);
+    const bool vec_ok = t.vector_store != 2 && (reinterpret_cast<uintptr_t>(a.out) & 15) == 0 &&
+                        a.n % VPL == 0 && a.chunk % VPL == 0;
+    return vec_ok ? mrg_dispatch_warps<OUT, true>(a, tab, t, stream, dev)
+                  : mrg_dispatch_warps<OUT, false>(a, tab, t, stream, dev);
+}
+
+template <int OUT, int U>
+cudaError_t philox_dispatch_u(const PhiloxGenArgs &a, const srng_tune &t, cudaStream_t stream,
+                              const DeviceInfo &dev)
+{
+    const uint32_t threads = t.block_threads ? t.block_threads : 256;
+    const uint64_t bps = (a.n + 3) / 4 + 1;  // blocks per stream, any start alignment
+    const uint64_t tb = (uint64_t)threads * U;
+    const uint64_t tps = (bps + tb - 1) / tb;
+    const uint64_t n_tiles = a.s_count * tps;
+    uint64_t blocks = n_tiles;
+    const uint64_t cap = (uint64_t)dev.sm_count * (t.blocks_per_sm ? t.blocks_per_sm : 2048 / threads);
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) blocks = 1;
+    const uint64_t qg = blocks / tps, rg = blocks % tps;
+    if (t.vector_store != 2)
+        k_philox_generate<OUT, U, true><<<(unsigned)blocks, threads, 0, stream>>>(a, tps, qg, rg);
+    else
+        k_philox_generate<OUT, U, false><<<(unsigned)blocks, threads, 0, stream>>>(a, tps, qg, rg);
+    return cudaGetLastError();
+}
+
+template <int OUT>
+cudaError_t philox_dispatch(const PhiloxGenArgs &a, const srng_tune &t, cudaStream_t stream, const DeviceInfo &dev)
+{
+    switch (t.unroll) {
+    case 1: return philox_dispatch_u<OUT, 1>(a, t, stream, dev);
+    case 4: return philox_dispatch_u<OUT, 4>(a, t, stream, dev);
+    default: return philox_dispatch_u<OUT, 2>(a, t, stream, dev);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_mrg_generate(const MrgGenArgs &a, srng_out type, const JumpTable &tab, const srng_tune &t,
+                                cudaStream_t stream, const DeviceInfo &dev)
+{
+    switch (type) {
+    case SRNG_OUT_U32: return mrg_dispatch<SRNG_OUT_U32>(a, tab, t, stream, dev);
+    case SRNG_OUT_F32: return mrg_dispatch<SRNG_OUT_F32>(a, tab, t, stream, dev);
+    default: return mrg_dispatch<SRNG_OUT_F64>(a, tab, t, stream, dev);
+    }
+}
+
+cudaError_t launch_philox_generate(const PhiloxGenArgs &a, srng_out type, const srng_tune &t,
+                                   cudaStream_t stream, const DeviceInfo &dev)
+{
+    switch (type) {
+    case SRNG_OUT_U32: return philox_dispatch<SRNG_OUT_U32>(a, t, stream, dev);
+    case SRNG_OUT_F32: return philox_dispatch<SRNG_OUT_F32>(a, t, stream, dev);
+    default: return philox_dispatch<SRNG_OUT_F64>(a, t, stream, dev);
+    }
+}
+
+cudaError_t launch_convert(srng_gen gen, srng_out type, const uint32_t *in, uint64_t n, void *out,
+                           cudaStream_t stream, const DeviceInfo &dev)
+{
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    const uint64_t cap = (uint64_t)dev.sm_count * 8;
+    if (blocks > cap) blocks = cap;
+    const unsigned g = (unsigned)blocks;
+    if (gen == SRNG_MRG32K3A) {
+        if (type == SRNG_OUT_U32) k_convert<SRNG_MRG32K3A, SRNG_OUT_U32><<<g, 256, 0, stream>>>(in, n, (uint32_t *)out);
+        else if (type == SRNG_OUT_F32) k_convert<SRNG_MRG32K3A, SRNG_OUT_F32><<<g, 256, 0, stream>>>(in, n, (float *)out);
+        else k_convert<SRNG_MRG32K3A, SRNG_OUT_F64><<<g, 256, 0, stream>>>(in, n, (double *)out);
+    } else {
+        if (type == SRNG_OUT_U32) k_convert<SRNG_PHILOX4X32_10, SRNG_OUT_U32><<<g, 256, 0, stream>>>(in, n, (uint32_t *)out);
+        else if (type == SRNG_OUT_F32) k_convert<SRNG_PHILOX4X32_10, SRNG_OUT_F32><<<g, 256, 0, stream>>>(in, n, (float *)out);
+        else k_convert<SRNG_PHILOX4X32_10, SRNG_OUT_F64><<<g, 256, 0, stream>>>(in, n, (double *)out);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace srng_impl

@@ -1,0 +1,118 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+
+#include "srng.h"
+
+namespace srng_impl {
+
+// ------------------------------------------------------------------ errors
+// Record a failure message for srng_last_error() and return the status.
+srng_status fail(srng_status st, const std::string &msg);
+// Map a CUDA error to SRNG_ERR_CUDA (or SRNG_ERR_OOM) with context.
+srng_status cuda_fail(cudaError_t e, const char *what);
+void clear_error();
+
+#define SRNG_CUDA_TRY(expr)                                          \
+    do {                                                             \
+        cudaError_t _e = (expr);                                     \
+        if (_e != cudaSuccess) return ::srng_impl::cuda_fail(_e, #expr); \
+    } while (0)
+
+// ------------------------------------------------------------- host maths
+constexpr uint64_t kM1 = 4294967087ull;
+constexpr uint64_t kM2 = 4294944443ull;
+
+// 3x3 matrices mod m (row-major, entries < m) for both components.
+struct MatPair {
+    uint32_t a[18];  // [0..8] component 1 (mod m1), [9..17] component 2 (mod m2)
+};
+
+MatPair mat_identity();
+MatPair mat_mul(const MatPair &x, const MatPair &y);
+// A^d with d = n * 2^shift, n = (hi, lo) 128-bit; shift in [0, 127].
+MatPair mat_pow_shifted(uint64_t n_hi, uint64_t n_lo, int shift);
+// A^(2^k) for k in [0, 255].
+MatPair mat_pow2(int k);
+void seed_expand(uint64_t seed, uint32_t out[6]);
+bool state_valid(const uint32_t s[6]);
+
+// -------------------------------------------------------------- devices
+struct DeviceInfo {
+    int device;
+    int sm_count;
+};
+srng_status current_device(DeviceInfo *out);
+
+// ---------------------------------------------------------------- tuning
+srng_tune effective_tune(srng_gen gen, srng_out type, const srng_tune *user);
+srng_status check_tune(const srng_tune *t);
+
+// --------------------------------------------------------- jump tables
+// Up to 64 matrix pairs J_k = B^(2^k) for a base matrix pair B; applied for
+// each set bit of an index (start of stream/chunk = B^index y).
+struct JumpTable {
+    uint32_t m[64][18];
+};
+
+// ------------------------------------------------------------ kernels
+// K1: stream placement and jumps (jump.cu).
+cudaError_t launch_mrg_place(uint32_t *state, uint64_t n_streams, uint64_t first, uint64_t count,
+                             const uint32_t y0[6], const JumpTable &tab, int nbits,
+                             cudaStream_t stream, const DeviceInfo &dev);
+cudaError_t launch_mrg_apply(uint32_t *state, uint64_t n_streams, uint64_t first, uint64_t count,
+                             const MatPair &m, cudaStream_t stream, const DeviceInfo &dev);
+cudaError_t launch_philox_advance(uint64_t *pos, uint64_t first, uint64_t count, uint64_t n,
+                                  cudaStream_t stream, const DeviceInfo &dev);
+
+// K2 / K3 / conversion (generate.cu).
+struct MrgGenArgs {
+    const uint32_t *state;
+    uint64_t n_streams;   // SoA stride
+    uint64_t s_begin, s_count, n;
+    uint64_t chunk;       // draws per thread item
+    uint64_t cps;         // chunks per stream
+    int nbits;            // table entries used for the chunk jumps
+    void *out;
+};
+cudaError_t launch_mrg_generate(const MrgGenArgs &a, srng_out type, const JumpTable &tab,
+                                const srng_tune &t, cudaStream_t stream, const DeviceInfo &dev);
+
+struct PhiloxGenArgs {
+    uint32_t k0, k1;
+    const uint64_t *pos;
+    uint64_t s_begin, s_count, n;
+    void *out;
+};
+cudaError_t launch_philox_generate(const PhiloxGenArgs &a, srng_out type, const srng_tune &t,
+                                   cudaStream_t stream, const DeviceInfo &dev);
+
+cudaError_t launch_convert(srng_gen gen, srng_out type, const uint32_t *in, uint64_t n, void *out,
+                           cudaStream_t stream, const DeviceInfo &dev);
+
+}  // namespace srng_impl
+
+// The stream set object behind the opaque srng_set handle.
+struct srng_set {
+    srng_gen gen;
+    srng_spacing spacing;
+    uint64_t n_streams;
+    uint64_t seed;
+    uint32_t y0[6];          // MRG32k3a seed state
+    uint32_t key0, key1;     // Philox key
+    int device;
+    uint32_t *d_state;       // MRG32k3a SoA states (6 x n_streams)
+    uint64_t *d_pos;         // Philox positions
+    uint64_t max_pos;        // host-side upper bound on any Philox position
+    // staging for srng_generate_host
+    void *d_stage[2];
+    size_t stage_bytes;
+    cudaStream_t copy_stream;
+    cudaEvent_t ev_gen[2], ev_copy[2];
+    std::mutex mu;
+};

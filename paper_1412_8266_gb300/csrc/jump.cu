@@ -1,0 +1,96 @@
+// K1 -- stream placement and jump-ahead on the device (paper Sec. 2.3 sequence
+// splitting, Sec. 4.1 MRG32k3a streams of 2^127 and substreams of 2^76).
+//
+// Placement: stream i of a set starts at B^i y0, B = A^(2^e).  With
+// J_k = B^(2^k) prepared on the host, one thread per stream multiplies y0 by
+// J_k for every set bit k of i: at most 64 exact 3x3 modular matrix-vector
+// products per component, no sequential dependence between streams.
+//
+// HBM traffic per stream: 24 bytes written (placement), 24 read + 24 written
+// (apply).  Both are small next to generation and are launched with a grid of
+// at most 8 blocks of 256 threads per SM.
+#include "internal.h"
+#include "srng_device.cuh"
+
+namespace srng_impl {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads)
+    k_mrg_place(uint32_t *__restrict__ st, uint64_t ns, uint64_t first, uint64_t count,
+                uint32_t y0, uint32_t y1, uint32_t y2, uint32_t y3, uint32_t y4, uint32_t y5,
+                const __grid_constant__ JumpTable tab, int nbits)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const uint64_t idx = first + i;
+        uint32_t s0 = y0, s1 = y1, s2 = y2, s3 = y3, s4 = y4, s5 = y5;
+        for (int k = 0; k < nbits; ++k)
+            if ((idx >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
+        st[0 * ns + idx] = s0; st[1 * ns + idx] = s1; st[2 * ns + idx] = s2;
+        st[3 * ns + idx] = s3; st[4 * ns + idx] = s4; st[5 * ns + idx] = s5;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_mrg_apply(uint32_t *__restrict__ st, uint64_t ns, uint64_t first, uint64_t count, const MatPair m)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const uint64_t idx = first + i;
+        uint32_t s0 = st[0 * ns + idx], s1 = st[1 * ns + idx], s2 = st[2 * ns + idx];
+        uint32_t s3 = st[3 * ns + idx], s4 = st[4 * ns + idx], s5 = st[5 * ns + idx];
+        srng::mrg::jump(m.a, s0, s1, s2, s3, s4, s5);
+        st[0 * ns + idx] = s0; st[1 * ns + idx] = s1; st[2 * ns + idx] = s2;
+        st[3 * ns + idx] = s3; st[4 * ns + idx] = s4; st[5 * ns + idx] = s5;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    k_philox_advance(uint64_t *__restrict__ pos, uint64_t first, uint64_t count, uint64_t n)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+        pos[first + i] += n;
+}
+
+unsigned grid_for(uint64_t count, const DeviceInfo &dev)
+{
+    uint64_t blocks = (count + kThreads - 1) / kThreads;
+    uint64_t cap = (uint64_t)dev.sm_count * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) blocks = 1;
+    return (unsigned)blocks;
+}
+
+}  // namespace
+
+cudaError_t launch_mrg_place(uint32_t *state, uint64_t n_streams, uint64_t first, uint64_t count,
+                             const uint32_t y0[6], const JumpTable &tab, int nbits,
+                             cudaStream_t stream, const DeviceInfo &dev)
+{
+    if (count == 0) return cudaSuccess;
+    k_mrg_place<<<grid_for(count, dev), kThreads, 0, stream>>>(state, n_streams, first, count, y0[0], y0[1],
+                                                               y0[2], y0[3], y0[4], y0[5], tab, nbits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mrg_apply(uint32_t *state, uint64_t n_streams, uint64_t first, uint64_t count,
+                             const MatPair &m, cudaStream_t stream, const DeviceInfo &dev)
+{
+    if (count == 0) return cudaSuccess;
+    k_mrg_apply<<<grid_for(count, dev), kThreads, 0, stream>>>(state, n_streams, first, count, m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox_advance(uint64_t *pos, uint64_t first, uint64_t count, uint64_t n,
+                                  cudaStream_t stream, const DeviceInfo &dev)
+{
+    if (count == 0 || n == 0) return cudaSuccess;
+    k_philox_advance<<<grid_for(count, dev), kThreads, 0, stream>>>(pos, first, count, n);
+    return cudaGetLastError();
+}
+
+}  // namespace srng_impl

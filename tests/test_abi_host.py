@@ -1,0 +1,117 @@
+"""The C ABI library loads, exports every declared entry point, and its host
+logic (seed expansion, jump matrices, argument validation) agrees with the
+oracle -- no GPU needed: none of these calls reach the device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_1412_8266_gb300 as srng
+from oracle import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1412_8266_gb300 import _build
+    _build.build()
+    return srng.load()
+
+
+def _declared_functions():
+    names = set()
+    for h in ("srng.h",):
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\**\s*(srng_[a-z_0-9]+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 25, names
+    out = subprocess.run(["nm", "-D", "--defined-only", srng.lib_path()], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(lib, n)
+
+
+def test_python_binding_covers_every_entry_point(lib):
+    for n in _declared_functions():
+        assert hasattr(srng, n), n
+
+
+def test_version_and_status_strings(lib):
+    assert srng.srng_abi_version() == 1
+    assert srng.srng_status_string(0) == "SRNG_OK"
+    assert srng.srng_status_string(3) == "SRNG_ERR_STATE"
+
+
+@pytest.mark.parametrize("seed", [0, 1, 0xC0FFEE, 0x5EED5EED5EED5EED, 2**64 - 1])
+def test_seed_expansion_matches_oracle(lib, seed):
+    assert srng.srng_seed_expand(seed) == [int(x) for x in O.seed_expand(seed)]
+
+
+@pytest.mark.parametrize("unit,shift", [(srng.SRNG_JUMP_DRAWS, 0), (srng.SRNG_JUMP_SUBSTREAMS, 76),
+                                        (srng.SRNG_JUMP_STREAMS, 127)])
+def test_jump_matrices_match_oracle(lib, unit, shift):
+    rng = np.random.default_rng(1)
+    for n in [0, 1, 2, 3, 7, 4096, 2**40 + 17, int(rng.integers(0, 2**63)) * 3 + 1]:
+        a1, a2 = srng.srng_jump_matrix(unit, n)
+        d = n << shift
+        assert a1 == O.mrg_matpow(0, d % (O.M1**3 - 1) if d >= 2**128 else d).tolist()
+        assert a2 == O.mrg_matpow(1, d % (O.M2**3 - 1) if d >= 2**128 else d).tolist()
+
+
+def test_argument_errors_need_no_gpu(lib):
+    with pytest.raises(srng.SrngError) as e:
+        srng.srng_create(srng.SRNG_MRG32K3A, 1, 0)
+    assert e.value.name == "SRNG_ERR_ARG"
+    with pytest.raises(srng.SrngError) as e:
+        srng.srng_create(7, 1, 10)
+    assert e.value.name == "SRNG_ERR_ARG"
+    with pytest.raises(srng.SrngError) as e:
+        srng.srng_create_from_state([0, 0, 0, 1, 2, 3], 4)
+    assert e.value.name == "SRNG_ERR_STATE"
+    with pytest.raises(srng.SrngError) as e:
+        srng.srng_create_from_state([O.M1, 1, 1, 1, 1, 1], 4)
+    assert e.value.name == "SRNG_ERR_STATE"
+    with pytest.raises(srng.SrngError) as e:
+        srng.srng_generate(0, 0, 1, 1, srng.SRNG_OUT_U32, 0)
+    assert e.value.name == "SRNG_ERR_ARG"
+    with pytest.raises(srng.SrngError) as e:
+        srng.srng_set_tune(srng.SRNG_PHILOX4X32_10, srng.SRNG_OUT_U32, {"unroll": 3})
+    assert e.value.name == "SRNG_ERR_ARG"
+    with pytest.raises(srng.SrngError) as e:
+        srng.srng_set_tune(srng.SRNG_MRG32K3A, srng.SRNG_OUT_U32, {"chunk": 100})
+    assert e.value.name == "SRNG_ERR_ARG"
+    assert "multiple of 32" in srng.srng_last_error()
+
+
+def test_tune_table_roundtrip(lib):
+    srng.srng_set_tune(srng.SRNG_PHILOX4X32_10, srng.SRNG_OUT_F32, {"unroll": 4, "block_threads": 128})
+    t = srng.srng_get_tune(srng.SRNG_PHILOX4X32_10, srng.SRNG_OUT_F32)
+    assert t.unroll == 4 and t.block_threads == 128
+    srng.srng_set_tune(srng.SRNG_PHILOX4X32_10, srng.SRNG_OUT_F32, None)
+    t = srng.srng_get_tune(srng.SRNG_PHILOX4X32_10, srng.SRNG_OUT_F32)
+    assert t.unroll == 2 and t.block_threads == 256
+
+
+def test_destroy_null_is_ok(lib):
+    srng.srng_destroy(0)
+
+
+def test_library_has_no_oracle_dependency(lib):
+    """The CUDA library must not link or name the oracle."""
+    out = subprocess.run(["nm", "-D", srng.lib_path()], capture_output=True, text=True, check=True).stdout
+    assert "oracle" not in out
+    ldd = subprocess.run(["ldd", srng.lib_path()], capture_output=True, text=True).stdout
+    assert "liboracle" not in ldd

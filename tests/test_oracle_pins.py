@@ -14,7 +14,7 @@ from fractions import Fraction
 
 import numpy as np
 import pytest
-import sympy
+sympy = pytest.importorskip("sympy")
 
 from oracle import oracle as O
 
