@@ -51,6 +51,10 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the other workloads")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
+    p.add_argument("--case", choices=sorted(CASES), default=None,
+                   help="time one kernel alone on a reduced size (for profiling), print one JSON line")
+    p.add_argument("--case-scale", type=int, default=4, help="--case size = full size / this")
+    p.add_argument("--reps", type=int, default=3)
     return p.parse_args()
 
 
@@ -421,8 +425,59 @@ def extras(torch, srng, dev, stream, peak):
     return res
 
 
+def run_case(args):
+    """One workload's kernel alone, args.reps launches, at full size / scale."""
+    import torch
+
+    import paper_1412_8266_gb300 as srng
+    from paper_1412_8266_gb300 import workload as W
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream(dev)
+    c = args.case
+    k = max(1, args.case_scale)
+    res = {"case": c, "scale": k}
+    if c.startswith("mrg"):
+        S = S_STREAMS // k
+        t = srng.SRNG_OUT_U32 if c == "mrg_u32" else srng.SRNG_OUT_F64
+        h = srng.srng_create(srng.SRNG_MRG32K3A, SEED, S, srng.SRNG_SPACING_STREAM, stream)
+        o = torch.empty(S * N_DRAWS, dtype=torch.int32 if t == 0 else torch.float64, device=dev)
+        fn = lambda: srng.srng_generate(h, 0, S, N_DRAWS, t, o, stream)
+        nbytes, nvals = o.numel() * o.element_size(), o.numel()
+    elif c.startswith("philox"):
+        n = (1 << 30) // k
+        t = srng.SRNG_OUT_U32 if c == "philox_u32" else srng.SRNG_OUT_F32
+        h = srng.srng_create(srng.SRNG_PHILOX4X32_10, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
+        o = torch.empty(n, dtype=torch.int32 if t == 0 else torch.float32, device=dev)
+        fn = lambda: srng.srng_generate(h, 0, 1, n, t, o, stream)
+        nbytes, nvals = n * 4, n
+    else:
+        gens, lengths, outoff = W.batched_instances(n_inst=W.BATCHED["n_inst"] // k)
+        ni = len(gens)
+        total = int(outoff[-1] + lengths[-1])
+        h = srng.srng_create(srng.SRNG_MRG32K3A, SEED, ni, srng.SRNG_SPACING_STREAM, stream)
+        h2 = srng.srng_create(srng.SRNG_PHILOX4X32_10, 0xC0FFEE, ni, srng.SRNG_SPACING_STREAM, stream)
+        inst = [srng.Instance(set_index=int(gens[i]), stream=i, offset=0, length=int(lengths[i]),
+                              out_offset=int(outoff[i])) for i in range(ni)]
+        mode = srng.SRNG_BATCH_WRITE if c == "batch_write" else srng.SRNG_BATCH_FUSED_PI
+        o = torch.empty(total if mode == 0 else ni, dtype=torch.int32 if mode == 0 else torch.int64, device=dev)
+        plan = srng.srng_batch_plan_create([h, h2], inst, mode, srng.SRNG_OUT_U32, o, None, stream)
+        fn = lambda: srng.srng_batch_plan_launch(plan, stream)
+        nbytes, nvals = (total * 4 if mode == 0 else ni * 8), total
+    best, med = _time(torch, stream, fn, reps=args.reps, warm=1)
+    res.update({"ms_best": best, "ms_median": med, "bytes": nbytes, "values": nvals,
+                "GB_s": nbytes / best / 1e6, "Guniforms_s": nvals / best / 1e6})
+    print(json.dumps(res), flush=True)
+    return 0
+
+
+CASES = {"mrg_u32", "mrg_f64", "philox_u32", "philox_f32", "batch_write", "batch_pi"}
+
+
 def main():
     args = parse()
+    if args.case:
+        return run_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
