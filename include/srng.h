@@ -291,6 +291,39 @@ srng_status srng_batch_run(srng_set *const *sets, uint32_t n_sets, const srng_in
                            uint64_t n_inst, srng_batch_mode mode, srng_out type, void *out_dev,
                            void *cuda_stream);
 
+/* ------------------------------------------- batched, without allocating */
+
+/* The paper has no counterpart to this entry point.  It gives the result of
+ * srng_batch_run to callers that must not allocate device memory per call:
+ * code whose device memory belongs to another allocator (a framework's
+ * caching allocator that holds the GPU, a plugin host that forbids
+ * cudaMalloc) and latency-critical loops that cannot pay for cudaMalloc /
+ * cudaFree and the device synchronisation cudaFree brings.
+ *
+ * Same arguments, same output, bit for bit, as srng_batch_run.  On success the
+ * call allocates nothing, on the host or on the device: its scratch (instance
+ * descriptors, per-instance work-item counts, the work counter) is one
+ * fixed-size __device__ array of about 0.6 MB inside this library, which
+ * every GPU that loads the library holds until the process exits.  Limits:
+ * at most SRNG_BATCH_STATIC_MAX_INSTANCES instances and
+ * SRNG_BATCH_STATIC_MAX_SETS sets, else SRNG_ERR_ARG with nothing enqueued.
+ *
+ * The first call on a device does that device's set-up (it looks up the
+ * array's device address with cudaGetSymbolAddress and sizes the grid); make
+ * that first call before any stream capture.  The call is asynchronous on
+ * cuda_stream: it copies `inst` to the device (the caller may reuse `inst`
+ * when the call returns), then launches three kernels (descriptors, prefix
+ * sums with the zeroing of the work counter and of the FUSED_PI counts, the
+ * persistent batch kernel).  Every call shares the one array, which keeps the
+ * last call's contents: calls whose work overlaps on the GPU (different
+ * streams without ordering, or several host threads on different streams)
+ * race on it.  Order the calls on one stream, or synchronise between them. */
+#define SRNG_BATCH_STATIC_MAX_INSTANCES 4096
+#define SRNG_BATCH_STATIC_MAX_SETS 8
+srng_status srng_batch_run_static(srng_set *const *sets, uint32_t n_sets, const srng_instance *inst,
+                                  uint64_t n_inst, srng_batch_mode mode, srng_out type, void *out_dev,
+                                  void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -105,6 +105,7 @@ _SIGS = {
     "srng_batch_plan_info": (_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
     "srng_batch_plan_destroy": (_int, [_vp]),
     "srng_batch_run": (_int, [_vp, _u32, _vp, _u64, _int, _int, _vp, _vp]),
+    "srng_batch_run_static": (_int, [_vp, _u32, _vp, _u64, _int, _int, _vp, _vp]),
 }
 
 
@@ -330,3 +331,12 @@ def srng_batch_run(sets, inst, mode: int, out_type: int, out_dev, stream=None) -
     sa, ns = _sets(sets)
     ia, ni = _instances(inst)
     _check(load().srng_batch_run(sa, ns, ia, ni, mode, out_type, _ptr(out_dev), _stream(stream)), "srng_batch_run")
+
+
+def srng_batch_run_static(sets, inst, mode: int, out_type: int, out_dev, stream=None) -> None:
+    """srng_batch_run without any allocation (fixed scratch inside the library;
+    at most 4096 instances and 8 sets; calls that overlap on the GPU race)."""
+    sa, ns = _sets(sets)
+    ia, ni = _instances(inst)
+    _check(load().srng_batch_run_static(sa, ns, ia, ni, mode, out_type, _ptr(out_dev), _stream(stream)),
+           "srng_batch_run_static")

@@ -24,6 +24,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -553,3 +554,295 @@ srng_status srng_batch_run(srng_set *const *sets, uint32_t n_sets, const srng_in
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// srng_batch_run_static: the batched launch without any allocation.
+//
+// The paper has no counterpart to this entry point.  It exists for callers
+// that must not allocate device memory per call: code whose device memory is
+// owned by another allocator (a framework's caching allocator or a plugin
+// host that forbids cudaMalloc), and latency-critical loops that cannot pay
+// for cudaMalloc / cudaFree and the device synchronisation cudaFree implies.
+// Its scratch (instance descriptors, per-instance work-item prefix sums, the
+// work counter) lives in one file-scope __device__ array of fixed size, which
+// every GPU that loads this library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace srng_impl {
+
+namespace {
+
+constexpr uint32_t kStaticMaxInst = SRNG_BATCH_STATIC_MAX_INSTANCES;
+constexpr uint32_t kStaticMaxSets = SRNG_BATCH_STATIC_MAX_SETS;
+constexpr uint64_t kStaticChunk = 512;       // MRG32k3a draws per lane-chunk
+constexpr uint32_t kStaticLaneBlocks = 64;   // Philox blocks per lane per work item
+
+constexpr size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+// Layout: [0,4) work counter, [4,8) total work items, then the prefix sums of
+// work items per instance (kStaticMaxInst + 1 words), the caller's instances
+// as copied, and the device-side instance descriptors.
+constexpr size_t kOffPrefix = 256;
+constexpr size_t kOffRaw = round256(kOffPrefix + 8 * (size_t)(kStaticMaxInst + 1));
+constexpr size_t kOffInst = round256(kOffRaw + sizeof(srng_instance) * (size_t)kStaticMaxInst);
+constexpr size_t kStaticBytes = round256(kOffInst + sizeof(BatchInst) * (size_t)kStaticMaxInst);
+
+static __device__ __align__(256) unsigned char g_batch_scratch[kStaticBytes];
+
+struct StaticSets {
+    uint32_t gen[kStaticMaxSets];
+    uint32_t key0[kStaticMaxSets], key1[kStaticMaxSets];
+    const uint32_t *state[kStaticMaxSets];
+    uint64_t ns[kStaticMaxSets];
+    const uint64_t *pos[kStaticMaxSets];
+};
+
+// One thread per instance: descriptor (start state by jump-ahead, as in
+// k_batch_setup) and its number of work items.
+__global__ void __launch_bounds__(256)
+    k_static_setup(unsigned char *scr, uint32_t n_inst, const StaticSets sets, const __grid_constant__ JumpTable unit)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inst) return;
+    const srng_instance r = reinterpret_cast<const srng_instance *>(scr + kOffRaw)[i];
+    const uint32_t si = r.set_index;
+    BatchInst b;
+    memset(&b, 0, sizeof b);
+    b.gen = sets.gen[si];
+    b.key0 = sets.key0[si];
+    b.key1 = sets.key1[si];
+    b.stream = r.stream;
+    b.offset = r.offset;
+    b.length = r.length;
+    b.out_offset = r.out_offset;
+    uint64_t items = 0;
+    if (b.gen == SRNG_MRG32K3A) {
+        const uint32_t *st = sets.state[si];
+        const uint64_t ns = sets.ns[si], s = r.stream;
+        uint32_t s0 = st[s], s1 = st[ns + s], s2 = st[2 * ns + s], s3 = st[3 * ns + s], s4 = st[4 * ns + s],
+                 s5 = st[5 * ns + s];
+        for (int k = 0; k < 64; ++k)
+            if ((r.offset >> k) & 1) srng::mrg::jump(unit.m[k], s0, s1, s2, s3, s4, s5);
+        b.st[0] = s0; b.st[1] = s1; b.st[2] = s2; b.st[3] = s3; b.st[4] = s4; b.st[5] = s5;
+        const uint64_t nch = (r.length + kStaticChunk - 1) / kStaticChunk;
+        items = (nch + 31) / 32;
+    } else {
+        b.pos = sets.pos[si][r.stream] + r.offset;
+        if (r.length) {
+            const uint64_t nb = (r.length + 3) / 4 + 1, per = 32ull * kStaticLaneBlocks;
+            items = (nb + per - 1) / per;
+        }
+    }
+    reinterpret_cast<BatchInst *>(scr + kOffInst)[i] = b;
+    reinterpret_cast<uint64_t *>(scr + kOffPrefix)[i + 1] = items;
+}
+
+// One block: exclusive prefix sums of the work items, the total, and the
+// zeroing of what must start at zero (work counter; hit counts in FUSED_PI).
+__global__ void __launch_bounds__(1024) k_static_scan(unsigned char *scr, uint32_t n_inst, int64_t *counts)
+{
+    __shared__ uint64_t warp_sums[32];
+    uint64_t *prefix = reinterpret_cast<uint64_t *>(scr + kOffPrefix);
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr uint32_t kPer = (kStaticMaxInst + 1023) / 1024;  // consecutive elements per thread
+    uint64_t v[kPer];
+    uint64_t local = 0;
+#pragma unroll
+    for (uint32_t e = 0; e < kPer; ++e) {
+        const uint32_t i = tid * kPer + e;
+        v[e] = i < n_inst ? prefix[i + 1] : 0;
+        local += v[e];
+    }
+    uint64_t incl = local;  // inclusive scan of the per-thread totals
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t w = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= (uint32_t)o) w += y;
+        }
+        warp_sums[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    uint64_t run = incl - local + (warp ? warp_sums[warp - 1] : 0);  // exclusive start of this thread
+#pragma unroll
+    for (uint32_t e = 0; e < kPer; ++e) {
+        const uint32_t i = tid * kPer + e;
+        if (i < n_inst) prefix[i] = run;
+        run += v[e];
+    }
+    if (tid == 1023) {
+        prefix[n_inst] = run;  // total (run ends at the grand total on the last thread)
+        reinterpret_cast<uint32_t *>(scr)[1] = (uint32_t)run;
+        reinterpret_cast<uint32_t *>(scr)[0] = 0u;
+    }
+    if (counts)
+        for (uint32_t i = tid; i < n_inst; i += 1024) counts[i] = 0;
+}
+
+template <int OUT>
+__global__ void __launch_bounds__(kWarps * 32)
+    k_batch_static(unsigned char *scr, uint32_t n_inst, BatchArgs a, const __grid_constant__ JumpTable tab)
+{
+    __shared__ __align__(16) Smem<OUT> sm;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t *prefix = reinterpret_cast<const uint64_t *>(scr + kOffPrefix);
+    const uint32_t total = reinterpret_cast<const volatile uint32_t *>(scr)[1];
+    a.inst = reinterpret_cast<const BatchInst *>(scr + kOffInst);
+    a.counter = reinterpret_cast<uint32_t *>(scr);
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(a.counter, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= total) break;
+        uint32_t lo = 0, hi = n_inst;  // largest lo < n_inst with prefix[lo] <= it
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (prefix[mid] <= it) lo = mid;
+            else hi = mid;
+        }
+        const uint32_t j = it - (uint32_t)prefix[lo];
+        if (a.inst[lo].gen == SRNG_MRG32K3A) mrg_item<OUT>(a, tab, lo, 32u * j, sm, warp, lane);
+        else philox_item<OUT>(a, lo, j, lane);
+    }
+}
+
+// Per-device set-up: the scratch array's device address, the persistent grid
+// size, and the two jump tables (computed once per process, on the stack of
+// the set-up call, no heap use).
+struct StaticDevice {
+    bool ready;
+    unsigned char *scratch;
+    int sm_count;
+    int blocks_per_sm[3];
+};
+constexpr int kMaxDevices = 64;
+StaticDevice g_static_dev[kMaxDevices];
+JumpTable g_static_unit;   // A^(2^k)
+JumpTable g_static_chunk;  // A^(kStaticChunk 2^k)
+bool g_static_tables = false;
+std::mutex g_static_mu;
+
+MatPair static_base()
+{
+    MatPair p;
+    memset(&p, 0, sizeof p);
+    uint32_t *a = p.a, *b = p.a + 9;
+    a[1] = 1; a[5] = 1; a[6] = (uint32_t)(kM1 - 810728u); a[7] = 1403580u;
+    b[1] = 1; b[5] = 1; b[6] = (uint32_t)(kM2 - 1370589u); b[8] = 527612u;
+    return p;
+}
+
+srng_status static_setup(int dev, StaticDevice **out)
+{
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_tables) {
+        MatPair m = static_base();
+        MatPair c = mat_identity(), sq = m;
+        for (uint64_t e = kStaticChunk; e; e >>= 1) {  // A^kStaticChunk by square-and-multiply
+            if (e & 1) c = mat_mul(c, sq);
+            sq = mat_mul(sq, sq);
+        }
+        for (int k = 0; k < 64; ++k) {
+            memcpy(g_static_unit.m[k], m.a, sizeof m.a);
+            memcpy(g_static_chunk.m[k], c.a, sizeof c.a);
+            m = mat_mul(m, m);
+            c = mat_mul(c, c);
+        }
+        g_static_tables = true;
+    }
+    StaticDevice &d = g_static_dev[dev];
+    if (!d.ready) {
+        void *p = nullptr;
+        SRNG_CUDA_TRY(cudaGetSymbolAddress(&p, g_batch_scratch));
+        SRNG_CUDA_TRY(cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev));
+        SRNG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm[0], k_batch_static<SRNG_OUT_U32>,
+                                                                    kWarps * 32, 0));
+        SRNG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm[1], k_batch_static<SRNG_OUT_F32>,
+                                                                    kWarps * 32, 0));
+        SRNG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm[2], k_batch_static<SRNG_OUT_F64>,
+                                                                    kWarps * 32, 0));
+        d.scratch = static_cast<unsigned char *>(p);
+        d.ready = true;
+    }
+    *out = &d;
+    return SRNG_OK;
+}
+
+}  // namespace
+}  // namespace srng_impl
+
+extern "C" srng_status srng_batch_run_static(srng_set *const *sets, uint32_t n_sets, const srng_instance *inst,
+                                             uint64_t n_inst, srng_batch_mode mode, srng_out type, void *out_dev,
+                                             void *cuda_stream)
+{
+    clear_error();
+    if (mode != SRNG_BATCH_WRITE && mode != SRNG_BATCH_FUSED_PI) return fail(SRNG_ERR_ARG, "unknown batch mode");
+    if (type != SRNG_OUT_U32 && type != SRNG_OUT_F32 && type != SRNG_OUT_F64)
+        return fail(SRNG_ERR_ARG, "unknown output type");
+    if (n_inst > kStaticMaxInst)
+        return fail(SRNG_ERR_ARG, "srng_batch_run_static: more than SRNG_BATCH_STATIC_MAX_INSTANCES (4096) instances");
+    if (n_sets > kStaticMaxSets)
+        return fail(SRNG_ERR_ARG, "srng_batch_run_static: more than SRNG_BATCH_STATIC_MAX_SETS (8) sets");
+    if (n_inst == 0) return SRNG_OK;
+    if (!inst || !sets || n_sets == 0 || !out_dev) return fail(SRNG_ERR_ARG, "NULL instances, sets or output");
+    const size_t esz = type == SRNG_OUT_F64 ? 8 : 4;
+    if (reinterpret_cast<uintptr_t>(out_dev) % (mode == SRNG_BATCH_WRITE ? esz : 8))
+        return fail(SRNG_ERR_ARG, "output pointer misaligned");
+    StaticSets ss;
+    memset(&ss, 0, sizeof ss);
+    for (uint32_t k = 0; k < n_sets; ++k) {
+        const srng_set *s = sets[k];
+        if (!s) return fail(SRNG_ERR_ARG, "NULL set");
+        ss.gen[k] = s->gen;
+        ss.key0[k] = s->key0;
+        ss.key1[k] = s->key1;
+        ss.state[k] = s->d_state;
+        ss.ns[k] = s->n_streams;
+        ss.pos[k] = s->d_pos;
+    }
+    for (uint64_t i = 0; i < n_inst; ++i) {
+        const srng_instance &x = inst[i];
+        if (x.set_index >= n_sets) return fail(SRNG_ERR_ARG, "instance with a bad set index");
+        const srng_set *s = sets[x.set_index];
+        if (x.stream >= s->n_streams) return fail(SRNG_ERR_RANGE, "instance stream outside its set");
+        if (x.length > (1ull << 48)) return fail(SRNG_ERR_ARG, "instance length above 2^48");
+        if (s->gen == SRNG_PHILOX4X32_10 &&
+            (x.offset > UINT64_MAX - s->max_pos || x.length > UINT64_MAX - s->max_pos - x.offset))
+            return fail(SRNG_ERR_RANGE, "instance Philox position would pass 2^64 - 1");
+    }
+    int dev = 0;
+    SRNG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(SRNG_ERR_ARG, "device ordinal out of range");
+    StaticDevice *d = nullptr;
+    srng_status st = static_setup(dev, &d);
+    if (st) return st;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    unsigned char *scr = d->scratch;
+    SRNG_CUDA_TRY(cudaMemcpyAsync(scr + kOffRaw, inst, n_inst * sizeof(srng_instance), cudaMemcpyHostToDevice, stream));
+    const uint32_t n = (uint32_t)n_inst;
+    k_static_setup<<<(n + 255) / 256, 256, 0, stream>>>(scr, n, ss, g_static_unit);
+    SRNG_CUDA_TRY(cudaGetLastError());
+    k_static_scan<<<1, 1024, 0, stream>>>(scr, n, mode == SRNG_BATCH_FUSED_PI ? static_cast<int64_t *>(out_dev)
+                                                                              : nullptr);
+    SRNG_CUDA_TRY(cudaGetLastError());
+    BatchArgs a;
+    memset(&a, 0, sizeof a);
+    a.chunk = kStaticChunk;
+    a.lane_blocks = kStaticLaneBlocks;
+    a.mode = mode;
+    a.out = out_dev;
+    const unsigned grid = (unsigned)(d->sm_count * (d->blocks_per_sm[type] > 0 ? d->blocks_per_sm[type] : 1));
+    switch (type) {
+    case SRNG_OUT_U32: k_batch_static<SRNG_OUT_U32><<<grid, kWarps * 32, 0, stream>>>(scr, n, a, g_static_chunk); break;
+    case SRNG_OUT_F32: k_batch_static<SRNG_OUT_F32><<<grid, kWarps * 32, 0, stream>>>(scr, n, a, g_static_chunk); break;
+    default: k_batch_static<SRNG_OUT_F64><<<grid, kWarps * 32, 0, stream>>>(scr, n, a, g_static_chunk); break;
+    }
+    SRNG_CUDA_TRY(cudaGetLastError());
+    return SRNG_OK;
+}
