@@ -208,17 +208,26 @@ def run_ours(args):
     import torch.distributed as dist
 
     import paper_1412_8266_gb300 as srng
+    from paper_1412_8266_gb300 import autotune
+    from paper_1412_8266_gb300.replicas import max_over_ranks, stream_range
 
     rank, world, local = dist_env()
+    torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     peak, peak_kind = measured_peaks()
 
+    # launch shapes for this workload, chosen by timing (outputs do not depend on them)
+    t_tune = time.perf_counter()
+    tune_u, _ = autotune.tune_generate(srng.SRNG_MRG32K3A, srng.SRNG_OUT_U32, S_STREAMS, N_DRAWS, use_cache=False)
+    tune_f, _ = autotune.tune_generate(srng.SRNG_MRG32K3A, srng.SRNG_OUT_F64, S_STREAMS, N_DRAWS, use_cache=False)
+    t_tune = time.perf_counter() - t_tune
+
+    # replicas: rank r generates streams [r S, (r+1) S) of one set
+    b, _ = stream_range(rank, world, S_STREAMS)
     h = srng.srng_create(srng.SRNG_MRG32K3A, SEED, S_STREAMS * world, srng.SRNG_SPACING_STREAM, stream)
-    b = rank * S_STREAMS
     out_u = torch.empty(S_STREAMS * N_DRAWS, dtype=torch.int32, device=dev)
     out_f = torch.empty(S_STREAMS * N_DRAWS, dtype=torch.float64, device=dev)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
@@ -254,11 +263,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms_total = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = max_over_ranks(t_start.elapsed_time(t_end), dev)
     ms_step = ms_total / args.steps
     numbers = 2 * S_STREAMS * N_DRAWS
     value = world * numbers / (ms_step / 1e3) / 1e9
@@ -288,11 +293,7 @@ def run_ours(args):
         for _ in range(args.e2e_steps):
             e2e_step()
         torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-        if world > 1:
-            tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dev)
         # the host copy must equal the device output of the same step
         same = bool(np.array_equal(host_u[:1 << 20].numpy(), out_u[:1 << 20].cpu().numpy()))
         e2e = {"value": world * numbers / e2e_s / 1e9, "unit": "Guniforms/s", "h2d_bytes_per_step": 0,
@@ -322,6 +323,7 @@ def run_ours(args):
                     "mrg_f64": {"ms": ms_f, "GB_s": bytes_f / (ms_f / 1e3) / 1e9,
                                 "Guniforms_s": S_STREAMS * N_DRAWS / (ms_f / 1e3) / 1e9}},
         "clocks": clk,
+        "tune": {"mrg_u32": tune_u, "mrg_f64": tune_f, "tuning_s": t_tune},
         "e2e": e2e,
         "gpu_launches": 5 * args.steps,
     }
@@ -357,10 +359,20 @@ def _time(torch, stream, fn, reps=5, warm=2):
     return min(ts), statistics.median(ts)
 
 
+def write_only_peak(torch, dev, stream):
+    """Context for the write-bound kernels: HBM write-only bandwidth of a plain
+    device fill (torch's zero_ on 8 GiB, best of 5) next to the measured copy peak."""
+    buf = torch.empty(1 << 31, dtype=torch.float32, device=dev)
+    best, med = _time(torch, stream, lambda: buf.zero_(), reps=5, warm=2)
+    del buf
+    torch.cuda.empty_cache()
+    return {"GB_s": (8 << 30) / best / 1e6, "ms_best": best, "how": "torch zero_ of 8 GiB, best of 5"}
+
+
 def extras(torch, srng, dev, stream, peak):
     import numpy as np
     from paper_1412_8266_gb300 import workload as W
-    res = {}
+    res = {"write_only_fill": write_only_peak(torch, dev, stream)}
     # MRG32k3a plain: 64 streams x 2^16 FP64
     h = srng.srng_create_from_state([12345] * 6, 64, srng.SRNG_SPACING_STREAM, stream)
     o = torch.empty(64 << 16, dtype=torch.float64, device=dev)
@@ -371,9 +383,13 @@ def extras(torch, srng, dev, stream, peak):
     srng.srng_destroy(h)
     del o
     # Philox bulk: 2^30 words u32 and f32
-    h = srng.srng_create(srng.SRNG_PHILOX4X32_10, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
+    from paper_1412_8266_gb300 import autotune
     n = 1 << 30
     ph = {}
+    for t in (srng.SRNG_OUT_U32, srng.SRNG_OUT_F32):
+        ph["tune_u32" if t == 0 else "tune_f32"] = autotune.tune_generate(srng.SRNG_PHILOX4X32_10, t, 1, n,
+                                                                          use_cache=False)[0]
+    h = srng.srng_create(srng.SRNG_PHILOX4X32_10, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
     for name, t, dt in (("u32", srng.SRNG_OUT_U32, torch.int32), ("f32", srng.SRNG_OUT_F32, torch.float32)):
         o = torch.empty(n, dtype=dt, device=dev)
         best, med = _time(torch, stream, lambda: (srng.srng_reset(h, stream),
@@ -392,7 +408,8 @@ def extras(torch, srng, dev, stream, peak):
     inst = [srng.Instance(set_index=int(gens[i]), stream=i, offset=0, length=int(lengths[i]),
                           out_offset=int(outoff[i])) for i in range(ni)]
     out = torch.empty(total, dtype=torch.int32, device=dev)
-    plan = srng.srng_batch_plan_create([hm, hp], inst, srng.SRNG_BATCH_WRITE, srng.SRNG_OUT_U32, out, None, stream)
+    btune, _ = autotune.tune_batch([hm, hp], inst, srng.SRNG_BATCH_WRITE, srng.SRNG_OUT_U32, out, reps=2)
+    plan = srng.srng_batch_plan_create([hm, hp], inst, srng.SRNG_BATCH_WRITE, srng.SRNG_OUT_U32, out, btune, stream)
     bb, bm = _time(torch, stream, lambda: srng.srng_batch_plan_launch(plan, stream), reps=5)
     items, _ = srng.srng_batch_plan_info(plan)
     srng.srng_batch_plan_destroy(plan)
@@ -404,7 +421,8 @@ def extras(torch, srng, dev, stream, peak):
 
     pb, pm = _time(torch, stream, plain, reps=2, warm=1)
     counts = torch.empty(ni, dtype=torch.int64, device=dev)
-    plan = srng.srng_batch_plan_create([hm, hp], inst, srng.SRNG_BATCH_FUSED_PI, srng.SRNG_OUT_U32, counts, None,
+    ptune, _ = autotune.tune_batch([hm, hp], inst, srng.SRNG_BATCH_FUSED_PI, srng.SRNG_OUT_U32, counts, reps=2)
+    plan = srng.srng_batch_plan_create([hm, hp], inst, srng.SRNG_BATCH_FUSED_PI, srng.SRNG_OUT_U32, counts, ptune,
                                        stream)
     fb, fm = _time(torch, stream, lambda: srng.srng_batch_plan_launch(plan, stream), reps=5)
     srng.srng_batch_plan_destroy(plan)
@@ -415,14 +433,43 @@ def extras(torch, srng, dev, stream, peak):
         "batched_ms": bb, "batched_Guniforms_s": total / bb / 1e6, "batched_GB_s": total * 4 / bb / 1e6,
         "batched_frac_of_copy_peak": total * 4 / bb / 1e6 / peak,
         "plain_per_instance_ms": pb, "plain_Guniforms_s": total / pb / 1e6, "plain_launches": 2 * ni,
-        "speedup_batched_vs_plain": pb / bb,
+        "speedup_batched_vs_plain": pb / bb, "tune_write": btune, "tune_fused_pi": ptune,
         "fused_pi_ms": fb, "fused_pi_Guniforms_s": total / fb / 1e6, "pi_estimate": 4.0 * c.sum() / pairs,
     }
     srng.srng_destroy(hm)
     srng.srng_destroy(hp)
     del out, views, counts
     torch.cuda.empty_cache()
+    res["serving"] = serving(srng)
     return res
+
+
+def serving(srng, seconds=1.0):
+    """Serving workload: Poisson arrivals (20k/s) of FP32 requests, n log-uniform
+    in [1e3, 1e8], over 10^6 MRG32k3a substreams, 16 GB output budget, replayed
+    by the library's native client; continuous batching vs one request per
+    step with one step in flight (plain per-request launches)."""
+    from paper_1412_8266_gb300 import workload as W
+    trace = [(r.arrival_s, r.stream, r.n) for r in W.serving_trace(seconds)]
+    h = srng.srng_create_from_state([12345] * 6, W.SERVING["n_streams"], srng.SRNG_SPACING_SUBSTREAM)
+    out = {"requests": len(trace), "draws": sum(r[2] for r in trace), "arrival_s": seconds,
+           "offered_Guniforms_s": sum(r[2] for r in trace) / seconds / 1e9}
+    try:
+        for name, cfg in (("batched", dict(budget_bytes=W.SERVING["budget"])),
+                          ("plain", dict(budget_bytes=W.SERVING["budget"], max_inflight=1, max_step_requests=1))):
+            srv = srng.srng_server_create(h, cfg)
+            try:
+                srng.srng_server_replay(srv, trace[:200], srng.SRNG_OUT_F32, 0.0)  # warm-up
+                st = srng.srng_server_replay(srv, trace, srng.SRNG_OUT_F32, 1.0, 300000)
+            finally:
+                srng.srng_server_destroy(srv)
+            out[name] = {"p50_us": st.p50_us, "p99_us": st.p99_us, "mean_us": st.mean_us, "max_us": st.max_us,
+                         "wall_s": st.wall_s, "Guniforms_s": st.draws_completed / st.wall_s / 1e9 if st.wall_s else None,
+                         "completed": st.completed, "steps": st.steps, "kernels": st.kernels,
+                         "peak_pool_GB": st.peak_pool_bytes / 1e9}
+    finally:
+        srng.srng_destroy(h)
+    return out
 
 
 def run_case(args):

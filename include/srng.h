@@ -291,6 +291,88 @@ srng_status srng_batch_run(srng_set *const *sets, uint32_t n_sets, const srng_in
                            uint64_t n_inst, srng_batch_mode mode, srng_out type, void *out_dev,
                            void *cuda_stream);
 
+/* --------------------------------------------------- serving loop (K6) */
+
+/* A request server over one stream set (paper Sec. 2.1: every processing
+ * element, here every request, autonomously gets its own part of its own
+ * stream).  A native dispatcher thread keeps the set's states on the device,
+ * admits submitted requests in arrival order as soon as their output fits in
+ * the output pool (the memory budget), cuts admitted work into steps of at
+ * most max_step_draws draws gathered across requests (continuous batching:
+ * requests that arrive while steps run join the next step), and runs up to
+ * max_inflight steps at once on separate CUDA streams with the batch kernel.
+ *
+ * Positions: a request for n draws of stream s receives the next n positions
+ * of s, counted from the set's state when the server was created, reserved at
+ * submission in submission order -- so every result depends only on the
+ * sequence of submissions, never on how requests were batched.  The server
+ * does not move the set; do not jump, reset, generate from or destroy the set
+ * while the server exists. */
+typedef struct srng_server srng_server;
+
+typedef struct srng_server_config {
+    uint64_t budget_bytes;      /* output pool allocated at create (0: 16 GiB)                 */
+    uint32_t max_inflight;      /* steps on the device at once, 1..8 (0: 4)                    */
+    uint32_t max_step_requests; /* request parts per step, 1..65536 (0: 4096)                  */
+    uint64_t max_step_draws;    /* draws per step (0: 2^25); larger requests span steps        */
+    uint32_t chunk;             /* MRG32k3a draws per lane chunk, multiple of 32 (0: 512)      */
+    uint32_t lane_blocks;       /* Philox blocks per lane per work item (0: 64)                */
+    uint32_t reserved[4];
+} srng_server_config;
+
+typedef struct srng_server_stats {
+    uint64_t submitted, completed, rejected;
+    uint64_t draws_completed;
+    uint64_t steps;             /* steps launched                                              */
+    uint64_t kernels;           /* kernels launched (set-up + batch per step)                  */
+    double p50_us, p99_us;      /* latency, submission -> completion seen by the dispatcher    */
+    double mean_us, max_us;
+    double wall_s;              /* first submission -> last completion                         */
+    uint64_t peak_pool_bytes;   /* largest pool use                                            */
+} srng_server_stats;
+
+/* Create a server over `set` (MRG32k3a or Philox).  cfg may be NULL
+ * (defaults).  Allocates the pool and per-step buffers once. */
+srng_status srng_server_create(srng_server **out, srng_set *set, const srng_server_config *cfg);
+/* Submit a request for n draws of `stream` as `type`; non-blocking.  Returns
+ * a ticket.  SRNG_ERR_BUDGET if n * sizeof(type) exceeds the whole pool;
+ * SRNG_ERR_RANGE if the stream is outside the set. */
+srng_status srng_server_submit(srng_server *srv, uint64_t stream, uint64_t n, srng_out type, uint64_t *ticket);
+/* Same, at an explicit start position (no reservation): the draws
+ * [pos, pos + n) of `stream`. */
+srng_status srng_server_submit_at(srng_server *srv, uint64_t stream, uint64_t pos, uint64_t n, srng_out type,
+                                  uint64_t *ticket);
+/* done = 1 once the request's output is complete; out_dev (may be NULL) then
+ * points to its n values inside the pool, valid until srng_server_release. */
+srng_status srng_server_poll(srng_server *srv, uint64_t ticket, int *done, const void **out_dev);
+/* Block until done or timeout_ms passes (SRNG_ERR_TIMEOUT; the request stays
+ * queued or running). */
+srng_status srng_server_wait(srng_server *srv, uint64_t ticket, uint32_t timeout_ms, const void **out_dev);
+/* Give the request's output memory back to the pool (after completion);
+ * SRNG_ERR_CLOSED for an unknown ticket, SRNG_ERR_ARG if not yet complete. */
+srng_status srng_server_release(srng_server *srv, uint64_t ticket);
+/* Copy a completed request's n values to dst (host memory if dst_is_host,
+ * else device memory); synchronous.  SRNG_ERR_ARG if not yet complete. */
+srng_status srng_server_read(srng_server *srv, uint64_t ticket, void *dst, int dst_is_host);
+srng_status srng_server_get_stats(srng_server *srv, srng_server_stats *out);
+srng_status srng_server_reset_stats(srng_server *srv);
+/* Stop the dispatcher (finishing the steps on the device), free everything. */
+srng_status srng_server_destroy(srng_server *srv);
+
+/* One request of a trace: arrival time (seconds after the replay starts). */
+typedef struct srng_request {
+    double arrival_s;
+    uint64_t stream;
+    uint64_t n;
+} srng_request;
+
+/* Replay a trace on the server from a native client thread: each request is
+ * submitted at its arrival time (or at once when time_scale = 0) and its
+ * output released as soon as it completes; returns when all have completed
+ * (or SRNG_ERR_TIMEOUT after timeout_ms).  Statistics cover this replay. */
+srng_status srng_server_replay(srng_server *srv, const srng_request *req, uint64_t n_req, srng_out type,
+                               double time_scale, uint32_t timeout_ms, srng_server_stats *out);
+
 /* ------------------------------------------- batched, without allocating */
 
 /* The paper has no counterpart to this entry point.  It gives the result of

@@ -49,33 +49,46 @@ constexpr uint32_t kA23 = 1370589u;
 /* One step.  s0..s2 = (x1[n-3], x1[n-2], x1[n-1]), s3..s5 likewise for x2.
  * Returns z = (x1[n] - x2[n]) mod m1 in [1, m1].
  *
- * Component 1: t = a12 s1 + a13 (m1 - s0) = a12 s1 - a13 s0 (mod m1), and
- *   t < 2^21 2^32 + 2^20 2^32 < 2^54.  Fold 1: u = (t >> 32) c1 + (t mod 2^32)
- *   < 2^30 + 2^32.  Fold 2: v = (u mod 2^32) + (u >> 32) c1, where u >> 32 is
- *   0 or 1 (and when it is 1, u mod 2^32 < 2^30, so v < m1); v < 2^32, and one
- *   conditional subtraction of m1 leaves v in [0, m1).
- * Component 2: t < 2^20 2^32 + 2^21 2^32 < 2^54.  Fold 1: u < 2^22 c2 + 2^32,
- *   so u >> 32 <= 23.  Fold 2: v = (u >> 32) c2 + (u mod 2^32) < 2^32 + 525619.
- *   Fold 3: w = (v mod 2^32) + (v >> 32) c2 < 2^32 (v >> 32 is 0 or 1, and when
- *   1, v mod 2^32 < 525619).  One conditional subtraction of m2 finishes. */
+ * The two products of each component are formed as one 64-bit sum t; the
+ * reduction then uses 2^32 = c (mod 2^32 - c) with 32-bit operations only
+ * (carries instead of wide multiplies keep the integer multiply pipe, the
+ * bottleneck of this recurrence on sm_103a, for the four main products):
+ *
+ * Component 1: t = a12 s1 + a13 (m1 - s0) = a12 s1 - a13 s0 (mod m1),
+ *   t < 2^21 2^32 + 2^20 2^32 < 2^54, so t = h 2^32 + l with h < 2^22.
+ *   p = h c1 < 2^30.  u = p + l (mod 2^32); on a carry u < p < 2^30, and the
+ *   carried 2^32 is c1 mod m1, so v = u + c1 < 2^30 + 209.  Without a carry
+ *   v = u < 2^32.  One conditional subtraction of m1 leaves v in [0, m1).
+ * Component 2: t < 2^20 2^32 + 2^21 2^32 < 2^54, h < 2^22, and h c2 < 2^37
+ *   is formed as one 64-bit product q = qh 2^32 + ql with qh <= 22.
+ *   u = ql + l (mod 2^32) carries into qh (qh <= 23).  w = qh c2 < 525619;
+ *   v = u + w (mod 2^32); on a carry v < w, and v + c2 < 2^20.  One
+ *   conditional subtraction of m2 leaves v in [0, m2). */
 __device__ __forceinline__ uint32_t step(uint32_t &s0, uint32_t &s1, uint32_t &s2, uint32_t &s3,
                                          uint32_t &s4, uint32_t &s5)
 {
-    uint64_t t1 = (uint64_t)kA12 * s1 + (uint64_t)kA13 * (kM1 - s0);
-    uint64_t u1 = (t1 >> 32) * kC1 + (uint32_t)t1;
-    uint32_t v1 = (uint32_t)u1 + (uint32_t)(u1 >> 32) * kC1;
+    const uint64_t t1 = (uint64_t)kA12 * s1 + (uint64_t)kA13 * (kM1 - s0);
+    const uint32_t h1 = (uint32_t)(t1 >> 32), l1 = (uint32_t)t1;
+    const uint32_t p1 = h1 * kC1;
+    const uint32_t u1 = p1 + l1;
+    uint32_t v1 = u1 + (u1 < p1 ? kC1 : 0u);
     v1 = min(v1, v1 - kM1);               /* v1 >= m1 ? v1 - m1 : v1 (unsigned wrap) */
 
-    uint64_t t2 = (uint64_t)kA21 * s5 + (uint64_t)kA23 * (kM2 - s3);
-    uint64_t u2 = (t2 >> 32) * kC2 + (uint32_t)t2;
-    uint64_t v2 = (u2 >> 32) * kC2 + (uint32_t)u2;
-    uint32_t w2 = (uint32_t)v2 + (uint32_t)(v2 >> 32) * kC2;
-    w2 = min(w2, w2 - kM2);
+    const uint64_t t2 = (uint64_t)kA21 * s5 + (uint64_t)kA23 * (kM2 - s3);
+    const uint32_t h2 = (uint32_t)(t2 >> 32), l2 = (uint32_t)t2;
+    const uint64_t q = (uint64_t)h2 * kC2;
+    const uint32_t ql = (uint32_t)q;
+    const uint32_t u2 = ql + l2;
+    const uint32_t qh = (uint32_t)(q >> 32) + (u2 < ql ? 1u : 0u);
+    const uint32_t w = qh * kC2;
+    uint32_t v2 = u2 + w;
+    v2 = v2 + (v2 < w ? kC2 : 0u);
+    v2 = min(v2, v2 - kM2);
 
     s0 = s1; s1 = s2; s2 = v1;
-    s3 = s4; s4 = s5; s5 = w2;
-    uint32_t d = v1 - w2;
-    return v1 > w2 ? d : d + kM1;
+    s3 = s4; s4 = s5; s5 = v2;
+    const uint32_t d = v1 - v2;
+    return v1 > v2 ? d : d + kM1;
 }
 
 /* x mod (2^32 - c) for any 64-bit x, c < 2^15 (three folds and one
@@ -115,27 +128,32 @@ __device__ __forceinline__ void jump(const uint32_t *M18, uint32_t &s0, uint32_t
 
 /* double nearest to z * norm, norm = 0x1.000000d00000bp-32 (the double nearest
  * 1/(m1+1)), built from integers, for z in [1, m1].  norm = M 2^-84 with
- * M = 2^52 + 0xd00000b, so the exact product is P = z 2^52 + z 0xd00000b
- * (< 2^85).  Keep its top 53 bits, round the rest to nearest, ties to even,
- * and place the exponent: value = mant 2^(s-84) with s = bitlength(P) - 53. */
+ * M = 2^52 + w, w = 0xd00000b.  With k = bitlength(z) and zn = z 2^(32-k) in
+ * [2^31, 2^32), the exact product is zn M 2^(k-116) and zn M = zn 2^52 + E,
+ * E = zn w < 2^60, lies in [2^83, 2^84 + 2^60).  Below 2^84 its top 53 bits are
+ * m = zn 2^21 + (E >> 31) with the 31-bit remainder E mod 2^31; at or above
+ * 2^84 (only when zn is within 208 of 2^32) one more bit is shifted out.  The
+ * remainder is rounded to nearest, ties to even, a carry into bit 53 moving
+ * the exponent through the addition, and the exponent field is k + 990 (or
+ * k + 991).  Equal, bit for bit, to the IEEE product for every z (checked
+ * exhaustively on the device against the FP64 multiply). */
 __device__ __forceinline__ double to_f64(uint32_t z)
 {
-    uint64_t w = (uint64_t)z * 0xd00000bu;
-    uint64_t lo = ((uint64_t)z << 52) + w;
-    uint64_t hi = (uint64_t)(z >> 12) + (lo < w ? 1u : 0u);
-    int b = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
-    int s = b - 53;                                    /* 0 .. 32 */
-    uint64_t mant, rem, half;
-    if (s == 0) {
-        mant = lo; rem = 0; half = 1;                  /* exact: nothing to round */
-    } else {
-        mant = (lo >> s) | (hi << (64 - s));
-        rem = lo & ((1ull << s) - 1);
-        half = 1ull << (s - 1);
+    const int lz = __clz(z);
+    const uint32_t zn = z << lz;
+    const uint64_t E = (uint64_t)zn * 0xd00000bu;
+    uint64_t m = ((uint64_t)zn << 21) + (E >> 31);
+    uint32_t rem = (uint32_t)E & 0x7FFFFFFFu;
+    uint32_t half = 0x40000000u;
+    int k = 32 - lz;
+    if (m >> 53) {
+        rem |= (uint32_t)(m & 1) << 31;
+        m >>= 1;
+        half = 0x80000000u;
+        k += 1;
     }
-    mant += (rem > half || (rem == half && (mant & 1))) ? 1 : 0;
-    uint64_t bits = ((uint64_t)(s + 990) << 52) + mant; /* biased exponent s + 991 */
-    return __longlong_as_double((long long)bits);
+    m += (rem > half || (rem == half && (m & 1))) ? 1 : 0;
+    return __longlong_as_double((long long)(((uint64_t)(k + 989) << 52) + m));
 }
 
 /* The same value through the FP64 multiply (IEEE round to nearest even). */
@@ -154,18 +172,20 @@ constexpr uint32_t kM1 = 0xCD9E8D57u;
 constexpr uint32_t kW0 = 0x9E3779B9u;
 constexpr uint32_t kW1 = 0xBB67AE85u;
 
-/* Ten rounds on counter (c0..c3) with key (k0, k1), in place. */
+/* Ten rounds on counter (c0..c3) with key (k0, k1), in place.  The 64-bit
+ * products are taken as separate low and high halves (mul.lo / mul.hi), which
+ * sm_103a issues at a higher rate than one 32x32->64 multiply. */
 __device__ __forceinline__ void block(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3,
                                       uint32_t k0, uint32_t k1)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        uint64_t p0 = (uint64_t)kM0 * c0;
-        uint64_t p1 = (uint64_t)kM1 * c2;
-        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
-        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
-        c1 = (uint32_t)p1;
-        c3 = (uint32_t)p0;
+        const uint32_t lo0 = kM0 * c0, hi0 = __umulhi(kM0, c0);
+        const uint32_t lo1 = kM1 * c2, hi1 = __umulhi(kM1, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c1 = lo1;
+        c3 = lo0;
         c0 = n0;
         c2 = n2;
         k0 += kW0;

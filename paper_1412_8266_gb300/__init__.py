@@ -19,7 +19,8 @@ import sys
 import threading
 
 __all__ = [
-    "SrngError", "Tune", "Instance", "SetDesc", "DevView", "lib_path", "load",
+    "SrngError", "Tune", "Instance", "SetDesc", "DevView", "ServerConfig", "ServerStats", "Request",
+    "lib_path", "load",
     "SRNG_MRG32K3A", "SRNG_PHILOX4X32_10", "SRNG_OUT_U32", "SRNG_OUT_F32", "SRNG_OUT_F64",
     "SRNG_SPACING_STREAM", "SRNG_SPACING_SUBSTREAM", "SRNG_JUMP_DRAWS", "SRNG_JUMP_SUBSTREAMS",
     "SRNG_JUMP_STREAMS", "SRNG_BATCH_WRITE", "SRNG_BATCH_FUSED_PI",
@@ -70,11 +71,24 @@ class DevView(ctypes.Structure):
                 ("philox_pos", ctypes.c_void_p)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
+                ("max_step_requests", ctypes.c_uint32), ("max_step_draws", ctypes.c_uint64),
+                ("chunk", ctypes.c_uint32), ("lane_blocks", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 4)]
+
+
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("draws_completed", ctypes.c_uint64), ("steps", ctypes.c_uint64), ("kernels", ctypes.c_uint64),
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
-                ("max_us", ctypes.c_double), ("busy_s", ctypes.c_double), ("peak_bytes", ctypes.c_uint64)]
+                ("max_us", ctypes.c_double), ("wall_s", ctypes.c_double), ("peak_pool_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("arrival_s", ctypes.c_double), ("stream", ctypes.c_uint64), ("n", ctypes.c_uint64)]
 
 
 _vp, _u64, _u32, _int = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
@@ -106,6 +120,17 @@ _SIGS = {
     "srng_batch_plan_destroy": (_int, [_vp]),
     "srng_batch_run": (_int, [_vp, _u32, _vp, _u64, _int, _int, _vp, _vp]),
     "srng_batch_run_static": (_int, [_vp, _u32, _vp, _u64, _int, _int, _vp, _vp]),
+    "srng_server_create": (_int, [ctypes.POINTER(_vp), _vp, ctypes.POINTER(ServerConfig)]),
+    "srng_server_submit": (_int, [_vp, _u64, _u64, _int, ctypes.POINTER(_u64)]),
+    "srng_server_submit_at": (_int, [_vp, _u64, _u64, _u64, _int, ctypes.POINTER(_u64)]),
+    "srng_server_poll": (_int, [_vp, _u64, ctypes.POINTER(_int), ctypes.POINTER(_vp)]),
+    "srng_server_wait": (_int, [_vp, _u64, _u32, ctypes.POINTER(_vp)]),
+    "srng_server_release": (_int, [_vp, _u64]),
+    "srng_server_read": (_int, [_vp, _u64, _vp, _int]),
+    "srng_server_get_stats": (_int, [_vp, ctypes.POINTER(ServerStats)]),
+    "srng_server_reset_stats": (_int, [_vp]),
+    "srng_server_destroy": (_int, [_vp]),
+    "srng_server_replay": (_int, [_vp, _vp, _u64, _int, ctypes.c_double, _u32, ctypes.POINTER(ServerStats)]),
 }
 
 
@@ -340,3 +365,72 @@ def srng_batch_run_static(sets, inst, mode: int, out_type: int, out_dev, stream=
     ia, ni = _instances(inst)
     _check(load().srng_batch_run_static(sa, ns, ia, ni, mode, out_type, _ptr(out_dev), _stream(stream)),
            "srng_batch_run_static")
+
+
+# ---------------------------------------------------------------- serving
+def srng_server_create(handle: int, cfg=None) -> int:
+    c = None
+    if cfg is not None:
+        c = ctypes.byref(cfg if isinstance(cfg, ServerConfig) else ServerConfig(**cfg))
+    h = _vp()
+    _check(load().srng_server_create(ctypes.byref(h), handle, c), "srng_server_create")
+    return h.value
+
+
+def srng_server_submit(srv: int, stream: int, n: int, out_type: int) -> int:
+    t = _u64()
+    _check(load().srng_server_submit(srv, stream, n, out_type, ctypes.byref(t)), "srng_server_submit")
+    return t.value
+
+
+def srng_server_submit_at(srv: int, stream: int, pos: int, n: int, out_type: int) -> int:
+    t = _u64()
+    _check(load().srng_server_submit_at(srv, stream, pos, n, out_type, ctypes.byref(t)), "srng_server_submit_at")
+    return t.value
+
+
+def srng_server_poll(srv: int, ticket: int):
+    done = _int()
+    p = _vp()
+    _check(load().srng_server_poll(srv, ticket, ctypes.byref(done), ctypes.byref(p)), "srng_server_poll")
+    return bool(done.value), p.value
+
+
+def srng_server_wait(srv: int, ticket: int, timeout_ms: int = 60000) -> int:
+    p = _vp()
+    _check(load().srng_server_wait(srv, ticket, timeout_ms, ctypes.byref(p)), "srng_server_wait")
+    return p.value
+
+
+def srng_server_release(srv: int, ticket: int) -> None:
+    _check(load().srng_server_release(srv, ticket), "srng_server_release")
+
+
+def srng_server_read(srv: int, ticket: int, dst, dst_is_host: bool) -> None:
+    _check(load().srng_server_read(srv, ticket, _ptr(dst), int(bool(dst_is_host))), "srng_server_read")
+
+
+def srng_server_get_stats(srv: int) -> ServerStats:
+    st = ServerStats()
+    _check(load().srng_server_get_stats(srv, ctypes.byref(st)), "srng_server_get_stats")
+    return st
+
+
+def srng_server_reset_stats(srv: int) -> None:
+    _check(load().srng_server_reset_stats(srv), "srng_server_reset_stats")
+
+
+def srng_server_destroy(srv: int) -> None:
+    _check(load().srng_server_destroy(srv), "srng_server_destroy")
+
+
+def srng_server_replay(srv: int, requests, out_type: int, time_scale: float = 1.0, timeout_ms: int = 600000):
+    """requests: sequence of (arrival_s, stream, n) or Request; returns ServerStats."""
+    arr = (Request * len(requests))()
+    for i, r in enumerate(requests):
+        arr[i] = r if isinstance(r, Request) else Request(*r)
+    st = ServerStats()
+    _check(load().srng_server_replay(srv, arr, len(requests), out_type, time_scale, timeout_ms, ctypes.byref(st)),
+           "srng_server_replay")
+    return st
+

@@ -34,32 +34,6 @@
 
 namespace srng_impl {
 
-// Per-instance descriptor on the device.
-struct BatchInst {
-    uint32_t gen;
-    uint32_t key0, key1;
-    uint32_t st[6];           // MRG32k3a start state (written by the set-up kernel)
-    uint64_t stream;          // stream index in its set
-    uint64_t offset;          // draws after the stream's current position
-    uint64_t pos;             // Philox start position (written by the set-up kernel)
-    uint64_t length;
-    uint64_t out_offset;
-    const uint32_t *src_state;  // MRG32k3a set states (SoA) and their stride
-    uint64_t src_ns;
-    const uint64_t *src_pos;    // Philox set positions
-};
-
-struct BatchArgs {
-    const BatchInst *inst;
-    const uint2 *items;       // {instance, first chunk (MRG32k3a) or segment (Philox)}
-    uint32_t *counter;
-    uint64_t n_items;
-    uint64_t chunk;           // MRG32k3a draws per lane-chunk
-    uint32_t lane_blocks;     // Philox blocks per lane per item
-    int32_t mode;             // srng_batch_mode
-    void *out;                // values (WRITE) or int64 counts (FUSED_PI)
-};
-
 namespace {
 
 template <int OUT> struct OutT;
@@ -353,6 +327,41 @@ static int occupancy_blocks(srng_out type)
     default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<SRNG_OUT_F64>, kWarps * 32, 0); break;
     }
     return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_batch_setup(BatchInst *d_inst, uint64_t n, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    static std::once_flag once;
+    static JumpTable unit_tab;  // J_k = A^(2^k)
+    std::call_once(once, [] {
+        for (int k = 0; k < 64; ++k) memcpy(unit_tab.m[k], mat_pow2(k).a, sizeof unit_tab.m[k]);
+    });
+    k_batch_setup<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_inst, n, unit_tab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchArgs &a, srng_out type, const JumpTable &chunk_tab, unsigned grid,
+                         cudaStream_t s)
+{
+    if (a.n_items == 0) return cudaSuccess;
+    switch (type) {
+    case SRNG_OUT_U32: k_batch<SRNG_OUT_U32><<<grid, kWarps * 32, 0, s>>>(a, chunk_tab); break;
+    case SRNG_OUT_F32: k_batch<SRNG_OUT_F32><<<grid, kWarps * 32, 0, s>>>(a, chunk_tab); break;
+    default: k_batch<SRNG_OUT_F64><<<grid, kWarps * 32, 0, s>>>(a, chunk_tab); break;
+    }
+    return cudaGetLastError();
+}
+
+int batch_blocks_per_sm(srng_out type) { return occupancy_blocks(type); }
+
+void chunk_jump_table(uint64_t chunk, JumpTable *out)
+{
+    MatPair m = mat_pow_shifted(0, chunk, 0);
+    for (int k = 0; k < 64; ++k) {
+        memcpy(out->m[k], m.a, sizeof m.a);
+        m = mat_mul(m, m);
+    }
 }
 
 // Validate, build instance descriptors and the item list on the host.

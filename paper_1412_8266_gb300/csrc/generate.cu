@@ -168,23 +168,36 @@ __global__ void __launch_bounds__(256)
     const uint64_t n_tiles = a.s_count * tps;
     uint64_t s_rel = blockIdx.x / tps;
     uint64_t tt = blockIdx.x - s_rel * tps;
+    uint64_t cur = ~0ull;  // stream whose position is loaded
+    uint32_t al = 0, c2 = 0, c3 = 0;
+    uint64_t q0 = 0, nb = 0;
+    T *row = nullptr;
     for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const uint64_t s = a.s_begin + s_rel;
-        const uint64_t p0 = a.pos[s];
-        const uint32_t al = (uint32_t)p0 & 3u;
-        const uint64_t q0 = p0 >> 2;
-        const uint64_t nb = (al + a.n + 3) >> 2;
-        T *row = static_cast<T *>(a.out) + s_rel * a.n;
-        const uint32_t c2 = (uint32_t)s, c3 = (uint32_t)(s >> 32);
+        if (s_rel != cur) {  // a block's tiles stay in one stream for long runs
+            cur = s_rel;
+            const uint64_t s = a.s_begin + s_rel;
+            const uint64_t p0 = a.pos[s];
+            al = (uint32_t)p0 & 3u;
+            q0 = p0 >> 2;
+            nb = (al + a.n + 3) >> 2;
+            row = static_cast<T *>(a.out) + s_rel * a.n;
+            c2 = (uint32_t)s;
+            c3 = (uint32_t)(s >> 32);
+        }
+        uint32_t x[U][4];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {  // U independent blocks in flight per thread
+            const uint64_t b = tt * tb + (uint64_t)u * blockDim.x + threadIdx.x;
+            ok[u] = b < nb;
+            const uint64_t q = q0 + b;
+            x[u][0] = (uint32_t)q; x[u][1] = (uint32_t)(q >> 32); x[u][2] = c2; x[u][3] = c3;
+            srng::philox::block(x[u][0], x[u][1], x[u][2], x[u][3], a.k0, a.k1);
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint64_t b = tt * tb + (uint64_t)u * blockDim.x + threadIdx.x;
-            if (b < nb) {
-                const uint64_t q = q0 + b;
-                uint32_t x0 = (uint32_t)q, x1 = (uint32_t)(q >> 32), x2 = c2, x3 = c3;
-                srng::philox::block(x0, x1, x2, x3, a.k0, a.k1);
-                store4<SRNG_PHILOX4X32_10, OUT, VEC>(row, (int64_t)(b * 4) - al, a.n, x0, x1, x2, x3);
-            }
+            if (ok[u]) store4<SRNG_PHILOX4X32_10, OUT, VEC>(row, (int64_t)(b * 4) - al, a.n, x[u][0], x[u][1], x[u][2], x[u][3]);
         }
         tt += r_grid;
         s_rel += q_grid;

@@ -95,6 +95,46 @@ cudaError_t launch_philox_generate(const PhiloxGenArgs &a, srng_out type, const 
 cudaError_t launch_convert(srng_gen gen, srng_out type, const uint32_t *in, uint64_t n, void *out,
                            cudaStream_t stream, const DeviceInfo &dev);
 
+// ------------------------------------------------- batched work (batch.cu)
+// Per-instance descriptor on the device.
+struct BatchInst {
+    uint32_t gen;
+    uint32_t key0, key1;
+    uint32_t st[6];           // MRG32k3a start state (written by the set-up kernel)
+    uint64_t stream;          // stream index in its set
+    uint64_t offset;          // draws after the stream's current position
+    uint64_t pos;             // Philox start position (written by the set-up kernel)
+    uint64_t length;
+    uint64_t out_offset;
+    const uint32_t *src_state;  // MRG32k3a set states (SoA) and their stride
+    uint64_t src_ns;
+    const uint64_t *src_pos;    // Philox set positions
+};
+
+struct BatchArgs {
+    const BatchInst *inst;
+    const uint2 *items;       // {instance, first chunk (MRG32k3a) or segment (Philox)}
+    uint32_t *counter;
+    uint64_t n_items;
+    uint64_t chunk;           // MRG32k3a draws per lane-chunk
+    uint32_t lane_blocks;     // Philox blocks per lane per item
+    int32_t mode;             // srng_batch_mode
+    void *out;                // values (WRITE) or int64 counts (FUSED_PI)
+};
+
+// Launchers shared by the batch plan and the server.
+// Instance start states: MRG32k3a = A^offset applied to the stream state;
+// Philox = stream position + offset (reads src_* fields, writes st / pos).
+cudaError_t launch_batch_setup(BatchInst *d_inst, uint64_t n, cudaStream_t s);
+// The persistent batch kernel over a.n_items items; a.counter must be zero.
+cudaError_t launch_batch(const BatchArgs &a, srng_out type, const JumpTable &chunk_tab, unsigned grid,
+                         cudaStream_t s);
+// Resident blocks per SM of the batch kernel for `type`.
+int batch_blocks_per_sm(srng_out type);
+// J_k = A^(chunk 2^k), k < 64.
+void chunk_jump_table(uint64_t chunk, JumpTable *out);
+constexpr int kBatchThreads = 256;
+
 }  // namespace srng_impl
 
 // The stream set object behind the opaque srng_set handle.
