@@ -221,8 +221,10 @@ def run_ours(args):
 
     # launch shapes for this workload, chosen by timing (outputs do not depend on them)
     t_tune = time.perf_counter()
-    tune_u, _ = autotune.tune_generate(srng.SRNG_MRG32K3A, srng.SRNG_OUT_U32, S_STREAMS, N_DRAWS, use_cache=False)
-    tune_f, _ = autotune.tune_generate(srng.SRNG_MRG32K3A, srng.SRNG_OUT_F64, S_STREAMS, N_DRAWS, use_cache=False)
+    tune_u, _ = autotune.tune_generate(srng.SRNG_MRG32K3A, srng.SRNG_OUT_U32, S_STREAMS, N_DRAWS, use_cache=False,
+                                       install=False)
+    tune_f, _ = autotune.tune_generate(srng.SRNG_MRG32K3A, srng.SRNG_OUT_F64, S_STREAMS, N_DRAWS, use_cache=False,
+                                       install=False)
     t_tune = time.perf_counter() - t_tune
 
     # replicas: rank r generates streams [r S, (r+1) S) of one set
@@ -236,11 +238,11 @@ def run_ours(args):
         srng.srng_reset(h, stream)
         if k is not None:
             ev[k][0].record(stream)
-        srng.srng_generate(h, b, S_STREAMS, N_DRAWS, srng.SRNG_OUT_U32, out_u, stream)
+        srng.srng_generate_tuned(h, b, S_STREAMS, N_DRAWS, srng.SRNG_OUT_U32, out_u, tune_u, stream)
         if k is not None:
             ev[k][1].record(stream)
             ev[k][2].record(stream)
-        srng.srng_generate(h, b, S_STREAMS, N_DRAWS, srng.SRNG_OUT_F64, out_f, stream)
+        srng.srng_generate_tuned(h, b, S_STREAMS, N_DRAWS, srng.SRNG_OUT_F64, out_f, tune_f, stream)
         if k is not None:
             ev[k][3].record(stream)
 
@@ -281,7 +283,7 @@ def run_ours(args):
         host_f = torch.empty(S_STREAMS * N_DRAWS, dtype=torch.float64, pin_memory=True)
 
         def e2e_step():
-            srng.srng_reset(h, stream)
+            srng.srng_reset(h, stream)  # generation into pinned host memory (see srng_generate_host)
             srng.srng_generate_host(h, b, S_STREAMS, N_DRAWS, srng.SRNG_OUT_U32, host_u, stream)
             srng.srng_generate_host(h, b, S_STREAMS, N_DRAWS, srng.SRNG_OUT_F64, host_f, stream)
 
@@ -386,14 +388,15 @@ def extras(torch, srng, dev, stream, peak):
     from paper_1412_8266_gb300 import autotune
     n = 1 << 30
     ph = {}
+    tunes = {}
     for t in (srng.SRNG_OUT_U32, srng.SRNG_OUT_F32):
-        ph["tune_u32" if t == 0 else "tune_f32"] = autotune.tune_generate(srng.SRNG_PHILOX4X32_10, t, 1, n,
-                                                                          use_cache=False)[0]
+        tunes[t] = autotune.tune_generate(srng.SRNG_PHILOX4X32_10, t, 1, n, use_cache=False, install=False)[0]
+        ph["tune_u32" if t == 0 else "tune_f32"] = tunes[t]
     h = srng.srng_create(srng.SRNG_PHILOX4X32_10, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
     for name, t, dt in (("u32", srng.SRNG_OUT_U32, torch.int32), ("f32", srng.SRNG_OUT_F32, torch.float32)):
         o = torch.empty(n, dtype=dt, device=dev)
         best, med = _time(torch, stream, lambda: (srng.srng_reset(h, stream),
-                                                  srng.srng_generate(h, 0, 1, n, t, o, stream)))
+                                                  srng.srng_generate_tuned(h, 0, 1, n, t, o, tunes[t], stream)))
         ph[name] = {"ms_best": best, "ms_median": med, "Guniforms_s": n / best / 1e6, "GB_s": n * 4 / best / 1e6,
                     "frac_of_copy_peak": n * 4 / best / 1e6 / peak}
         del o
@@ -428,13 +431,14 @@ def extras(torch, srng, dev, stream, peak):
     srng.srng_batch_plan_destroy(plan)
     c = counts.cpu().numpy()
     pairs = int(np.sum(lengths // 2))
+    draws = int(np.sum(lengths))
     res["batched_10k_u32"] = {
-        "draws": total, "work_items": items,
-        "batched_ms": bb, "batched_Guniforms_s": total / bb / 1e6, "batched_GB_s": total * 4 / bb / 1e6,
-        "batched_frac_of_copy_peak": total * 4 / bb / 1e6 / peak,
-        "plain_per_instance_ms": pb, "plain_Guniforms_s": total / pb / 1e6, "plain_launches": 2 * ni,
+        "draws": draws, "work_items": items, "slots": "prefix-sum offsets rounded up to 32 bytes",
+        "batched_ms": bb, "batched_Guniforms_s": draws / bb / 1e6, "batched_GB_s": draws * 4 / bb / 1e6,
+        "batched_frac_of_copy_peak": draws * 4 / bb / 1e6 / peak,
+        "plain_per_instance_ms": pb, "plain_Guniforms_s": draws / pb / 1e6, "plain_launches": 2 * ni,
         "speedup_batched_vs_plain": pb / bb, "tune_write": btune, "tune_fused_pi": ptune,
-        "fused_pi_ms": fb, "fused_pi_Guniforms_s": total / fb / 1e6, "pi_estimate": 4.0 * c.sum() / pairs,
+        "fused_pi_ms": fb, "fused_pi_Guniforms_s": draws / fb / 1e6, "pi_estimate": 4.0 * c.sum() / pairs,
     }
     srng.srng_destroy(hm)
     srng.srng_destroy(hp)
@@ -510,7 +514,8 @@ def run_case(args):
         o = torch.empty(total if mode == 0 else ni, dtype=torch.int32 if mode == 0 else torch.int64, device=dev)
         plan = srng.srng_batch_plan_create([h, h2], inst, mode, srng.SRNG_OUT_U32, o, None, stream)
         fn = lambda: srng.srng_batch_plan_launch(plan, stream)
-        nbytes, nvals = (total * 4 if mode == 0 else ni * 8), total
+        nvals = int(sum(int(x) for x in lengths))
+        nbytes = nvals * 4 if mode == 0 else ni * 8
     best, med = _time(torch, stream, fn, reps=args.reps, warm=1)
     res.update({"ms_best": best, "ms_median": med, "bytes": nbytes, "values": nvals,
                 "GB_s": nbytes / best / 1e6, "Guniforms_s": nvals / best / 1e6})

@@ -189,11 +189,13 @@ srng_status srng_generate_tuned(srng_set *set, uint64_t stream_begin, uint64_t s
                                 uint64_t n_per_stream, srng_out type, void *out_dev,
                                 const srng_tune *tune, void *cuda_stream);
 
-/* Same result as srng_generate, written to a HOST buffer: the library
- * generates into an internal device staging ring (allocated on first use,
- * kept by the set, at most 2 x 256 MiB) and overlaps generation of one piece
- * with the device-to-host copy of the previous one.  Synchronises
- * cuda_stream before returning. */
+/* Same result as srng_generate, written to a HOST buffer.  Pinned host
+ * memory that the device can address (cudaHostAlloc, cudaHostRegister) is
+ * written directly by the generation kernels over the host link.  Other
+ * (pageable) memory goes through an internal device staging ring (allocated
+ * on first use, kept by the set, 2 x 256 MiB) whose pieces are copied to the
+ * host while the next piece is generated.  Synchronises cuda_stream before
+ * returning. */
 srng_status srng_generate_host(srng_set *set, uint64_t stream_begin, uint64_t stream_count,
                                uint64_t n_per_stream, srng_out type, void *out_host,
                                void *cuda_stream);

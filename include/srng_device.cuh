@@ -139,21 +139,38 @@ __device__ __forceinline__ void jump(const uint32_t *M18, uint32_t &s0, uint32_t
  * exhaustively on the device against the FP64 multiply). */
 __device__ __forceinline__ double to_f64(uint32_t z)
 {
-    const int lz = __clz(z);
+    const uint32_t lz = (uint32_t)__clz(z);
     const uint32_t zn = z << lz;
-    const uint64_t E = (uint64_t)zn * 0xd00000bu;
-    uint64_t m = ((uint64_t)zn << 21) + (E >> 31);
-    uint32_t rem = (uint32_t)E & 0x7FFFFFFFu;
-    uint32_t half = 0x40000000u;
-    int k = 32 - lz;
-    if (m >> 53) {
-        rem |= (uint32_t)(m & 1) << 31;
-        m >>= 1;
-        half = 0x80000000u;
-        k += 1;
+    /* E = zn w with w = 0xd00000b: E >> 31 and E mod 2^31 are the high word
+     * and half the (even) low word of zn (2w), 2w < 2^32. */
+    const uint32_t elo = zn * 0x1A000016u;
+    const uint32_t ehi = __umulhi(zn, 0x1A000016u);
+    if (zn >= 0xFFFFFF30u) {
+        /* The only inputs whose product can reach 2^84 (zn within 208 of 2^32;
+         * below that zn 2^21 + ehi < (2^32 - 208) 2^21 + 2w < 2^53): general
+         * path with a variable final shift. */
+        uint64_t m = ((uint64_t)zn << 21) + ehi;
+        uint32_t e = 1021u - lz;
+        if (m >> 53) {
+            const uint32_t rem = (elo >> 1) | ((uint32_t)m << 31);
+            m >>= 1;
+            m += (rem > 0x80000000u || (rem == 0x80000000u && (m & 1u))) ? 1u : 0u;
+            e += 1;
+        } else {
+            m += (elo + ((uint32_t)m & 1u) > 0x80000000u) ? 1u : 0u;
+        }
+        return __longlong_as_double((long long)(((uint64_t)e << 52) + m));
     }
-    m += (rem > half || (rem == half && (m & 1))) ? 1 : 0;
-    return __longlong_as_double((long long)(((uint64_t)(k + 989) << 52) + m));
+    /* m = zn 2^21 + ehi < 2^53 as (hi, lo); the exponent field (1021 - lz,
+     * plus 1 from m's 2^52 bit) is added into hi; rounding to nearest even:
+     * remainder elo / 2 > 2^30, or = 2^30 with m odd, i.e. elo + (m & 1) > 2^31
+     * (elo is even, no overflow); the carries go through the add chain. */
+    const uint32_t hi0 = (zn >> 11) + ((1021u - lz) << 20);
+    uint32_t lo, hi;
+    asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, 0;" : "=r"(lo), "=r"(hi) : "r"(zn << 21), "r"(ehi), "r"(hi0));
+    const uint32_t up = (elo + (lo & 1u)) > 0x80000000u ? 1u : 0u;
+    asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+r"(lo), "+r"(hi) : "r"(up));
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 /* The same value through the FP64 multiply (IEEE round to nearest even). */
@@ -204,10 +221,15 @@ __device__ __forceinline__ double to_f64(uint32_t w)
 }
 }  // namespace philox
 
-/* (v >> 8) 2^-24 as a float, exact. */
+/* (v >> 8) 2^-24 as a float, exact, without an integer-to-float conversion:
+ * with a = v >> 8 = 2k + b, the bit pattern 0x3F800000 | k is 1 + k 2^-23, so
+ * subtracting 1 gives k 2^-23 exactly, and adding b 2^-24 (bit pattern
+ * 0x33800000 when b = 1) is exact because 2k + b < 2^24. */
 __device__ __forceinline__ float to_f32(uint32_t v)
 {
-    return __uint2float_rn(v >> 8) * 0x1p-24f;
+    const float hi = __uint_as_float(0x3F800000u | (v >> 9)) - 1.0f;
+    const float lo = __uint_as_float((v & 0x100u) ? 0x33800000u : 0u);
+    return hi + lo;
 }
 
 /* ------------------------------------------------------- generator objects */

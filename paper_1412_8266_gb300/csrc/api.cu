@@ -68,10 +68,10 @@ srng_tune builtin_tune(srng_gen gen, srng_out)
 {
     srng_tune t;
     memset(&t, 0, sizeof t);
-    t.block_threads = gen == SRNG_MRG32K3A ? 256 : 256;
-    t.blocks_per_sm = gen == SRNG_MRG32K3A ? 5 : 8;
+    t.block_threads = 256;
+    t.blocks_per_sm = 8;
     t.chunk = 0;  // chosen from the problem shape
-    t.unroll = 2;
+    t.unroll = 4;
     t.vector_store = 1;
     t.lane_blocks = 64;
     return t;
@@ -248,6 +248,9 @@ static srng_status generate_dev(srng_set *s, uint64_t b, uint64_t c, uint64_t n,
             chunk = (n + splits - 1) / splits;
             chunk = ((chunk + 31) / 32) * 32;
             if (chunk < 256) chunk = 256;
+            // prefer a chunk that divides n (whole-row items, the fast kernel)
+            for (uint64_t d = chunk; d <= 2 * chunk && d <= n; d += 32)
+                if (n % d == 0) { chunk = d; break; }
         }
         if (chunk > n) chunk = n;
         a.chunk = chunk;
@@ -455,6 +458,21 @@ srng_status srng_generate_host(srng_set *set, uint64_t stream_begin, uint64_t st
     if ((st = current_device(&dev))) return st;
     std::lock_guard<std::mutex> lk(set->mu);
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    {
+        // Pinned host memory the device can address (cudaHostAlloc /
+        // cudaHostRegister): the kernels store straight into it over the
+        // host link, no staging and no copy engine.
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, out_host) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+            attr.devicePointer) {
+            const srng_tune t = effective_tune(set->gen, type, nullptr);
+            st = generate_dev(set, stream_begin, stream_count, n_per_stream, type, attr.devicePointer, t, stream, dev);
+            if (st) return st;
+            SRNG_CUDA_TRY(cudaStreamSynchronize(stream));
+            return SRNG_OK;
+        }
+        cudaGetLastError();  // clear a "not a device pointer" result for pageable memory
+    }
     const size_t kStage = 256ull << 20;
     if (!set->d_stage[0]) {
         for (int i = 0; i < 2; ++i) SRNG_CUDA_TRY(cudaMalloc(&set->d_stage[i], kStage));

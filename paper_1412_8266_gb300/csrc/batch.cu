@@ -74,16 +74,29 @@ struct Smem {
     static constexpr int VPL = 16 / sizeof(T);
     static constexpr int RS = G + VPL;
     T tile[kWarps][32 * RS];
-    uint32_t row_len[kWarps][32];
 };
 
+__device__ __forceinline__ void bst256(void *p, uint4 x, uint4 y)
+{
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(x.x), "r"(x.y),
+                 "r"(x.z), "r"(x.w), "r"(y.x), "r"(y.y), "r"(y.z), "r"(y.w)
+                 : "memory");
+}
+
 // ---------------------------------------------------- MRG32k3a work item
+// Lane l owns chunk t = first_chunk + l of the instance (chunk draws, the last
+// chunk shorter).  Row r of the warp's tile is chunk first_chunk + r, which
+// starts at element out_offset + (first_chunk + r) * chunk: rows are at a
+// fixed stride, so row addresses and lengths are arithmetic.  32-byte stores
+// (4 lanes per 128-byte row) when the instance's rows are 32-byte aligned,
+// element stores (one row per warp instruction) otherwise.
 template <int OUT>
 __device__ void mrg_item(const BatchArgs &a, const JumpTable &tab, uint32_t ii, uint32_t first_chunk,
                          Smem<OUT> &sm, int warp, int lane)
 {
     using T = typename OutT<OUT>::T;
     constexpr int G = Smem<OUT>::G, VPL = Smem<OUT>::VPL, RS = Smem<OUT>::RS;
+    constexpr int EPQ = 32 / sizeof(T);
     const BatchInst &in = a.inst[ii];
     const uint64_t t = (uint64_t)first_chunk + lane;
     const uint64_t start = t * a.chunk;
@@ -108,13 +121,12 @@ __device__ void mrg_item(const BatchArgs &a, const JumpTable &tab, uint32_t ii, 
     T *out = static_cast<T *>(a.out);
     T *my = &sm.tile[warp][lane * RS];
     const uint64_t row0 = in.out_offset + (uint64_t)first_chunk * a.chunk;  // row r starts at row0 + r * chunk
-    const bool vec = ((reinterpret_cast<uintptr_t>(out + row0) & 15) == 0) && (a.chunk % VPL == 0);
-    const uint32_t ntiles = (uint32_t)((len + G - 1) / G);
-    const uint32_t max_tiles = __reduce_max_sync(0xffffffffu, ntiles);
+    const uint64_t first_start = (uint64_t)first_chunk * a.chunk;             // draw index of row 0
+    const bool vec = ((reinterpret_cast<uintptr_t>(out + row0) & 31) == 0) && (a.chunk % EPQ == 0);
+    const uint32_t max_tiles = (uint32_t)((min(a.chunk, in.length - first_start) + G - 1) / G);  // row 0 is the longest
     for (uint32_t g = 0; g < max_tiles; ++g) {
         const uint64_t done = (uint64_t)g * G;
         const uint32_t rl = len > done ? (uint32_t)min((uint64_t)G, len - done) : 0u;
-        sm.row_len[warp][lane] = rl;
         for (uint32_t j = 0; j < rl; j += VPL) {
             if constexpr (sizeof(T) == 4) {
                 T x[4];
@@ -130,26 +142,33 @@ __device__ void mrg_item(const BatchArgs &a, const JumpTable &tab, uint32_t ii, 
         }
         __syncwarp();
         if (vec) {
-            constexpr int LPR = G / VPL, RPI = 32 / LPR;
-            const int q = lane % LPR, rsub = lane / LPR;
-            for (int r0 = 0; r0 < 32; r0 += RPI) {
+            const int q = lane & 3, rsub = lane >> 2;
+#pragma unroll
+            for (int r0 = 0; r0 < 32; r0 += 8) {
                 const int r = r0 + rsub;
-                const uint32_t rlen = sm.row_len[warp][r];
-                const uint32_t e = q * VPL;
-                T *dst = out + row0 + (uint64_t)r * a.chunk + done + e;
-                if (e + VPL <= rlen) {
-                    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(&sm.tile[warp][r * RS + e]);
+                const uint64_t rstart = first_start + (uint64_t)r * a.chunk;  // draw index of the row
+                if (rstart >= in.length) continue;
+                const uint64_t rlen = min(a.chunk, in.length - rstart);
+                const uint64_t e = done + (uint64_t)q * EPQ;                  // element within the row
+                if (e >= rlen) continue;
+                const T *src = &sm.tile[warp][r * RS + q * EPQ];
+                T *dst = out + row0 + (uint64_t)r * a.chunk + e;
+                if (e + EPQ <= rlen) {
+                    bst256(dst, *reinterpret_cast<const uint4 *>(src), *reinterpret_cast<const uint4 *>(src + VPL));
                 } else {
-                    for (uint32_t x = e; x < rlen; ++x) out[row0 + (uint64_t)r * a.chunk + done + x] = sm.tile[warp][r * RS + x];
+                    for (uint64_t x = 0; x < rlen - e; ++x) dst[x] = src[x];
                 }
             }
         } else {
             constexpr int LPR = G, RPI = 32 / LPR;
-            const int q = lane % LPR, rsub = lane / LPR;
+            const int qe = lane % LPR, rsub = lane / LPR;
             for (int r0 = 0; r0 < 32; r0 += RPI) {
                 const int r = r0 + rsub;
-                if ((uint32_t)q < sm.row_len[warp][r])
-                    out[row0 + (uint64_t)r * a.chunk + done + q] = sm.tile[warp][r * RS + q];
+                const uint64_t rstart = first_start + (uint64_t)r * a.chunk;
+                if (rstart >= in.length) continue;
+                const uint64_t rlen = min(a.chunk, in.length - rstart);
+                const uint64_t e = done + qe;
+                if (e < rlen) out[row0 + (uint64_t)r * a.chunk + e] = sm.tile[warp][r * RS + qe];
             }
         }
         __syncwarp();
@@ -157,6 +176,8 @@ __device__ void mrg_item(const BatchArgs &a, const JumpTable &tab, uint32_t ii, 
 }
 
 // ------------------------------------------------------- Philox work item
+// Lane l computes pairs of adjacent blocks; eight values per pair go out as
+// 32-byte stores when inside the instance and aligned, else element stores.
 template <int OUT>
 __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int lane)
 {
@@ -199,27 +220,32 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
         return;
     }
     T *row = static_cast<T *>(a.out) + in.out_offset;
-    for (uint32_t u = 0; u < a.lane_blocks; ++u) {
-        const uint64_t b = b0 + (uint64_t)u * 32 + lane;
+    // draws this item may write: its own blocks only (an odd lane_blocks leaves
+    // the last pair half outside), and the instance's length
+    const int64_t lim = min((int64_t)L, (int64_t)(4 * (b0 + 32ull * a.lane_blocks)) - (int64_t)al);
+    for (uint32_t u = 0; u < a.lane_blocks; u += 2) {
+        const uint64_t b = b0 + (uint64_t)u * 32 + 2 * lane;  // this lane's pair: blocks b, b + 1
         if (b >= nb) break;
-        const uint64_t q = q0 + b;
-        uint32_t x0 = (uint32_t)q, x1 = (uint32_t)(q >> 32), x2 = c2, x3 = c3;
-        srng::philox::block(x0, x1, x2, x3, in.key0, in.key1);
+        uint32_t w[8];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint64_t q = q0 + b + h;
+            w[4 * h] = (uint32_t)q; w[4 * h + 1] = (uint32_t)(q >> 32); w[4 * h + 2] = c2; w[4 * h + 3] = c3;
+            srng::philox::block(w[4 * h], w[4 * h + 1], w[4 * h + 2], w[4 * h + 3], in.key0, in.key1);
+        }
         const int64_t k0 = (int64_t)(b * 4) - al;
-        const T v[4] = {bconvert<SRNG_PHILOX4X32_10, OUT>(x0), bconvert<SRNG_PHILOX4X32_10, OUT>(x1),
-                        bconvert<SRNG_PHILOX4X32_10, OUT>(x2), bconvert<SRNG_PHILOX4X32_10, OUT>(x3)};
-        if (k0 >= 0 && (uint64_t)k0 + 4 <= L && ((reinterpret_cast<uintptr_t>(row + k0) & 15) == 0)) {
-            if constexpr (sizeof(T) == 4) {
-                *reinterpret_cast<uint4 *>(row + k0) = *reinterpret_cast<const uint4 *>(v);
-            } else {
-                *reinterpret_cast<double2 *>(row + k0) = make_double2(v[0], v[1]);
-                *reinterpret_cast<double2 *>(row + k0 + 2) = make_double2(v[2], v[3]);
-            }
+        T v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = bconvert<SRNG_PHILOX4X32_10, OUT>(w[j]);
+        if (k0 >= 0 && k0 + 8 <= lim && ((reinterpret_cast<uintptr_t>(row + k0) & 31) == 0)) {
+            const uint4 *p = reinterpret_cast<const uint4 *>(v);
+            bst256(row + k0, p[0], p[1]);
+            if constexpr (sizeof(T) == 8) bst256(row + k0 + 4, p[2], p[3]);
         } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < 8; ++j) {
                 const int64_t k = k0 + j;
-                if (k >= 0 && (uint64_t)k < L) row[k] = v[j];
+                if (k >= 0 && k < lim) row[k] = v[j];
             }
         }
     }

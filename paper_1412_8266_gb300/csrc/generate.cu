@@ -126,6 +126,84 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
 }
 
+// K2, uniform rows: every item is a whole chunk (n a multiple of chunk, chunk a
+// multiple of the 128-byte row) and the output is 32-byte aligned, so item i's
+// row starts at element i * chunk and every tile row is full.  Rows are written
+// with 32-byte stores, four lanes per row, eight rows per warp instruction.
+__device__ __forceinline__ void st256(void *p, uint4 a, uint4 b)
+{
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a.x), "r"(a.y),
+                 "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+                 : "memory");
+}
+
+template <int OUT, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_mrg_generate_rows(const MrgGenArgs a, const __grid_constant__ JumpTable tab)
+{
+    using T = typename OutType<OUT>::T;
+    constexpr int G = 128 / sizeof(T);    // elements per 128-byte row
+    constexpr int VPL = 16 / sizeof(T);   // elements per 16 bytes
+    constexpr int RS = G + VPL;           // 144-byte row stride in shared memory
+    constexpr int EPQ = 32 / sizeof(T);   // elements per 32-byte store
+    __shared__ __align__(16) T tile[WARPS][32 * RS];
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T *my = &tile[warp][lane * RS];
+    T *out = static_cast<T *>(a.out);
+    const uint64_t n_items = a.s_count * a.cps;
+    const uint64_t wstride = (uint64_t)gridDim.x * WARPS * 32;
+    const int q = lane & 3, rsub = lane >> 2;
+
+    for (uint64_t base = ((uint64_t)blockIdx.x * WARPS + warp) * 32; base < n_items; base += wstride) {
+        const uint64_t item = base + lane;
+        const bool active = item < n_items;
+        const uint32_t rows = (uint32_t)min((uint64_t)32, n_items - base);
+        uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
+        if (active) {
+            const uint64_t s_rel = item / a.cps;
+            const uint64_t t = item - s_rel * a.cps;
+            const uint64_t s = a.s_begin + s_rel;
+            const uint64_t ns = a.n_streams;
+            s0 = a.state[s]; s1 = a.state[ns + s]; s2 = a.state[2 * ns + s];
+            s3 = a.state[3 * ns + s]; s4 = a.state[4 * ns + s]; s5 = a.state[5 * ns + s];
+            for (int k = 0; k < a.nbits; ++k)
+                if ((t >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
+        }
+        T *dst0 = out + base * a.chunk + (uint64_t)q * EPQ;
+        for (uint64_t done = 0; done < a.chunk; done += G) {
+            if (active) {
+#pragma unroll
+                for (int j = 0; j < G; j += VPL) {
+                    if constexpr (sizeof(T) == 4) {
+                        T x[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            x[e] = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+                        *reinterpret_cast<uint4 *>(&my[j]) = *reinterpret_cast<uint4 *>(x);
+                    } else {
+                        double2 v;
+                        v.x = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+                        v.y = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+                        *reinterpret_cast<double2 *>(&my[j]) = v;
+                    }
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r0 = 0; r0 < 32; r0 += 8) {
+                const int r = r0 + rsub;
+                if ((uint32_t)r < rows) {
+                    const T *src = &tile[warp][r * RS + q * EPQ];
+                    st256(dst0 + (uint64_t)r * a.chunk + done, *reinterpret_cast<const uint4 *>(src),
+                          *reinterpret_cast<const uint4 *>(src + VPL));
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
 // ------------------------------------------------------------------ K3
 template <int GEN, int OUT, bool VEC>
 __device__ __forceinline__ void store4(typename OutType<OUT>::T *row, int64_t k0, uint64_t n, uint32_t w0,
@@ -156,15 +234,41 @@ __device__ __forceinline__ void store4(typename OutType<OUT>::T *row, int64_t k0
     }
 }
 
-// Tiles of blockDim.x * U Philox blocks; tps tiles per stream; the grid takes
-// tiles by a stride of gridDim.x, tracked as (stream, tile) with the host's
-// quotient / remainder of gridDim.x by tps.
+// Eight consecutive output values (two Philox blocks) from one lane: one or two
+// 32-byte stores when the run is inside the row and 32-byte aligned, else the
+// 16-byte / element path of store4.
+template <int GEN, int OUT, bool VEC>
+__device__ __forceinline__ void store8(typename OutType<OUT>::T *row, int64_t k0, uint64_t n, const uint32_t *w)
+{
+    using T = typename OutType<OUT>::T;
+    if (VEC && k0 >= 0 && (uint64_t)k0 + 8 <= n && ((reinterpret_cast<uintptr_t>(row + k0) & 31) == 0)) {
+        T v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = convert<GEN, OUT>(w[j]);
+        const uint4 *p = reinterpret_cast<const uint4 *>(v);
+        if constexpr (sizeof(T) == 4) {
+            st256(row + k0, p[0], p[1]);
+        } else {
+            st256(row + k0, p[0], p[1]);
+            st256(row + k0 + 4, p[2], p[3]);
+        }
+    } else {
+        store4<GEN, OUT, VEC>(row, k0, n, w[0], w[1], w[2], w[3]);
+        store4<GEN, OUT, VEC>(row, k0 + 4, n, w[4], w[5], w[6], w[7]);
+    }
+}
+
+// Tiles of 2 * blockDim.x * U Philox blocks; tps tiles per stream; the grid
+// takes tiles by a stride of gridDim.x, tracked as (stream, tile) with the
+// host's quotient / remainder of gridDim.x by tps.  Each lane computes U pairs
+// of adjacent blocks (2U independent blocks in flight) and writes each pair's
+// eight values with 32-byte stores: a warp store covers 1 KiB (u32 / f32).
 template <int OUT, int U, bool VEC>
 __global__ void __launch_bounds__(256)
     k_philox_generate(const PhiloxGenArgs a, uint64_t tps, uint64_t q_grid, uint64_t r_grid)
 {
     using T = typename OutType<OUT>::T;
-    const uint64_t tb = (uint64_t)blockDim.x * U;
+    const uint64_t tb = 2ull * blockDim.x * U;
     const uint64_t n_tiles = a.s_count * tps;
     uint64_t s_rel = blockIdx.x / tps;
     uint64_t tt = blockIdx.x - s_rel * tps;
@@ -184,20 +288,22 @@ __global__ void __launch_bounds__(256)
             c2 = (uint32_t)s;
             c3 = (uint32_t)(s >> 32);
         }
-        uint32_t x[U][4];
-        bool ok[U];
+        uint32_t x[U][8];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {  // U independent blocks in flight per thread
-            const uint64_t b = tt * tb + (uint64_t)u * blockDim.x + threadIdx.x;
-            ok[u] = b < nb;
-            const uint64_t q = q0 + b;
-            x[u][0] = (uint32_t)q; x[u][1] = (uint32_t)(q >> 32); x[u][2] = c2; x[u][3] = c3;
-            srng::philox::block(x[u][0], x[u][1], x[u][2], x[u][3], a.k0, a.k1);
+        for (int u = 0; u < U; ++u) {
+            const uint64_t b = tt * tb + (uint64_t)u * 2 * blockDim.x + 2 * threadIdx.x;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint64_t q = q0 + b + h;
+                uint32_t *y = &x[u][4 * h];
+                y[0] = (uint32_t)q; y[1] = (uint32_t)(q >> 32); y[2] = c2; y[3] = c3;
+                srng::philox::block(y[0], y[1], y[2], y[3], a.k0, a.k1);
+            }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const uint64_t b = tt * tb + (uint64_t)u * blockDim.x + threadIdx.x;
-            if (ok[u]) store4<SRNG_PHILOX4X32_10, OUT, VEC>(row, (int64_t)(b * 4) - al, a.n, x[u][0], x[u][1], x[u][2], x[u][3]);
+            const uint64_t b = tt * tb + (uint64_t)u * 2 * blockDim.x + 2 * threadIdx.x;
+            if (b < nb) store8<SRNG_PHILOX4X32_10, OUT, VEC>(row, (int64_t)(b * 4) - al, a.n, x[u]);
         }
         tt += r_grid;
         s_rel += q_grid;
@@ -231,11 +337,30 @@ cudaError_t mrg_dispatch_warps(const MrgGenArgs &a, const JumpTable &tab, const 
 }
 
 template <int OUT>
+cudaError_t mrg_dispatch_rows(const MrgGenArgs &a, const JumpTable &tab, const srng_tune &t, cudaStream_t stream,
+                              const DeviceInfo &dev)
+{
+    const uint64_t items = a.s_count * a.cps;
+    const int warps = t.block_threads >= 256 ? 8 : 4;
+    uint64_t blocks = (items + warps * 32 - 1) / (warps * 32);
+    uint64_t cap = (uint64_t)dev.sm_count * (t.blocks_per_sm ? t.blocks_per_sm : 5);
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) blocks = 1;
+    if (warps == 8) k_mrg_generate_rows<OUT, 8><<<(unsigned)blocks, 256, 0, stream>>>(a, tab);
+    else k_mrg_generate_rows<OUT, 4><<<(unsigned)blocks, 128, 0, stream>>>(a, tab);
+    return cudaGetLastError();
+}
+
+template <int OUT>
 cudaError_t mrg_dispatch(const MrgGenArgs &a, const JumpTable &tab, const srng_tune &t, cudaStream_t stream,
                          const DeviceInfo &dev)
 {
     using T = typename OutType<OUT>::T;
     constexpr uint64_t VPL = 16 / sizeof(T);
+    constexpr uint64_t G = 128 / sizeof(T);
+    if (t.vector_store != 2 && (reinterpret_cast<uintptr_t>(a.out) & 31) == 0 && a.n % a.chunk == 0 &&
+        a.chunk % G == 0)
+        return mrg_dispatch_rows<OUT>(a, tab, t, stream, dev);
     const bool vec_ok = t.vector_store != 2 && (reinterpret_cast<uintptr_t>(a.out) & 15) == 0 &&
                         a.n % VPL == 0 && a.chunk % VPL == 0;
     return vec_ok ? mrg_dispatch_warps<OUT, true>(a, tab, t, stream, dev)
@@ -248,7 +373,7 @@ cudaError_t philox_dispatch_u(const PhiloxGenArgs &a, const srng_tune &t, cudaSt
 {
     const uint32_t threads = t.block_threads ? t.block_threads : 256;
     const uint64_t bps = (a.n + 3) / 4 + 1;  // blocks per stream, any start alignment
-    const uint64_t tb = (uint64_t)threads * U;
+    const uint64_t tb = 2ull * threads * U;
     const uint64_t tps = (bps + tb - 1) / tb;
     const uint64_t n_tiles = a.s_count * tps;
     uint64_t blocks = n_tiles;

@@ -14,7 +14,8 @@ Workloads (sizes as in the configurations this library is measured on):
                (one stream, 2^30 words), as uint32 and as FP32.
   batched      10,000 instances, lengths log-uniform in [1e2, 1e7], even
                instances MRG32k3a (stream i of a mrg_bulk-seeded set), odd
-               instances Philox (stream i under the philox_bulk key).
+               instances Philox (stream i under the philox_bulk key); output
+               slots at prefix-sum offsets rounded up to 32 bytes.
   serving      Poisson arrivals at 20,000 requests/s, n log-uniform in
                [1e3, 1e8] FP32 draws, stream uniform over 10^6 MRG32k3a
                substreams of the all-12345 state; 16 GB output budget.
@@ -46,14 +47,18 @@ def log_uniform_ints(n: int, lo: float, hi: float, seed: int) -> np.ndarray:
 
 
 def batched_instances(n_inst: int = BATCHED["n_inst"], lo: float = BATCHED["lo"], hi: float = BATCHED["hi"],
-                      seed: int = BATCHED["length_seed"]):
+                      seed: int = BATCHED["length_seed"], align: int = 8):
     """Returns (gens, lengths, out_offsets): gens[i] = 0 (MRG32k3a) for even i,
-    1 (Philox) for odd i; out_offsets are the prefix sums of the lengths."""
+    1 (Philox) for odd i; instance i's output slot starts at the prefix sum of
+    the earlier lengths, each slot rounded up to a multiple of `align`
+    elements (8 x 4 bytes: every slot starts on a 32-byte boundary; align=1
+    packs the slots back to back)."""
     lengths = log_uniform_ints(n_inst, lo, hi, seed)
     gens = np.array([i % 2 for i in range(n_inst)], dtype=np.int32)
+    slots = (lengths + np.uint64(align - 1)) // np.uint64(align) * np.uint64(align)
     offs = np.zeros(n_inst, dtype=np.uint64)
     if n_inst > 1:
-        offs[1:] = np.cumsum(lengths[:-1], dtype=np.uint64)
+        offs[1:] = np.cumsum(slots[:-1], dtype=np.uint64)
     return gens, lengths, offs
 
 

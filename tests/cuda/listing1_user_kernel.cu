@@ -1,0 +1,37 @@
+// A user kernel written against include/srng_device.cuh, shaped like the
+// paper's Listing 1 (Sec. 5): the host places the streams once (srng_create),
+// each thread constructs its generator from the set's device view and calls
+// next() -- here several times, writing its draws and storing the state back
+// so a later launch continues the stream.  Built by the test with nvcc.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "srng.h"
+#include "srng_device.cuh"
+
+__global__ void listing1_mrg(float *ddata, srng_dev_view v, int per_thread)
+{
+    const uint64_t s = (uint64_t)blockDim.x * blockIdx.x + threadIdx.x;
+    if (s >= v.n_streams) return;
+    srng::Mrg32k3a rng(v, s);
+    for (int k = 0; k < per_thread; ++k) ddata[s * per_thread + k] = rng.next_f32();
+    rng.store(v, s);
+}
+
+__global__ void listing1_philox(uint32_t *ddata, srng_dev_view v, int per_thread)
+{
+    const uint64_t s = (uint64_t)blockDim.x * blockIdx.x + threadIdx.x;
+    if (s >= v.n_streams) return;
+    srng::Philox4x32_10 rng(v, s);
+    for (int k = 0; k < per_thread; ++k) ddata[s * per_thread + k] = rng.next_u32();
+    rng.store(v);
+}
+
+extern "C" int run_listing1(const srng_dev_view *v, void *out, int per_thread)
+{
+    const unsigned threads = 128, blocks = (unsigned)((v->n_streams + threads - 1) / threads);
+    if (v->gen == SRNG_MRG32K3A) listing1_mrg<<<blocks, threads>>>((float *)out, *v, per_thread);
+    else listing1_philox<<<blocks, threads>>>((uint32_t *)out, *v, per_thread);
+    if (cudaGetLastError() != cudaSuccess) return 1;
+    return cudaDeviceSynchronize() == cudaSuccess ? 0 : 2;
+}

@@ -102,7 +102,7 @@ def test_tune_table_roundtrip(lib):
     assert t.unroll == 4 and t.block_threads == 128
     srng.srng_set_tune(srng.SRNG_PHILOX4X32_10, srng.SRNG_OUT_F32, None)
     t = srng.srng_get_tune(srng.SRNG_PHILOX4X32_10, srng.SRNG_OUT_F32)
-    assert t.unroll == 2 and t.block_threads == 256
+    assert t.unroll == 4 and t.block_threads == 256
 
 
 def test_destroy_null_is_ok(lib):

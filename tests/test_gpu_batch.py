@@ -125,13 +125,13 @@ def test_full_size_batched_vs_plain_and_oracle():
         mst = _states(hm, n)
         inst = [srng.Instance(set_index=int(gens[i]), stream=i, offset=0, length=int(lengths[i]),
                               out_offset=int(outoff[i])) for i in range(n)]
-        out = torch.empty(total, dtype=torch.int32, device="cuda")
+        out = torch.zeros(total, dtype=torch.int32, device="cuda")  # padding between slots stays 0
         plan = srng.srng_batch_plan_create([hm, hp], inst, srng.SRNG_BATCH_WRITE, srng.SRNG_OUT_U32, out)
         srng.srng_batch_plan_launch(plan)
         torch.cuda.synchronize()
         srng.srng_batch_plan_destroy(plan)
         # plain per-instance launches
-        plain = torch.empty(total, dtype=torch.int32, device="cuda")
+        plain = torch.zeros(total, dtype=torch.int32, device="cuda")
         for i in range(n):
             h = hm if gens[i] == 0 else hp
             o = int(outoff[i])

@@ -1,0 +1,72 @@
+"""The device header used from a user's own kernel (the paper's Listing 1
+shape): constructor + next() inside the kernel, state stored back."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1412_8266_gb300 as srng
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+
+@pytest.fixture(scope="module")
+def user_lib(tmp_path_factory):
+    nvcc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    if not os.path.exists(nvcc):
+        nvcc = shutil.which("nvcc")
+    assert nvcc, "nvcc is needed to build the user kernel"
+    out = str(tmp_path_factory.mktemp("user") / "liblisting1.so")
+    subprocess.run([nvcc, "-shared", "-Xcompiler", "-fPIC", "-O2", "-gencode", "arch=compute_103a,code=sm_103a",
+                    "-I", os.path.join(ROOT, "include"), os.path.join(HERE, "cuda", "listing1_user_kernel.cu"),
+                    "-o", out], check=True)
+    lib = ctypes.CDLL(out)
+    lib.run_listing1.restype = ctypes.c_int
+    lib.run_listing1.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
+    return lib
+
+
+def test_mrg_listing1_kernel(user_lib):
+    n_streams, per = 1000, 7
+    h = srng.srng_create_from_state([12345] * 6, n_streams, srng.SRNG_SPACING_STREAM)
+    try:
+        v = srng.srng_get_device_view(h)
+        out = torch.empty(n_streams * per, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        assert user_lib.run_listing1(ctypes.byref(v), out.data_ptr(), per) == 0
+        ref, _ = O.mrg_bulk(O.mrg_stream_starts([12345] * 6, 127, 0, n_streams), 2 * per, O.OUT_F32)
+        got = out.cpu().numpy().reshape(n_streams, per)
+        assert np.array_equal(got.view(np.uint32), ref[:, :per].view(np.uint32))
+        # the state was stored back: the library's generate continues the streams
+        nxt = torch.empty(n_streams * per, dtype=torch.float32, device="cuda")
+        srng.srng_generate(h, 0, n_streams, per, srng.SRNG_OUT_F32, nxt)
+        torch.cuda.synchronize()
+        assert np.array_equal(nxt.cpu().numpy().reshape(n_streams, per).view(np.uint32), ref[:, per:].view(np.uint32))
+    finally:
+        srng.srng_destroy(h)
+
+
+def test_philox_listing1_kernel(user_lib):
+    n_streams, per = 300, 9
+    seed = 0xC0FFEE
+    h = srng.srng_create(srng.SRNG_PHILOX4X32_10, seed, n_streams)
+    try:
+        srng.srng_jump(h, 0, n_streams, srng.SRNG_JUMP_DRAWS, 3)  # start mid-block
+        v = srng.srng_get_device_view(h)
+        out = torch.empty(n_streams * per, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        assert user_lib.run_listing1(ctypes.byref(v), out.data_ptr(), per) == 0
+        ref, _ = O.philox_bulk((seed, 0), 0, [3] * n_streams, per, O.OUT_U32)
+        assert np.array_equal(out.cpu().numpy().view(np.uint32).reshape(n_streams, per), ref)
+        pos = np.zeros(n_streams, dtype=np.uint64)
+        srng.srng_get_state(h, 0, n_streams, pos)
+        assert np.all(pos == 3 + per)
+    finally:
+        srng.srng_destroy(h)

@@ -245,3 +245,30 @@ def test_device_view_exposes_states(sets):
     h2 = sets(srng.srng_create(srng.SRNG_PHILOX4X32_10, (5 << 32) | 9, 8))
     v2 = srng.srng_get_device_view(h2)
     assert v2.gen == 1 and v2.key0 == 9 and v2.key1 == 5 and v2.philox_pos
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("gen", [srng.SRNG_MRG32K3A, srng.SRNG_PHILOX4X32_10])
+def test_generate_into_host_memory(gen, pinned):
+    """srng_generate_host (pinned: direct kernel stores over the host link;
+    pageable: staged pieces and copies) equals srng_generate on the device,
+    also when one stream is longer than a staging piece."""
+    S, n = 3, (70 << 20) // 3 + 5  # 3 streams x ~23M f64 > one 256 MiB piece per stream
+    ha = srng.srng_create(gen, 31, S)
+    hb = srng.srng_create(gen, 31, S)
+    try:
+        dev = torch.empty(S * n, dtype=torch.float64, device="cuda")
+        srng.srng_generate(ha, 0, S, n, srng.SRNG_OUT_F64, dev)
+        if pinned:
+            host = torch.empty(S * n, dtype=torch.float64, pin_memory=True)
+        else:
+            host = np.empty(S * n, dtype=np.float64)
+        srng.srng_generate_host(hb, 0, S, n, srng.SRNG_OUT_F64, host)
+        got = host.numpy() if pinned else host
+        assert np.array_equal(got.view(np.uint64), dev.cpu().numpy().view(np.uint64))
+        # both sets moved by n draws
+        if gen == srng.SRNG_MRG32K3A:
+            assert np.array_equal(get_states(ha, 0, S), get_states(hb, 0, S))
+    finally:
+        srng.srng_destroy(ha)
+        srng.srng_destroy(hb)
