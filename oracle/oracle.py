@@ -53,13 +53,14 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
-def _load():
+def _load(path: str | None = None):
     global _lib
     with _lock:
-        if _lib is not None:
+        if _lib is not None and path is None:
             return _lib
-        build()
-        lib = ctypes.CDLL(_LIB_PATH)
+        if path is None:
+            build()
+        lib = ctypes.CDLL(path or _LIB_PATH)
         u32p = ctypes.POINTER(ctypes.c_uint32)
         u64p = ctypes.POINTER(ctypes.c_uint64)
         vp = ctypes.c_void_p
@@ -95,6 +96,17 @@ def _load():
             fn.argtypes = args
         _lib = lib
         return lib
+
+
+def use_library(path: str | None) -> None:
+    """Test hook: route every oracle function through another build of
+    srng_oracle.c (the mutation tests load deliberately broken copies);
+    None returns to the regular build."""
+    global _lib
+    with _lock:
+        _lib = None
+    if path is not None:
+        _load(path)
 
 
 def _u32p(a):

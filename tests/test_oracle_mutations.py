@@ -1,0 +1,170 @@
+"""Mutation check of the oracle's pins: plausible mistakes planted in copies of
+the oracle's C source (a wrong coefficient, a swapped operand, a dropped term,
+a wrong constant, an off-by-one conversion) must each make at least one pin
+fail.  Everything runs on the CPU; the regular oracle is untouched."""
+import ctypes
+import math
+import os
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests.conftest import find_libcurand
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "srng_oracle.c")
+
+MUTATIONS = {
+    "a12 coefficient": ("#define ORC_A12 1403580LL", "#define ORC_A12 1403581LL"),
+    "a23 coefficient": ("#define ORC_A23 1370589LL", "#define ORC_A23 1370598LL"),
+    "m2 modulus": ("#define ORC_M2 4294944443ULL", "#define ORC_M2 4294944437ULL"),
+    "component 1 lag": ("(ORC_A12 * (int64_t)s[1] - ORC_A13 * (int64_t)s[0])",
+                        "(ORC_A12 * (int64_t)s[2] - ORC_A13 * (int64_t)s[0])"),
+    "component 2 sign": ("(ORC_A21 * (int64_t)s[5] - ORC_A23 * (int64_t)s[3])",
+                         "(ORC_A21 * (int64_t)s[5] + ORC_A23 * (int64_t)s[3])"),
+    "combination wrap": ("return (uint32_t)(p1 - p2 + (int64_t)ORC_M1);", "return (uint32_t)(p1 - p2 + (int64_t)ORC_M2);"),
+    "output from old state": ("    s[0] = s[1]; s[1] = s[2]; s[2] = (uint32_t)p1;\n",
+                              "    s[0] = s[1]; s[1] = s[2]; s[2] = (uint32_t)p1; p1 = s[1];\n"),
+    "matrix entry": ("a[2 * 3 + 1] = (uint64_t)ORC_A12;", "a[2 * 3 + 1] = (uint64_t)ORC_A13;"),
+    "jump exponent word": ("uint64_t word = bit < 64 ? e_lo : e_hi;", "uint64_t word = bit < 63 ? e_lo : e_hi;"),
+    "jump squaring": ("mat_mul(base, base, m, base);", "mat_mul(base, r, m, base);"),
+    "philox multiplier": ("#define ORC_PHILOX_M0 0xD2511F53U", "#define ORC_PHILOX_M0 0xD2511F55U"),
+    "philox weyl": ("#define ORC_PHILOX_W1 0xBB67AE85U", "#define ORC_PHILOX_W1 0xBB67AE86U"),
+    "philox word order": ("uint32_t y1 = lo1;", "uint32_t y1 = lo0;"),
+    "philox key use": ("uint32_t y2 = hi0 ^ x3 ^ k1;", "uint32_t y2 = hi0 ^ x3 ^ k0;"),
+    "philox rounds": ("for (int round = 0; round < 10; ++round) {", "for (int round = 0; round < 9; ++round) {"),
+    "f32 shift": ("return ldexpf((float)(v >> 8), -24);", "return ldexpf((float)(v >> 9), -23);"),
+    "f64 norm": ("const double norm = 1.0 / 4294967088.0;", "const double norm = 1.0 / 4294967087.0;"),
+    "philox f64 offset": ("return ((double)w + 0.5) / 4294967296.0;", "return ((double)w + 1.0) / 4294967296.0;"),
+    "pi threshold philox": ("return a * a + b * b < ((unsigned __int128)1 << 48);",
+                            "return a * a + b * b < ((unsigned __int128)1 << 47);"),
+    "pi radius mrg": ("unsigned __int128 a = z0, b = z1, r = ORC_M1 + 1;", "unsigned __int128 a = z0, b = z1, r = ORC_M1;"),
+}
+
+
+def _build(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert old in src, name
+    mutated = src.replace(old, new, 1)
+    c = tmp_path / (name.replace(" ", "_") + ".c")
+    c.write_text(mutated)
+    so = tmp_path / (name.replace(" ", "_") + ".so")
+    subprocess.run(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", str(c), "-o",
+                    str(so), "-lm"], check=True)
+    return str(so)
+
+
+def _curand_outputs():
+    path = find_libcurand()
+    if path is None:
+        return None
+    lib = ctypes.CDLL(path)
+    g = ctypes.c_void_p()
+    lib.curandCreateGeneratorHost(ctypes.byref(g), 121)
+    lib.curandSetPseudoRandomGeneratorSeed(g, ctypes.c_ulonglong(0))
+    buf = (ctypes.c_double * 64)()
+    lib.curandGenerateUniformDouble(g, buf, ctypes.c_size_t(64))
+    lib.curandDestroyGenerator(g)
+    mrg = np.rint(np.frombuffer(buf, dtype=np.float64) * O.M1).astype(np.uint64)
+    g = ctypes.c_void_p()
+    lib.curandCreateGeneratorHost(ctypes.byref(g), 161)
+    lib.curandSetPseudoRandomGeneratorSeed(g, ctypes.c_ulonglong(0x0123456789ABCDEF))
+    pb = (ctypes.c_uint32 * 64)()
+    lib.curandGenerate(g, pb, ctypes.c_size_t(64))
+    lib.curandDestroyGenerator(g)
+    return mrg, np.frombuffer(pb, dtype=np.uint32).copy()
+
+
+def _pymatpow(a, e, m):
+    r = [[int(i == j) for j in range(3)] for i in range(3)]
+    a = [[int(x) for x in row] for row in a]
+    while e:
+        if e & 1:
+            r = [[sum(r[i][k] * a[k][j] for k in range(3)) % m for j in range(3)] for i in range(3)]
+        a = [[sum(a[i][k] * a[k][j] for k in range(3)) % m for j in range(3)] for i in range(3)]
+        e >>= 1
+    return r
+
+
+def _pins_fail(ref):
+    """True if any pin (a subset of tests/test_oracle_pins.py) fails."""
+    try:
+        # third-party implementation (cuRAND host generators)
+        if ref is not None:
+            mrg, phx = ref
+            starts = O.mrg_stream_starts([12345] * 6, 76, 0, 64)
+            first = np.array([O.mrg_generate(st, 1)[0][0] for st in starts], dtype=np.uint64)
+            if not np.array_equal(first, mrg):
+                return True
+            key = (0x89ABCDEF, 0x01234567)
+            for s in range(16):
+                if list(O.philox4x32_10([0, 0, s, 0], key)) != list(phx[4 * s: 4 * s + 4]):
+                    return True
+        # period 2^191: each component matrix has order m^3 - 1 (identity at the order)
+        for comp, m in ((0, O.M1), (1, O.M2)):
+            if not np.array_equal(O.mrg_matpow(comp, m**3 - 1), np.eye(3, dtype=np.uint64)):
+                return True
+        # 128-bit exponents (both words, bit 63 set) against Python big-int powers
+        for comp, m in ((0, O.M1), (1, O.M2)):
+            e = (1 << 63) | (1 << 64) | (1 << 100) | 12345
+            if O.mrg_matpow(comp, e).tolist() != _pymatpow(O.mrg_matrix(comp).tolist(), e, m):
+                return True
+        # jump equals stepping
+        s = [1, 2, 3, 4, 5, 6]
+        _, stepped = O.mrg_generate(s, 1000)
+        if list(O.mrg_jump(s, 1000)) != list(stepped):
+            return True
+        # step agrees with its matrix (unit states)
+        a = O.mrg_matrix(0)
+        _, st = O.mrg_step([1, 0, 0, 1, 2, 3])
+        if [int(x) for x in st[:3]] != [int(a[i][0]) for i in range(3)]:
+            return True
+        # conversions against exact rationals
+        for v in (0, 255, 256, 2**24, 2**31 + 5, 2**32 - 1):
+            if Fraction(O.to_f32(v)) != Fraction(v >> 8, 1 << 24):
+                return True
+            if Fraction(O.philox_to_f64(v)) != Fraction(2 * v + 1, 1 << 33):
+                return True
+        norm = O.mrg_to_f64(1)
+        if Fraction(norm) != Fraction(float(Fraction(1, O.M1 + 1))):
+            return True
+        # hit tests against exact geometry near the circle
+        av = 11863283
+        for b in range(av - 3, av + 4):
+            if O.pi_hit_philox(av << 8, b << 8) != (av * av + b * b < 1 << 48):
+                return True
+        r = O.M1 + 1
+        z0 = 3037000000
+        z1 = math.isqrt(r * r - z0 * z0)
+        for d in (-1, 0, 1, 2):
+            if O.pi_hit_mrg(z0, z1 + d) != (z0 * z0 + (z1 + d) ** 2 < r * r):
+                return True
+        # output range
+        z, _ = O.mrg_generate([7, 8, 9, 10, 11, 12], 2000)
+        if z.min() < 1 or int(z.max()) > O.M1:
+            return True
+        return False
+    except Exception:
+        return True
+
+
+def test_unmutated_oracle_passes_the_same_checks():
+    O.use_library(None)
+    assert not _pins_fail(_curand_outputs())
+
+
+def test_every_planted_mistake_is_caught(tmp_path):
+    ref = _curand_outputs()
+    if ref is None:
+        pytest.skip("libcurand not found")
+    missed = []
+    try:
+        for name, (old, new) in MUTATIONS.items():
+            O.use_library(_build(tmp_path, name, old, new))
+            if not _pins_fail(ref):
+                missed.append(name)
+    finally:
+        O.use_library(None)
+    assert not missed, missed

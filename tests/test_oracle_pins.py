@@ -125,7 +125,7 @@ def test_matpow_agrees_with_python_bigint():
     independent Python big-integer power, for the stream/substream spacings."""
     for comp, m in ((0, M1), (1, M2)):
         a = O.mrg_matrix(comp)
-        for e in (1 << 76, 1 << 127, (1 << 127) + (1 << 76) + 12345, 3 << 100):
+        for e in (1 << 76, 1 << 127, (1 << 127) + (1 << 76) + 12345, 3 << 100, (1 << 63) | (1 << 64) | 12345):
             assert O.mrg_matpow(comp, e).tolist() == _pymatpow(a, e, m)
 
 
