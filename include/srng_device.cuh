@@ -28,6 +28,12 @@
 
 #include <stdint.h>
 
+#include <type_traits>
+#include <utility>
+#if __cplusplus >= 202002L
+#include <concepts>
+#endif
+
 #include "srng.h"
 
 namespace srng {
@@ -294,6 +300,118 @@ class Philox4x32_10 {
 
     uint32_t k0, k1;
     uint64_t stream_, pos_;
+};
+
+/* ----------------------------------------- the paper's Listing-1 form */
+
+/* Compile-time interface check of a generator class (the paper's Sec. 6
+ * checks, at compile time and without virtual calls, that every generator
+ * provides its draw method and its state members): a device generator here
+ * must provide next_u32 / next_f32 / next_f64 returning uint32_t / float /
+ * double and store its state back with store(view, stream) or store(view). */
+template <class G, class = void> struct is_generator : std::false_type {};
+template <class G>
+struct is_generator<G, std::void_t<decltype(std::declval<G &>().next_u32()), decltype(std::declval<G &>().next_f32()),
+                                   decltype(std::declval<G &>().next_f64())>>
+    : std::integral_constant<bool, std::is_same<decltype(std::declval<G &>().next_u32()), uint32_t>::value &&
+                                       std::is_same<decltype(std::declval<G &>().next_f32()), float>::value &&
+                                       std::is_same<decltype(std::declval<G &>().next_f64()), double>::value> {};
+static_assert(is_generator<Mrg32k3a>::value, "Mrg32k3a must provide next_u32/next_f32/next_f64");
+static_assert(is_generator<Philox4x32_10>::value, "Philox4x32_10 must provide next_u32/next_f32/next_f64");
+#if __cplusplus >= 202002L
+template <class G>
+concept DeviceGenerator = requires(G g) {
+    { g.next_u32() } -> std::same_as<uint32_t>;
+    { g.next_f32() } -> std::same_as<float>;
+    { g.next_f64() } -> std::same_as<double>;
+};
+static_assert(DeviceGenerator<Mrg32k3a> && DeviceGenerator<Philox4x32_10>);
+#endif
+
+namespace detail {
+/* The set bound by RNG<T, Gen>::init in this translation unit (internal
+ * linkage: every .cu file that includes this header binds its own). */
+static __constant__ srng_dev_view bound_view;
+
+__device__ __forceinline__ uint64_t global_thread_index()
+{
+    const uint64_t block = (uint64_t)blockIdx.x + (uint64_t)gridDim.x * (blockIdx.y + (uint64_t)gridDim.y * blockIdx.z);
+    const uint64_t tid = threadIdx.x + (uint64_t)blockDim.x * (threadIdx.y + (uint64_t)blockDim.y * threadIdx.z);
+    return block * ((uint64_t)blockDim.x * blockDim.y * blockDim.z) + tid;
+}
+
+template <class T> struct draw;
+template <> struct draw<uint32_t> { template <class G> __device__ static uint32_t f(G &g) { return g.next_u32(); } };
+template <> struct draw<float> { template <class G> __device__ static float f(G &g) { return g.next_f32(); } };
+template <> struct draw<double> { template <class G> __device__ static double f(G &g) { return g.next_f64(); } };
+
+template <class Gen> struct gen_id;
+template <> struct gen_id<Mrg32k3a> { static constexpr int value = SRNG_MRG32K3A; };
+template <> struct gen_id<Philox4x32_10> { static constexpr int value = SRNG_PHILOX4X32_10; };
+}  // namespace detail
+
+/* The paper's device object (Listing 1): constructed inside a kernel with no
+ * arguments, it picks up the stream of the calling thread -- stream number =
+ * global thread index, blocks in grid order, threads in block order -- from
+ * the set bound on the host by init(); next() returns the next value of type
+ * T (uint32_t, float or double, with the fixed conversions of srng.h).  The
+ * destructor stores the stream's state back, so the next kernel that uses
+ * the set continues where this one stopped.  The bound set must have at
+ * least as many streams as threads launched. */
+template <class T, class Gen>
+class RNG {
+  public:
+    __device__ RNG() : s_(detail::global_thread_index()), g_(detail::bound_view, s_) {}
+    __device__ ~RNG()
+    {
+        if constexpr (detail::gen_id<Gen>::value == SRNG_MRG32K3A) g_.store(detail::bound_view, s_);
+        else g_.store(detail::bound_view);
+    }
+    __device__ __forceinline__ T next() { return detail::draw<T>::f(g_); }
+    __device__ uint64_t stream() const { return s_; }
+
+    /* Host set-up (Sec. 5.1): create a set of n_streams streams (one per thread
+     * of the kernels to come) from `seed` and bind it.  The set is owned
+     * until release(). */
+    static srng_status init(uint64_t n_streams, uint64_t seed = 0x5EED5EED5EED5EEDull,
+                            srng_spacing spacing = SRNG_SPACING_STREAM)
+    {
+        srng_set *s = nullptr;
+        srng_status st = srng_create(&s, (srng_gen)detail::gen_id<Gen>::value, seed, n_streams, spacing, nullptr);
+        if (st != SRNG_OK) return st;
+        st = bind(s);
+        if (st != SRNG_OK) { srng_destroy(s); return st; }
+        owned() = s;
+        return SRNG_OK;
+    }
+    /* Bind an existing set of the same generator (not owned). */
+    static srng_status bind(const srng_set *set)
+    {
+        srng_dev_view v;
+        srng_status st = srng_get_device_view(set, &v);
+        if (st != SRNG_OK) return st;
+        if (v.gen != detail::gen_id<Gen>::value) return SRNG_ERR_ARG;
+        return cudaMemcpyToSymbol(detail::bound_view, &v, sizeof v) == cudaSuccess ? SRNG_OK : SRNG_ERR_CUDA;
+    }
+    /* Release (Sec. 5.1, Listing 1): destroy the set created by init(). */
+    static srng_status release()
+    {
+        srng_status st = srng_destroy(owned());
+        owned() = nullptr;
+        return st;
+    }
+    static srng_set *set() { return owned(); }
+
+  private:
+    static srng_set *&owned()
+    {
+        static srng_set *s = nullptr;
+        return s;
+    }
+
+  private:
+    uint64_t s_;
+    Gen g_;
 };
 
 }  // namespace srng

@@ -70,3 +70,44 @@ def test_philox_listing1_kernel(user_lib):
         assert np.all(pos == 3 + per)
     finally:
         srng.srng_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def paper_form_lib(tmp_path_factory):
+    from paper_1412_8266_gb300 import _build
+    nvcc = _build.nvcc()
+    out = str(tmp_path_factory.mktemp("paper") / "libpaperform.so")
+    pkg = os.path.dirname(srng.lib_path())
+    subprocess.run([nvcc, "-shared", "-Xcompiler", "-fPIC", "-O2", "-std=c++20",
+                    "-gencode", "arch=compute_103a,code=sm_103a", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(HERE, "cuda", "listing1_paper_form.cu"), "-o", out,
+                    "-L", pkg, "-lsrng", "-Xlinker", "-rpath=" + pkg], check=True)
+    lib = ctypes.CDLL(out)
+    lib.run_paper_listing1.restype = ctypes.c_int
+    lib.run_paper_listing1.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
+    lib.run_philox_form.restype = ctypes.c_int
+    lib.run_philox_form.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
+    return lib
+
+
+def test_paper_listing1_form(paper_form_lib):
+    """RNG<float, MRG32k3a> rng; ddata[blockDim.x * blockIdx.x + threadIdx.x] = rng.next();
+    launched three times: launch l holds draw l of every thread's stream."""
+    block_num, thread_num, launches, seed = 37, 128, 3, 0x5EED
+    n = block_num * thread_num
+    out = torch.empty(launches * n, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    assert paper_form_lib.run_paper_listing1(out.data_ptr(), block_num, thread_num, launches, seed) == 0
+    ref, _ = O.mrg_bulk(O.mrg_stream_starts(O.seed_expand(seed), 127, 0, n), launches, O.OUT_F32)
+    got = out.cpu().numpy().reshape(launches, n).T
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+def test_paper_form_philox(paper_form_lib):
+    block_num, thread_num, seed = 5, 96, 0xC0FFEE
+    n = block_num * thread_num
+    out = torch.empty(2 * n, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    assert paper_form_lib.run_philox_form(out.data_ptr(), block_num, thread_num, seed) == 0
+    ref, _ = O.philox_bulk((seed, 0), 0, [0] * n, 2, O.OUT_U32)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32).reshape(n, 2), ref)
