@@ -402,6 +402,20 @@ def extras(torch, srng, dev, stream, peak):
         del o
     srng.srng_destroy(h)
     res["philox_bulk_2^30"] = ph
+    # Philox layouts at the many-stream shape (2^18 streams x 4096 words, uint32):
+    # counter split (one key) vs keyed (key = stream, Sec. 4.3)
+    lay = {}
+    o = torch.empty(S_STREAMS * N_DRAWS, dtype=torch.int32, device=dev)
+    for name, g in (("counter_split", srng.SRNG_PHILOX4X32_10), ("keyed", srng.SRNG_PHILOX4X32_10_KEYED)):
+        h = srng.srng_create(g, 0xC0FFEE, S_STREAMS, srng.SRNG_SPACING_STREAM, stream)
+        best, med = _time(torch, stream, lambda: (srng.srng_reset(h, stream),
+                                                  srng.srng_generate_tuned(h, 0, S_STREAMS, N_DRAWS, srng.SRNG_OUT_U32,
+                                                                           o, tunes[srng.SRNG_OUT_U32], stream)))
+        lay[name] = {"ms_best": best, "GB_s": o.numel() * 4 / best / 1e6,
+                     "frac_of_copy_peak": o.numel() * 4 / best / 1e6 / peak}
+        srng.srng_destroy(h)
+    del o
+    res["philox_layouts_2^18x4096_u32"] = lay
     # Batched: 10^4 instances, plain per-instance launches vs one graph launch; fused pi
     gens, lengths, outoff = W.batched_instances()
     ni = len(gens)

@@ -64,7 +64,8 @@ typedef enum srng_status {
 
 typedef enum srng_gen {
     SRNG_MRG32K3A = 0,
-    SRNG_PHILOX4X32_10 = 1
+    SRNG_PHILOX4X32_10 = 1,      /* streams split the counter, one key per set        */
+    SRNG_PHILOX4X32_10_KEYED = 2 /* one key per stream (paper Sec. 4.3): see srng_create */
 } srng_gen;
 
 typedef enum srng_out {
@@ -136,6 +137,11 @@ int srng_abi_version(void);
  *   Philox4x32-10: key = (seed & 0xffffffff, seed >> 32); stream s uses
  *     counter words 2-3 = s and counter words 0-1 = position / 4, draw =
  *     word position % 4; every position starts at 0.  `spacing` is ignored.
+ *   Philox4x32-10, keyed (SRNG_PHILOX4X32_10_KEYED; the paper's Sec. 4.3
+ *     parameterisation: the key is the stream's own identifier): stream s
+ *     uses key = (s & 0xffffffff, s >> 32), counter words 2-3 = the seed's
+ *     two words, counter words 0-1 = position / 4.  Everything else as
+ *     above; srng_describe reports this generator value.
  * n_streams: 1 .. 2^40 (MRG32k3a with SRNG_SPACING_STREAM: at most 2^64 by
  * the paper, here limited by device memory: 24 bytes per stream; Philox: 8).
  * The set owns its device memory until srng_destroy.  Synchronises
@@ -227,8 +233,9 @@ srng_status srng_convert(srng_gen gen, srng_out type, const uint32_t *in_dev, ui
  * owned by the set and valid until srng_destroy. */
 typedef struct srng_dev_view {
     int32_t gen;            /* SRNG_MRG32K3A or SRNG_PHILOX4X32_10              */
-    uint32_t key0, key1;    /* Philox key                                      */
-    uint32_t pad;
+    uint32_t key0, key1;    /* Philox: the set's seed words (key, or counter
+                             * words 2-3 when keyed)                           */
+    uint32_t flags;         /* bit 0: Philox keyed layout (key = stream)        */
     uint64_t n_streams;
     uint32_t *mrg_state;    /* MRG32k3a, SoA: word j of stream i at
                              * [j * n_streams + i], j in the srng_create_from_state order */

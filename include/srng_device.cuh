@@ -270,19 +270,23 @@ class Mrg32k3a {
     uint32_t s0, s1, s2, s3, s4, s5;
 };
 
-/* Philox4x32-10 stream handle: counter words 2-3 = stream, 0-1 = block index. */
+/* Philox4x32-10 stream handle: counter words 0-1 = block index; words 2-3 =
+ * the stream and key = the set's seed, or -- keyed layout -- key = the stream
+ * and words 2-3 = the seed. */
 class Philox4x32_10 {
   public:
     __device__ Philox4x32_10(const srng_dev_view &v, uint64_t stream)
-        : k0(v.key0), k1(v.key1), stream_(stream), pos_(v.philox_pos[stream]) {}
+        : k0((v.flags & 1u) ? (uint32_t)stream : v.key0), k1((v.flags & 1u) ? (uint32_t)(stream >> 32) : v.key1),
+          stream_(stream), ctr_hi_((v.flags & 1u) ? ((uint64_t)v.key1 << 32 | v.key0) : stream),
+          pos_(v.philox_pos[stream]) {}
     __device__ Philox4x32_10(uint32_t key0, uint32_t key1, uint64_t stream, uint64_t position)
-        : k0(key0), k1(key1), stream_(stream), pos_(position) {}
+        : k0(key0), k1(key1), stream_(stream), ctr_hi_(stream), pos_(position) {}
 
     /* The four words of block q of this stream. */
     __device__ __forceinline__ uint4 block(uint64_t q) const
     {
         uint32_t c0 = (uint32_t)q, c1 = (uint32_t)(q >> 32);
-        uint32_t c2 = (uint32_t)stream_, c3 = (uint32_t)(stream_ >> 32);
+        uint32_t c2 = (uint32_t)ctr_hi_, c3 = (uint32_t)(ctr_hi_ >> 32);
         philox::block(c0, c1, c2, c3, k0, k1);
         return make_uint4(c0, c1, c2, c3);
     }
@@ -299,7 +303,7 @@ class Philox4x32_10 {
     __device__ uint64_t position() const { return pos_; }
 
     uint32_t k0, k1;
-    uint64_t stream_, pos_;
+    uint64_t stream_, ctr_hi_, pos_;
 };
 
 /* ----------------------------------------- the paper's Listing-1 form */

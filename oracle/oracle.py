@@ -212,6 +212,15 @@ def philox_generate(key, stream: int, pos: int, n: int, out_type: int = OUT_U32)
     return out
 
 
+def philox_keyed_generate(seed: int, stream: int, pos: int, n: int, out_type: int = OUT_U32) -> np.ndarray:
+    """n words of stream `stream` in the keyed layout (reading of Sec. 4.3, the
+    key set from the stream's own identifier): key = (stream low word, stream
+    high word), counter words 2-3 = (seed low word, seed high word), counter
+    words 0-1 = position / 4 -- the same Philox4x32-10 block with the roles of
+    the key and counter words 2-3 exchanged."""
+    return philox_generate((stream & 0xFFFFFFFF, stream >> 32), seed, pos, n, out_type)
+
+
 def philox_bulk(key, stream0: int, positions, n: int, out_type: int = OUT_U32, threads: int = 0):
     pos = np.ascontiguousarray(np.array(positions, dtype=np.uint64))
     out = np.empty((pos.shape[0], n), dtype=_DTYPES[out_type])

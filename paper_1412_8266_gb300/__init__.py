@@ -21,12 +21,12 @@ import threading
 __all__ = [
     "SrngError", "Tune", "Instance", "SetDesc", "DevView", "ServerConfig", "ServerStats", "Request",
     "lib_path", "load",
-    "SRNG_MRG32K3A", "SRNG_PHILOX4X32_10", "SRNG_OUT_U32", "SRNG_OUT_F32", "SRNG_OUT_F64",
+    "SRNG_MRG32K3A", "SRNG_PHILOX4X32_10", "SRNG_PHILOX4X32_10_KEYED", "SRNG_OUT_U32", "SRNG_OUT_F32", "SRNG_OUT_F64",
     "SRNG_SPACING_STREAM", "SRNG_SPACING_SUBSTREAM", "SRNG_JUMP_DRAWS", "SRNG_JUMP_SUBSTREAMS",
     "SRNG_JUMP_STREAMS", "SRNG_BATCH_WRITE", "SRNG_BATCH_FUSED_PI",
 ]
 
-SRNG_MRG32K3A, SRNG_PHILOX4X32_10 = 0, 1
+SRNG_MRG32K3A, SRNG_PHILOX4X32_10, SRNG_PHILOX4X32_10_KEYED = 0, 1, 2
 SRNG_OUT_U32, SRNG_OUT_F32, SRNG_OUT_F64 = 0, 1, 2
 SRNG_SPACING_STREAM, SRNG_SPACING_SUBSTREAM = 0, 1
 SRNG_JUMP_DRAWS, SRNG_JUMP_SUBSTREAMS, SRNG_JUMP_STREAMS = 0, 1, 2
@@ -67,7 +67,7 @@ class SetDesc(ctypes.Structure):
 
 class DevView(ctypes.Structure):
     _fields_ = [("gen", ctypes.c_int32), ("key0", ctypes.c_uint32), ("key1", ctypes.c_uint32),
-                ("pad", ctypes.c_uint32), ("n_streams", ctypes.c_uint64), ("mrg_state", ctypes.c_void_p),
+                ("flags", ctypes.c_uint32), ("n_streams", ctypes.c_uint64), ("mrg_state", ctypes.c_void_p),
                 ("philox_pos", ctypes.c_void_p)]
 
 

@@ -188,7 +188,7 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
     const uint64_t q0 = p0 >> 2;
     const uint64_t nb = (al + in.length + 3) >> 2;
     const uint64_t b0 = (uint64_t)seg * 32 * a.lane_blocks;
-    const uint32_t c2 = (uint32_t)in.stream, c3 = (uint32_t)(in.stream >> 32);
+    const uint32_t c2 = (uint32_t)in.ctr_hi, c3 = (uint32_t)(in.ctr_hi >> 32);
     const uint64_t L = in.length;
     if (a.mode == SRNG_BATCH_FUSED_PI) {
         uint32_t hits = 0;
@@ -422,8 +422,9 @@ srng_status batch_build(srng_set *const *sets, uint32_t n_sets, const srng_insta
         BatchInst b;
         memset(&b, 0, sizeof b);
         b.gen = s->gen;
-        b.key0 = s->key0;
-        b.key1 = s->key1;
+        b.key0 = s->keyed ? (uint32_t)x.stream : s->key0;
+        b.key1 = s->keyed ? (uint32_t)(x.stream >> 32) : s->key1;
+        b.ctr_hi = s->keyed ? ((uint64_t)s->key1 << 32 | s->key0) : x.stream;
         b.stream = x.stream;
         b.offset = x.offset;
         b.length = x.length;
@@ -625,6 +626,7 @@ static __device__ __align__(256) unsigned char g_batch_scratch[kStaticBytes];
 struct StaticSets {
     uint32_t gen[kStaticMaxSets];
     uint32_t key0[kStaticMaxSets], key1[kStaticMaxSets];
+    uint32_t keyed[kStaticMaxSets];
     const uint32_t *state[kStaticMaxSets];
     uint64_t ns[kStaticMaxSets];
     const uint64_t *pos[kStaticMaxSets];
@@ -642,8 +644,9 @@ __global__ void __launch_bounds__(256)
     BatchInst b;
     memset(&b, 0, sizeof b);
     b.gen = sets.gen[si];
-    b.key0 = sets.key0[si];
-    b.key1 = sets.key1[si];
+    b.key0 = sets.keyed[si] ? (uint32_t)r.stream : sets.key0[si];
+    b.key1 = sets.keyed[si] ? (uint32_t)(r.stream >> 32) : sets.key1[si];
+    b.ctr_hi = sets.keyed[si] ? ((uint64_t)sets.key1[si] << 32 | sets.key0[si]) : r.stream;
     b.stream = r.stream;
     b.offset = r.offset;
     b.length = r.length;
@@ -837,6 +840,7 @@ extern "C" srng_status srng_batch_run_static(srng_set *const *sets, uint32_t n_s
         ss.gen[k] = s->gen;
         ss.key0[k] = s->key0;
         ss.key1[k] = s->key1;
+        ss.keyed[k] = s->keyed ? 1u : 0u;
         ss.state[k] = s->d_state;
         ss.ns[k] = s->n_streams;
         ss.pos[k] = s->d_pos;

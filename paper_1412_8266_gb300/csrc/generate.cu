@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(256)
     uint64_t s_rel = blockIdx.x / tps;
     uint64_t tt = blockIdx.x - s_rel * tps;
     uint64_t cur = ~0ull;  // stream whose position is loaded
-    uint32_t al = 0, c2 = 0, c3 = 0;
+    uint32_t al = 0, c2 = 0, c3 = 0, kk0 = a.k0, kk1 = a.k1;
     uint64_t q0 = 0, nb = 0;
     T *row = nullptr;
     for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -285,8 +285,11 @@ __global__ void __launch_bounds__(256)
             q0 = p0 >> 2;
             nb = (al + a.n + 3) >> 2;
             row = static_cast<T *>(a.out) + s_rel * a.n;
-            c2 = (uint32_t)s;
-            c3 = (uint32_t)(s >> 32);
+            if (a.keyed) {  // key = the stream, counter words 2-3 = the seed
+                kk0 = (uint32_t)s; kk1 = (uint32_t)(s >> 32); c2 = a.k0; c3 = a.k1;
+            } else {
+                c2 = (uint32_t)s; c3 = (uint32_t)(s >> 32);
+            }
         }
         uint32_t x[U][8];
 #pragma unroll
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(256)
                 const uint64_t q = q0 + b + h;
                 uint32_t *y = &x[u][4 * h];
                 y[0] = (uint32_t)q; y[1] = (uint32_t)(q >> 32); y[2] = c2; y[3] = c3;
-                srng::philox::block(y[0], y[1], y[2], y[3], a.k0, a.k1);
+                srng::philox::block(y[0], y[1], y[2], y[3], kk0, kk1);
             }
         }
 #pragma unroll

@@ -49,6 +49,10 @@ struct DeviceInfo {
 };
 srng_status current_device(DeviceInfo *out);
 
+// The kernels (and tuning tables) of a generator value: the keyed Philox
+// layout runs the Philox kernels.
+inline int kernel_gen(int g) { return g == SRNG_MRG32K3A ? SRNG_MRG32K3A : SRNG_PHILOX4X32_10; }
+
 // ---------------------------------------------------------------- tuning
 srng_tune effective_tune(srng_gen gen, srng_out type, const srng_tune *user);
 srng_status check_tune(const srng_tune *t);
@@ -84,7 +88,8 @@ cudaError_t launch_mrg_generate(const MrgGenArgs &a, srng_out type, const JumpTa
                                 const srng_tune &t, cudaStream_t stream, const DeviceInfo &dev);
 
 struct PhiloxGenArgs {
-    uint32_t k0, k1;
+    uint32_t k0, k1;      // the set's seed words
+    int keyed;            // 0: key = (k0, k1), counter words 2-3 = stream; 1: key = stream, words 2-3 = (k0, k1)
     const uint64_t *pos;
     uint64_t s_begin, s_count, n;
     void *out;
@@ -99,9 +104,10 @@ cudaError_t launch_convert(srng_gen gen, srng_out type, const uint32_t *in, uint
 // Per-instance descriptor on the device.
 struct BatchInst {
     uint32_t gen;
-    uint32_t key0, key1;
+    uint32_t key0, key1;      // Philox key of this instance's stream
     uint32_t st[6];           // MRG32k3a start state (written by the set-up kernel)
     uint64_t stream;          // stream index in its set
+    uint64_t ctr_hi;          // Philox counter words 2-3 (the stream, or the seed when keyed)
     uint64_t offset;          // draws after the stream's current position
     uint64_t pos;             // Philox start position (written by the set-up kernel)
     uint64_t length;
@@ -144,7 +150,8 @@ struct srng_set {
     uint64_t n_streams;
     uint64_t seed;
     uint32_t y0[6];          // MRG32k3a seed state
-    uint32_t key0, key1;     // Philox key
+    uint32_t key0, key1;     // Philox seed words (key, or counter words 2-3 when keyed)
+    bool keyed;              // Philox key-per-stream layout
     int device;
     uint32_t *d_state;       // MRG32k3a SoA states (6 x n_streams)
     uint64_t *d_pos;         // Philox positions

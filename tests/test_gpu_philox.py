@@ -136,3 +136,75 @@ def test_empty_and_range_edges(philox_set):
     with pytest.raises(srng.SrngError) as e:
         srng.srng_generate(h, 3, 2, 10, srng.SRNG_OUT_U32, torch.empty(20, dtype=torch.int32, device="cuda"))
     assert e.value.name == "SRNG_ERR_RANGE"
+
+
+# ------------------------------------------------------------- keyed layout
+@pytest.mark.parametrize("out_type", TYPES)
+@pytest.mark.parametrize("n_streams,n,start", [(1, 5, 0), (7, 4097, 0), (33, 1000, 3), (5, 70001, 6)])
+def test_keyed_layout_vs_oracle(philox_set, out_type, n_streams, n, start):
+    """Key per stream (Sec. 4.3): key = stream index, counter words 2-3 = seed."""
+    seed = 0x0123456789ABCDEF
+    h = srng.srng_create(srng.SRNG_PHILOX4X32_10_KEYED, seed, n_streams + 2)
+    try:
+        assert srng.srng_describe(h).gen == srng.SRNG_PHILOX4X32_10_KEYED
+        v = srng.srng_get_device_view(h)
+        assert v.flags & 1
+        if start:
+            srng.srng_jump(h, 0, n_streams + 2, srng.SRNG_JUMP_DRAWS, start)
+        _, out = empty(n_streams * n, out_type, pad=1 if start else 0)
+        srng.srng_generate(h, 2, n_streams, n, out_type, out)
+        torch.cuda.synchronize()
+        ref = np.stack([O.philox_keyed_generate(seed, 2 + i, start, n, out_type) for i in range(n_streams)])
+        assert_bitexact(to_np(out, out_type).reshape(n_streams, n), ref, out_type)
+    finally:
+        srng.srng_destroy(h)
+
+
+def test_keyed_layout_differs_from_counter_split():
+    a = srng.srng_create(srng.SRNG_PHILOX4X32_10, 7, 4)
+    b = srng.srng_create(srng.SRNG_PHILOX4X32_10_KEYED, 7, 4)
+    try:
+        x = torch.empty(4 * 64, dtype=torch.int32, device="cuda")
+        y = torch.empty(4 * 64, dtype=torch.int32, device="cuda")
+        srng.srng_generate(a, 0, 4, 64, srng.SRNG_OUT_U32, x)
+        srng.srng_generate(b, 0, 4, 64, srng.SRNG_OUT_U32, y)
+        torch.cuda.synchronize()
+        assert not torch.equal(x, y)
+    finally:
+        srng.srng_destroy(a)
+        srng.srng_destroy(b)
+
+
+def test_keyed_layout_in_batch_and_server():
+    seed = 0xC0FFEE
+    h = srng.srng_create(srng.SRNG_PHILOX4X32_10_KEYED, seed, 50)
+    try:
+        lengths = [0, 1, 5, 1000, 40001, 7]
+        offs = [0, 3, 1, 0, 2, 5]
+        outoff = np.concatenate([[0], np.cumsum(lengths[:-1])]).astype(int)
+        inst = [srng.Instance(set_index=0, stream=10 + i, offset=offs[i], length=lengths[i],
+                              out_offset=int(outoff[i])) for i in range(len(lengths))]
+        out = torch.zeros(sum(lengths), dtype=torch.int32, device="cuda")
+        srng.srng_batch_run([h], inst, srng.SRNG_BATCH_WRITE, srng.SRNG_OUT_U32, out)
+        got = out.cpu().numpy().view(np.uint32)
+        for i, L in enumerate(lengths):
+            ref = O.philox_keyed_generate(seed, 10 + i, offs[i], L)
+            assert np.array_equal(got[outoff[i]:outoff[i] + L], ref), i
+        static = torch.zeros(sum(lengths), dtype=torch.int32, device="cuda")
+        srng.srng_batch_run_static([h], inst, srng.SRNG_BATCH_WRITE, srng.SRNG_OUT_U32, static)
+        torch.cuda.synchronize()
+        assert torch.equal(static, out)
+        srv = srng.srng_server_create(h, dict(budget_bytes=16 << 20))
+        try:
+            t1 = srng.srng_server_submit(srv, 3, 12345, srng.SRNG_OUT_U32)
+            t2 = srng.srng_server_submit(srv, 3, 999, srng.SRNG_OUT_U32)
+            for t, pos, n in ((t1, 0, 12345), (t2, 12345, 999)):
+                srng.srng_server_wait(srv, t, 60000)
+                host = np.empty(n, dtype=np.uint32)
+                srng.srng_server_read(srv, t, host, True)
+                assert np.array_equal(host, O.philox_keyed_generate(seed, 3, pos, n))
+                srng.srng_server_release(srv, t)
+        finally:
+            srng.srng_server_destroy(srv)
+    finally:
+        srng.srng_destroy(h)
