@@ -18,7 +18,8 @@ streams) on the host cores on a bounded sample of the same workload.
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
 torch.distributed.run (one process per GPU, independent replicas: rank r
-generates streams [r S, (r+1) S) of one set; no data-path collective).
+holds and generates streams [r S, (r+1) S) of the sequence, a range set of
+its own; no data-path collective).
 """
 from __future__ import annotations
 
@@ -227,9 +228,10 @@ def run_ours(args):
                                        install=False)
     t_tune = time.perf_counter() - t_tune
 
-    # replicas: rank r generates streams [r S, (r+1) S) of one set
-    b, _ = stream_range(rank, world, S_STREAMS)
-    h = srng.srng_create(srng.SRNG_MRG32K3A, SEED, S_STREAMS * world, srng.SRNG_SPACING_STREAM, stream)
+    # replicas: rank r holds and generates streams [r S, (r+1) S) of one sequence
+    base, _ = stream_range(rank, world, S_STREAMS)
+    h = srng.srng_create_range(srng.SRNG_MRG32K3A, SEED, base, S_STREAMS, srng.SRNG_SPACING_STREAM, None, stream)
+    b = 0
     out_u = torch.empty(S_STREAMS * N_DRAWS, dtype=torch.int32, device=dev)
     out_f = torch.empty(S_STREAMS * N_DRAWS, dtype=torch.float64, device=dev)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]

@@ -155,6 +155,18 @@ srng_status srng_create(srng_set **out, srng_gen gen, uint64_t seed, uint64_t n_
 srng_status srng_create_from_state(srng_set **out, const uint32_t state[6], uint64_t n_streams,
                                    srng_spacing spacing, void *cuda_stream);
 
+/* A set holding streams [stream_base, stream_base + n_streams) of the same
+ * sequence (the set's stream i is stream stream_base + i of srng_create's
+ * numbering; every stream-index argument of the other calls is relative to
+ * the set): replicas on several GPUs each hold their own range, and stream
+ * numbers up to 2^64 - 1 (the paper's 2^64 streams, Sec. 4.1) are reachable
+ * without allocating the streams below them.  `state` NULL: from `seed` as
+ * srng_create; else MRG32k3a from an explicit seed state (as
+ * srng_create_from_state; `seed` ignored).  SRNG_ERR_RANGE if
+ * stream_base + n_streams - 1 passes 2^64 - 1. */
+srng_status srng_create_range(srng_set **out, srng_gen gen, uint64_t seed, const uint32_t state[6],
+                              uint64_t stream_base, uint64_t n_streams, srng_spacing spacing, void *cuda_stream);
+
 /* Free the set and its device memory (after the device is done with it:
  * synchronises the device first).  NULL is accepted. */
 srng_status srng_destroy(srng_set *set);
@@ -168,7 +180,8 @@ typedef struct srng_set_desc {
     srng_spacing spacing;
     uint64_t n_streams;
     uint64_t seed;
-    uint32_t seed_state[6]; /* MRG32k3a y0; Philox: key in [0], [1] */
+    uint32_t seed_state[6]; /* MRG32k3a y0; Philox: seed words in [0], [1] */
+    uint64_t stream_base;   /* stream number of the set's first stream     */
 } srng_set_desc;
 srng_status srng_describe(const srng_set *set, srng_set_desc *out);
 
@@ -240,6 +253,7 @@ typedef struct srng_dev_view {
     uint32_t *mrg_state;    /* MRG32k3a, SoA: word j of stream i at
                              * [j * n_streams + i], j in the srng_create_from_state order */
     uint64_t *philox_pos;   /* Philox: current position of each stream          */
+    uint64_t stream_base;   /* stream number of slot 0 (srng_create_range)      */
 } srng_dev_view;
 srng_status srng_get_device_view(const srng_set *set, srng_dev_view *out);
 

@@ -275,9 +275,12 @@ class Mrg32k3a {
  * and words 2-3 = the seed. */
 class Philox4x32_10 {
   public:
+    /* `stream` is the slot in the set; the key / counter use its stream number
+     * v.stream_base + stream. */
     __device__ Philox4x32_10(const srng_dev_view &v, uint64_t stream)
-        : k0((v.flags & 1u) ? (uint32_t)stream : v.key0), k1((v.flags & 1u) ? (uint32_t)(stream >> 32) : v.key1),
-          stream_(stream), ctr_hi_((v.flags & 1u) ? ((uint64_t)v.key1 << 32 | v.key0) : stream),
+        : k0((v.flags & 1u) ? (uint32_t)(v.stream_base + stream) : v.key0),
+          k1((v.flags & 1u) ? (uint32_t)((v.stream_base + stream) >> 32) : v.key1), stream_(stream),
+          ctr_hi_((v.flags & 1u) ? ((uint64_t)v.key1 << 32 | v.key0) : v.stream_base + stream),
           pos_(v.philox_pos[stream]) {}
     __device__ Philox4x32_10(uint32_t key0, uint32_t key1, uint64_t stream, uint64_t position)
         : k0(key0), k1(key1), stream_(stream), ctr_hi_(stream), pos_(position) {}

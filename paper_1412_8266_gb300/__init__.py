@@ -62,13 +62,13 @@ class Instance(ctypes.Structure):
 
 class SetDesc(ctypes.Structure):
     _fields_ = [("gen", ctypes.c_int), ("spacing", ctypes.c_int), ("n_streams", ctypes.c_uint64),
-                ("seed", ctypes.c_uint64), ("seed_state", ctypes.c_uint32 * 6)]
+                ("seed", ctypes.c_uint64), ("seed_state", ctypes.c_uint32 * 6), ("stream_base", ctypes.c_uint64)]
 
 
 class DevView(ctypes.Structure):
     _fields_ = [("gen", ctypes.c_int32), ("key0", ctypes.c_uint32), ("key1", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("n_streams", ctypes.c_uint64), ("mrg_state", ctypes.c_void_p),
-                ("philox_pos", ctypes.c_void_p)]
+                ("philox_pos", ctypes.c_void_p), ("stream_base", ctypes.c_uint64)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -98,6 +98,7 @@ _SIGS = {
     "srng_abi_version": (_int, []),
     "srng_create": (_int, [ctypes.POINTER(_vp), _int, _u64, _u64, _int, _vp]),
     "srng_create_from_state": (_int, [ctypes.POINTER(_vp), _vp, _u64, _int, _vp]),
+    "srng_create_range": (_int, [ctypes.POINTER(_vp), _int, _u64, _vp, _u64, _u64, _int, _vp]),
     "srng_destroy": (_int, [_vp]),
     "srng_reset": (_int, [_vp, _vp]),
     "srng_describe": (_int, [_vp, ctypes.POINTER(SetDesc)]),
@@ -227,6 +228,15 @@ def srng_create_from_state(state, n_streams: int, spacing: int = SRNG_SPACING_ST
     h = _vp()
     _check(load().srng_create_from_state(ctypes.byref(h), ctypes.addressof(st), n_streams, spacing,
                                          _stream(stream)), "srng_create_from_state")
+    return h.value
+
+
+def srng_create_range(gen: int, seed: int, stream_base: int, n_streams: int, spacing: int = SRNG_SPACING_STREAM,
+                      state=None, stream=None) -> int:
+    st = None if state is None else (ctypes.c_uint32 * 6)(*[int(x) for x in state])
+    h = _vp()
+    _check(load().srng_create_range(ctypes.byref(h), gen, seed, ctypes.addressof(st) if st is not None else None,
+                                    stream_base, n_streams, spacing, _stream(stream)), "srng_create_range")
     return h.value
 
 

@@ -162,14 +162,15 @@ static srng_status place_streams(srng_set *s, uint64_t first, uint64_t count, cu
     DeviceInfo dev;
     srng_status st = current_device(&dev);
     if (st) return st;
-    const int nbits = bit_length(first + count - 1);
+    const int nbits = bit_length(s->stream_base + first + count - 1);
     const JumpTable &tab = jump_table(spacing_shift(s->spacing), 1);
-    SRNG_CUDA_TRY(launch_mrg_place(s->d_state, s->n_streams, first, count, s->y0, tab, nbits, stream, dev));
+    SRNG_CUDA_TRY(launch_mrg_place(s->d_state, s->n_streams, first, count, s->stream_base, s->y0, tab, nbits, stream,
+                                   dev));
     return SRNG_OK;
 }
 
 static srng_status create_common(srng_set **out, srng_gen gen, uint64_t seed, const uint32_t *state,
-                                 uint64_t n_streams, srng_spacing spacing, void *cuda_stream)
+                                 uint64_t stream_base, uint64_t n_streams, srng_spacing spacing, void *cuda_stream)
 {
     if (!out) return fail(SRNG_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -177,6 +178,7 @@ static srng_status create_common(srng_set **out, srng_gen gen, uint64_t seed, co
     if (spacing != SRNG_SPACING_STREAM && spacing != SRNG_SPACING_SUBSTREAM)
         return fail(SRNG_ERR_ARG, "unknown spacing");
     if (n_streams == 0 || n_streams > (1ull << 40)) return fail(SRNG_ERR_ARG, "n_streams must be in [1, 2^40]");
+    if (stream_base > UINT64_MAX - (n_streams - 1)) return fail(SRNG_ERR_RANGE, "stream numbers would pass 2^64 - 1");
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     srng_set *s = new (std::nothrow) srng_set();
     if (!s) return fail(SRNG_ERR_OOM, "host allocation failed");
@@ -184,6 +186,7 @@ static srng_status create_common(srng_set **out, srng_gen gen, uint64_t seed, co
     s->gen = (srng_gen)kernel_gen(gen);
     s->spacing = spacing;
     s->n_streams = n_streams;
+    s->stream_base = stream_base;
     s->seed = seed;
     s->d_state = nullptr;
     s->d_pos = nullptr;
@@ -264,6 +267,7 @@ static srng_status generate_dev(srng_set *s, uint64_t b, uint64_t c, uint64_t n,
         SRNG_CUDA_TRY(launch_mrg_apply(s->d_state, s->n_streams, b, c, mat_pow_shifted(0, n, 0), stream, dev));
     } else {
         PhiloxGenArgs a;
+        a.stream_base = s->stream_base;
         a.k0 = s->key0;
         a.k1 = s->key1;
         a.keyed = s->keyed ? 1 : 0;
@@ -327,7 +331,19 @@ srng_status srng_create(srng_set **out, srng_gen gen, uint64_t seed, uint64_t n_
                         void *cuda_stream)
 {
     clear_error();
-    return create_common(out, gen, seed, nullptr, n_streams, spacing, cuda_stream);
+    return create_common(out, gen, seed, nullptr, 0, n_streams, spacing, cuda_stream);
+}
+
+srng_status srng_create_range(srng_set **out, srng_gen gen, uint64_t seed, const uint32_t state[6],
+                              uint64_t stream_base, uint64_t n_streams, srng_spacing spacing, void *cuda_stream)
+{
+    clear_error();
+    if (state) {
+        if (gen != SRNG_MRG32K3A) return fail(SRNG_ERR_ARG, "an explicit seed state is MRG32k3a only");
+        if (!state_valid(state))
+            return fail(SRNG_ERR_STATE, "seed state must have x1 words < m1, x2 words < m2, no all-zero component");
+    }
+    return create_common(out, gen, seed, state, stream_base, n_streams, spacing, cuda_stream);
 }
 
 srng_status srng_create_from_state(srng_set **out, const uint32_t state[6], uint64_t n_streams,
@@ -337,7 +353,7 @@ srng_status srng_create_from_state(srng_set **out, const uint32_t state[6], uint
     if (!state) return fail(SRNG_ERR_ARG, "state is NULL");
     if (!state_valid(state))
         return fail(SRNG_ERR_STATE, "seed state must have x1 words < m1, x2 words < m2, no all-zero component");
-    return create_common(out, SRNG_MRG32K3A, 0, state, n_streams, spacing, cuda_stream);
+    return create_common(out, SRNG_MRG32K3A, 0, state, 0, n_streams, spacing, cuda_stream);
 }
 
 srng_status srng_destroy(srng_set *set)
@@ -387,6 +403,7 @@ srng_status srng_describe(const srng_set *set, srng_set_desc *out)
     out->seed = set->seed;
     if (set->gen == SRNG_MRG32K3A) memcpy(out->seed_state, set->y0, sizeof set->y0);
     else { out->seed_state[0] = set->key0; out->seed_state[1] = set->key1; }
+    out->stream_base = set->stream_base;
     return SRNG_OK;
 }
 
@@ -402,6 +419,7 @@ srng_status srng_get_device_view(const srng_set *set, srng_dev_view *out)
     out->n_streams = set->n_streams;
     out->mrg_state = set->d_state;
     out->philox_pos = set->d_pos;
+    out->stream_base = set->stream_base;
     return SRNG_OK;
 }
 

@@ -422,9 +422,10 @@ srng_status batch_build(srng_set *const *sets, uint32_t n_sets, const srng_insta
         BatchInst b;
         memset(&b, 0, sizeof b);
         b.gen = s->gen;
-        b.key0 = s->keyed ? (uint32_t)x.stream : s->key0;
-        b.key1 = s->keyed ? (uint32_t)(x.stream >> 32) : s->key1;
-        b.ctr_hi = s->keyed ? ((uint64_t)s->key1 << 32 | s->key0) : x.stream;
+        const uint64_t gs = s->stream_base + x.stream;  // stream number
+        b.key0 = s->keyed ? (uint32_t)gs : s->key0;
+        b.key1 = s->keyed ? (uint32_t)(gs >> 32) : s->key1;
+        b.ctr_hi = s->keyed ? ((uint64_t)s->key1 << 32 | s->key0) : gs;
         b.stream = x.stream;
         b.offset = x.offset;
         b.length = x.length;
@@ -627,6 +628,7 @@ struct StaticSets {
     uint32_t gen[kStaticMaxSets];
     uint32_t key0[kStaticMaxSets], key1[kStaticMaxSets];
     uint32_t keyed[kStaticMaxSets];
+    uint64_t base[kStaticMaxSets];
     const uint32_t *state[kStaticMaxSets];
     uint64_t ns[kStaticMaxSets];
     const uint64_t *pos[kStaticMaxSets];
@@ -644,9 +646,10 @@ __global__ void __launch_bounds__(256)
     BatchInst b;
     memset(&b, 0, sizeof b);
     b.gen = sets.gen[si];
-    b.key0 = sets.keyed[si] ? (uint32_t)r.stream : sets.key0[si];
-    b.key1 = sets.keyed[si] ? (uint32_t)(r.stream >> 32) : sets.key1[si];
-    b.ctr_hi = sets.keyed[si] ? ((uint64_t)sets.key1[si] << 32 | sets.key0[si]) : r.stream;
+    const uint64_t gs = sets.base[si] + r.stream;  // stream number
+    b.key0 = sets.keyed[si] ? (uint32_t)gs : sets.key0[si];
+    b.key1 = sets.keyed[si] ? (uint32_t)(gs >> 32) : sets.key1[si];
+    b.ctr_hi = sets.keyed[si] ? ((uint64_t)sets.key1[si] << 32 | sets.key0[si]) : gs;
     b.stream = r.stream;
     b.offset = r.offset;
     b.length = r.length;
@@ -841,6 +844,7 @@ extern "C" srng_status srng_batch_run_static(srng_set *const *sets, uint32_t n_s
         ss.key0[k] = s->key0;
         ss.key1[k] = s->key1;
         ss.keyed[k] = s->keyed ? 1u : 0u;
+        ss.base[k] = s->stream_base;
         ss.state[k] = s->d_state;
         ss.ns[k] = s->n_streams;
         ss.pos[k] = s->d_pos;

@@ -279,8 +279,9 @@ __global__ void __launch_bounds__(256)
     for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         if (s_rel != cur) {  // a block's tiles stay in one stream for long runs
             cur = s_rel;
-            const uint64_t s = a.s_begin + s_rel;
-            const uint64_t p0 = a.pos[s];
+            const uint64_t slot = a.s_begin + s_rel;
+            const uint64_t p0 = a.pos[slot];
+            const uint64_t s = a.stream_base + slot;  // stream number
             al = (uint32_t)p0 & 3u;
             q0 = p0 >> 2;
             nb = (al + a.n + 3) >> 2;

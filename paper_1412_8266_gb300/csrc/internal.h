@@ -66,8 +66,10 @@ struct JumpTable {
 
 // ------------------------------------------------------------ kernels
 // K1: stream placement and jumps (jump.cu).
+// Slots [first, first + count) get streams index_base + slot: y0 times J_k for
+// every set bit k of the stream number.
 cudaError_t launch_mrg_place(uint32_t *state, uint64_t n_streams, uint64_t first, uint64_t count,
-                             const uint32_t y0[6], const JumpTable &tab, int nbits,
+                             uint64_t index_base, const uint32_t y0[6], const JumpTable &tab, int nbits,
                              cudaStream_t stream, const DeviceInfo &dev);
 cudaError_t launch_mrg_apply(uint32_t *state, uint64_t n_streams, uint64_t first, uint64_t count,
                              const MatPair &m, cudaStream_t stream, const DeviceInfo &dev);
@@ -88,6 +90,7 @@ cudaError_t launch_mrg_generate(const MrgGenArgs &a, srng_out type, const JumpTa
                                 const srng_tune &t, cudaStream_t stream, const DeviceInfo &dev);
 
 struct PhiloxGenArgs {
+    uint64_t stream_base; // stream number of the set's slot 0
     uint32_t k0, k1;      // the set's seed words
     int keyed;            // 0: key = (k0, k1), counter words 2-3 = stream; 1: key = stream, words 2-3 = (k0, k1)
     const uint64_t *pos;
@@ -148,6 +151,7 @@ struct srng_set {
     srng_gen gen;
     srng_spacing spacing;
     uint64_t n_streams;
+    uint64_t stream_base;    // stream number of slot 0 (a set may hold any range of streams)
     uint64_t seed;
     uint32_t y0[6];          // MRG32k3a seed state
     uint32_t key0, key1;     // Philox seed words (key, or counter words 2-3 when keyed)

@@ -19,18 +19,19 @@ namespace {
 constexpr int kThreads = 256;
 
 __global__ void __launch_bounds__(kThreads)
-    k_mrg_place(uint32_t *__restrict__ st, uint64_t ns, uint64_t first, uint64_t count,
+    k_mrg_place(uint32_t *__restrict__ st, uint64_t ns, uint64_t first, uint64_t count, uint64_t index_base,
                 uint32_t y0, uint32_t y1, uint32_t y2, uint32_t y3, uint32_t y4, uint32_t y5,
                 const __grid_constant__ JumpTable tab, int nbits)
 {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
-        const uint64_t idx = first + i;
+        const uint64_t slot = first + i;          // storage slot in the set
+        const uint64_t idx = index_base + slot;   // stream number in the whole sequence
         uint32_t s0 = y0, s1 = y1, s2 = y2, s3 = y3, s4 = y4, s5 = y5;
         for (int k = 0; k < nbits; ++k)
             if ((idx >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
-        st[0 * ns + idx] = s0; st[1 * ns + idx] = s1; st[2 * ns + idx] = s2;
-        st[3 * ns + idx] = s3; st[4 * ns + idx] = s4; st[5 * ns + idx] = s5;
+        st[0 * ns + slot] = s0; st[1 * ns + slot] = s1; st[2 * ns + slot] = s2;
+        st[3 * ns + slot] = s3; st[4 * ns + slot] = s4; st[5 * ns + slot] = s5;
     }
 }
 
@@ -68,12 +69,12 @@ unsigned grid_for(uint64_t count, const DeviceInfo &dev)
 }  // namespace
 
 cudaError_t launch_mrg_place(uint32_t *state, uint64_t n_streams, uint64_t first, uint64_t count,
-                             const uint32_t y0[6], const JumpTable &tab, int nbits,
+                             uint64_t index_base, const uint32_t y0[6], const JumpTable &tab, int nbits,
                              cudaStream_t stream, const DeviceInfo &dev)
 {
     if (count == 0) return cudaSuccess;
-    k_mrg_place<<<grid_for(count, dev), kThreads, 0, stream>>>(state, n_streams, first, count, y0[0], y0[1],
-                                                               y0[2], y0[3], y0[4], y0[5], tab, nbits);
+    k_mrg_place<<<grid_for(count, dev), kThreads, 0, stream>>>(state, n_streams, first, count, index_base, y0[0],
+                                                               y0[1], y0[2], y0[3], y0[4], y0[5], tab, nbits);
     return cudaGetLastError();
 }
 

@@ -192,9 +192,10 @@ srng_status launch_step(srng_server *srv, Slot &sl)
         BatchInst &b = sl.h_inst[n_inst];
         memset(&b, 0, sizeof b);
         b.gen = set->gen;
-        b.key0 = set->keyed ? (uint32_t)r.stream : set->key0;
-        b.key1 = set->keyed ? (uint32_t)(r.stream >> 32) : set->key1;
-        b.ctr_hi = set->keyed ? ((uint64_t)set->key1 << 32 | set->key0) : r.stream;
+        const uint64_t gs = set->stream_base + r.stream;  // stream number
+        b.key0 = set->keyed ? (uint32_t)gs : set->key0;
+        b.key1 = set->keyed ? (uint32_t)(gs >> 32) : set->key1;
+        b.ctr_hi = set->keyed ? ((uint64_t)set->key1 << 32 | set->key0) : gs;
         b.stream = r.stream;
         b.offset = r.pos + r.scheduled;
         b.length = take;

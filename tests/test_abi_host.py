@@ -115,3 +115,15 @@ def test_library_has_no_oracle_dependency(lib):
     assert "oracle" not in out
     ldd = subprocess.run(["ldd", srng.lib_path()], capture_output=True, text=True).stdout
     assert "liboracle" not in ldd
+
+
+def test_range_set_argument_errors(lib):
+    with pytest.raises(srng.SrngError) as e:
+        srng.srng_create_range(srng.SRNG_MRG32K3A, 1, 2**64 - 3, 5)
+    assert e.value.name == "SRNG_ERR_RANGE"
+    with pytest.raises(srng.SrngError) as e:
+        srng.srng_create_range(srng.SRNG_PHILOX4X32_10, 1, 0, 5, state=[1, 2, 3, 4, 5, 6])
+    assert e.value.name == "SRNG_ERR_ARG"
+    with pytest.raises(srng.SrngError) as e:
+        srng.srng_create_range(srng.SRNG_MRG32K3A, 1, 0, 5, state=[0, 0, 0, 4, 5, 6])
+    assert e.value.name == "SRNG_ERR_STATE"

@@ -272,3 +272,66 @@ def test_generate_into_host_memory(gen, pinned):
     finally:
         srng.srng_destroy(ha)
         srng.srng_destroy(hb)
+
+
+# ------------------------------------------------------------- stream ranges
+@pytest.mark.parametrize("base,spacing,e", [(1 << 40, srng.SRNG_SPACING_STREAM, 127),
+                                            (2**64 - 8, srng.SRNG_SPACING_STREAM, 127),
+                                            (123456789, srng.SRNG_SPACING_SUBSTREAM, 76)])
+def test_range_set_places_far_streams(base, spacing, e):
+    """A set holding streams [base, base + 8): far stream numbers (up to the
+    paper's 2^64 - 1) without the streams below them."""
+    seed = 0x5EED5EED5EED5EED
+    h = srng.srng_create_range(srng.SRNG_MRG32K3A, seed, base, 8, spacing)
+    try:
+        st = get_states(h, 0, 8)
+        ref = O.mrg_stream_starts(O.seed_expand(seed), e, base, 8)
+        assert np.array_equal(st, ref)
+        assert srng.srng_describe(h).stream_base == base
+        out = torch.empty(8 * 1000, dtype=torch.int32, device="cuda")
+        srng.srng_generate(h, 0, 8, 1000, srng.SRNG_OUT_U32, out)
+        torch.cuda.synchronize()
+        want, _ = O.mrg_bulk(ref, 1000, O.OUT_U32)
+        assert np.array_equal(out.cpu().numpy().view(np.uint32).reshape(8, 1000), want)
+    finally:
+        srng.srng_destroy(h)
+
+
+def test_range_set_equals_slice_of_full_set():
+    full = srng.srng_create_from_state([12345] * 6, 100, srng.SRNG_SPACING_STREAM)
+    part = srng.srng_create_range(srng.SRNG_MRG32K3A, 0, 60, 40, srng.SRNG_SPACING_STREAM, state=[12345] * 6)
+    try:
+        assert np.array_equal(get_states(full, 60, 40), get_states(part, 0, 40))
+    finally:
+        srng.srng_destroy(full)
+        srng.srng_destroy(part)
+
+
+@pytest.mark.parametrize("gen", [srng.SRNG_PHILOX4X32_10, srng.SRNG_PHILOX4X32_10_KEYED])
+def test_philox_range_set_top_stream_numbers(gen):
+    seed, base, n = 0x0123456789ABCDEF, 2**64 - 5, 777
+    h = srng.srng_create_range(gen, seed, base, 5, srng.SRNG_SPACING_STREAM)
+    try:
+        out = torch.empty(5 * n, dtype=torch.int32, device="cuda")
+        srng.srng_generate(h, 0, 5, n, srng.SRNG_OUT_U32, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint32).reshape(5, n)
+        for i in range(5):
+            if gen == srng.SRNG_PHILOX4X32_10:
+                ref = O.philox_generate((seed & 0xFFFFFFFF, seed >> 32), base + i, 0, n)
+            else:
+                ref = O.philox_keyed_generate(seed, base + i, 0, n)
+            assert np.array_equal(got[i], ref), i
+        # batch and server on the range set use the same stream numbers
+        inst = [srng.Instance(set_index=0, stream=i, offset=3, length=100, out_offset=100 * i) for i in range(5)]
+        b = torch.zeros(500, dtype=torch.int32, device="cuda")
+        srng.srng_batch_run([h], inst, srng.SRNG_BATCH_WRITE, srng.SRNG_OUT_U32, b)
+        bb = b.cpu().numpy().view(np.uint32).reshape(5, 100)
+        for i in range(5):
+            if gen == srng.SRNG_PHILOX4X32_10:
+                ref = O.philox_generate((seed & 0xFFFFFFFF, seed >> 32), base + i, n + 3, 100)
+            else:
+                ref = O.philox_keyed_generate(seed, base + i, n + 3, 100)
+            assert np.array_equal(bb[i], ref), i
+    finally:
+        srng.srng_destroy(h)
