@@ -315,6 +315,79 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Division by an invariant 32-bit d (Granlund & Montgomery, PLDI 1994): with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, for every 32-bit n,
+// t = umulhi(m, n) and n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0).
+struct Divider {
+    uint32_t d, m;
+    uint32_t sh1, sh2;
+};
+
+inline Divider make_divider(uint32_t d)
+{
+    uint32_t l = 0;
+    while (l < 32 && (1ull << l) < d) ++l;
+    Divider v;
+    v.d = d;
+    v.m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+    v.sh1 = l < 1 ? l : 1;
+    v.sh2 = l > 1 ? l - 1 : 0;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t divide(uint32_t n, const Divider &v)
+{
+    const uint32_t t = __umulhi(v.m, n);
+    return (t + ((n - t) >> v.sh1)) >> v.sh2;
+}
+
+// Flat Philox generation for many short streams: the work is the flat list of
+// (stream, block pair) with pps pairs per stream; consecutive lanes take
+// consecutive pairs, so a warp's 32-byte stores stay contiguous within a
+// stream and no lane idles at a stream's end beyond one pair.
+template <int OUT, int U, bool VEC>
+__global__ void __launch_bounds__(256)
+    k_philox_generate_flat(const PhiloxGenArgs a, uint32_t total_pairs, const Divider pps)
+{
+    using T = typename OutType<OUT>::T;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t p0 = blockIdx.x * blockDim.x + threadIdx.x; p0 < total_pairs; p0 += U * stride) {
+        uint32_t x[U][8];
+        uint64_t bb[U];
+        uint32_t srel[U], al[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {  // U independent pairs (2U Philox blocks) in flight
+            const uint32_t p = p0 + u * stride;
+            const uint32_t s_rel = p < total_pairs ? divide(p, pps) : 0u;
+            const uint64_t b = 2ull * (p - s_rel * pps.d);  // first block of the pair
+            const uint64_t slot = a.s_begin + s_rel;
+            const uint64_t pos = a.pos[slot];
+            al[u] = (uint32_t)pos & 3u;
+            ok[u] = p < total_pairs && b < ((al[u] + a.n + 3) >> 2);
+            srel[u] = s_rel;
+            bb[u] = b;
+            const uint64_t s = a.stream_base + slot;
+            uint32_t kk0 = a.k0, kk1 = a.k1, c2, c3;
+            if (a.keyed) { kk0 = (uint32_t)s; kk1 = (uint32_t)(s >> 32); c2 = a.k0; c3 = a.k1; }
+            else { c2 = (uint32_t)s; c3 = (uint32_t)(s >> 32); }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint64_t q = (pos >> 2) + b + h;
+                x[u][4 * h] = (uint32_t)q; x[u][4 * h + 1] = (uint32_t)(q >> 32);
+                x[u][4 * h + 2] = c2; x[u][4 * h + 3] = c3;
+                srng::philox::block(x[u][4 * h], x[u][4 * h + 1], x[u][4 * h + 2], x[u][4 * h + 3], kk0, kk1);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (!ok[u]) continue;
+            T *row = static_cast<T *>(a.out) + (uint64_t)srel[u] * a.n;
+            store8<SRNG_PHILOX4X32_10, OUT, VEC>(row, (int64_t)(bb[u] * 4) - al[u], a.n, x[u]);
+        }
+    }
+}
+
 // ---------------------------------------------------------- conversion
 template <int GEN, int OUT>
 __global__ void __launch_bounds__(256) k_convert(const uint32_t *__restrict__ in, uint64_t n,
@@ -395,6 +468,27 @@ cudaError_t philox_dispatch_u(const PhiloxGenArgs &a, const srng_tune &t, cudaSt
 template <int OUT>
 cudaError_t philox_dispatch(const PhiloxGenArgs &a, const srng_tune &t, cudaStream_t stream, const DeviceInfo &dev)
 {
+    // Many short streams: the flat kernel (no idle lanes at stream ends), when
+    // the pair count fits 32 bits and a stream is shorter than one tile.
+    const uint64_t pps = ((a.n + 3) / 4 + 2) / 2;  // block pairs per stream, any start alignment
+    const uint32_t threads = t.block_threads ? t.block_threads : 256;
+    const uint64_t tile_pairs = (uint64_t)threads * (t.unroll ? t.unroll : 4);
+    if (a.s_count > 1 && pps < tile_pairs && a.s_count * pps < (1ull << 32)) {
+        const uint32_t total = (uint32_t)(a.s_count * pps);
+        uint64_t blocks = (total + threads - 1) / threads;
+        const uint64_t cap = (uint64_t)dev.sm_count * (t.blocks_per_sm ? t.blocks_per_sm : 2048 / threads);
+        if (blocks > cap) blocks = cap;
+        const Divider dv = make_divider((uint32_t)pps);
+        const bool vec = t.vector_store != 2;
+        if (t.unroll == 1) {
+            if (vec) k_philox_generate_flat<OUT, 1, true><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
+            else k_philox_generate_flat<OUT, 1, false><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
+        } else {
+            if (vec) k_philox_generate_flat<OUT, 2, true><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
+            else k_philox_generate_flat<OUT, 2, false><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
+        }
+        return cudaGetLastError();
+    }
     switch (t.unroll) {
     case 1: return philox_dispatch_u<OUT, 1>(a, t, stream, dev);
     case 4: return philox_dispatch_u<OUT, 4>(a, t, stream, dev);
