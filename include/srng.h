@@ -99,8 +99,12 @@ typedef struct srng_set srng_set;
  *                   is split into chunks whose start states are reached by
  *                   jump-ahead); multiple of 32
  *   unroll        : Philox blocks per thread per loop trip (1, 2 or 4)
- *   vector_store  : 1 = 16-byte stores where the output alignment allows,
- *                   2 = never (element stores, always coalesced)
+ *   vector_store  : 1 = wide (16/32-byte) stores where the output alignment
+ *                   allows, staged through shared memory so each warp store
+ *                   covers whole 128-byte lines; 2 = never (element stores,
+ *                   always coalesced); 3 = MRG32k3a whole-chunk rows written
+ *                   by each lane directly with 32-byte stores (one full
+ *                   sector per lane), else as 1
  *   lane_blocks   : batched launches only: Philox blocks each lane computes
  *                   per work item (a Philox work item covers 32 x lane_blocks
  *                   blocks of one instance); MRG32k3a work items are 32

@@ -9,6 +9,7 @@ and device (name and SM count).
 
 Search spaces (all values valid for every problem):
   MRG32k3a  block_threads x resident blocks/SM x chunk (draws per thread item)
+            x store path (shared-memory staged rows or direct per-lane rows)
   Philox    block_threads x unroll (blocks per thread per trip) x blocks/SM
   batch     chunk (MRG32k3a) x lane_blocks (Philox) per work item
 """
@@ -22,8 +23,8 @@ import time
 
 import paper_1412_8266_gb300 as srng
 
-MRG_SPACE = [dict(block_threads=bt, blocks_per_sm=b, chunk=c)
-             for bt, b, c in itertools.product((128, 256), (4, 5, 8), (512, 1024, 2048, 4096))]
+MRG_SPACE = [dict(block_threads=bt, blocks_per_sm=b, chunk=c, vector_store=v)
+             for bt, b, c, v in itertools.product((128, 256), (4, 8), (512, 1024, 2048, 4096), (1, 3))]
 PHILOX_SPACE = [dict(block_threads=bt, unroll=u, blocks_per_sm=b)
                 for bt, u, b in itertools.product((128, 256), (1, 2, 4), (4, 8))]
 BATCH_SPACE = [dict(chunk=c, lane_blocks=lb) for c, lb in itertools.product((256, 512, 1024), (32, 64, 128))]

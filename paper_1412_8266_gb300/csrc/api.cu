@@ -114,7 +114,7 @@ srng_status check_tune(const srng_tune *t)
     if (t->chunk && t->chunk % 32) return fail(SRNG_ERR_ARG, "tune.chunk must be a multiple of 32");
     if (t->unroll && t->unroll != 1 && t->unroll != 2 && t->unroll != 4)
         return fail(SRNG_ERR_ARG, "tune.unroll must be 1, 2 or 4");
-    if (t->vector_store > 2) return fail(SRNG_ERR_ARG, "tune.vector_store must be 0, 1 or 2");
+    if (t->vector_store > 3) return fail(SRNG_ERR_ARG, "tune.vector_store must be 0, 1, 2 or 3");
     if (t->lane_blocks > 4096) return fail(SRNG_ERR_ARG, "tune.lane_blocks must be <= 4096");
     return SRNG_OK;
 }

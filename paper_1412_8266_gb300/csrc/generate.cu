@@ -204,6 +204,39 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
 }
 
+// K2, uniform rows, direct: each lane writes its own row with 32-byte stores
+// straight from registers -- every store fills one whole 32-byte sector, 32
+// sectors per warp instruction, no shared-memory transpose.  Same preconditions
+// as k_mrg_generate_rows.
+template <int OUT, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_mrg_generate_direct(const MrgGenArgs a, const __grid_constant__ JumpTable tab)
+{
+    using T = typename OutType<OUT>::T;
+    constexpr int EPQ = 32 / sizeof(T);  // values per 32-byte store
+    T *out = static_cast<T *>(a.out);
+    const uint64_t n_items = a.s_count * a.cps;
+    const uint64_t stride = (uint64_t)gridDim.x * WARPS * 32;
+    for (uint64_t item = (uint64_t)blockIdx.x * WARPS * 32 + threadIdx.x; item < n_items; item += stride) {
+        const uint64_t s_rel = item / a.cps;
+        const uint64_t t = item - s_rel * a.cps;
+        const uint64_t s = a.s_begin + s_rel;
+        const uint64_t ns = a.n_streams;
+        uint32_t s0 = a.state[s], s1 = a.state[ns + s], s2 = a.state[2 * ns + s];
+        uint32_t s3 = a.state[3 * ns + s], s4 = a.state[4 * ns + s], s5 = a.state[5 * ns + s];
+        for (int k = 0; k < a.nbits; ++k)
+            if ((t >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
+        T *dst = out + item * a.chunk;
+        for (uint64_t j = 0; j < a.chunk; j += EPQ) {
+            T v[EPQ];
+#pragma unroll
+            for (int e = 0; e < EPQ; ++e) v[e] = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+            const uint4 *p = reinterpret_cast<const uint4 *>(v);
+            st256(dst + j, p[0], p[1]);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ K3
 template <int GEN, int OUT, bool VEC>
 __device__ __forceinline__ void store4(typename OutType<OUT>::T *row, int64_t k0, uint64_t n, uint32_t w0,
@@ -423,8 +456,13 @@ cudaError_t mrg_dispatch_rows(const MrgGenArgs &a, const JumpTable &tab, const s
     uint64_t cap = (uint64_t)dev.sm_count * (t.blocks_per_sm ? t.blocks_per_sm : 5);
     if (blocks > cap) blocks = cap;
     if (blocks == 0) blocks = 1;
-    if (warps == 8) k_mrg_generate_rows<OUT, 8><<<(unsigned)blocks, 256, 0, stream>>>(a, tab);
-    else k_mrg_generate_rows<OUT, 4><<<(unsigned)blocks, 128, 0, stream>>>(a, tab);
+    if (t.vector_store == 3) {
+        if (warps == 8) k_mrg_generate_direct<OUT, 8><<<(unsigned)blocks, 256, 0, stream>>>(a, tab);
+        else k_mrg_generate_direct<OUT, 4><<<(unsigned)blocks, 128, 0, stream>>>(a, tab);
+    } else {
+        if (warps == 8) k_mrg_generate_rows<OUT, 8><<<(unsigned)blocks, 256, 0, stream>>>(a, tab);
+        else k_mrg_generate_rows<OUT, 4><<<(unsigned)blocks, 128, 0, stream>>>(a, tab);
+    }
     return cudaGetLastError();
 }
 

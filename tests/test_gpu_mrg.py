@@ -105,10 +105,13 @@ def test_chunked_and_unaligned_vs_oracle(sets, out_type, pad, chunk):
     assert np.array_equal(get_states(h, 0, S), final)
 
 
+@pytest.mark.parametrize("n", [4096, 5000])
 @pytest.mark.parametrize("tune", [dict(chunk=32), dict(chunk=4096), dict(block_threads=128),
-                                  dict(vector_store=2), dict(blocks_per_sm=1, chunk=512)])
-def test_tuning_never_changes_output(sets, tune):
-    S, n = 300, 5000
+                                  dict(vector_store=2), dict(blocks_per_sm=1, chunk=512),
+                                  dict(vector_store=3, chunk=512), dict(vector_store=3, chunk=4096),
+                                  dict(vector_store=3, chunk=32, block_threads=128)])
+def test_tuning_never_changes_output(sets, tune, n):
+    S = 300
     outs = []
     for t in (None, tune):
         h = sets(srng.srng_create(srng.SRNG_MRG32K3A, 77, S))
