@@ -16,6 +16,9 @@ Parity status per function (what pins it is in tests/test_oracle_pins.py):
   philox4x32_10 / philox_word                             pinned
   to_f32 / mrg_to_f64 / philox_to_f64                     pinned
   pi hit tests / pi counts                                pinned
+  dist_constants / ln_unit_f32 / sincos_2pi_f32 / transform  pinned (exhaustive
+      over the 2^24 FP32 uniforms against float64 libm, constants against
+      exact rationals, distribution tests)
   seed_expand (SplitMix64)                                structure pinned; the two
       mixing multipliers are parity unpinned (no implementation in this
       environment to compare with, and the paper is silent on seeding)
@@ -78,6 +81,12 @@ def _load(path: str | None = None):
             "oracle_philox_word": (u32, [u32, u32, u64, u64]),
             "oracle_to_f32": (ctypes.c_float, [u32]),
             "oracle_mrg_to_f64": (ctypes.c_double, [u32]),
+            "oracle_dist_constants": (None, [ctypes.POINTER(ctypes.c_float)]),
+            "oracle_ln_unit_f32": (ctypes.c_float, [ctypes.c_float]),
+            "oracle_sincos_2pi_f32": (None, [ctypes.c_float, ctypes.POINTER(ctypes.c_float),
+                                             ctypes.POINTER(ctypes.c_float)]),
+            "oracle_transform": (None, [i32, vp, u64, vp]),
+            "oracle_sincos_2pi_array": (None, [vp, u64, vp, vp]),
             "oracle_philox_to_f64": (ctypes.c_double, [u32]),
             "oracle_mrg_generate": (None, [u32p, u64, i32, vp]),
             "oracle_philox_generate": (None, [u32, u32, u64, u64, u64, i32, vp]),
@@ -297,6 +306,45 @@ def batch(gens, mrg_states, key, philox_streams, philox_pos, lengths, out_offset
     _load().oracle_batch(n, vp(g), vp(ms), key[0], key[1], vp(ps), vp(pp), vp(ln), vp(oo), mode,
                          out_type, outp, vp(counts), threads)
     return out if mode == 0 else counts
+
+
+DIST_EXPONENTIAL, DIST_NORMAL = 0, 1
+
+
+def dist_constants() -> dict:
+    """The single-precision constants the variate transforms use."""
+    buf = (ctypes.c_float * 18)()
+    _load().oracle_dist_constants(buf)
+    v = list(buf)
+    return {"ln2_hi": v[0], "ln2_lo": v[1], "inv_odd": v[2:8], "sc": [None] + v[8:18]}
+
+
+def ln_unit_f32(x: float) -> float:
+    return float(_load().oracle_ln_unit_f32(x))
+
+
+def sincos_2pi_f32(u: float):
+    s, c = ctypes.c_float(), ctypes.c_float()
+    _load().oracle_sincos_2pi_f32(u, ctypes.byref(s), ctypes.byref(c))
+    return s.value, c.value
+
+
+def sincos_2pi_array(u: np.ndarray):
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    s, c = np.empty_like(u), np.empty_like(u)
+    _load().oracle_sincos_2pi_array(u.ctypes.data, u.size, s.ctypes.data, c.ctypes.data)
+    return s, c
+
+
+def transform(dist: int, u: np.ndarray) -> np.ndarray:
+    """Exponential (dist 0) or Box-Muller normal (dist 1, even length)
+    variates from FP32 uniforms in [0, 1)."""
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    if dist == DIST_NORMAL and u.size % 2:
+        raise ValueError("normal variates come in pairs")
+    out = np.empty_like(u)
+    _load().oracle_transform(dist, u.ctypes.data, u.size, out.ctypes.data)
+    return out
 
 
 def max_threads() -> int:

@@ -412,6 +412,149 @@ void oracle_batch(uint64_t n_inst, const int32_t *gens, const uint32_t *mrg_stat
     }
 }
 
+/* ---------------------------------------------------------------------- */
+/* Non-uniform variates from FP32 uniforms (beyond the paper, which covers  */
+/* uniform draws only): exponential by inversion, normal by Box & Muller    */
+/* (1958).  The reading taken: single precision throughout, every step one  */
+/* correctly rounded IEEE single operation or fused multiply-add, so that a */
+/* device following the same steps agrees bit for bit.  ln, sin and cos are */
+/* written out here from their series, not taken from libm:                 */
+/*   ln x  = e ln2 + 2 atanh(s), x = 2^e m, m in [sqrt(1/2), sqrt(2)],      */
+/*           s = (m-1)/(m+1), atanh(s) = s + s^3/3 + ... + s^11/11, the     */
+/*           leading 2s added last,                                         */
+/*           ln2 = hi + lo, hi = its leading 15 bits (Cody & Waite 1980);   */
+/*   sin/cos(2 pi u): 4u = q + r, quadrant q, r in [0,1), r -> 1 - r with   */
+/*           sin and cos exchanged when r > 1/2, then the Taylor series of  */
+/*           sin((pi/2) r) to r^9 and cos((pi/2) r) to r^10.               */
+/* Domain: uniforms in [0, 1).                                              */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    float ln2_hi, ln2_lo;
+    float inv_odd[6];   /* 1/1, 1/3, ..., 1/11 */
+    float sc[11];       /* sc[n] = (-1)^floor(n/2) (pi/2)^n / n!, n = 1..10 */
+} orc_dist_k;
+
+static void orc_dist_init(orc_dist_k *k)
+{
+    const double ln2 = log(2.0);
+    const double hi = ldexp(floor(ldexp(ln2, 15)), -15);
+    k->ln2_hi = (float)hi;
+    k->ln2_lo = (float)(ln2 - hi);
+    for (int j = 0; j < 6; ++j) k->inv_odd[j] = 1.0f / (float)(2 * j + 1);
+    /* (pi/2)^n / n! by the ratio of successive terms: t_n = t_(n-1) (pi/2) / n */
+    const double half_pi = acos(-1.0) / 2.0;
+    double t = 1.0;
+    k->sc[0] = 1.0f;
+    for (int n = 1; n <= 10; ++n) {
+        t = t * half_pi / (double)n;
+        k->sc[n] = (float)(((n / 2) % 2) ? -t : t);
+    }
+}
+
+/* The constants as used: out[0] = ln2 hi, out[1] = ln2 lo,
+ * out[2 + j] = 1/(2j+1) for j = 0..5, out[8 + n - 1] = sc[n] for n = 1..10. */
+void oracle_dist_constants(float out[18])
+{
+    orc_dist_k k;
+    orc_dist_init(&k);
+    out[0] = k.ln2_hi;
+    out[1] = k.ln2_lo;
+    for (int j = 0; j < 6; ++j) out[2 + j] = k.inv_odd[j];
+    for (int n = 1; n <= 10; ++n) out[8 + n - 1] = k.sc[n];
+}
+
+static float orc_ln(const orc_dist_k *k, float x)
+{
+    uint32_t bits;
+    memcpy(&bits, &x, 4);
+    int e = (int)((bits >> 23) & 0xFFu) - 127;
+    uint32_t mbits = (bits & 0x007FFFFFu) | 0x3F800000u;   /* m in [1, 2) */
+    float m;
+    memcpy(&m, &mbits, 4);
+    if ((double)m * (double)m > 2.0) {                      /* m > sqrt 2 */
+        m = m * 0.5f;
+        e = e + 1;
+    }
+    float s = (m - 1.0f) / (m + 1.0f);
+    float s2 = s * s;
+    float p = k->inv_odd[5];
+    for (int j = 4; j >= 1; --j) p = fmaf(p, s2, k->inv_odd[j]);
+    /* 2 atanh(s) = 2s + 2s (s^2/3 + s^4/5 + ... + s^10/11) */
+    float ln_m = fmaf(2.0f * s, s2 * p, 2.0f * s);
+    float ef = (float)e;
+    return fmaf(ef, k->ln2_hi, fmaf(ef, k->ln2_lo, ln_m));
+}
+
+static void orc_sincos_2pi(const orc_dist_k *k, float u, float *sin_out, float *cos_out)
+{
+    float v = u * 4.0f;
+    int q = (int)v;
+    float r = v - (float)q;
+    int exchanged = r > 0.5f;
+    if (exchanged) r = 1.0f - r;
+    float r2 = r * r;
+    float ps = k->sc[9];
+    for (int n = 7; n >= 1; n -= 2) ps = fmaf(ps, r2, k->sc[n]);
+    float pc = k->sc[10];
+    for (int n = 8; n >= 2; n -= 2) pc = fmaf(pc, r2, k->sc[n]);
+    float sin_r = ps * r;                 /* sin((pi/2) r) */
+    float cos_r = fmaf(pc, r2, 1.0f);     /* cos((pi/2) r) */
+    float sn = exchanged ? cos_r : sin_r;
+    float cs = exchanged ? sin_r : cos_r;
+    /* sin and cos of q pi/2 + phi */
+    if (q % 4 == 0) { *sin_out = sn; *cos_out = cs; }
+    else if (q % 4 == 1) { *sin_out = cs; *cos_out = -sn; }
+    else if (q % 4 == 2) { *sin_out = -sn; *cos_out = -cs; }
+    else { *sin_out = -cs; *cos_out = sn; }
+}
+
+float oracle_ln_unit_f32(float x)
+{
+    orc_dist_k k;
+    orc_dist_init(&k);
+    return orc_ln(&k, x);
+}
+
+void oracle_sincos_2pi_f32(float u, float *s, float *c)
+{
+    orc_dist_k k;
+    orc_dist_init(&k);
+    orc_sincos_2pi(&k, u, s, c);
+}
+
+void oracle_sincos_2pi_array(const float *u, uint64_t n, float *s, float *c)
+{
+    orc_dist_k k;
+    orc_dist_init(&k);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < (int64_t)n; ++i) orc_sincos_2pi(&k, u[i], &s[i], &c[i]);
+}
+
+enum { ORC_DIST_EXPONENTIAL = 0, ORC_DIST_NORMAL = 1 };
+
+/* dist 0: out[i] = -ln(1 - in[i]);
+ * dist 1: out[2j] = r cos t, out[2j+1] = r sin t with
+ *         r = sqrt(-2 ln(1 - in[2j])), t = 2 pi in[2j+1]   (n even). */
+void oracle_transform(int dist, const float *in, uint64_t n, float *out)
+{
+    orc_dist_k k;
+    orc_dist_init(&k);
+    if (dist == ORC_DIST_EXPONENTIAL) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < (int64_t)n; ++i) out[i] = 0.0f - orc_ln(&k, 1.0f - in[i]);
+    } else {
+#pragma omp parallel for schedule(static)
+        for (int64_t j = 0; j < (int64_t)(n / 2); ++j) {
+            float r = sqrtf(-2.0f * orc_ln(&k, 1.0f - in[2 * j]));
+            float s, c;
+            orc_sincos_2pi(&k, in[2 * j + 1], &s, &c);
+            out[2 * j] = r * c;
+            out[2 * j + 1] = r * s;
+        }
+    }
+}
+
 int oracle_max_threads(void)
 {
 #ifdef _OPENMP

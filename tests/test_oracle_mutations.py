@@ -41,6 +41,15 @@ MUTATIONS = {
     "pi threshold philox": ("return a * a + b * b < ((unsigned __int128)1 << 48);",
                             "return a * a + b * b < ((unsigned __int128)1 << 47);"),
     "pi radius mrg": ("unsigned __int128 a = z0, b = z1, r = ORC_M1 + 1;", "unsigned __int128 a = z0, b = z1, r = ORC_M1;"),
+    "ln2 low part sign": ("k->ln2_lo = (float)(ln2 - hi);", "k->ln2_lo = (float)(hi - ln2);"),
+    "atanh series term": ("k->inv_odd[j] = 1.0f / (float)(2 * j + 1);", "k->inv_odd[j] = 1.0f / (float)(2 * j + 3);"),
+    "ln leading term": ("float ln_m = fmaf(2.0f * s, s2 * p, 2.0f * s);", "float ln_m = fmaf(2.0f * s, s2 * p, s);"),
+    "taylor sign": ("k->sc[n] = (float)(((n / 2) % 2) ? -t : t);", "k->sc[n] = (float)((n % 2) ? -t : t);"),
+    "quadrant order": ("else if (q % 4 == 1) { *sin_out = cs; *cos_out = -sn; }",
+                       "else if (q % 4 == 1) { *sin_out = cs; *cos_out = sn; }"),
+    "reflection": ("if (exchanged) r = 1.0f - r;", "if (exchanged) r = r - 0.5f;"),
+    "box-muller radius": ("float r = sqrtf(-2.0f * orc_ln(&k, 1.0f - in[2 * j]));",
+                          "float r = sqrtf(-2.0f * orc_ln(&k, in[2 * j]));"),
 }
 
 
@@ -144,6 +153,22 @@ def _pins_fail(ref):
         # output range
         z, _ = O.mrg_generate([7, 8, 9, 10, 11, 12], 2000)
         if z.min() < 1 or int(z.max()) > O.M1:
+            return True
+        # variates: float64 libm on a strided subset of the FP32 uniforms
+        u = np.arange(1, 1 << 24, 251, dtype=np.float64) * 2.0**-24
+        sp = lambda r: np.spacing(np.abs(r).astype(np.float32)).astype(np.float64)
+        ref = -np.log1p(-u)
+        if np.any(np.abs(O.transform(O.DIST_EXPONENTIAL, u.astype(np.float32)) - ref) > 2 * sp(ref)):
+            return True
+        s, c = O.sincos_2pi_array(u.astype(np.float32))
+        t = 2 * np.pi * u
+        if np.any(np.abs(s - np.sin(t)) > 2 * sp(np.sin(t)) + 1e-12) or \
+                np.any(np.abs(c - np.cos(t)) > 2 * sp(np.cos(t)) + 1e-12):
+            return True
+        w = u[: (u.size // 2) * 2].astype(np.float32)
+        g = O.transform(O.DIST_NORMAL, w).astype(np.float64)
+        r = np.sqrt(-2 * np.log1p(-w[0::2].astype(np.float64)))
+        if np.any(np.abs(g[0::2] - r * np.cos(2 * np.pi * w[1::2].astype(np.float64))) > 4 * sp(r) + 1e-12):
             return True
         return False
     except Exception:
