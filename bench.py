@@ -402,8 +402,20 @@ def extras(torch, srng, dev, stream, peak):
         ph[name] = {"ms_best": best, "ms_median": med, "Guniforms_s": n / best / 1e6, "GB_s": n * 4 / best / 1e6,
                     "frac_of_copy_peak": n * 4 / best / 1e6 / peak}
         del o
+    # Variates: 2^30 FP32 Philox uniforms -> exponential / normal (read 4 B, write 4 B per value)
+    u = torch.empty(n, dtype=torch.float32, device=dev)
+    srng.srng_reset(h, stream)
+    srng.srng_generate_tuned(h, 0, 1, n, srng.SRNG_OUT_F32, u, tunes[srng.SRNG_OUT_F32], stream)
+    z = torch.empty_like(u)
+    var = {}
+    for name, d in (("exponential", srng.SRNG_DIST_EXPONENTIAL), ("normal", srng.SRNG_DIST_NORMAL)):
+        best, med = _time(torch, stream, lambda: srng.srng_transform(d, u, n, z, stream))
+        var[name] = {"ms_best": best, "ms_median": med, "Gvariates_s": n / best / 1e6, "GB_s": n * 8 / best / 1e6,
+                     "frac_of_copy_peak": n * 8 / best / 1e6 / peak}
+    del u, z
     srng.srng_destroy(h)
     res["philox_bulk_2^30"] = ph
+    res["variates_2^30_f32"] = var
     # Philox layouts at the many-stream shape (2^18 streams x 4096 words, uint32):
     # counter split (one key) vs keyed (key = stream, Sec. 4.3)
     lay = {}
@@ -518,6 +530,15 @@ def run_case(args):
         o = torch.empty(n, dtype=torch.int32 if t == 0 else torch.float32, device=dev)
         fn = lambda: srng.srng_generate(h, 0, 1, n, t, o, stream)
         nbytes, nvals = n * 4, n
+    elif c.startswith("transform"):
+        n = (1 << 30) // k
+        d = srng.SRNG_DIST_NORMAL if c == "transform_normal" else srng.SRNG_DIST_EXPONENTIAL
+        h = srng.srng_create(srng.SRNG_PHILOX4X32_10, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
+        u = torch.empty(n, dtype=torch.float32, device=dev)
+        srng.srng_generate(h, 0, 1, n, srng.SRNG_OUT_F32, u, stream)
+        o = torch.empty_like(u)
+        fn = lambda: srng.srng_transform(d, u, n, o, stream)
+        nbytes, nvals = n * 8, n
     else:
         gens, lengths, outoff = W.batched_instances(n_inst=W.BATCHED["n_inst"] // k)
         ni = len(gens)
@@ -539,7 +560,8 @@ def run_case(args):
     return 0
 
 
-CASES = {"mrg_u32", "mrg_f64", "philox_u32", "philox_f32", "batch_write", "batch_pi"}
+CASES = {"mrg_u32", "mrg_f64", "philox_u32", "philox_f32", "batch_write", "batch_pi", "transform_exponential",
+         "transform_normal"}
 
 
 def main():

@@ -261,6 +261,23 @@ typedef struct srng_dev_view {
 } srng_dev_view;
 srng_status srng_get_device_view(const srng_set *set, srng_dev_view *out);
 
+/* Non-uniform variates from FP32 uniforms (SRNG_OUT_F32 outputs of either
+ * generator; the paper itself covers uniforms only).
+ *   SRNG_DIST_EXPONENTIAL: out[i] = -ln(1 - in[i]), rate 1;
+ *   SRNG_DIST_NORMAL: Box-Muller on the pairs (in[2k], in[2k+1]):
+ *     r = sqrt(-2 ln(1 - in[2k])), t = 2 pi in[2k+1],
+ *     out[2k] = r cos t, out[2k+1] = r sin t (n must be even).
+ * ln, sin and cos are this library's own (srng_device.cuh, srng::dist), every
+ * step one correctly rounded IEEE single operation or fused multiply-add, so
+ * the results are reproducible bit for bit on any IEEE machine that follows
+ * the same steps; in and out may be the same buffer.  Inputs must lie in
+ * [0, 1).  Asynchronous on cuda_stream. */
+typedef enum srng_dist {
+    SRNG_DIST_EXPONENTIAL = 0,
+    SRNG_DIST_NORMAL = 1
+} srng_dist;
+srng_status srng_transform(srng_dist dist, const float *in_dev, uint64_t n, float *out_dev, void *cuda_stream);
+
 /* ------------------------------------------------------------ host maths */
 
 /* The SplitMix64 seed expansion used by srng_create (pure host function). */

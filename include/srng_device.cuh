@@ -309,6 +309,112 @@ class Philox4x32_10 {
     uint64_t stream_, ctr_hi_, pos_;
 };
 
+/* --------------------------------------------- non-uniform variates (FP32) */
+
+/* Exponential and normal variates from the FP32 uniforms, computed with this
+ * header's own elementary functions so that every machine that follows the
+ * same IEEE-754 single operations (each product, sum, quotient and square root
+ * rounded to nearest even; fused multiply-adds rounded once) gets the same
+ * bits.  Every operation below is an explicit correctly rounded intrinsic, so
+ * the compiler cannot contract or reorder it.  Accuracy: a few units in the
+ * last place against the exact functions. */
+namespace dist {
+
+/* Non-uniform variates from FP32 uniforms.  Every step below is one correctly
+ * rounded IEEE single operation (add, multiply, divide, square root) or fused
+ * multiply-add, so a CPU that takes the same steps gets the same bits.
+ *
+ * ln_unit: natural logarithm of x in (0, 1], Cody & Waite style.  x = 2^e m
+ * with m in [sqrt(1/2), sqrt(2)); ln m = 2 atanh(s), s = (m - 1) / (m + 1),
+ * |s| <= 0.1716, by the odd series 2 (s + s^3/3 + ... + s^11/11) (truncation
+ * below 2^-33 relative), its leading term 2s added last; ln x = e ln2 + ln m with ln2 split into hi, its
+ * leading 15 bits (e hi is exact for |e| < 512), and lo = ln2 - hi. */
+__device__ __forceinline__ float ln_unit(float x)
+{
+    const uint32_t bits = __float_as_uint(x);
+    int e = (int)((bits >> 23) & 0xFFu) - 127;
+    float m = __uint_as_float((bits & 0x007FFFFFu) | 0x3F800000u);  /* [1, 2) */
+    if (m > 1.41421356237309504880f) { m = __fmul_rn(m, 0.5f); e += 1; }
+    const float f = __fadd_rn(m, -1.0f);                              /* exact */
+    const float sv = __fdiv_rn(f, __fadd_rn(m, 1.0f));
+    const float z = __fmul_rn(sv, sv);
+    float p = (float)(1.0 / 11.0);
+    p = __fmaf_rn(p, z, (float)(1.0 / 9.0));
+    p = __fmaf_rn(p, z, (float)(1.0 / 7.0));
+    p = __fmaf_rn(p, z, (float)(1.0 / 5.0));
+    p = __fmaf_rn(p, z, (float)(1.0 / 3.0));
+    const float s2 = __fmul_rn(2.0f, sv);                              /* exact */
+    const float lnm = __fmaf_rn(s2, __fmul_rn(z, p), s2);              /* leading term last */
+    const float ef = (float)e;                                         /* |e| <= 150 */
+    constexpr float kLn2Hi = 0.693145751953125f;                       /* 22713 / 2^15 */
+    constexpr float kLn2Lo = (float)(0.69314718055994530942 - 0.693145751953125);
+    return __fmaf_rn(ef, kLn2Hi, __fmaf_rn(ef, kLn2Lo, lnm));
+}
+
+/* Taylor coefficients of sin((pi/2) r) and cos((pi/2) r) in r:
+ * coef(n) = (-1)^(n/2) (pi/2)^n / n!, evaluated in double, rounded once to float. */
+namespace detail_sc {
+constexpr double kHalfPi = 3.14159265358979323846 / 2.0;
+constexpr double pw(int n) { return n == 0 ? 1.0 : kHalfPi * pw(n - 1); }
+constexpr double fact(int n) { return n <= 1 ? 1.0 : n * fact(n - 1); }
+constexpr float coef(int n) { return (float)(((n / 2) % 2 ? -1.0 : 1.0) * pw(n) / fact(n)); }
+constexpr float kS1 = coef(1), kS3 = coef(3), kS5 = coef(5), kS7 = coef(7), kS9 = coef(9);
+constexpr float kC2 = coef(2), kC4 = coef(4), kC6 = coef(6), kC8 = coef(8), kC10 = coef(10);
+}  // namespace detail_sc
+
+/* sin and cos of 2 pi u for u in [0, 1).  4u = q + r exactly (u has at most
+ * 24 significant bits): q is the quadrant, r in [0, 1).  For r > 1/2 the
+ * complement r' = 1 - r (exact) is used with sin and cos exchanged, so the
+ * polynomials only see (pi/2) r' <= pi/4: sine to degree 9, cosine to degree
+ * 10 (truncation below 2^-28), each with small relative error, also near the
+ * zeros of sin and cos.  The quadrant then fixes signs and order. */
+__device__ __forceinline__ void sincos_2pi(float u, float *s, float *c)
+{
+    using namespace detail_sc;
+    const float v = __fmul_rn(u, 4.0f);
+    const int q = (int)v;                                  /* 0..3 */
+    float r = __fadd_rn(v, -(float)q);                     /* exact */
+    const bool flip = r > 0.5f;
+    if (flip) r = __fadd_rn(1.0f, -r);                     /* exact */
+    const float r2 = __fmul_rn(r, r);
+    float ps = kS9;
+    ps = __fmaf_rn(ps, r2, kS7);
+    ps = __fmaf_rn(ps, r2, kS5);
+    ps = __fmaf_rn(ps, r2, kS3);
+    ps = __fmaf_rn(ps, r2, kS1);
+    float pc = kC10;
+    pc = __fmaf_rn(pc, r2, kC8);
+    pc = __fmaf_rn(pc, r2, kC6);
+    pc = __fmaf_rn(pc, r2, kC4);
+    pc = __fmaf_rn(pc, r2, kC2);
+    const float sr = __fmul_rn(ps, r);
+    const float cr = __fmaf_rn(pc, r2, 1.0f);
+    const float sn = flip ? cr : sr, cs = flip ? sr : cr;  /* of (pi/2)(4u - q) */
+    switch (q & 3) {
+    case 0: *s = sn; *c = cs; break;
+    case 1: *s = cs; *c = -sn; break;
+    case 2: *s = -sn; *c = -cs; break;
+    default: *s = -cs; *c = sn; break;
+    }
+}
+
+/* Exponential(1) variate from an FP32 uniform u in [0, 1): -ln(1 - u).  For u
+ * a multiple of 2^-24 (every FP32 output of the generators) 1 - u is exact. */
+__device__ __forceinline__ float exponential(float u) { return __fsub_rn(0.0f, ln_unit(__fadd_rn(1.0f, -u))); }
+
+/* Two standard normal variates from two FP32 uniforms (Box & Muller 1958):
+ * r = sqrt(-2 ln(1 - u0)), t = 2 pi u1, (r cos t, r sin t). */
+__device__ __forceinline__ void normal_pair(float u0, float u1, float *n0, float *n1)
+{
+    const float r = __fsqrt_rn(__fmul_rn(-2.0f, ln_unit(__fadd_rn(1.0f, -u0))));
+    float s, c;
+    sincos_2pi(u1, &s, &c);
+    *n0 = __fmul_rn(r, c);
+    *n1 = __fmul_rn(r, s);
+}
+
+}  // namespace dist
+
 /* ----------------------------------------- the paper's Listing-1 form */
 
 /* Compile-time interface check of a generator class (the paper's Sec. 6

@@ -31,6 +31,7 @@ SRNG_OUT_U32, SRNG_OUT_F32, SRNG_OUT_F64 = 0, 1, 2
 SRNG_SPACING_STREAM, SRNG_SPACING_SUBSTREAM = 0, 1
 SRNG_JUMP_DRAWS, SRNG_JUMP_SUBSTREAMS, SRNG_JUMP_STREAMS = 0, 1, 2
 SRNG_BATCH_WRITE, SRNG_BATCH_FUSED_PI = 0, 1
+SRNG_DIST_EXPONENTIAL, SRNG_DIST_NORMAL = 0, 1
 OUT_ITEMSIZE = {SRNG_OUT_U32: 4, SRNG_OUT_F32: 4, SRNG_OUT_F64: 8}
 
 STATUS_NAMES = {0: "SRNG_OK", 1: "SRNG_ERR_ARG", 2: "SRNG_ERR_OOM", 3: "SRNG_ERR_STATE", 4: "SRNG_ERR_CUDA",
@@ -112,6 +113,7 @@ _SIGS = {
     "srng_set_tune": (_int, [_int, _int, ctypes.POINTER(Tune)]),
     "srng_get_tune": (_int, [_int, _int, ctypes.POINTER(Tune)]),
     "srng_convert": (_int, [_int, _int, _vp, _u64, _vp, _vp]),
+    "srng_transform": (_int, [_int, _vp, _u64, _vp, _vp]),
     "srng_seed_expand": (_int, [_u64, _vp]),
     "srng_jump_matrix": (_int, [_int, _u64, _u64, _vp, _vp]),
     "srng_batch_plan_create": (_int, [ctypes.POINTER(_vp), _vp, _u32, _vp, _u64, _int, _int, _vp,
@@ -303,6 +305,10 @@ def srng_get_tune(gen: int, out_type: int) -> Tune:
 
 def srng_convert(gen: int, out_type: int, in_dev, n: int, out_dev, stream=None) -> None:
     _check(load().srng_convert(gen, out_type, _ptr(in_dev), n, _ptr(out_dev), _stream(stream)), "srng_convert")
+
+
+def srng_transform(dist: int, in_dev, n: int, out_dev, stream=None) -> None:
+    _check(load().srng_transform(dist, _ptr(in_dev), n, _ptr(out_dev), _stream(stream)), "srng_transform")
 
 
 def srng_seed_expand(seed: int) -> list:

@@ -644,6 +644,23 @@ srng_status srng_convert(srng_gen gen, srng_out type, const uint32_t *in_dev, ui
     return SRNG_OK;
 }
 
+srng_status srng_transform(srng_dist dist, const float *in_dev, uint64_t n, float *out_dev, void *cuda_stream)
+{
+    clear_error();
+    if (dist != SRNG_DIST_EXPONENTIAL && dist != SRNG_DIST_NORMAL) return fail(SRNG_ERR_ARG, "unknown distribution");
+    if (n == 0) return SRNG_OK;
+    if (!in_dev || !out_dev) return fail(SRNG_ERR_ARG, "NULL pointer");
+    if (dist == SRNG_DIST_NORMAL && (n & 1)) return fail(SRNG_ERR_ARG, "normal variates come in pairs: n must be even");
+    const uintptr_t align = dist == SRNG_DIST_NORMAL ? 8 : 4;
+    if (reinterpret_cast<uintptr_t>(in_dev) % align || reinterpret_cast<uintptr_t>(out_dev) % align)
+        return fail(SRNG_ERR_ARG, "misaligned pointer");
+    DeviceInfo dev;
+    srng_status st = current_device(&dev);
+    if (st) return st;
+    SRNG_CUDA_TRY(launch_transform(dist, in_dev, n, out_dev, static_cast<cudaStream_t>(cuda_stream), dev));
+    return SRNG_OK;
+}
+
 srng_status srng_seed_expand(uint64_t seed, uint32_t state[6])
 {
     clear_error();

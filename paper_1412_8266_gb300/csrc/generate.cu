@@ -421,6 +421,77 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// ---------------------------------------------------------- variates
+// Exponential: out[i] = -ln(1 - in[i]); normal: Box-Muller on the pairs
+// (in[2k], in[2k+1]).  Elementwise, 4 bytes read and 4 written per value:
+// HBM bound (normal: close to the FP32 pipe as well).  Each block takes
+// contiguous tiles of 1024 float4, four 16-byte loads in flight per thread;
+// the n mod 4 tail goes scalar.
+template <int DIST> __device__ __forceinline__ float4 variates4(float4 u)
+{
+    float4 v;
+    if (DIST == SRNG_DIST_EXPONENTIAL) {
+        v.x = srng::dist::exponential(u.x); v.y = srng::dist::exponential(u.y);
+        v.z = srng::dist::exponential(u.z); v.w = srng::dist::exponential(u.w);
+    } else {
+        srng::dist::normal_pair(u.x, u.y, &v.x, &v.y);
+        srng::dist::normal_pair(u.z, u.w, &v.z, &v.w);
+    }
+    return v;
+}
+
+template <int DIST>
+__global__ void __launch_bounds__(256) k_transform(const float *in, uint64_t n, float *out)  // in == out allowed
+{
+    constexpr int U = 4;                      // float4 loads in flight per thread
+    constexpr uint64_t kTile = 256 * U;       // float4 per block per trip, contiguous
+    const uint64_t n4 = n / 4;
+    const float4 *in4 = reinterpret_cast<const float4 *>(in);
+    float4 *out4 = reinterpret_cast<float4 *>(out);
+    for (uint64_t base = (uint64_t)blockIdx.x * kTile; base < n4; base += (uint64_t)gridDim.x * kTile) {
+        float4 a[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint64_t i = base + k * 256 + threadIdx.x;
+            if (i < n4) a[k] = in4[i];
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const uint64_t i = base + k * 256 + threadIdx.x;
+            if (i < n4) out4[i] = variates4<DIST>(a[k]);
+        }
+    }
+    if (blockIdx.x == 0) {                    // the n mod 4 tail
+        const uint64_t t = 4 * n4 + (DIST == SRNG_DIST_EXPONENTIAL ? threadIdx.x : 2 * threadIdx.x);
+        if (DIST == SRNG_DIST_EXPONENTIAL) {
+            if (t < n) out[t] = srng::dist::exponential(in[t]);
+        } else if (t + 1 < n) {
+            float z0, z1;
+            srng::dist::normal_pair(in[t], in[t + 1], &z0, &z1);
+            out[t] = z0;
+            out[t + 1] = z1;
+        }
+    }
+}
+
+// Pointers not 16-byte aligned: one value (exponential) or pair (normal) per step.
+template <int DIST>
+__global__ void __launch_bounds__(256) k_transform_scalar(const float *in, uint64_t n, float *out)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (DIST == SRNG_DIST_NORMAL ? n / 2 : n);
+         i += stride) {
+        if (DIST == SRNG_DIST_EXPONENTIAL) {
+            out[i] = srng::dist::exponential(in[i]);
+        } else {
+            float z0, z1;
+            srng::dist::normal_pair(in[2 * i], in[2 * i + 1], &z0, &z1);
+            out[2 * i] = z0;
+            out[2 * i + 1] = z1;
+        }
+    }
+}
+
 // ---------------------------------------------------------- conversion
 template <int GEN, int OUT>
 __global__ void __launch_bounds__(256) k_convert(const uint32_t *__restrict__ in, uint64_t n,
@@ -554,6 +625,28 @@ cudaError_t launch_philox_generate(const PhiloxGenArgs &a, srng_out type, const 
     case SRNG_OUT_F32: return philox_dispatch<SRNG_OUT_F32>(a, t, stream, dev);
     default: return philox_dispatch<SRNG_OUT_F64>(a, t, stream, dev);
     }
+}
+
+cudaError_t launch_transform(int dist, const float *in, uint64_t n, float *out, cudaStream_t stream,
+                             const DeviceInfo &dev)
+{
+    if (n == 0) return cudaSuccess;
+    // resident blocks per SM: 4 for the exponential (memory bound), 8 for the
+    // normal (more arithmetic to hide); measured on GB300 at 2^30 values
+    const uint64_t cap = (uint64_t)dev.sm_count * (dist == SRNG_DIST_NORMAL ? 8 : 4);
+    const bool vec = (reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % 16 == 0;
+    uint64_t blocks = vec ? (n / 4 + 1023) / 1024 : (n + 255) / 256;
+    if (blocks > cap) blocks = cap;
+    if (blocks == 0) blocks = 1;   // the scalar tail of a short input
+    const unsigned g = (unsigned)blocks;
+    if (vec) {
+        if (dist == SRNG_DIST_EXPONENTIAL) k_transform<SRNG_DIST_EXPONENTIAL><<<g, 256, 0, stream>>>(in, n, out);
+        else k_transform<SRNG_DIST_NORMAL><<<g, 256, 0, stream>>>(in, n, out);
+    } else {
+        if (dist == SRNG_DIST_EXPONENTIAL) k_transform_scalar<SRNG_DIST_EXPONENTIAL><<<g, 256, 0, stream>>>(in, n, out);
+        else k_transform_scalar<SRNG_DIST_NORMAL><<<g, 256, 0, stream>>>(in, n, out);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_convert(srng_gen gen, srng_out type, const uint32_t *in, uint64_t n, void *out,

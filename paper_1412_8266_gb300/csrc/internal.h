@@ -102,6 +102,8 @@ cudaError_t launch_philox_generate(const PhiloxGenArgs &a, srng_out type, const 
 
 cudaError_t launch_convert(srng_gen gen, srng_out type, const uint32_t *in, uint64_t n, void *out,
                            cudaStream_t stream, const DeviceInfo &dev);
+cudaError_t launch_transform(int dist, const float *in, uint64_t n, float *out, cudaStream_t stream,
+                             const DeviceInfo &dev);
 
 // ------------------------------------------------- batched work (batch.cu)
 // Per-instance descriptor on the device.

@@ -27,6 +27,28 @@ __global__ void listing1_philox(uint32_t *ddata, srng_dev_view v, int per_thread
     rng.store(v);
 }
 
+// Normal variates inside a user kernel: each thread draws FP32 uniform pairs
+// from its own stream and turns them into Box-Muller pairs with srng::dist.
+__global__ void user_normals(float *ddata, srng_dev_view v, int pairs)
+{
+    const uint64_t s = (uint64_t)blockDim.x * blockIdx.x + threadIdx.x;
+    if (s >= v.n_streams) return;
+    srng::Philox4x32_10 rng(v, s);
+    for (int k = 0; k < pairs; ++k) {
+        const float u0 = rng.next_f32(), u1 = rng.next_f32();
+        srng::dist::normal_pair(u0, u1, &ddata[s * 2 * pairs + 2 * k], &ddata[s * 2 * pairs + 2 * k + 1]);
+    }
+    rng.store(v);
+}
+
+extern "C" int run_user_normals(const srng_dev_view *v, float *out, int pairs)
+{
+    const unsigned threads = 128, blocks = (unsigned)((v->n_streams + threads - 1) / threads);
+    user_normals<<<blocks, threads>>>(out, *v, pairs);
+    if (cudaGetLastError() != cudaSuccess) return 1;
+    return cudaDeviceSynchronize() == cudaSuccess ? 0 : 2;
+}
+
 extern "C" int run_listing1(const srng_dev_view *v, void *out, int per_thread)
 {
     const unsigned threads = 128, blocks = (unsigned)((v->n_streams + threads - 1) / threads);

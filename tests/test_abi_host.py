@@ -94,6 +94,12 @@ def test_argument_errors_need_no_gpu(lib):
         srng.srng_set_tune(srng.SRNG_MRG32K3A, srng.SRNG_OUT_U32, {"chunk": 100})
     assert e.value.name == "SRNG_ERR_ARG"
     assert "multiple of 32" in srng.srng_last_error()
+    for dist, n, ptr, why in ((5, 4, 64, "distribution"), (srng.SRNG_DIST_NORMAL, 3, 64, "pairs"),
+                              (srng.SRNG_DIST_NORMAL, 4, 68, "misaligned"), (srng.SRNG_DIST_EXPONENTIAL, 4, 0, "NULL")):
+        with pytest.raises(srng.SrngError) as e:
+            srng.srng_transform(dist, ptr, n, ptr)
+        assert e.value.name == "SRNG_ERR_ARG" and why in srng.srng_last_error()
+    srng.srng_transform(srng.SRNG_DIST_NORMAL, 0, 0, 0)   # empty: nothing to do, no device needed
 
 
 def test_tune_table_roundtrip(lib):

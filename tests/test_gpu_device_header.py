@@ -30,6 +30,8 @@ def user_lib(tmp_path_factory):
     lib = ctypes.CDLL(out)
     lib.run_listing1.restype = ctypes.c_int
     lib.run_listing1.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
+    lib.run_user_normals.restype = ctypes.c_int
+    lib.run_user_normals.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
     return lib
 
 
@@ -68,6 +70,23 @@ def test_philox_listing1_kernel(user_lib):
         pos = np.zeros(n_streams, dtype=np.uint64)
         srng.srng_get_state(h, 0, n_streams, pos)
         assert np.all(pos == 3 + per)
+    finally:
+        srng.srng_destroy(h)
+
+
+def test_user_kernel_normals(user_lib):
+    """srng::dist::normal_pair inside a user kernel equals the oracle's
+    Box-Muller on the oracle's Philox FP32 uniforms, bit for bit."""
+    n_streams, pairs, seed = 257, 33, 0xC0FFEE
+    h = srng.srng_create(srng.SRNG_PHILOX4X32_10, seed, n_streams)
+    try:
+        v = srng.srng_get_device_view(h)
+        out = torch.empty(n_streams * 2 * pairs, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        assert user_lib.run_user_normals(ctypes.byref(v), out.data_ptr(), pairs) == 0
+        u, _ = O.philox_bulk((seed, 0), 0, [0] * n_streams, 2 * pairs, O.OUT_F32)
+        ref = O.transform(O.DIST_NORMAL, u.ravel())
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), ref.view(np.uint32))
     finally:
         srng.srng_destroy(h)
 
