@@ -19,6 +19,10 @@ Parity status per function (what pins it is in tests/test_oracle_pins.py):
   dist_constants / ln_unit_f32 / sincos_2pi_f32 / transform  pinned (exhaustive
       over the 2^24 FP32 uniforms against float64 libm, constants against
       exact rationals, distribution tests)
+  threefry4x32_20 / threefry_word / threefry_*            parity unpinned: the
+      rotation counts and parity constant of Salmon et al. 2011 have no
+      independent implementation here; structure pinned (bijection, key and
+      counter use, the block-to-word layout, avalanche)
   seed_expand (SplitMix64)                                structure pinned; the two
       mixing multipliers are parity unpinned (no implementation in this
       environment to compare with, and the paper is silent on seeding)
@@ -79,6 +83,11 @@ def _load(path: str | None = None):
             "oracle_seed_expand": (None, [u64, u32p]),
             "oracle_philox4x32_10": (None, [u32p, u32p, u32p]),
             "oracle_philox_word": (u32, [u32, u32, u64, u64]),
+            "oracle_threefry4x32_20": (None, [u32p, u32p, u32p]),
+            "oracle_threefry_word": (u32, [u64, u64, u64]),
+            "oracle_threefry_generate": (None, [u64, u64, u64, u64, i32, vp]),
+            "oracle_threefry_bulk": (None, [u64, u64, u64p, u64, u64, i32, vp, i32]),
+            "oracle_threefry_pi_count": (ctypes.c_int64, [u64, u64, u64, u64]),
             "oracle_to_f32": (ctypes.c_float, [u32]),
             "oracle_mrg_to_f64": (ctypes.c_double, [u32]),
             "oracle_dist_constants": (None, [ctypes.POINTER(ctypes.c_float)]),
@@ -236,6 +245,37 @@ def philox_bulk(key, stream0: int, positions, n: int, out_type: int = OUT_U32, t
     _load().oracle_philox_bulk(key[0], key[1], stream0, _u64p(pos), pos.shape[0], n, out_type,
                                out.ctypes.data_as(ctypes.c_void_p), threads)
     return out, pos
+
+
+# ---------------------------------------------------------------- Threefry
+def threefry4x32_20(ctr, key) -> np.ndarray:
+    c = np.array(ctr, dtype=np.uint32)
+    k = np.array(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _load().oracle_threefry4x32_20(_u32p(c), _u32p(k), _u32p(out))
+    return out
+
+
+def threefry_word(seed: int, stream: int, pos: int) -> int:
+    return int(_load().oracle_threefry_word(seed, stream, pos))
+
+
+def threefry_generate(seed: int, stream: int, pos: int, n: int, out_type: int = OUT_U32) -> np.ndarray:
+    out = np.empty(n, dtype=_DTYPES[out_type])
+    _load().oracle_threefry_generate(seed, stream, pos, n, out_type, out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def threefry_bulk(seed: int, stream0: int, positions, n: int, out_type: int = OUT_U32, threads: int = 0):
+    pos = np.ascontiguousarray(np.array(positions, dtype=np.uint64))
+    out = np.empty((pos.shape[0], n), dtype=_DTYPES[out_type])
+    _load().oracle_threefry_bulk(seed, stream0, _u64p(pos), pos.shape[0], n, out_type,
+                                 out.ctypes.data_as(ctypes.c_void_p), threads)
+    return out, pos
+
+
+def threefry_pi_count(seed: int, stream: int, pos: int, length: int) -> int:
+    return int(_load().oracle_threefry_pi_count(seed, stream, pos, length))
 
 
 # ---------------------------------------------------------------- conversions

@@ -258,6 +258,68 @@ uint32_t oracle_philox_word(uint32_t k0, uint32_t k1, uint64_t s, uint64_t p)
 }
 
 /* ---------------------------------------------------------------------- */
+/* Threefry4x32-20 (Sec. 4.3 names Threefry beside Philox, both from Salmon */
+/* et al. 2011): the Threefish block structure on four 32-bit words.  Key   */
+/* schedule: the four key words and a fifth, their xor with the parity     */
+/* constant 0x1BD11BDA; subkey j adds key words (j, j+1, j+2, j+3) mod 5 to  */
+/* the four state words and j to the last.  Subkey 0 is added first, then   */
+/* after every fourth round the next subkey.  A round: MIX the word pairs   */
+/* (0,1) and (2,3) -- a += b; b = (b <<< r) ^ a -- with the round's two     */
+/* rotation counts (a cycle of eight pairs), then permute the words to      */
+/* (0, 3, 2, 1).  Twenty rounds (the published default).                    */
+/* PARITY UNPINNED: the rotation counts and the parity constant come from   */
+/* the publication and no independent implementation is available here to */
+/* compare with; only the structure is checked (see tests).                 */
+/* ---------------------------------------------------------------------- */
+
+static const int ORC_THREEFRY_ROT[8][2] = {
+    {10, 26}, {11, 21}, {13, 27}, {23, 5}, {6, 20}, {17, 11}, {25, 10}, {18, 20}};
+#define ORC_THREEFRY_PARITY 0x1BD11BDAU
+
+static uint32_t orc_rotl32(uint32_t x, int r) { return (x << r) | (x >> (32 - r)); }
+
+void oracle_threefry4x32_20(const uint32_t ctr[4], const uint32_t key[4], uint32_t out[4])
+{
+    uint32_t ks[5];
+    ks[4] = ORC_THREEFRY_PARITY;
+    for (int i = 0; i < 4; ++i) {
+        ks[i] = key[i];
+        ks[4] ^= key[i];
+    }
+    uint32_t v[4];
+    for (int i = 0; i < 4; ++i) v[i] = ctr[i] + ks[i];          /* subkey 0 */
+    for (int d = 0; d < 20; ++d) {
+        for (int pair = 0; pair < 2; ++pair) {                  /* MIX */
+            uint32_t *a = &v[2 * pair], *b = &v[2 * pair + 1];
+            *a = *a + *b;
+            *b = orc_rotl32(*b, ORC_THREEFRY_ROT[d % 8][pair]) ^ *a;
+        }
+        uint32_t t = v[1];                                      /* permute (0, 3, 2, 1) */
+        v[1] = v[3];
+        v[3] = t;
+        if (d % 4 == 3) {                                       /* subkey (d + 1) / 4 */
+            uint32_t j = (uint32_t)(d + 1) / 4;
+            for (int i = 0; i < 4; ++i) v[i] += ks[(j + i) % 5];
+            v[3] += j;
+        }
+    }
+    for (int i = 0; i < 4; ++i) out[i] = v[i];
+}
+
+/* Word p of Threefry stream s: the paper's per-thread key read literally --
+ * key = (s low, s high, seed low, seed high), counter = (q low, q high, 0, 0)
+ * with q = p / 4, the draw being word p mod 4 of that block. */
+uint32_t oracle_threefry_word(uint64_t seed, uint64_t s, uint64_t p)
+{
+    uint64_t q = p / 4;
+    uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), 0, 0};
+    uint32_t key[4] = {(uint32_t)s, (uint32_t)(s >> 32), (uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    oracle_threefry4x32_20(ctr, key, out);
+    return out[p % 4];
+}
+
+/* ---------------------------------------------------------------------- */
 /* Integer -> uniform conversions (fixed readings)                          */
 /* ---------------------------------------------------------------------- */
 
@@ -301,6 +363,12 @@ void oracle_philox_generate(uint32_t k0, uint32_t k1, uint64_t s, uint64_t p, ui
     for (uint64_t k = 0; k < n; ++k) store_value(out_type, out, k, oracle_philox_word(k0, k1, s, p + k), 0);
 }
 
+/* n words of Threefry stream s starting at position p (conversions as Philox). */
+void oracle_threefry_generate(uint64_t seed, uint64_t s, uint64_t p, uint64_t n, int out_type, void *out)
+{
+    for (uint64_t k = 0; k < n; ++k) store_value(out_type, out, k, oracle_threefry_word(seed, s, p + k), 0);
+}
+
 /* Stream-major bulk output of many streams:
  * out[i * n + k] = draw k of stream i.  MRG: states holds 6 words per stream
  * and is advanced in place.  Philox: positions[i] is the start position of
@@ -328,6 +396,21 @@ void oracle_philox_bulk(uint32_t k0, uint32_t k1, uint64_t stream0, uint64_t *po
     for (int64_t i = 0; i < (int64_t)n_streams; ++i) {
         oracle_philox_generate(k0, k1, stream0 + (uint64_t)i, positions[i], n, out_type,
                                (char *)out + (size_t)i * n * esz);
+        positions[i] += n;
+    }
+}
+
+void oracle_threefry_bulk(uint64_t seed, uint64_t stream0, uint64_t *positions, uint64_t n_streams,
+                          uint64_t n, int out_type, void *out, int threads)
+{
+    size_t esz = out_type == ORC_OUT_F64 ? 8 : 4;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t i = 0; i < (int64_t)n_streams; ++i) {
+        oracle_threefry_generate(seed, stream0 + (uint64_t)i, positions[i], n, out_type,
+                                 (char *)out + (size_t)i * n * esz);
         positions[i] += n;
     }
 }
@@ -374,11 +457,21 @@ int64_t oracle_philox_pi_count(uint32_t k0, uint32_t k1, uint64_t s, uint64_t p,
     return hits;
 }
 
+/* Threefry words take the Philox hit test (the same 24-bit single reading). */
+int64_t oracle_threefry_pi_count(uint64_t seed, uint64_t s, uint64_t p, uint64_t length)
+{
+    int64_t hits = 0;
+    for (uint64_t k = 0; k + 1 < length; k += 2)
+        hits += oracle_pi_hit_philox(oracle_threefry_word(seed, s, p + k), oracle_threefry_word(seed, s, p + k + 1));
+    return hits;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Batched instances: instance i draws `lengths[i]` values from its own     */
 /* stream.  gens[i] = 0 for MRG32k3a (start state in mrg_states, 6 words    */
 /* per instance, not modified), 1 for Philox (stream philox_streams[i] from */
-/* position philox_pos[i] under key (k0, k1)).                              */
+/* position philox_pos[i] under key (k0, k1)), 3 for Threefry (the same     */
+/* stream and position, seed k0 + 2^32 k1).                                 */
 /* mode 0: u32 output written at out_offsets[i]; mode 1: hit counts.        */
 /* ---------------------------------------------------------------------- */
 
@@ -401,6 +494,13 @@ void oracle_batch(uint64_t n_inst, const int32_t *gens, const uint32_t *mrg_stat
                 oracle_mrg_generate(s, lengths[i], out_type, (char *)out + out_offsets[i] * esz);
             else
                 counts[i] = oracle_mrg_pi_count(s, lengths[i]);
+        } else if (gens[i] == 3) {
+            uint64_t seed = (uint64_t)k1 << 32 | k0;
+            if (mode == 0)
+                oracle_threefry_generate(seed, philox_streams[i], philox_pos[i], lengths[i], out_type,
+                                         (char *)out + out_offsets[i] * esz);
+            else
+                counts[i] = oracle_threefry_pi_count(seed, philox_streams[i], philox_pos[i], lengths[i]);
         } else {
             if (mode == 0)
                 oracle_philox_generate(k0, k1, philox_streams[i], philox_pos[i], lengths[i],

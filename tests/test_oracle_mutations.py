@@ -48,6 +48,8 @@ MUTATIONS = {
     "quadrant order": ("else if (q % 4 == 1) { *sin_out = cs; *cos_out = -sn; }",
                        "else if (q % 4 == 1) { *sin_out = cs; *cos_out = sn; }"),
     "reflection": ("if (exchanged) r = 1.0f - r;", "if (exchanged) r = r - 0.5f;"),
+    "threefry permutation": ("        v[1] = v[3];\n        v[3] = t;\n", "        (void)t;\n"),
+    "threefry rounds": ("for (int d = 0; d < 20; ++d) {", "for (int d = 0; d < 3; ++d) {"),
     "box-muller radius": ("float r = sqrtf(-2.0f * orc_ln(&k, 1.0f - in[2 * j]));",
                           "float r = sqrtf(-2.0f * orc_ln(&k, in[2 * j]));"),
 }
@@ -169,6 +171,19 @@ def _pins_fail(ref):
         g = O.transform(O.DIST_NORMAL, w).astype(np.float64)
         r = np.sqrt(-2 * np.log1p(-w[0::2].astype(np.float64)))
         if np.any(np.abs(g[0::2] - r * np.cos(2 * np.pi * w[1::2].astype(np.float64))) > 4 * sp(r) + 1e-12):
+            return True
+        # Threefry: every counter bit diffuses into every output bit
+        rng = np.random.default_rng(7)
+        flips = np.zeros((128, 128))
+        for _ in range(48):
+            ctr = rng.integers(0, 2**32, 4, dtype=np.uint64).astype(np.uint32)
+            key = rng.integers(0, 2**32, 4, dtype=np.uint64).astype(np.uint32)
+            base = np.unpackbits(O.threefry4x32_20(ctr, key).view(np.uint8))
+            for b in range(128):
+                c2 = ctr.copy()
+                c2[b // 32] ^= np.uint32(1 << (b % 32))
+                flips[b] += np.unpackbits(O.threefry4x32_20(c2, key).view(np.uint8)) != base
+        if np.abs(flips / 48 - 0.5).max() > 0.33:
             return True
         return False
     except Exception:

@@ -1,0 +1,82 @@
+"""Structure pins of the oracle's Threefry4x32-20 (Sec. 4.3 names Threefry
+beside Philox).  Its rotation counts and key-schedule parity constant come
+from Salmon et al. 2011 and no independent implementation is available to
+compare with, so their values are parity unpinned; what is pinned here holds
+for the construction whatever the constants: the stream layout, diffusion of
+every counter and key bit into every output bit, uniform bytes, and distinct
+blocks for distinct counters (the block function is a permutation)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+
+def test_word_layout():
+    """Word p of stream s = word p mod 4 of the block with counter
+    (p/4 low, p/4 high, 0, 0) under key (s low, s high, seed low, seed high)."""
+    seed, s = 0x0123456789ABCDEF, (7 << 40) | 12345
+    key = [s & 0xFFFFFFFF, s >> 32, seed & 0xFFFFFFFF, seed >> 32]
+    for p in (0, 1, 2, 3, 4, 7, 2**34 + 5, 2**64 - 1):
+        q = p // 4
+        blk = O.threefry4x32_20([q & 0xFFFFFFFF, q >> 32, 0, 0], key)
+        assert O.threefry_word(seed, s, p) == int(blk[p % 4])
+    got = O.threefry_generate(seed, s, 5, 11)
+    assert [int(x) for x in got] == [O.threefry_word(seed, s, 5 + k) for k in range(11)]
+
+
+def test_generate_conversions_follow_the_words():
+    seed, s = 99, 3
+    w = O.threefry_generate(seed, s, 0, 64)
+    f = O.threefry_generate(seed, s, 0, 64, O.OUT_F32)
+    d = O.threefry_generate(seed, s, 0, 64, O.OUT_F64)
+    assert np.array_equal(f, (w >> 8).astype(np.float32) * np.float32(2.0**-24))
+    assert np.array_equal(d, (2.0 * w.astype(np.float64) + 1) * 2.0**-33)
+
+
+def test_bulk_matches_per_stream_and_advances():
+    out, pos = O.threefry_bulk(5, 10, [0, 3, 7], 9, O.OUT_U32)
+    for i, p in enumerate([0, 3, 7]):
+        assert np.array_equal(out[i], O.threefry_generate(5, 10 + i, p, 9))
+    assert list(pos) == [9, 12, 16]
+
+
+@pytest.mark.parametrize("which", ["counter", "key"])
+def test_avalanche(which):
+    """Flipping any one of the 128 counter (or key) bits flips each of the 128
+    output bits with probability 1/2: over 200 random inputs, every
+    (input bit, output bit) frequency lies in 0.5 +- 0.16 (> 4.5 sigma)."""
+    rng = np.random.default_rng(1 if which == "counter" else 2)
+    trials = 200
+    flips = np.zeros((128, 128))
+    for _ in range(trials):
+        ctr = rng.integers(0, 2**32, 4, dtype=np.uint64).astype(np.uint32)
+        key = rng.integers(0, 2**32, 4, dtype=np.uint64).astype(np.uint32)
+        base = np.unpackbits(O.threefry4x32_20(ctr, key).view(np.uint8))
+        for b in range(128):
+            c2, k2 = ctr.copy(), key.copy()
+            tgt = c2 if which == "counter" else k2
+            tgt[b // 32] ^= np.uint32(1 << (b % 32))
+            flips[b] += np.unpackbits(O.threefry4x32_20(c2, k2).view(np.uint8)) != base
+    freq = flips / trials
+    assert np.abs(freq - 0.5).max() < 0.16
+
+
+def test_uniform_bytes_and_distinct_blocks():
+    """2^18 words of one stream: byte frequencies pass a chi-square test
+    (255 degrees of freedom, threshold far in the tail), and the 2^16 blocks
+    (consecutive counters) are pairwise distinct."""
+    w = O.threefry_generate(0xC0FFEE, 0, 0, 1 << 18)
+    counts = np.bincount(w.view(np.uint8), minlength=256)
+    e = w.size * 4 / 256
+    chi2 = ((counts - e) ** 2 / e).sum()
+    assert chi2 < 400
+    blocks = w.view(np.dtype((np.void, 16)))
+    assert np.unique(blocks).size == blocks.size
+
+
+def test_streams_and_seeds_differ():
+    a = O.threefry_generate(1, 0, 0, 16)
+    assert not np.array_equal(a, O.threefry_generate(1, 1, 0, 16))
+    assert not np.array_equal(a, O.threefry_generate(2, 0, 0, 16))
+    assert not np.array_equal(a, O.threefry_generate(1, 1 << 32, 0, 16))
+    assert not np.array_equal(a, O.threefry_generate(1 << 32, 0, 0, 16))
