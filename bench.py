@@ -416,6 +416,19 @@ def extras(torch, srng, dev, stream, peak):
     srng.srng_destroy(h)
     res["philox_bulk_2^30"] = ph
     res["variates_2^30_f32"] = var
+    # Threefry4x32-20 bulk: 2^30 words of one stream, u32 and f32 (ALU bound: 20 add/rotate/xor rounds)
+    tf = {}
+    h = srng.srng_create(srng.SRNG_THREEFRY4X32_20, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
+    for name, t, dt in (("u32", srng.SRNG_OUT_U32, torch.int32), ("f32", srng.SRNG_OUT_F32, torch.float32)):
+        tt = autotune.tune_generate(srng.SRNG_THREEFRY4X32_20, t, 1, n, use_cache=False, install=False)[0]
+        o = torch.empty(n, dtype=dt, device=dev)
+        best, med = _time(torch, stream, lambda: (srng.srng_reset(h, stream),
+                                                  srng.srng_generate_tuned(h, 0, 1, n, t, o, tt, stream)))
+        tf[name] = {"ms_best": best, "ms_median": med, "Guniforms_s": n / best / 1e6, "GB_s": n * 4 / best / 1e6,
+                    "frac_of_copy_peak": n * 4 / best / 1e6 / peak, "tune": tt}
+        del o
+    srng.srng_destroy(h)
+    res["threefry_bulk_2^30"] = tf
     # Philox layouts at the many-stream shape (2^18 streams x 4096 words, uint32):
     # counter split (one key) vs keyed (key = stream, Sec. 4.3)
     lay = {}
@@ -523,10 +536,11 @@ def run_case(args):
         o = torch.empty(S * N_DRAWS, dtype=torch.int32 if t == 0 else torch.float64, device=dev)
         fn = lambda: srng.srng_generate(h, 0, S, N_DRAWS, t, o, stream)
         nbytes, nvals = o.numel() * o.element_size(), o.numel()
-    elif c.startswith("philox"):
+    elif c.startswith("philox") or c.startswith("threefry"):
         n = (1 << 30) // k
-        t = srng.SRNG_OUT_U32 if c == "philox_u32" else srng.SRNG_OUT_F32
-        h = srng.srng_create(srng.SRNG_PHILOX4X32_10, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
+        t = srng.SRNG_OUT_U32 if c.endswith("u32") else srng.SRNG_OUT_F32
+        g = srng.SRNG_PHILOX4X32_10 if c.startswith("philox") else srng.SRNG_THREEFRY4X32_20
+        h = srng.srng_create(g, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
         o = torch.empty(n, dtype=torch.int32 if t == 0 else torch.float32, device=dev)
         fn = lambda: srng.srng_generate(h, 0, 1, n, t, o, stream)
         nbytes, nvals = n * 4, n
@@ -560,8 +574,8 @@ def run_case(args):
     return 0
 
 
-CASES = {"mrg_u32", "mrg_f64", "philox_u32", "philox_f32", "batch_write", "batch_pi", "transform_exponential",
-         "transform_normal"}
+CASES = {"mrg_u32", "mrg_f64", "philox_u32", "philox_f32", "threefry_u32", "threefry_f32", "batch_write", "batch_pi",
+         "transform_exponential", "transform_normal"}
 
 
 def main():

@@ -65,7 +65,8 @@ typedef enum srng_status {
 typedef enum srng_gen {
     SRNG_MRG32K3A = 0,
     SRNG_PHILOX4X32_10 = 1,      /* streams split the counter, one key per set        */
-    SRNG_PHILOX4X32_10_KEYED = 2 /* one key per stream (paper Sec. 4.3): see srng_create */
+    SRNG_PHILOX4X32_10_KEYED = 2, /* one key per stream (paper Sec. 4.3): see srng_create */
+    SRNG_THREEFRY4X32_20 = 3      /* Threefry4x32, 20 rounds (Sec. 4.3): see srng_create  */
 } srng_gen;
 
 typedef enum srng_out {
@@ -146,8 +147,15 @@ int srng_abi_version(void);
  *     uses key = (s & 0xffffffff, s >> 32), counter words 2-3 = the seed's
  *     two words, counter words 0-1 = position / 4.  Everything else as
  *     above; srng_describe reports this generator value.
+ *   Threefry4x32-20 (SRNG_THREEFRY4X32_20; Salmon et al. 2011, named in the
+ *     paper's Sec. 4.3 beside Philox, key per stream): stream s uses the
+ *     128-bit key (s & 0xffffffff, s >> 32, seed & 0xffffffff, seed >> 32)
+ *     and counter (position / 4 low, high, 0, 0), draw = word position % 4;
+ *     conversions, positions and limits as Philox.  Tuning entries are
+ *     shared with Philox (srng_set_tune of either applies to both).
  * n_streams: 1 .. 2^40 (MRG32k3a with SRNG_SPACING_STREAM: at most 2^64 by
- * the paper, here limited by device memory: 24 bytes per stream; Philox: 8).
+ * the paper, here limited by device memory: 24 bytes per stream; Philox and
+ * Threefry: 8).
  * The set owns its device memory until srng_destroy.  Synchronises
  * cuda_stream before returning (the set is ready to use on any stream). */
 srng_status srng_create(srng_set **out, srng_gen gen, uint64_t seed, uint64_t n_streams,
@@ -249,14 +257,16 @@ srng_status srng_convert(srng_gen gen, srng_out type, const uint32_t *in_dev, ui
  * (the paper's in-kernel constructor + next(), Sec. 5.2).  The pointers stay
  * owned by the set and valid until srng_destroy. */
 typedef struct srng_dev_view {
-    int32_t gen;            /* SRNG_MRG32K3A or SRNG_PHILOX4X32_10              */
-    uint32_t key0, key1;    /* Philox: the set's seed words (key, or counter
-                             * words 2-3 when keyed)                           */
+    int32_t gen;            /* SRNG_MRG32K3A, SRNG_PHILOX4X32_10 (either layout)
+                             * or SRNG_THREEFRY4X32_20                         */
+    uint32_t key0, key1;    /* Philox / Threefry: the set's seed words (Philox
+                             * key, or counter words 2-3 when keyed; Threefry
+                             * key words 2-3)                                   */
     uint32_t flags;         /* bit 0: Philox keyed layout (key = stream)        */
     uint64_t n_streams;
     uint32_t *mrg_state;    /* MRG32k3a, SoA: word j of stream i at
                              * [j * n_streams + i], j in the srng_create_from_state order */
-    uint64_t *philox_pos;   /* Philox: current position of each stream          */
+    uint64_t *philox_pos;   /* Philox / Threefry: position of each stream       */
     uint64_t stream_base;   /* stream number of slot 0 (srng_create_range)      */
 } srng_dev_view;
 srng_status srng_get_device_view(const srng_set *set, srng_dev_view *out);

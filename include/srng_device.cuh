@@ -227,6 +227,47 @@ __device__ __forceinline__ double to_f64(uint32_t w)
 }
 }  // namespace philox
 
+namespace threefry {
+/* Threefry-4x32 (Salmon et al. 2011; the paper's Sec. 4.3 names it beside
+ * Philox): add / rotate / xor on four 32-bit words in the Threefish pattern.
+ * Round r pairs the words as (0,1),(2,3) when r is even and (0,3),(2,1) when
+ * it is odd; in each pair a += b, b = rotl(b, R) ^ a, with the rotation counts
+ * R of round r mod 8 below.  The key schedule has the four key words and their
+ * xor with kParity; subkey j (j = 0 first, then after every fourth round) adds
+ * key words j..j+3 (mod 5) to the state and j to word 3.  Twenty rounds. */
+constexpr uint32_t kParity = 0x1BD11BDAu;
+__host__ __device__ constexpr int rot(int r, int half)
+{
+    return r == 0 ? (half ? 26 : 10) : r == 1 ? (half ? 21 : 11) : r == 2 ? (half ? 27 : 13)
+         : r == 3 ? (half ? 5 : 23) : r == 4 ? (half ? 20 : 6) : r == 5 ? (half ? 11 : 17)
+         : r == 6 ? (half ? 10 : 25) : (half ? 20 : 18);
+}
+
+__device__ __forceinline__ uint32_t rotl(uint32_t x, int r) { return __funnelshift_l(x, x, r); }
+
+/* Twenty rounds on counter (c0..c3) with key (k0..k3), in place. */
+__device__ __forceinline__ void block(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3, uint32_t k0,
+                                      uint32_t k1, uint32_t k2, uint32_t k3)
+{
+    const uint32_t ks[5] = {k0, k1, k2, k3, kParity ^ k0 ^ k1 ^ k2 ^ k3};
+    c0 += ks[0]; c1 += ks[1]; c2 += ks[2]; c3 += ks[3];
+#pragma unroll
+    for (int r = 0; r < 20; ++r) {
+        if ((r & 1) == 0) {
+            c0 += c1; c1 = rotl(c1, rot(r & 7, 0)) ^ c0;
+            c2 += c3; c3 = rotl(c3, rot(r & 7, 1)) ^ c2;
+        } else {
+            c0 += c3; c3 = rotl(c3, rot(r & 7, 0)) ^ c0;
+            c2 += c1; c1 = rotl(c1, rot(r & 7, 1)) ^ c2;
+        }
+        if ((r & 3) == 3) {
+            const int j = (r + 1) >> 2;
+            c0 += ks[j % 5]; c1 += ks[(j + 1) % 5]; c2 += ks[(j + 2) % 5]; c3 += ks[(j + 3) % 5] + (uint32_t)j;
+        }
+    }
+}
+}  // namespace threefry
+
 /* (v >> 8) 2^-24 as a float, exact, without an integer-to-float conversion:
  * with a = v >> 8 = 2k + b, the bit pattern 0x3F800000 | k is 1 + k 2^-23, so
  * subtracting 1 gives k 2^-23 exactly, and adding b 2^-24 (bit pattern
@@ -309,6 +350,43 @@ class Philox4x32_10 {
     uint64_t stream_, ctr_hi_, pos_;
 };
 
+/* Threefry4x32-20 stream handle (the paper's per-thread key, Sec. 4.3):
+ * key = (stream low, stream high, seed low, seed high), counter = (q low,
+ * q high, 0, 0) for block q; word p mod 4 of block p / 4 is draw p.  Doubles
+ * and singles as for Philox. */
+class Threefry4x32_20 {
+  public:
+    /* `stream` is the slot in the set; the key uses its stream number
+     * v.stream_base + stream and the set's seed words v.key0, v.key1. */
+    __device__ Threefry4x32_20(const srng_dev_view &v, uint64_t stream)
+        : k0((uint32_t)(v.stream_base + stream)), k1((uint32_t)((v.stream_base + stream) >> 32)), k2(v.key0),
+          k3(v.key1), stream_(stream), pos_(v.philox_pos[stream]) {}
+    __device__ Threefry4x32_20(uint64_t seed, uint64_t stream, uint64_t position)
+        : k0((uint32_t)stream), k1((uint32_t)(stream >> 32)), k2((uint32_t)seed), k3((uint32_t)(seed >> 32)),
+          stream_(stream), pos_(position) {}
+
+    __device__ __forceinline__ uint4 block(uint64_t q) const
+    {
+        uint32_t c0 = (uint32_t)q, c1 = (uint32_t)(q >> 32), c2 = 0, c3 = 0;
+        threefry::block(c0, c1, c2, c3, k0, k1, k2, k3);
+        return make_uint4(c0, c1, c2, c3);
+    }
+    __device__ __forceinline__ uint32_t next_u32()
+    {
+        uint4 b = block(pos_ >> 2);
+        uint32_t j = (uint32_t)pos_ & 3u;
+        ++pos_;
+        return j == 0 ? b.x : j == 1 ? b.y : j == 2 ? b.z : b.w;
+    }
+    __device__ __forceinline__ float next_f32() { return to_f32(next_u32()); }
+    __device__ __forceinline__ double next_f64() { return philox::to_f64(next_u32()); }
+    __device__ void store(const srng_dev_view &v) const { v.philox_pos[stream_] = pos_; }
+    __device__ uint64_t position() const { return pos_; }
+
+    uint32_t k0, k1, k2, k3;
+    uint64_t stream_, pos_;
+};
+
 /* --------------------------------------------- non-uniform variates (FP32) */
 
 /* Exponential and normal variates from the FP32 uniforms, computed with this
@@ -320,15 +398,12 @@ class Philox4x32_10 {
  * last place against the exact functions. */
 namespace dist {
 
-/* Non-uniform variates from FP32 uniforms.  Every step below is one correctly
- * rounded IEEE single operation (add, multiply, divide, square root) or fused
- * multiply-add, so a CPU that takes the same steps gets the same bits.
- *
- * ln_unit: natural logarithm of x in (0, 1], Cody & Waite style.  x = 2^e m
+/* ln_unit: natural logarithm of x in (0, 1], Cody & Waite style.  x = 2^e m
  * with m in [sqrt(1/2), sqrt(2)); ln m = 2 atanh(s), s = (m - 1) / (m + 1),
  * |s| <= 0.1716, by the odd series 2 (s + s^3/3 + ... + s^11/11) (truncation
- * below 2^-33 relative), its leading term 2s added last; ln x = e ln2 + ln m with ln2 split into hi, its
- * leading 15 bits (e hi is exact for |e| < 512), and lo = ln2 - hi. */
+ * below 2^-33 relative), its leading term 2s added last; ln x = e ln2 + ln m
+ * with ln2 split into hi, its leading 15 bits (e hi is exact for |e| < 512),
+ * and lo = ln2 - hi. */
 __device__ __forceinline__ float ln_unit(float x)
 {
     const uint32_t bits = __float_as_uint(x);
@@ -431,6 +506,7 @@ struct is_generator<G, std::void_t<decltype(std::declval<G &>().next_u32()), dec
                                        std::is_same<decltype(std::declval<G &>().next_f64()), double>::value> {};
 static_assert(is_generator<Mrg32k3a>::value, "Mrg32k3a must provide next_u32/next_f32/next_f64");
 static_assert(is_generator<Philox4x32_10>::value, "Philox4x32_10 must provide next_u32/next_f32/next_f64");
+static_assert(is_generator<Threefry4x32_20>::value, "Threefry4x32_20 must provide next_u32/next_f32/next_f64");
 #if __cplusplus >= 202002L
 template <class G>
 concept DeviceGenerator = requires(G g) {
@@ -438,7 +514,7 @@ concept DeviceGenerator = requires(G g) {
     { g.next_f32() } -> std::same_as<float>;
     { g.next_f64() } -> std::same_as<double>;
 };
-static_assert(DeviceGenerator<Mrg32k3a> && DeviceGenerator<Philox4x32_10>);
+static_assert(DeviceGenerator<Mrg32k3a> && DeviceGenerator<Philox4x32_10> && DeviceGenerator<Threefry4x32_20>);
 #endif
 
 namespace detail {
@@ -461,6 +537,7 @@ template <> struct draw<double> { template <class G> __device__ static double f(
 template <class Gen> struct gen_id;
 template <> struct gen_id<Mrg32k3a> { static constexpr int value = SRNG_MRG32K3A; };
 template <> struct gen_id<Philox4x32_10> { static constexpr int value = SRNG_PHILOX4X32_10; };
+template <> struct gen_id<Threefry4x32_20> { static constexpr int value = SRNG_THREEFRY4X32_20; };
 }  // namespace detail
 
 /* The paper's device object (Listing 1): constructed inside a kernel with no

@@ -21,12 +21,12 @@ import threading
 __all__ = [
     "SrngError", "Tune", "Instance", "SetDesc", "DevView", "ServerConfig", "ServerStats", "Request",
     "lib_path", "load",
-    "SRNG_MRG32K3A", "SRNG_PHILOX4X32_10", "SRNG_PHILOX4X32_10_KEYED", "SRNG_OUT_U32", "SRNG_OUT_F32", "SRNG_OUT_F64",
+    "SRNG_MRG32K3A", "SRNG_PHILOX4X32_10", "SRNG_PHILOX4X32_10_KEYED", "SRNG_THREEFRY4X32_20", "SRNG_OUT_U32", "SRNG_OUT_F32", "SRNG_OUT_F64",
     "SRNG_SPACING_STREAM", "SRNG_SPACING_SUBSTREAM", "SRNG_JUMP_DRAWS", "SRNG_JUMP_SUBSTREAMS",
-    "SRNG_JUMP_STREAMS", "SRNG_BATCH_WRITE", "SRNG_BATCH_FUSED_PI",
+    "SRNG_JUMP_STREAMS", "SRNG_BATCH_WRITE", "SRNG_BATCH_FUSED_PI", "SRNG_DIST_EXPONENTIAL", "SRNG_DIST_NORMAL",
 ]
 
-SRNG_MRG32K3A, SRNG_PHILOX4X32_10, SRNG_PHILOX4X32_10_KEYED = 0, 1, 2
+SRNG_MRG32K3A, SRNG_PHILOX4X32_10, SRNG_PHILOX4X32_10_KEYED, SRNG_THREEFRY4X32_20 = 0, 1, 2, 3
 SRNG_OUT_U32, SRNG_OUT_F32, SRNG_OUT_F64 = 0, 1, 2
 SRNG_SPACING_STREAM, SRNG_SPACING_SUBSTREAM = 0, 1
 SRNG_JUMP_DRAWS, SRNG_JUMP_SUBSTREAMS, SRNG_JUMP_STREAMS = 0, 1, 2

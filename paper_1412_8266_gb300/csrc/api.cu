@@ -149,7 +149,10 @@ int bit_length(uint64_t x)
 
 size_t out_size(srng_out t) { return t == SRNG_OUT_F64 ? 8 : 4; }
 
-bool valid_gen(int g) { return g == SRNG_MRG32K3A || g == SRNG_PHILOX4X32_10 || g == SRNG_PHILOX4X32_10_KEYED; }
+bool valid_gen(int g)
+{
+    return g == SRNG_MRG32K3A || g == SRNG_PHILOX4X32_10 || g == SRNG_PHILOX4X32_10_KEYED || g == SRNG_THREEFRY4X32_20;
+}
 bool valid_out(int t) { return t == SRNG_OUT_U32 || t == SRNG_OUT_F32 || t == SRNG_OUT_F64; }
 
 int spacing_shift(srng_spacing sp) { return sp == SRNG_SPACING_SUBSTREAM ? 76 : 127; }
@@ -182,7 +185,8 @@ static srng_status create_common(srng_set **out, srng_gen gen, uint64_t seed, co
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     srng_set *s = new (std::nothrow) srng_set();
     if (!s) return fail(SRNG_ERR_OOM, "host allocation failed");
-    s->keyed = gen == SRNG_PHILOX4X32_10_KEYED;
+    s->keyed = gen == SRNG_PHILOX4X32_10_KEYED || gen == SRNG_THREEFRY4X32_20;
+    s->threefry = gen == SRNG_THREEFRY4X32_20;
     s->gen = (srng_gen)kernel_gen(gen);
     s->spacing = spacing;
     s->n_streams = n_streams;
@@ -271,6 +275,7 @@ static srng_status generate_dev(srng_set *s, uint64_t b, uint64_t c, uint64_t n,
         a.k0 = s->key0;
         a.k1 = s->key1;
         a.keyed = s->keyed ? 1 : 0;
+        a.threefry = s->threefry ? 1 : 0;
         a.pos = s->d_pos;
         a.s_begin = b;
         a.s_count = c;
@@ -397,7 +402,7 @@ srng_status srng_describe(const srng_set *set, srng_set_desc *out)
     clear_error();
     if (!set || !out) return fail(SRNG_ERR_ARG, "NULL argument");
     memset(out, 0, sizeof *out);
-    out->gen = set->keyed ? SRNG_PHILOX4X32_10_KEYED : set->gen;
+    out->gen = set->threefry ? SRNG_THREEFRY4X32_20 : set->keyed ? SRNG_PHILOX4X32_10_KEYED : set->gen;
     out->spacing = set->spacing;
     out->n_streams = set->n_streams;
     out->seed = set->seed;
@@ -412,10 +417,10 @@ srng_status srng_get_device_view(const srng_set *set, srng_dev_view *out)
     clear_error();
     if (!set || !out) return fail(SRNG_ERR_ARG, "NULL argument");
     memset(out, 0, sizeof *out);
-    out->gen = set->gen;
+    out->gen = (int32_t)inst_gen(set);
     out->key0 = set->key0;
     out->key1 = set->key1;
-    out->flags = set->keyed ? 1u : 0u;
+    out->flags = set->keyed && !set->threefry ? 1u : 0u;
     out->n_streams = set->n_streams;
     out->mrg_state = set->d_state;
     out->philox_pos = set->d_pos;

@@ -6,7 +6,8 @@
 //   - MRG32k3a item: 32 consecutive chunks of `chunk` draws of one instance,
 //     one chunk per lane; a lane reaches its chunk's start by jump-ahead
 //     ((A^chunk)^t applied to the instance's start state, Sec. 2.3);
-//   - Philox item: 32 x lane_blocks consecutive Philox blocks of one instance.
+//   - Philox / Threefry item: 32 x lane_blocks consecutive counter blocks of
+//     one instance.
 // A persistent grid (one wave of resident blocks) takes items from a global
 // counter with one atomicAdd per warp and item, so instance lengths spread
 // over five decades still load every SM evenly, and one launch serves them
@@ -29,6 +30,7 @@
 #include <string>
 #include <vector>
 
+#include "counter_based.cuh"
 #include "internal.h"
 #include "srng_device.cuh"
 
@@ -176,6 +178,14 @@ __device__ void mrg_item(const BatchArgs &a, const JumpTable &tab, uint32_t ii, 
 }
 
 // ------------------------------------------------------- Philox work item
+// Block q of an instance's stream (x0, x1 = q on entry), Philox or Threefry.
+__device__ __forceinline__ void item_block(bool tf, uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x3,
+                                           uint32_t kk0, uint32_t kk1, uint32_t c2, uint32_t c3)
+{
+    if (tf) cb_block<kCipherThreefry>(x0, x1, x2, x3, kk0, kk1, c2, c3);
+    else cb_block<kCipherPhilox>(x0, x1, x2, x3, kk0, kk1, c2, c3);
+}
+
 // Lane l computes pairs of adjacent blocks; eight values per pair go out as
 // 32-byte stores when inside the instance and aligned, else element stores.
 template <int OUT>
@@ -189,6 +199,7 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
     const uint64_t nb = (al + in.length + 3) >> 2;
     const uint64_t b0 = (uint64_t)seg * 32 * a.lane_blocks;
     const uint32_t c2 = (uint32_t)in.ctr_hi, c3 = (uint32_t)(in.ctr_hi >> 32);
+    const bool tf = in.gen == SRNG_THREEFRY4X32_20;  // uniform over the warp
     const uint64_t L = in.length;
     if (a.mode == SRNG_BATCH_FUSED_PI) {
         uint32_t hits = 0;
@@ -196,8 +207,8 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
             const uint64_t b = b0 + (uint64_t)u * 32 + lane;
             if (b >= nb) break;
             const uint64_t q = q0 + b;
-            uint32_t x0 = (uint32_t)q, x1 = (uint32_t)(q >> 32), x2 = c2, x3 = c3;
-            srng::philox::block(x0, x1, x2, x3, in.key0, in.key1);
+            uint32_t x0 = (uint32_t)q, x1 = (uint32_t)(q >> 32), x2, x3;
+            item_block(tf, x0, x1, x2, x3, in.key0, in.key1, c2, c3);
             const int64_t k0 = (int64_t)(b * 4) - al;  // draw index of word 0
             if ((al & 1) == 0) {
                 // pairs are (word 0, word 1) and (word 2, word 3)
@@ -208,8 +219,8 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
                 if (k0 + 1 >= 0 && (uint64_t)(k0 + 1) + 1 < L) hits += hit_philox(x1, x2);
                 if (k0 + 3 >= 0 && (uint64_t)(k0 + 3) + 1 < L) {
                     const uint64_t qn = q + 1;
-                    uint32_t y0 = (uint32_t)qn, y1 = (uint32_t)(qn >> 32), y2 = c2, y3 = c3;
-                    srng::philox::block(y0, y1, y2, y3, in.key0, in.key1);
+                    uint32_t y0 = (uint32_t)qn, y1 = (uint32_t)(qn >> 32), y2, y3;
+                    item_block(tf, y0, y1, y2, y3, in.key0, in.key1, c2, c3);
                     hits += hit_philox(x3, y0);
                 }
             }
@@ -230,8 +241,8 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const uint64_t q = q0 + b + h;
-            w[4 * h] = (uint32_t)q; w[4 * h + 1] = (uint32_t)(q >> 32); w[4 * h + 2] = c2; w[4 * h + 3] = c3;
-            srng::philox::block(w[4 * h], w[4 * h + 1], w[4 * h + 2], w[4 * h + 3], in.key0, in.key1);
+            w[4 * h] = (uint32_t)q; w[4 * h + 1] = (uint32_t)(q >> 32);
+            item_block(tf, w[4 * h], w[4 * h + 1], w[4 * h + 2], w[4 * h + 3], in.key0, in.key1, c2, c3);
         }
         const int64_t k0 = (int64_t)(b * 4) - al;
         T v[8];
@@ -421,7 +432,7 @@ srng_status batch_build(srng_set *const *sets, uint32_t n_sets, const srng_insta
             return fail(SRNG_ERR_RANGE, "instance " + std::to_string(i) + ": Philox position would pass 2^64 - 1");
         BatchInst b;
         memset(&b, 0, sizeof b);
-        b.gen = s->gen;
+        b.gen = inst_gen(s);
         const uint64_t gs = s->stream_base + x.stream;  // stream number
         b.key0 = s->keyed ? (uint32_t)gs : s->key0;
         b.key1 = s->keyed ? (uint32_t)(gs >> 32) : s->key1;
@@ -840,7 +851,7 @@ extern "C" srng_status srng_batch_run_static(srng_set *const *sets, uint32_t n_s
     for (uint32_t k = 0; k < n_sets; ++k) {
         const srng_set *s = sets[k];
         if (!s) return fail(SRNG_ERR_ARG, "NULL set");
-        ss.gen[k] = s->gen;
+        ss.gen[k] = inst_gen(s);
         ss.key0[k] = s->key0;
         ss.key1[k] = s->key1;
         ss.keyed[k] = s->keyed ? 1u : 0u;

@@ -11,8 +11,8 @@
 // element stores when the output alignment does not allow vectors), so every
 // warp store instruction fills whole 128-byte lines.
 //
-// K3 (Philox4x32-10, Sec. 4.3): counter-based, so any position is computed
-// directly.  A block of threads covers a contiguous run of Philox blocks of
+// K3 (Philox4x32-10 and Threefry4x32-20, Sec. 4.3): counter-based, so any
+// position is computed directly.  A block of threads covers a contiguous run of Philox blocks of
 // one stream; lane-consecutive blocks are 16 bytes apart in the output, so a
 // warp writes 512 contiguous bytes per store (u32 / f32).
 //
@@ -20,6 +20,7 @@
 // and positions add 24 and 8 bytes per stream per call.
 #include <stdint.h>
 
+#include "counter_based.cuh"
 #include "internal.h"
 #include "srng_device.cuh"
 
@@ -296,7 +297,7 @@ __device__ __forceinline__ void store8(typename OutType<OUT>::T *row, int64_t k0
 // host's quotient / remainder of gridDim.x by tps.  Each lane computes U pairs
 // of adjacent blocks (2U independent blocks in flight) and writes each pair's
 // eight values with 32-byte stores: a warp store covers 1 KiB (u32 / f32).
-template <int OUT, int U, bool VEC>
+template <int OUT, int U, bool VEC, int CIPHER>
 __global__ void __launch_bounds__(256)
     k_philox_generate(const PhiloxGenArgs a, uint64_t tps, uint64_t q_grid, uint64_t r_grid)
 {
@@ -333,8 +334,8 @@ __global__ void __launch_bounds__(256)
             for (int h = 0; h < 2; ++h) {
                 const uint64_t q = q0 + b + h;
                 uint32_t *y = &x[u][4 * h];
-                y[0] = (uint32_t)q; y[1] = (uint32_t)(q >> 32); y[2] = c2; y[3] = c3;
-                srng::philox::block(y[0], y[1], y[2], y[3], kk0, kk1);
+                y[0] = (uint32_t)q; y[1] = (uint32_t)(q >> 32);
+                cb_block<CIPHER>(y[0], y[1], y[2], y[3], kk0, kk1, c2, c3);
             }
         }
 #pragma unroll
@@ -378,7 +379,7 @@ __device__ __forceinline__ uint32_t divide(uint32_t n, const Divider &v)
 // (stream, block pair) with pps pairs per stream; consecutive lanes take
 // consecutive pairs, so a warp's 32-byte stores stay contiguous within a
 // stream and no lane idles at a stream's end beyond one pair.
-template <int OUT, int U, bool VEC>
+template <int OUT, int U, bool VEC, int CIPHER>
 __global__ void __launch_bounds__(256)
     k_philox_generate_flat(const PhiloxGenArgs a, uint32_t total_pairs, const Divider pps)
 {
@@ -408,8 +409,7 @@ __global__ void __launch_bounds__(256)
             for (int h = 0; h < 2; ++h) {
                 const uint64_t q = (pos >> 2) + b + h;
                 x[u][4 * h] = (uint32_t)q; x[u][4 * h + 1] = (uint32_t)(q >> 32);
-                x[u][4 * h + 2] = c2; x[u][4 * h + 3] = c3;
-                srng::philox::block(x[u][4 * h], x[u][4 * h + 1], x[u][4 * h + 2], x[u][4 * h + 3], kk0, kk1);
+                cb_block<CIPHER>(x[u][4 * h], x[u][4 * h + 1], x[u][4 * h + 2], x[u][4 * h + 3], kk0, kk1, c2, c3);
             }
         }
 #pragma unroll
@@ -553,7 +553,7 @@ cudaError_t mrg_dispatch(const MrgGenArgs &a, const JumpTable &tab, const srng_t
                   : mrg_dispatch_warps<OUT, false>(a, tab, t, stream, dev);
 }
 
-template <int OUT, int U>
+template <int OUT, int U, int CIPHER>
 cudaError_t philox_dispatch_u(const PhiloxGenArgs &a, const srng_tune &t, cudaStream_t stream,
                               const DeviceInfo &dev)
 {
@@ -568,13 +568,13 @@ cudaError_t philox_dispatch_u(const PhiloxGenArgs &a, const srng_tune &t, cudaSt
     if (blocks == 0) blocks = 1;
     const uint64_t qg = blocks / tps, rg = blocks % tps;
     if (t.vector_store != 2)
-        k_philox_generate<OUT, U, true><<<(unsigned)blocks, threads, 0, stream>>>(a, tps, qg, rg);
+        k_philox_generate<OUT, U, true, CIPHER><<<(unsigned)blocks, threads, 0, stream>>>(a, tps, qg, rg);
     else
-        k_philox_generate<OUT, U, false><<<(unsigned)blocks, threads, 0, stream>>>(a, tps, qg, rg);
+        k_philox_generate<OUT, U, false, CIPHER><<<(unsigned)blocks, threads, 0, stream>>>(a, tps, qg, rg);
     return cudaGetLastError();
 }
 
-template <int OUT>
+template <int OUT, int CIPHER>
 cudaError_t philox_dispatch(const PhiloxGenArgs &a, const srng_tune &t, cudaStream_t stream, const DeviceInfo &dev)
 {
     // Many short streams: the flat kernel (no idle lanes at stream ends), when
@@ -590,18 +590,18 @@ cudaError_t philox_dispatch(const PhiloxGenArgs &a, const srng_tune &t, cudaStre
         const Divider dv = make_divider((uint32_t)pps);
         const bool vec = t.vector_store != 2;
         if (t.unroll == 1) {
-            if (vec) k_philox_generate_flat<OUT, 1, true><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
-            else k_philox_generate_flat<OUT, 1, false><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
+            if (vec) k_philox_generate_flat<OUT, 1, true, CIPHER><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
+            else k_philox_generate_flat<OUT, 1, false, CIPHER><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
         } else {
-            if (vec) k_philox_generate_flat<OUT, 2, true><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
-            else k_philox_generate_flat<OUT, 2, false><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
+            if (vec) k_philox_generate_flat<OUT, 2, true, CIPHER><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
+            else k_philox_generate_flat<OUT, 2, false, CIPHER><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
         }
         return cudaGetLastError();
     }
     switch (t.unroll) {
-    case 1: return philox_dispatch_u<OUT, 1>(a, t, stream, dev);
-    case 4: return philox_dispatch_u<OUT, 4>(a, t, stream, dev);
-    default: return philox_dispatch_u<OUT, 2>(a, t, stream, dev);
+    case 1: return philox_dispatch_u<OUT, 1, CIPHER>(a, t, stream, dev);
+    case 4: return philox_dispatch_u<OUT, 4, CIPHER>(a, t, stream, dev);
+    default: return philox_dispatch_u<OUT, 2, CIPHER>(a, t, stream, dev);
     }
 }
 
@@ -620,10 +620,17 @@ cudaError_t launch_mrg_generate(const MrgGenArgs &a, srng_out type, const JumpTa
 cudaError_t launch_philox_generate(const PhiloxGenArgs &a, srng_out type, const srng_tune &t,
                                    cudaStream_t stream, const DeviceInfo &dev)
 {
+    if (a.threefry) {
+        switch (type) {
+        case SRNG_OUT_U32: return philox_dispatch<SRNG_OUT_U32, kCipherThreefry>(a, t, stream, dev);
+        case SRNG_OUT_F32: return philox_dispatch<SRNG_OUT_F32, kCipherThreefry>(a, t, stream, dev);
+        default: return philox_dispatch<SRNG_OUT_F64, kCipherThreefry>(a, t, stream, dev);
+        }
+    }
     switch (type) {
-    case SRNG_OUT_U32: return philox_dispatch<SRNG_OUT_U32>(a, t, stream, dev);
-    case SRNG_OUT_F32: return philox_dispatch<SRNG_OUT_F32>(a, t, stream, dev);
-    default: return philox_dispatch<SRNG_OUT_F64>(a, t, stream, dev);
+    case SRNG_OUT_U32: return philox_dispatch<SRNG_OUT_U32, kCipherPhilox>(a, t, stream, dev);
+    case SRNG_OUT_F32: return philox_dispatch<SRNG_OUT_F32, kCipherPhilox>(a, t, stream, dev);
+    default: return philox_dispatch<SRNG_OUT_F64, kCipherPhilox>(a, t, stream, dev);
     }
 }
 

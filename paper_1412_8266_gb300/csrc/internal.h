@@ -93,6 +93,7 @@ struct PhiloxGenArgs {
     uint64_t stream_base; // stream number of the set's slot 0
     uint32_t k0, k1;      // the set's seed words
     int keyed;            // 0: key = (k0, k1), counter words 2-3 = stream; 1: key = stream, words 2-3 = (k0, k1)
+    int threefry;         // 1: Threefry4x32-20, key = (stream, k0, k1), counter words 2-3 = 0
     const uint64_t *pos;
     uint64_t s_begin, s_count, n;
     void *out;
@@ -108,11 +109,12 @@ cudaError_t launch_transform(int dist, const float *in, uint64_t n, float *out, 
 // ------------------------------------------------- batched work (batch.cu)
 // Per-instance descriptor on the device.
 struct BatchInst {
-    uint32_t gen;
-    uint32_t key0, key1;      // Philox key of this instance's stream
+    uint32_t gen;             // SRNG_MRG32K3A, SRNG_PHILOX4X32_10 or SRNG_THREEFRY4X32_20
+    uint32_t key0, key1;      // Philox key of this instance's stream (Threefry: key words 0-1)
     uint32_t st[6];           // MRG32k3a start state (written by the set-up kernel)
     uint64_t stream;          // stream index in its set
-    uint64_t ctr_hi;          // Philox counter words 2-3 (the stream, or the seed when keyed)
+    uint64_t ctr_hi;          // Philox counter words 2-3 (the stream, or the seed when keyed);
+                              // Threefry key words 2-3 (the seed)
     uint64_t offset;          // draws after the stream's current position
     uint64_t pos;             // Philox start position (written by the set-up kernel)
     uint64_t length;
@@ -156,8 +158,9 @@ struct srng_set {
     uint64_t stream_base;    // stream number of slot 0 (a set may hold any range of streams)
     uint64_t seed;
     uint32_t y0[6];          // MRG32k3a seed state
-    uint32_t key0, key1;     // Philox seed words (key, or counter words 2-3 when keyed)
-    bool keyed;              // Philox key-per-stream layout
+    uint32_t key0, key1;     // Philox / Threefry seed words (Philox key, or counter words 2-3 when keyed)
+    bool keyed;              // key = the stream (keyed Philox, Threefry)
+    bool threefry;           // Threefry4x32-20 (counter-based family, kernels as Philox)
     int device;
     uint32_t *d_state;       // MRG32k3a SoA states (6 x n_streams)
     uint64_t *d_pos;         // Philox positions
@@ -169,3 +172,9 @@ struct srng_set {
     cudaEvent_t ev_gen[2], ev_copy[2];
     std::mutex mu;
 };
+
+namespace srng_impl {
+// Generator value of a set's work descriptors: the kernels' choice of block function.
+inline uint32_t inst_gen(const srng_set *s) { return s->threefry ? SRNG_THREEFRY4X32_20 : (uint32_t)s->gen; }
+}  // namespace srng_impl
+

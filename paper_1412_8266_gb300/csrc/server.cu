@@ -191,7 +191,7 @@ srng_status launch_step(srng_server *srv, Slot &sl)
         }
         BatchInst &b = sl.h_inst[n_inst];
         memset(&b, 0, sizeof b);
-        b.gen = set->gen;
+        b.gen = inst_gen(set);
         const uint64_t gs = set->stream_base + r.stream;  // stream number
         b.key0 = set->keyed ? (uint32_t)gs : set->key0;
         b.key1 = set->keyed ? (uint32_t)(gs >> 32) : set->key1;

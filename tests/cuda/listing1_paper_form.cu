@@ -24,6 +24,12 @@ __global__ void barKernel(uint32_t *ddata)
     ddata[2 * i + 1] = rng.next();
 }
 
+__global__ void bazKernel(double *ddata)
+{
+    RNG<double, srng::Threefry4x32_20> rng;
+    ddata[blockDim.x * blockIdx.x + threadIdx.x] = rng.next();
+}
+
 // launches = number of fooKernel launches (each continues every stream).
 extern "C" int run_paper_listing1(float *d_data, int block_num, int thread_num, int launches, uint64_t seed)
 {
@@ -41,5 +47,14 @@ extern "C" int run_philox_form(uint32_t *d_data, int block_num, int thread_num, 
     barKernel<<<block_num, thread_num>>>(d_data);
     const int rc = cudaDeviceSynchronize() == cudaSuccess ? 0 : 2;
     RNG<uint32_t, srng::Philox4x32_10>::release();
+    return rc;
+}
+
+extern "C" int run_threefry_form(double *d_data, int block_num, int thread_num, uint64_t seed)
+{
+    if (RNG<double, srng::Threefry4x32_20>::init((uint64_t)block_num * thread_num, seed) != SRNG_OK) return 1;
+    bazKernel<<<block_num, thread_num>>>(d_data);
+    const int rc = cudaDeviceSynchronize() == cudaSuccess ? 0 : 2;
+    RNG<double, srng::Threefry4x32_20>::release();
     return rc;
 }

@@ -30,6 +30,8 @@ def user_lib(tmp_path_factory):
     lib = ctypes.CDLL(out)
     lib.run_listing1.restype = ctypes.c_int
     lib.run_listing1.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
+    lib.run_user_threefry.restype = ctypes.c_int
+    lib.run_user_threefry.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
     lib.run_user_normals.restype = ctypes.c_int
     lib.run_user_normals.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
     return lib
@@ -74,6 +76,27 @@ def test_philox_listing1_kernel(user_lib):
         srng.srng_destroy(h)
 
 
+def test_user_kernel_threefry(user_lib):
+    """srng::Threefry4x32_20 in a user kernel: draws equal the oracle's and the
+    stored positions let the library continue the streams."""
+    n_streams, per, seed = 300, 9, 0xC0FFEE
+    h = srng.srng_create(srng.SRNG_THREEFRY4X32_20, seed, n_streams)
+    try:
+        srng.srng_jump(h, 0, n_streams, srng.SRNG_JUMP_DRAWS, 3)
+        v = srng.srng_get_device_view(h)
+        out = torch.empty(n_streams * per, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        assert user_lib.run_user_threefry(ctypes.byref(v), out.data_ptr(), per) == 0
+        ref, _ = O.threefry_bulk(seed, 0, [3] * n_streams, 2 * per)
+        assert np.array_equal(out.cpu().numpy().view(np.uint32).reshape(n_streams, per), ref[:, :per])
+        nxt = torch.empty(n_streams * per, dtype=torch.int32, device="cuda")
+        srng.srng_generate(h, 0, n_streams, per, srng.SRNG_OUT_U32, nxt)
+        torch.cuda.synchronize()
+        assert np.array_equal(nxt.cpu().numpy().view(np.uint32).reshape(n_streams, per), ref[:, per:])
+    finally:
+        srng.srng_destroy(h)
+
+
 def test_user_kernel_normals(user_lib):
     """srng::dist::normal_pair inside a user kernel equals the oracle's
     Box-Muller on the oracle's Philox FP32 uniforms, bit for bit."""
@@ -106,6 +129,8 @@ def paper_form_lib(tmp_path_factory):
     lib.run_paper_listing1.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
     lib.run_philox_form.restype = ctypes.c_int
     lib.run_philox_form.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
+    lib.run_threefry_form.restype = ctypes.c_int
+    lib.run_threefry_form.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
     return lib
 
 
@@ -130,3 +155,13 @@ def test_paper_form_philox(paper_form_lib):
     assert paper_form_lib.run_philox_form(out.data_ptr(), block_num, thread_num, seed) == 0
     ref, _ = O.philox_bulk((seed, 0), 0, [0] * n, 2, O.OUT_U32)
     assert np.array_equal(out.cpu().numpy().view(np.uint32).reshape(n, 2), ref)
+
+
+def test_paper_form_threefry(paper_form_lib):
+    block_num, thread_num, seed = 7, 64, 0xBEEF
+    n = block_num * thread_num
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    assert paper_form_lib.run_threefry_form(out.data_ptr(), block_num, thread_num, seed) == 0
+    ref, _ = O.threefry_bulk(seed, 0, [0] * n, 1, O.OUT_F64)
+    assert np.array_equal(out.cpu().numpy(), ref.ravel())
