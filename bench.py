@@ -56,6 +56,8 @@ def parse():
                    help="time one kernel alone on a reduced size (for profiling), print one JSON line")
     p.add_argument("--case-scale", type=int, default=4, help="--case size = full size / this")
     p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--case-tune", default=None,
+                   help='--case launch shape as JSON, e.g. \'{"chunk": 2048, "vector_store": 3}\' (default: built-in)')
     return p.parse_args()
 
 
@@ -120,15 +122,28 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
 
 
-def source_hash(files):
+def source_hash(parts):
+    """Hash of the kernel's source: whole files, or (file, first line, last
+    line) regions -- the generation file and the MRG32k3a device maths of the
+    header, so that additions elsewhere in the header keep the counters valid."""
     h = hashlib.sha256()
-    for f in files:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+    for part in parts:
+        if isinstance(part, str):
+            with open(os.path.join(ROOT, part), "rb") as fh:
+                h.update(fh.read())
+            continue
+        path, first, last = part
+        with open(os.path.join(ROOT, path), "rb") as fh:
+            text = fh.read()
+        a = text.index(first.encode())
+        b = text.index(last.encode(), a) + len(last)
+        h.update(text[a:b])
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = ["paper_1412_8266_gb300/csrc/generate.cu", "include/srng_device.cuh"]
+KERNEL_SOURCES = ["paper_1412_8266_gb300/csrc/generate.cu",
+                  ("include/srng_device.cuh", "namespace mrg {", "}  // namespace mrg"),
+                  ("include/srng_device.cuh", "__device__ __forceinline__ float to_f32(uint32_t v)", "\n}\n")]
 
 
 def ncu_traffic(kernel_key: str):
@@ -528,13 +543,14 @@ def run_case(args):
     stream = torch.cuda.current_stream(dev)
     c = args.case
     k = max(1, args.case_scale)
-    res = {"case": c, "scale": k}
+    res = {"case": c, "scale": k, "tune": args.case_tune}
     if c.startswith("mrg"):
         S = S_STREAMS // k
         t = srng.SRNG_OUT_U32 if c == "mrg_u32" else srng.SRNG_OUT_F64
         h = srng.srng_create(srng.SRNG_MRG32K3A, SEED, S, srng.SRNG_SPACING_STREAM, stream)
         o = torch.empty(S * N_DRAWS, dtype=torch.int32 if t == 0 else torch.float64, device=dev)
-        fn = lambda: srng.srng_generate(h, 0, S, N_DRAWS, t, o, stream)
+        tune = json.loads(args.case_tune) if args.case_tune else None
+        fn = lambda: srng.srng_generate_tuned(h, 0, S, N_DRAWS, t, o, tune, stream)
         nbytes, nvals = o.numel() * o.element_size(), o.numel()
     elif c.startswith("philox") or c.startswith("threefry"):
         n = (1 << 30) // k
