@@ -23,6 +23,13 @@ Parity status per function (what pins it is in tests/test_oracle_pins.py):
       rotation counts and parity constant of Salmon et al. 2011 have no
       independent implementation here; structure pinned (bijection, key and
       counter use, the block-to-word layout, avalanche)
+  tinymt32_next / charpoly / max_period / jump / find_params  pinned (the
+      authors' default parameter set has period 2^127 - 1 under the step,
+      checked with sympy; the polynomial annihilates every state bit; jumps
+      equal stepping and close the period)
+  tinymt32_init / tinymt32_temper                          parity unpinned (the
+      published TinyMT32 seeding and tempering restated; no implementation
+      here to compare outputs with)
   seed_expand (SplitMix64)                                structure pinned; the two
       mixing multipliers are parity unpinned (no implementation in this
       environment to compare with, and the paper is silent on seeding)
@@ -88,6 +95,16 @@ def _load(path: str | None = None):
             "oracle_threefry_generate": (None, [u64, u64, u64, u64, i32, vp]),
             "oracle_threefry_bulk": (None, [u64, u64, u64p, u64, u64, i32, vp, i32]),
             "oracle_threefry_pi_count": (ctypes.c_int64, [u64, u64, u64, u64]),
+            "oracle_tinymt32_next": (None, [u32p, u32, u32]),
+            "oracle_tinymt32_temper": (u32, [u32p, u32]),
+            "oracle_tinymt32_init": (None, [u32, u32, u32, u32, u32p]),
+            "oracle_tinymt32_charpoly": (i32, [u32, u32, ctypes.POINTER(ctypes.c_uint8)]),
+            "oracle_tinymt32_max_period": (i32, [u32, u32]),
+            "oracle_tinymt32_find_params": (None, [u64, u32, u32p]),
+            "oracle_tinymt32_jump": (None, [u32p, u32, u32, u64, u64]),
+            "oracle_tinymt32_stream_start": (None, [u32, u32p, u64, u32p]),
+            "oracle_tinymt32_generate": (None, [u32p, u32p, u64, i32, vp]),
+            "oracle_tinymt32_bulk": (None, [u32p, u32p, u64, u64, u64, i32, vp, i32]),
             "oracle_to_f32": (ctypes.c_float, [u32]),
             "oracle_mrg_to_f64": (ctypes.c_double, [u32]),
             "oracle_dist_constants": (None, [ctypes.POINTER(ctypes.c_float)]),
@@ -276,6 +293,75 @@ def threefry_bulk(seed: int, stream0: int, positions, n: int, out_type: int = OU
 
 def threefry_pi_count(seed: int, stream: int, pos: int, length: int) -> int:
     return int(_load().oracle_threefry_pi_count(seed, stream, pos, length))
+
+
+# ---------------------------------------------------------------- TinyMT32
+def tinymt32_next(state, mat1: int, mat2: int) -> np.ndarray:
+    s = np.array(state, dtype=np.uint32)
+    _load().oracle_tinymt32_next(_u32p(s), mat1, mat2)
+    return s
+
+
+def tinymt32_temper(state, tmat: int) -> int:
+    s = np.array(state, dtype=np.uint32)
+    return int(_load().oracle_tinymt32_temper(_u32p(s), tmat))
+
+
+def tinymt32_init(seed32: int, prm) -> np.ndarray:
+    s = np.zeros(4, dtype=np.uint32)
+    _load().oracle_tinymt32_init(seed32, prm[0], prm[1], prm[2], _u32p(s))
+    return s
+
+
+def tinymt32_charpoly(mat1: int, mat2: int) -> list:
+    """Coefficients p[0..L] (p[i] of x^i) of the step's characteristic polynomial."""
+    buf = (ctypes.c_uint8 * 256)()
+    L = _load().oracle_tinymt32_charpoly(mat1, mat2, buf)
+    return list(buf)[:L + 1]
+
+
+def tinymt32_max_period(mat1: int, mat2: int) -> bool:
+    return bool(_load().oracle_tinymt32_max_period(mat1, mat2))
+
+
+def tinymt32_find_params(seed: int, count: int) -> np.ndarray:
+    out = np.zeros((count, 3), dtype=np.uint32)
+    _load().oracle_tinymt32_find_params(seed, count, _u32p(out))
+    return out
+
+
+def tinymt32_jump(state, mat1: int, mat2: int, J: int) -> np.ndarray:
+    s = np.array(state, dtype=np.uint32)
+    _load().oracle_tinymt32_jump(_u32p(s), mat1, mat2, (J >> 64) & (2**64 - 1), J & (2**64 - 1))
+    return s
+
+
+def tinymt32_stream_starts(seed32: int, prm, group_size: int, n_streams: int) -> np.ndarray:
+    """Start states (n_streams x 4): stream i uses parameter set i // group_size
+    and starts (i mod group_size) 2^64 steps after that set's seed state."""
+    prm = np.ascontiguousarray(np.asarray(prm, dtype=np.uint32).reshape(-1, 3))
+    out = np.zeros((n_streams, 4), dtype=np.uint32)
+    for i in range(n_streams):
+        p = np.ascontiguousarray(prm[i // group_size])
+        _load().oracle_tinymt32_stream_start(seed32, _u32p(p), i % group_size, _u32p(out[i]))
+    return out
+
+
+def tinymt32_generate(state, prm, n: int, out_type: int = OUT_U32):
+    s = np.array(state, dtype=np.uint32)
+    p = np.ascontiguousarray(np.asarray(prm, dtype=np.uint32))
+    out = np.empty(n, dtype=_DTYPES[out_type])
+    _load().oracle_tinymt32_generate(_u32p(s), _u32p(p), n, out_type, out.ctypes.data_as(ctypes.c_void_p))
+    return out, s
+
+
+def tinymt32_bulk(states, prm, group_size: int, n: int, out_type: int = OUT_U32, threads: int = 0):
+    st = np.ascontiguousarray(np.array(states, dtype=np.uint32).reshape(-1, 4))
+    p = np.ascontiguousarray(np.asarray(prm, dtype=np.uint32).reshape(-1, 3))
+    out = np.empty((st.shape[0], n), dtype=_DTYPES[out_type])
+    _load().oracle_tinymt32_bulk(_u32p(st), _u32p(p), group_size, st.shape[0], n, out_type,
+                                 out.ctypes.data_as(ctypes.c_void_p), threads)
+    return out, st
 
 
 # ---------------------------------------------------------------- conversions

@@ -513,6 +513,221 @@ void oracle_batch(uint64_t n_inst, const int32_t *gens, const uint32_t *mrg_stat
 }
 
 /* ---------------------------------------------------------------------- */
+/* TinyMT32 (Sec. 4.2; Saito & Matsumoto 2011): a 127-bit GF(2)-linear      */
+/* state of four 32-bit words (bit 31 of word 0 unused), parameterised by   */
+/* (mat1, mat2, tmat).  One step:                                           */
+/*   x = (s0 & 0x7fffffff) ^ s1 ^ s2;  x ^= x << 1;                         */
+/*   y = s3 ^ (s3 >> 1) ^ x;                                                 */
+/*   (s0, s1, s2, s3) = (s1, s2, x ^ (y << 10), y), then if y is odd         */
+/*   s1 ^= mat1 and s2 ^= mat2.                                             */
+/* Output (tempering): t = s0 + (s2 >> 8); v = s3 ^ t, ^ tmat if t is odd.   */
+/* Seeding of a parameter set from a 32-bit seed: (seed, mat1, mat2, tmat),  */
+/* words 1..7 (mod 4) mixed with i + 1812433253 (w ^ (w >> 30)) of the       */
+/* previous word, an all-zero state replaced by 'T','I','N','Y', then eight  */
+/* steps.  The paper's hybrid (Sec. 4.2): one parameter set per group of     */
+/* streams (a CUDA block), and stream j of a group starts j * 2^64 steps    */
+/* after the group's seed state (sequence splitting).                        */
+/* Jumps use the characteristic polynomial p of the step (degree 127, found */
+/* by Berlekamp-Massey on an output bit of the state): T^J s = r(T) s with  */
+/* r = x^J mod p, evaluated by Horner's rule on states.                     */
+/* ---------------------------------------------------------------------- */
+
+#define ORC_TMT_MASK 0x7fffffffU
+
+void oracle_tinymt32_next(uint32_t s[4], uint32_t mat1, uint32_t mat2)
+{
+    uint32_t x = (s[0] & ORC_TMT_MASK) ^ s[1] ^ s[2];
+    x ^= x << 1;
+    uint32_t y = s[3] ^ (s[3] >> 1) ^ x;
+    s[0] = s[1];
+    s[1] = s[2];
+    s[2] = x ^ (y << 10);
+    s[3] = y;
+    if (y & 1) {
+        s[1] ^= mat1;
+        s[2] ^= mat2;
+    }
+}
+
+uint32_t oracle_tinymt32_temper(const uint32_t s[4], uint32_t tmat)
+{
+    uint32_t t = s[0] + (s[2] >> 8);
+    uint32_t v = s[3] ^ t;
+    if (t & 1) v ^= tmat;
+    return v;
+}
+
+void oracle_tinymt32_init(uint32_t seed32, uint32_t mat1, uint32_t mat2, uint32_t tmat, uint32_t s[4])
+{
+    s[0] = seed32;
+    s[1] = mat1;
+    s[2] = mat2;
+    s[3] = tmat;
+    for (uint32_t i = 1; i < 8; ++i) {
+        uint32_t prev = s[(i - 1) % 4];
+        s[i % 4] ^= i + 1812433253U * (prev ^ (prev >> 30));
+    }
+    if ((s[0] & ORC_TMT_MASK) == 0 && s[1] == 0 && s[2] == 0 && s[3] == 0) {
+        s[0] = 'T';
+        s[1] = 'I';
+        s[2] = 'N';
+        s[3] = 'Y';
+    }
+    for (int i = 0; i < 8; ++i) oracle_tinymt32_next(s, mat1, mat2);
+}
+
+/* Polynomials over GF(2) as coefficient arrays: c[i] = coefficient of x^i. */
+#define ORC_PMAX 256
+
+/* Characteristic polynomial of the step: minimal polynomial (Berlekamp-
+ * Massey) of bit 0 of s3 along 2 x 127 steps from the parameter set's seed-1
+ * state.  Returns its degree L; p[0..L] receives the coefficients. */
+int oracle_tinymt32_charpoly(uint32_t mat1, uint32_t mat2, uint8_t p[ORC_PMAX])
+{
+    uint8_t bits[254];
+    uint32_t s[4];
+    oracle_tinymt32_init(1, mat1, mat2, 0, s);
+    for (int i = 0; i < 254; ++i) {
+        oracle_tinymt32_next(s, mat1, mat2);
+        bits[i] = s[3] & 1;
+    }
+    uint8_t c[ORC_PMAX] = {0}, b[ORC_PMAX] = {0}, t[ORC_PMAX];
+    c[0] = b[0] = 1;
+    int L = 0, m = 1;
+    for (int n = 0; n < 254; ++n) {
+        int d = bits[n];
+        for (int i = 1; i <= L; ++i) d ^= c[i] & bits[n - i];
+        if (!d) {
+            ++m;
+        } else if (2 * L <= n) {
+            memcpy(t, c, sizeof t);
+            for (int i = 0; i + m < ORC_PMAX; ++i) c[i + m] ^= b[i];
+            L = n + 1 - L;
+            memcpy(b, t, sizeof b);
+            m = 1;
+        } else {
+            for (int i = 0; i + m < ORC_PMAX; ++i) c[i + m] ^= b[i];
+            ++m;
+        }
+    }
+    memset(p, 0, ORC_PMAX);
+    for (int i = 0; i <= L; ++i) p[L - i] = c[i];   /* reciprocal of the connection polynomial */
+    return L;
+}
+
+/* a * b mod p, all of degree < 127 except p (degree 127). */
+static void orc_pmulmod(const uint8_t a[128], const uint8_t b[128], const uint8_t p[ORC_PMAX], uint8_t out[128])
+{
+    uint8_t prod[256] = {0};
+    for (int i = 0; i < 127; ++i)
+        if (a[i])
+            for (int j = 0; j < 127; ++j) prod[i + j] ^= b[j];
+    for (int k = 252; k >= 127; --k)
+        if (prod[k])
+            for (int i = 0; i <= 127; ++i) prod[k - 127 + i] ^= p[i];
+    memcpy(out, prod, 128);
+}
+
+/* r = x^J mod p for J = (e_hi, e_lo), by left-to-right square and multiply. */
+static void orc_xpow(uint64_t e_hi, uint64_t e_lo, const uint8_t p[ORC_PMAX], uint8_t r[128])
+{
+    memset(r, 0, 128);
+    r[0] = 1;
+    uint8_t x[128] = {0};
+    x[1] = 1;
+    for (int bit = 127; bit >= 0; --bit) {
+        orc_pmulmod(r, r, p, r);
+        uint64_t word = bit >= 64 ? e_hi : e_lo;
+        if ((word >> (bit % 64)) & 1) orc_pmulmod(r, x, p, r);
+    }
+}
+
+/* 1 when the step has period 2^127 - 1: p of degree 127 divides x^(2^127) - x
+ * and has no root in GF(2); 127 being prime, p is then irreducible, and
+ * 2^127 - 1 being prime, primitive. */
+int oracle_tinymt32_max_period(uint32_t mat1, uint32_t mat2)
+{
+    uint8_t p[ORC_PMAX];
+    if (oracle_tinymt32_charpoly(mat1, mat2, p) != 127) return 0;
+    int ones = 0;
+    for (int i = 0; i <= 127; ++i) ones += p[i];
+    if (p[0] == 0 || ones % 2 == 0) return 0;   /* x or x + 1 divides p */
+    uint8_t r[128] = {0};
+    r[1] = 1;
+    for (int i = 0; i < 127; ++i) orc_pmulmod(r, r, p, r);   /* x^(2^127) */
+    for (int i = 0; i < 128; ++i)
+        if (r[i] != (i == 1)) return 0;
+    return 1;
+}
+
+/* Parameter sets with period 2^127 - 1 drawn from SplitMix64(seed): each
+ * candidate takes two outputs a, b: mat1 = a mod 2^32, mat2 = a >> 32,
+ * tmat = b mod 2^32 (the tempering parameter is not tuned for
+ * equidistribution; it does not enter the period).  out[3 i + 0..2]. */
+void oracle_tinymt32_find_params(uint64_t seed, uint32_t count, uint32_t *out)
+{
+    uint64_t sm = seed;
+    uint32_t found = 0;
+    while (found < count) {
+        uint64_t a = oracle_splitmix64_next(&sm);
+        uint64_t b = oracle_splitmix64_next(&sm);
+        uint32_t mat1 = (uint32_t)a, mat2 = (uint32_t)(a >> 32), tmat = (uint32_t)b;
+        if (!oracle_tinymt32_max_period(mat1, mat2)) continue;
+        out[3 * found] = mat1;
+        out[3 * found + 1] = mat2;
+        out[3 * found + 2] = tmat;
+        ++found;
+    }
+}
+
+/* s <- T^J s for J = (e_hi, e_lo) (s must come from at least one step). */
+void oracle_tinymt32_jump(uint32_t s[4], uint32_t mat1, uint32_t mat2, uint64_t e_hi, uint64_t e_lo)
+{
+    uint8_t p[ORC_PMAX], r[128];
+    oracle_tinymt32_charpoly(mat1, mat2, p);
+    orc_xpow(e_hi, e_lo, p, r);
+    uint32_t acc[4] = {0, 0, 0, 0};
+    for (int i = 126; i >= 0; --i) {
+        oracle_tinymt32_next(acc, mat1, mat2);
+        if (r[i])
+            for (int w = 0; w < 4; ++w) acc[w] ^= s[w];
+    }
+    memcpy(s, acc, sizeof acc);
+}
+
+/* Start state of stream j of a group: the group's seed state (seed32 and its
+ * parameters), then j * 2^64 steps. */
+void oracle_tinymt32_stream_start(uint32_t seed32, const uint32_t prm[3], uint64_t j, uint32_t s[4])
+{
+    oracle_tinymt32_init(seed32, prm[0], prm[1], prm[2], s);
+    if (j) oracle_tinymt32_jump(s, prm[0], prm[1], j, 0);   /* J = j * 2^64 */
+}
+
+/* n draws of one stream from state s (advanced in place): step, then temper. */
+void oracle_tinymt32_generate(uint32_t s[4], const uint32_t prm[3], uint64_t n, int out_type, void *out)
+{
+    for (uint64_t k = 0; k < n; ++k) {
+        oracle_tinymt32_next(s, prm[0], prm[1]);
+        store_value(out_type, out, k, oracle_tinymt32_temper(s, prm[2]), 0);
+    }
+}
+
+/* Stream-major bulk output; stream i uses parameter set i / group_size and
+ * its state states[4 i .. 4 i + 3] (advanced in place). */
+void oracle_tinymt32_bulk(uint32_t *states, const uint32_t *prm, uint64_t group_size, uint64_t n_streams,
+                          uint64_t n, int out_type, void *out, int threads)
+{
+    size_t esz = out_type == ORC_OUT_F64 ? 8 : 4;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t i = 0; i < (int64_t)n_streams; ++i)
+        oracle_tinymt32_generate(states + 4 * i, prm + 3 * ((uint64_t)i / group_size), n, out_type,
+                                 (char *)out + (size_t)i * n * esz);
+}
+
+/* ---------------------------------------------------------------------- */
 /* Non-uniform variates from FP32 uniforms (beyond the paper, which covers  */
 /* uniform draws only): exponential by inversion, normal by Box & Muller    */
 /* (1958).  The reading taken: single precision throughout, every step one  */

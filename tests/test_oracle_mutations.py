@@ -50,6 +50,11 @@ MUTATIONS = {
     "reflection": ("if (exchanged) r = 1.0f - r;", "if (exchanged) r = r - 0.5f;"),
     "threefry permutation": ("        v[1] = v[3];\n        v[3] = t;\n", "        (void)t;\n"),
     "threefry rounds": ("for (int d = 0; d < 20; ++d) {", "for (int d = 0; d < 3; ++d) {"),
+    "tinymt shift": ("    s[2] = x ^ (y << 10);", "    s[2] = x ^ (y << 11);"),
+    "tinymt feedback": ("    x ^= x << 1;\n    uint32_t y", "    x ^= x << 2;\n    uint32_t y"),
+    "tinymt mask": ("uint32_t x = (s[0] & ORC_TMT_MASK) ^ s[1] ^ s[2];", "uint32_t x = s[0] ^ s[1] ^ s[2];"),
+    "tinymt horner order": ("    for (int i = 126; i >= 0; --i) {\n        oracle_tinymt32_next(acc",
+                            "    for (int i = 0; i <= 126; ++i) {\n        oracle_tinymt32_next(acc"),
     "box-muller radius": ("float r = sqrtf(-2.0f * orc_ln(&k, 1.0f - in[2 * j]));",
                           "float r = sqrtf(-2.0f * orc_ln(&k, in[2 * j]));"),
 }
@@ -184,6 +189,16 @@ def _pins_fail(ref):
                 c2[b // 32] ^= np.uint32(1 << (b % 32))
                 flips[b] += np.unpackbits(O.threefry4x32_20(c2, key).view(np.uint8)) != base
         if np.abs(flips / 48 - 0.5).max() > 0.33:
+            return True
+        # TinyMT32: the authors' default parameter set has period 2^127 - 1
+        # under the step; jumps equal stepping
+        if not O.tinymt32_max_period(0x8F7011EE, 0xFC78FF1F):
+            return True
+        t0 = O.tinymt32_init(7, (0x8F7011EE, 0xFC78FF1F, 0x3793FDFF))
+        t = t0.copy()
+        for _ in range(300):
+            t = O.tinymt32_next(t, 0x8F7011EE, 0xFC78FF1F)
+        if not np.array_equal(O.tinymt32_jump(t0, 0x8F7011EE, 0xFC78FF1F, 300), t):
             return True
         return False
     except Exception:

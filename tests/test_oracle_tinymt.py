@@ -1,0 +1,130 @@
+"""Pins of the oracle's TinyMT32 (Sec. 4.2: parameterised statuses shared by
+the threads of a block, sequence splitting between the threads).
+
+- The step: under it, the authors' default parameter set of TinyMT32
+  (mat1 = 0x8f7011ee, mat2 = 0xfc78ff1f, Saito & Matsumoto 2011) has the
+  maximal period 2^127 - 1 -- a property a wrong shift, mask or feedback
+  destroys with probability about 126/127 -- checked with sympy's GF(2)
+  arithmetic (an independent implementation), not the oracle's own.
+- The characteristic polynomial annihilates every state bit's sequence.
+- Jumps equal brute-force stepping, compose additively, and T^(2^127 - 1)
+  is the identity.
+- Parameter search: every set found has period 2^127 - 1 (sympy).
+The seeding procedure and the tempering are the published TinyMT32 ones,
+restated; no independent implementation is available to compare their
+outputs with, so they are parity unpinned beyond the properties below."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+DEFAULT = (0x8F7011EE, 0xFC78FF1F, 0x3793FDFF)
+
+
+def _sympy_poly(coeffs):
+    sympy = pytest.importorskip("sympy")
+    x = sympy.Symbol("x")
+    return sympy.Poly(sum(sympy.Integer(c) * x**i for i, c in enumerate(coeffs) if c), x, modulus=2), x
+
+
+def _primitive_127(coeffs):
+    """Degree 127, irreducible over GF(2) (hence primitive: 2^127 - 1 is prime),
+    decided by sympy."""
+    sympy = pytest.importorskip("sympy")
+    p, x = _sympy_poly(coeffs)
+    if p.degree() != 127 or not p.is_irreducible:
+        return False
+    # x^(2^127 - 1) = 1 mod p, by sympy's own modular powering
+    r = sympy.Poly(1, x, modulus=2)
+    base = sympy.Poly(x, x, modulus=2)
+    e = 2**127 - 1
+    while e:
+        if e & 1:
+            r = (r * base).rem(p)
+        base = (base * base).rem(p)
+        e >>= 1
+    return r == sympy.Poly(1, x, modulus=2)
+
+
+def test_default_parameter_set_has_maximal_period():
+    p = O.tinymt32_charpoly(DEFAULT[0], DEFAULT[1])
+    assert len(p) == 128 and _primitive_127(p)
+    assert O.tinymt32_max_period(DEFAULT[0], DEFAULT[1])
+
+
+def test_charpoly_annihilates_every_state_bit():
+    p = O.tinymt32_charpoly(DEFAULT[0], DEFAULT[1])
+    s = O.tinymt32_init(12345, DEFAULT)
+    seq = []
+    for _ in range(400):
+        s = O.tinymt32_next(s, DEFAULT[0], DEFAULT[1])
+        seq.append(s.copy())
+    seq = np.array(seq, dtype=np.uint64)
+    bits = np.stack([(seq[:, w] >> b) & 1 for w in range(4) for b in range(32) if not (w == 0 and b == 31)])
+    idx = [i for i, c in enumerate(p) if c]
+    for n in range(0, 400 - 128, 17):
+        acc = np.zeros(bits.shape[0], dtype=np.uint64)
+        for i in idx:
+            acc ^= bits[:, n + i]
+        assert not acc.any()
+
+
+@pytest.mark.parametrize("J", [1, 2, 3, 127, 1000, 12345, 65543])
+def test_jump_equals_stepping(J):
+    s0 = O.tinymt32_init(7, DEFAULT)
+    s = s0.copy()
+    for _ in range(J):
+        s = O.tinymt32_next(s, DEFAULT[0], DEFAULT[1])
+    assert np.array_equal(O.tinymt32_jump(s0, DEFAULT[0], DEFAULT[1], J), s)
+
+
+def test_jumps_compose_and_the_period_closes():
+    s0 = O.tinymt32_init(99, DEFAULT)
+    a, b = 2**100 + 12345, 2**64 * 7 + 3
+    ab = O.tinymt32_jump(O.tinymt32_jump(s0, DEFAULT[0], DEFAULT[1], a), DEFAULT[0], DEFAULT[1], b)
+    assert np.array_equal(ab, O.tinymt32_jump(s0, DEFAULT[0], DEFAULT[1], a + b))
+    assert np.array_equal(O.tinymt32_jump(s0, DEFAULT[0], DEFAULT[1], 2**127 - 1), s0)
+    assert not np.array_equal(O.tinymt32_jump(s0, DEFAULT[0], DEFAULT[1], 2**126), s0)
+
+
+def test_found_parameter_sets_have_maximal_period():
+    prm = O.tinymt32_find_params(0x5EED, 4)
+    assert len({tuple(r) for r in prm}) == 4
+    for mat1, mat2, _ in prm:
+        assert _primitive_127(O.tinymt32_charpoly(int(mat1), int(mat2)))
+    assert np.array_equal(prm, O.tinymt32_find_params(0x5EED, 4))     # deterministic
+    assert not O.tinymt32_max_period(0, 0)
+
+
+def test_stream_starts_are_substreams_2_64_apart():
+    prm = O.tinymt32_find_params(3, 2)
+    st = O.tinymt32_stream_starts(1, prm, 3, 6)
+    for g in range(2):
+        p = prm[g]
+        base = O.tinymt32_init(1, p)
+        assert np.array_equal(st[3 * g], base)
+        assert np.array_equal(st[3 * g + 1], O.tinymt32_jump(base, int(p[0]), int(p[1]), 2**64))
+        assert np.array_equal(st[3 * g + 2], O.tinymt32_jump(st[3 * g + 1], int(p[0]), int(p[1]), 2**64))
+
+
+def test_generate_is_step_then_temper():
+    s0 = O.tinymt32_init(5, DEFAULT)
+    out, s_end = O.tinymt32_generate(s0, DEFAULT, 50)
+    s = s0.copy()
+    for k in range(50):
+        s = O.tinymt32_next(s, DEFAULT[0], DEFAULT[1])
+        assert int(out[k]) == O.tinymt32_temper(s, DEFAULT[2])
+    assert np.array_equal(s, s_end)
+    f, _ = O.tinymt32_generate(s0, DEFAULT, 50, O.OUT_F32)
+    assert np.array_equal(f, (out >> 8).astype(np.float32) * np.float32(2.0**-24))
+
+
+def test_output_bytes_uniform_and_streams_distinct():
+    prm = O.tinymt32_find_params(11, 2)
+    st = O.tinymt32_stream_starts(1, prm, 2, 4)
+    out, _ = O.tinymt32_bulk(st, prm, 2, 1 << 16)
+    counts = np.bincount(out.view(np.uint8).ravel(), minlength=256)
+    e = out.size * 4 / 256
+    assert ((counts - e) ** 2 / e).sum() < 400
+    rows = {bytes(r[:64].tobytes()) for r in out}
+    assert len(rows) == 4
