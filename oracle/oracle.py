@@ -103,6 +103,7 @@ def _load(path: str | None = None):
             "oracle_tinymt32_find_params": (None, [u64, u32, u32p]),
             "oracle_tinymt32_jump": (None, [u32p, u32, u32, u64, u64]),
             "oracle_tinymt32_stream_start": (None, [u32, u32p, u64, u32p]),
+            "oracle_tinymt32_stream_starts": (None, [u32, u32p, u64, u64, u32p]),
             "oracle_tinymt32_generate": (None, [u32p, u32p, u64, i32, vp]),
             "oracle_tinymt32_bulk": (None, [u32p, u32p, u64, u64, u64, i32, vp, i32]),
             "oracle_to_f32": (ctypes.c_float, [u32]),
@@ -336,14 +337,20 @@ def tinymt32_jump(state, mat1: int, mat2: int, J: int) -> np.ndarray:
     return s
 
 
+def tinymt32_stream_start(seed32: int, prm, j: int) -> np.ndarray:
+    """Start state of stream j of a group: the seed state, then j * 2^64 steps."""
+    p = np.ascontiguousarray(np.asarray(prm, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    _load().oracle_tinymt32_stream_start(seed32, _u32p(p), j, _u32p(out))
+    return out
+
+
 def tinymt32_stream_starts(seed32: int, prm, group_size: int, n_streams: int) -> np.ndarray:
     """Start states (n_streams x 4): stream i uses parameter set i // group_size
     and starts (i mod group_size) 2^64 steps after that set's seed state."""
     prm = np.ascontiguousarray(np.asarray(prm, dtype=np.uint32).reshape(-1, 3))
     out = np.zeros((n_streams, 4), dtype=np.uint32)
-    for i in range(n_streams):
-        p = np.ascontiguousarray(prm[i // group_size])
-        _load().oracle_tinymt32_stream_start(seed32, _u32p(p), i % group_size, _u32p(out[i]))
+    _load().oracle_tinymt32_stream_starts(seed32, _u32p(prm), group_size, n_streams, _u32p(out))
     return out
 
 

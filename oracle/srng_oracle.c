@@ -703,6 +703,37 @@ void oracle_tinymt32_stream_start(uint32_t seed32, const uint32_t prm[3], uint64
     if (j) oracle_tinymt32_jump(s, prm[0], prm[1], j, 0);   /* J = j * 2^64 */
 }
 
+/* Start states of n_streams streams, stream i in group i / group_size:
+ * the group's seed state, then each next stream of the group 2^64 steps
+ * after the previous one (r = x^(2^64) mod p applied once per stream).
+ * out[4 i .. 4 i + 3]; prm[3 g .. 3 g + 2] per group. */
+void oracle_tinymt32_stream_starts(uint32_t seed32, const uint32_t *prm, uint64_t group_size, uint64_t n_streams,
+                                   uint32_t *out)
+{
+    uint64_t n_groups = (n_streams + group_size - 1) / group_size;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t g = 0; g < (int64_t)n_groups; ++g) {
+        const uint32_t *p = prm + 3 * g;
+        uint8_t poly[ORC_PMAX], r[128];
+        oracle_tinymt32_charpoly(p[0], p[1], poly);
+        orc_xpow(1, 0, poly, r);                       /* x^(2^64) mod p */
+        uint32_t s[4];
+        oracle_tinymt32_init(seed32, p[0], p[1], p[2], s);
+        for (uint64_t j = 0; j < group_size && g * group_size + j < n_streams; ++j) {
+            if (j > 0) {                               /* s <- r(T) s */
+                uint32_t acc[4] = {0, 0, 0, 0};
+                for (int i = 126; i >= 0; --i) {
+                    oracle_tinymt32_next(acc, p[0], p[1]);
+                    if (r[i])
+                        for (int w = 0; w < 4; ++w) acc[w] ^= s[w];
+                }
+                memcpy(s, acc, sizeof acc);
+            }
+            memcpy(out + 4 * (g * group_size + j), s, sizeof s);
+        }
+    }
+}
+
 /* n draws of one stream from state s (advanced in place): step, then temper. */
 void oracle_tinymt32_generate(uint32_t s[4], const uint32_t prm[3], uint64_t n, int out_type, void *out)
 {

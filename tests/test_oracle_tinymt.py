@@ -96,6 +96,13 @@ def test_found_parameter_sets_have_maximal_period():
     assert not O.tinymt32_max_period(0, 0)
 
 
+def test_bulk_stream_starts_equal_one_by_one():
+    prm = O.tinymt32_find_params(5, 3)
+    bulk = O.tinymt32_stream_starts(77, prm, 4, 10)
+    for i in range(10):
+        assert np.array_equal(bulk[i], O.tinymt32_stream_start(77, prm[i // 4], i % 4)), i
+
+
 def test_stream_starts_are_substreams_2_64_apart():
     prm = O.tinymt32_find_params(3, 2)
     st = O.tinymt32_stream_starts(1, prm, 3, 6)
