@@ -444,6 +444,20 @@ def extras(torch, srng, dev, stream, peak):
         del o
     srng.srng_destroy(h)
     res["threefry_bulk_2^30"] = tf
+    # TinyMT32 bulk at the MRG32k3a bulk shape: 2^18 streams (1024 parameter sets of 256) x 4096, u32 and FP64
+    tm = {}
+    t0 = time.perf_counter()
+    h = srng.srng_create(srng.SRNG_TINYMT32, SEED, S_STREAMS, srng.SRNG_SPACING_STREAM, stream)
+    tm["create_s"] = time.perf_counter() - t0
+    for name, t, dt in (("u32", srng.SRNG_OUT_U32, torch.int32), ("f64", srng.SRNG_OUT_F64, torch.float64)):
+        o = torch.empty(S_STREAMS * N_DRAWS, dtype=dt, device=dev)
+        best, med = _time(torch, stream, lambda: srng.srng_generate(h, 0, S_STREAMS, N_DRAWS, t, o, stream))
+        nb = o.numel() * o.element_size()
+        tm[name] = {"ms_best": best, "ms_median": med, "Guniforms_s": o.numel() / best / 1e6, "GB_s": nb / best / 1e6,
+                    "frac_of_copy_peak": nb / best / 1e6 / peak}
+        del o
+    srng.srng_destroy(h)
+    res["tinymt_bulk_2^18x4096"] = tm
     # Philox layouts at the many-stream shape (2^18 streams x 4096 words, uint32):
     # counter split (one key) vs keyed (key = stream, Sec. 4.3)
     lay = {}
@@ -560,6 +574,13 @@ def run_case(args):
         o = torch.empty(n, dtype=torch.int32 if t == 0 else torch.float32, device=dev)
         fn = lambda: srng.srng_generate(h, 0, 1, n, t, o, stream)
         nbytes, nvals = n * 4, n
+    elif c.startswith("tinymt"):
+        S = S_STREAMS // k
+        t = srng.SRNG_OUT_U32 if c == "tinymt_u32" else srng.SRNG_OUT_F64
+        h = srng.srng_create(srng.SRNG_TINYMT32, SEED, S, srng.SRNG_SPACING_STREAM, stream)
+        o = torch.empty(S * N_DRAWS, dtype=torch.int32 if t == 0 else torch.float64, device=dev)
+        fn = lambda: srng.srng_generate(h, 0, S, N_DRAWS, t, o, stream)
+        nbytes, nvals = o.numel() * o.element_size(), o.numel()
     elif c.startswith("transform"):
         n = (1 << 30) // k
         d = srng.SRNG_DIST_NORMAL if c == "transform_normal" else srng.SRNG_DIST_EXPONENTIAL
@@ -590,8 +611,8 @@ def run_case(args):
     return 0
 
 
-CASES = {"mrg_u32", "mrg_f64", "philox_u32", "philox_f32", "threefry_u32", "threefry_f32", "batch_write", "batch_pi",
-         "transform_exponential", "transform_normal"}
+CASES = {"mrg_u32", "mrg_f64", "philox_u32", "philox_f32", "threefry_u32", "threefry_f32", "tinymt_u32", "tinymt_f64",
+         "batch_write", "batch_pi", "transform_exponential", "transform_normal"}
 
 
 def main():

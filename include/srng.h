@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define SRNG_ABI_VERSION 1
+#define SRNG_ABI_VERSION 2
 
 typedef enum srng_status {
     SRNG_OK = 0,
@@ -66,7 +66,8 @@ typedef enum srng_gen {
     SRNG_MRG32K3A = 0,
     SRNG_PHILOX4X32_10 = 1,      /* streams split the counter, one key per set        */
     SRNG_PHILOX4X32_10_KEYED = 2, /* one key per stream (paper Sec. 4.3): see srng_create */
-    SRNG_THREEFRY4X32_20 = 3      /* Threefry4x32, 20 rounds (Sec. 4.3): see srng_create  */
+    SRNG_THREEFRY4X32_20 = 3,     /* Threefry4x32, 20 rounds (Sec. 4.3): see srng_create  */
+    SRNG_TINYMT32 = 4             /* TinyMT32 (Sec. 4.2): see srng_create_tinymt          */
 } srng_gen;
 
 typedef enum srng_out {
@@ -179,6 +180,47 @@ srng_status srng_create_from_state(srng_set **out, const uint32_t state[6], uint
 srng_status srng_create_range(srng_set **out, srng_gen gen, uint64_t seed, const uint32_t state[6],
                               uint64_t stream_base, uint64_t n_streams, srng_spacing spacing, void *cuda_stream);
 
+/* TinyMT32 (paper Sec. 4.2; Saito & Matsumoto 2011).  A 127-bit GF(2)-linear
+ * state of four uint32 words (bit 31 of word 0 unused) and a parameter set
+ * (mat1, mat2, tmat).  One step:
+ *   x = (s0 & 0x7fffffff) ^ s1 ^ s2;  x ^= x << 1;  y = s3 ^ (s3 >> 1) ^ x;
+ *   (s0, s1, s2, s3) = (s1, s2, x ^ (y << 10), y);  if y is odd: s1 ^= mat1,
+ *   s2 ^= mat2.
+ * Draw = tempering of the stepped state: t = s0 + (s2 >> 8);
+ *   v = s3 ^ t, and ^ tmat when t is odd.  Conversions as Philox (32-bit words).
+ * The paper's hybrid partition: the n_params parameter sets each serve a group
+ * of group_size consecutive streams (a CUDA block's threads); stream j of a
+ * group starts j * 2^64 steps after the group's seed state (sequence
+ * splitting; the period is 2^127 - 1).  The seed state of a group is the
+ * TinyMT32 seeding of (seed mod 2^32) with the group's parameters (words
+ * (seed, mat1, mat2, tmat), seven mixing steps w ^= i + 1812433253 (p ^ (p >> 30)),
+ * an all-zero state replaced, eight steps).
+ *
+ * srng_create_tinymt: params = 3 uint32 per set (mat1, mat2, tmat); every set
+ *   must have period 2^127 - 1 (SRNG_ERR_ARG otherwise); n_streams =
+ *   n_params * group_size (<= 2^40).  Synchronises cuda_stream.
+ * srng_create(SRNG_TINYMT32, seed, n_streams, ...) = srng_create_tinymt with
+ *   group_size 256 and ceil(n_streams / 256) parameter sets found by
+ *   srng_tinymt_find_params(seed, ...); the last group may be partial.
+ * srng_tinymt_find_params: parameter sets with period 2^127 - 1 drawn in
+ *   order from SplitMix64(seed) (two outputs a, b per candidate: mat1 = a mod
+ *   2^32, mat2 = a >> 32, tmat = b mod 2^32; a candidate is kept when the
+ *   characteristic polynomial of the step, found by Berlekamp-Massey, has
+ *   degree 127 and is irreducible -- primitive, 2^127 - 1 being prime).  The
+ *   tempering parameter is not tuned for equidistribution.  Host only;
+ *   about 1-2 ms per set, spread over the host's cores.
+ * srng_tinymt_check_params: *max_period = 1 when (mat1, mat2) gives period
+ *   2^127 - 1.
+ * Jumps (srng_jump, SRNG_JUMP_DRAWS only) and chunked generation use
+ * T^J s = r(T) s with r = x^J mod p: the polynomial on the host, its
+ * evaluation on each state (Horner's rule, 127 steps) on the device.
+ * TinyMT sets are not accepted by the batch calls or the server
+ * (SRNG_ERR_UNSUPPORTED). */
+srng_status srng_create_tinymt(srng_set **out, const uint32_t *params, uint64_t n_params, uint64_t group_size,
+                               uint64_t seed, void *cuda_stream);
+srng_status srng_tinymt_find_params(uint64_t seed, uint32_t count, uint32_t *params_out);
+srng_status srng_tinymt_check_params(uint32_t mat1, uint32_t mat2, int *max_period);
+
 /* Free the set and its device memory (after the device is done with it:
  * synchronises the device first).  NULL is accepted. */
 srng_status srng_destroy(srng_set *set);
@@ -203,7 +245,8 @@ srng_status srng_describe(const srng_set *set, srng_set_desc *out);
  *     3x3 power is computed exactly on the host, its product with each state
  *     on the device.
  *   Philox: only SRNG_JUMP_DRAWS with n_hi = 0; position += n_lo
- *     (SRNG_ERR_RANGE if a position would pass 2^64 - 1).           */
+ *     (SRNG_ERR_RANGE if a position would pass 2^64 - 1).
+ *   TinyMT32: only SRNG_JUMP_DRAWS; state <- T^n state (any 128-bit n).  */
 srng_status srng_jump(srng_set *set, uint64_t stream_begin, uint64_t count, srng_jump_unit unit,
                       uint64_t n_hi, uint64_t n_lo, void *cuda_stream);
 
@@ -233,8 +276,10 @@ srng_status srng_generate_host(srng_set *set, uint64_t stream_begin, uint64_t st
 
 /* Copy per-stream state to / from the host (checkpoint / resume; paper
  * Sec. 1 asks for reproducible streams).  MRG32k3a: 6 uint32 per stream in
- * the order of srng_create_from_state; Philox: one uint64 position per
- * stream.  srng_set_state validates MRG32k3a states (SRNG_ERR_STATE).
+ * the order of srng_create_from_state; Philox and Threefry: one uint64
+ * position per stream; TinyMT32: 4 uint32 per stream (s0..s3).
+ * srng_set_state validates MRG32k3a states (SRNG_ERR_STATE) and rejects
+ * all-zero TinyMT32 states (bit 31 of s0 ignored).
  * Both synchronise cuda_stream. */
 srng_status srng_get_state(const srng_set *set, uint64_t stream_begin, uint64_t count,
                            void *state_host, void *cuda_stream);
@@ -268,6 +313,10 @@ typedef struct srng_dev_view {
                              * [j * n_streams + i], j in the srng_create_from_state order */
     uint64_t *philox_pos;   /* Philox / Threefry: position of each stream       */
     uint64_t stream_base;   /* stream number of slot 0 (srng_create_range)      */
+    uint32_t *tinymt_state; /* TinyMT32, SoA: word j of stream i at
+                             * [j * n_streams + i]                              */
+    const uint32_t *tinymt_params; /* TinyMT32: (mat1, mat2, tmat, 0) per set */
+    uint64_t tinymt_group_size;    /* TinyMT32: streams per parameter set     */
 } srng_dev_view;
 srng_status srng_get_device_view(const srng_set *set, srng_dev_view *out);
 

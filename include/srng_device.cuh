@@ -268,6 +268,56 @@ __device__ __forceinline__ void block(uint32_t &c0, uint32_t &c1, uint32_t &c2, 
 }
 }  // namespace threefry
 
+namespace tinymt {
+/* TinyMT32 (Saito & Matsumoto 2011; the paper's Sec. 4.2): one step of the
+ * 127-bit GF(2)-linear state (bit 31 of s0 unused) with parameters
+ * (mat1, mat2); the conditional feedback of y's low bit as a mask. */
+__device__ __forceinline__ void step(uint32_t &s0, uint32_t &s1, uint32_t &s2, uint32_t &s3, uint32_t mat1,
+                                     uint32_t mat2)
+{
+    uint32_t x = (s0 & 0x7fffffffu) ^ s1 ^ s2;
+    x ^= x << 1;
+    const uint32_t y = s3 ^ (s3 >> 1) ^ x;
+    const uint32_t m = 0u - (y & 1u);
+    s0 = s1;
+    s1 = s2 ^ (m & mat1);
+    s2 = x ^ (y << 10) ^ (m & mat2);
+    s3 = y;
+}
+
+/* The output of a stepped state: t = s0 + (s2 >> 8), s3 ^ t, ^ tmat if t is odd. */
+__device__ __forceinline__ uint32_t temper(uint32_t s0, uint32_t s2, uint32_t s3, uint32_t tmat)
+{
+    const uint32_t t = s0 + (s2 >> 8);
+    return s3 ^ t ^ ((0u - (t & 1u)) & tmat);
+}
+
+/* s <- r(T) s by Horner's rule, r a polynomial of degree < 127 over GF(2)
+ * (bit i of the 128-bit (r.x, r.y, r.z, r.w) = coefficient of x^i): with
+ * r = x^J mod p, p the characteristic polynomial, this is J steps.  The state
+ * must come from at least one step (the unused bit then lies in the image). */
+__device__ __forceinline__ void horner_word(uint32_t word, int hi, uint32_t &a0, uint32_t &a1, uint32_t &a2,
+                                            uint32_t &a3, uint32_t s0, uint32_t s1, uint32_t s2, uint32_t s3,
+                                            uint32_t mat1, uint32_t mat2)
+{
+    for (int b = hi; b >= 0; --b) {
+        step(a0, a1, a2, a3, mat1, mat2);
+        const uint32_t m = 0u - ((word >> b) & 1u);
+        a0 ^= m & s0; a1 ^= m & s1; a2 ^= m & s2; a3 ^= m & s3;
+    }
+}
+__device__ __forceinline__ void jump(const uint4 r, uint32_t &s0, uint32_t &s1, uint32_t &s2, uint32_t &s3,
+                                     uint32_t mat1, uint32_t mat2)
+{
+    uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    horner_word(r.w, 30, a0, a1, a2, a3, s0, s1, s2, s3, mat1, mat2);
+    horner_word(r.z, 31, a0, a1, a2, a3, s0, s1, s2, s3, mat1, mat2);
+    horner_word(r.y, 31, a0, a1, a2, a3, s0, s1, s2, s3, mat1, mat2);
+    horner_word(r.x, 31, a0, a1, a2, a3, s0, s1, s2, s3, mat1, mat2);
+    s0 = a0; s1 = a1; s2 = a2; s3 = a3;
+}
+}  // namespace tinymt
+
 /* (v >> 8) 2^-24 as a float, exact, without an integer-to-float conversion:
  * with a = v >> 8 = 2k + b, the bit pattern 0x3F800000 | k is 1 + k 2^-23, so
  * subtracting 1 gives k 2^-23 exactly, and adding b 2^-24 (bit pattern
@@ -385,6 +435,35 @@ class Threefry4x32_20 {
 
     uint32_t k0, k1, k2, k3;
     uint64_t stream_, pos_;
+};
+
+/* TinyMT32 stream handle (the paper's Sec. 4.2 hybrid: the parameter set of
+ * the stream's group, a CUDA block's threads, and the stream's own state). */
+class TinyMT32 {
+  public:
+    __device__ TinyMT32(const srng_dev_view &v, uint64_t stream)
+    {
+        const uint64_t n = v.n_streams;
+        s0 = v.tinymt_state[stream]; s1 = v.tinymt_state[n + stream];
+        s2 = v.tinymt_state[2 * n + stream]; s3 = v.tinymt_state[3 * n + stream];
+        const uint32_t *p = v.tinymt_params + 4 * (stream / v.tinymt_group_size);
+        mat1 = p[0]; mat2 = p[1]; tmat = p[2];
+    }
+    __device__ __forceinline__ uint32_t next_u32()
+    {
+        tinymt::step(s0, s1, s2, s3, mat1, mat2);
+        return tinymt::temper(s0, s2, s3, tmat);
+    }
+    __device__ __forceinline__ float next_f32() { return to_f32(next_u32()); }
+    __device__ __forceinline__ double next_f64() { return philox::to_f64(next_u32()); }
+    __device__ void store(const srng_dev_view &v, uint64_t stream) const
+    {
+        const uint64_t n = v.n_streams;
+        v.tinymt_state[stream] = s0; v.tinymt_state[n + stream] = s1;
+        v.tinymt_state[2 * n + stream] = s2; v.tinymt_state[3 * n + stream] = s3;
+    }
+
+    uint32_t s0, s1, s2, s3, mat1, mat2, tmat;
 };
 
 /* --------------------------------------------- non-uniform variates (FP32) */
@@ -507,6 +586,7 @@ struct is_generator<G, std::void_t<decltype(std::declval<G &>().next_u32()), dec
 static_assert(is_generator<Mrg32k3a>::value, "Mrg32k3a must provide next_u32/next_f32/next_f64");
 static_assert(is_generator<Philox4x32_10>::value, "Philox4x32_10 must provide next_u32/next_f32/next_f64");
 static_assert(is_generator<Threefry4x32_20>::value, "Threefry4x32_20 must provide next_u32/next_f32/next_f64");
+static_assert(is_generator<TinyMT32>::value, "TinyMT32 must provide next_u32/next_f32/next_f64");
 #if __cplusplus >= 202002L
 template <class G>
 concept DeviceGenerator = requires(G g) {
@@ -514,7 +594,8 @@ concept DeviceGenerator = requires(G g) {
     { g.next_f32() } -> std::same_as<float>;
     { g.next_f64() } -> std::same_as<double>;
 };
-static_assert(DeviceGenerator<Mrg32k3a> && DeviceGenerator<Philox4x32_10> && DeviceGenerator<Threefry4x32_20>);
+static_assert(DeviceGenerator<Mrg32k3a> && DeviceGenerator<Philox4x32_10> && DeviceGenerator<Threefry4x32_20> &&
+              DeviceGenerator<TinyMT32>);
 #endif
 
 namespace detail {
@@ -538,6 +619,7 @@ template <class Gen> struct gen_id;
 template <> struct gen_id<Mrg32k3a> { static constexpr int value = SRNG_MRG32K3A; };
 template <> struct gen_id<Philox4x32_10> { static constexpr int value = SRNG_PHILOX4X32_10; };
 template <> struct gen_id<Threefry4x32_20> { static constexpr int value = SRNG_THREEFRY4X32_20; };
+template <> struct gen_id<TinyMT32> { static constexpr int value = SRNG_TINYMT32; };
 }  // namespace detail
 
 /* The paper's device object (Listing 1): constructed inside a kernel with no
@@ -554,7 +636,8 @@ class RNG {
     __device__ RNG() : s_(detail::global_thread_index()), g_(detail::bound_view, s_) {}
     __device__ ~RNG()
     {
-        if constexpr (detail::gen_id<Gen>::value == SRNG_MRG32K3A) g_.store(detail::bound_view, s_);
+        if constexpr (detail::gen_id<Gen>::value == SRNG_MRG32K3A || detail::gen_id<Gen>::value == SRNG_TINYMT32)
+            g_.store(detail::bound_view, s_);
         else g_.store(detail::bound_view);
     }
     __device__ __forceinline__ T next() { return detail::draw<T>::f(g_); }

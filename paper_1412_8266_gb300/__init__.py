@@ -21,12 +21,14 @@ import threading
 __all__ = [
     "SrngError", "Tune", "Instance", "SetDesc", "DevView", "ServerConfig", "ServerStats", "Request",
     "lib_path", "load",
-    "SRNG_MRG32K3A", "SRNG_PHILOX4X32_10", "SRNG_PHILOX4X32_10_KEYED", "SRNG_THREEFRY4X32_20", "SRNG_OUT_U32", "SRNG_OUT_F32", "SRNG_OUT_F64",
+    "SRNG_MRG32K3A", "SRNG_PHILOX4X32_10", "SRNG_PHILOX4X32_10_KEYED", "SRNG_THREEFRY4X32_20", "SRNG_TINYMT32",
+    "SRNG_OUT_U32", "SRNG_OUT_F32", "SRNG_OUT_F64",
     "SRNG_SPACING_STREAM", "SRNG_SPACING_SUBSTREAM", "SRNG_JUMP_DRAWS", "SRNG_JUMP_SUBSTREAMS",
     "SRNG_JUMP_STREAMS", "SRNG_BATCH_WRITE", "SRNG_BATCH_FUSED_PI", "SRNG_DIST_EXPONENTIAL", "SRNG_DIST_NORMAL",
 ]
 
-SRNG_MRG32K3A, SRNG_PHILOX4X32_10, SRNG_PHILOX4X32_10_KEYED, SRNG_THREEFRY4X32_20 = 0, 1, 2, 3
+SRNG_ABI_VERSION = 2  # the struct layouts below follow this version of include/srng.h
+SRNG_MRG32K3A, SRNG_PHILOX4X32_10, SRNG_PHILOX4X32_10_KEYED, SRNG_THREEFRY4X32_20, SRNG_TINYMT32 = 0, 1, 2, 3, 4
 SRNG_OUT_U32, SRNG_OUT_F32, SRNG_OUT_F64 = 0, 1, 2
 SRNG_SPACING_STREAM, SRNG_SPACING_SUBSTREAM = 0, 1
 SRNG_JUMP_DRAWS, SRNG_JUMP_SUBSTREAMS, SRNG_JUMP_STREAMS = 0, 1, 2
@@ -69,7 +71,9 @@ class SetDesc(ctypes.Structure):
 class DevView(ctypes.Structure):
     _fields_ = [("gen", ctypes.c_int32), ("key0", ctypes.c_uint32), ("key1", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("n_streams", ctypes.c_uint64), ("mrg_state", ctypes.c_void_p),
-                ("philox_pos", ctypes.c_void_p), ("stream_base", ctypes.c_uint64)]
+                ("philox_pos", ctypes.c_void_p), ("stream_base", ctypes.c_uint64),
+                ("tinymt_state", ctypes.c_void_p), ("tinymt_params", ctypes.c_void_p),
+                ("tinymt_group_size", ctypes.c_uint64)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -100,6 +104,9 @@ _SIGS = {
     "srng_create": (_int, [ctypes.POINTER(_vp), _int, _u64, _u64, _int, _vp]),
     "srng_create_from_state": (_int, [ctypes.POINTER(_vp), _vp, _u64, _int, _vp]),
     "srng_create_range": (_int, [ctypes.POINTER(_vp), _int, _u64, _vp, _u64, _u64, _int, _vp]),
+    "srng_create_tinymt": (_int, [ctypes.POINTER(_vp), _vp, _u64, _u64, _u64, _vp]),
+    "srng_tinymt_find_params": (_int, [_u64, _u32, _vp]),
+    "srng_tinymt_check_params": (_int, [_u32, _u32, ctypes.POINTER(_int)]),
     "srng_destroy": (_int, [_vp]),
     "srng_reset": (_int, [_vp, _vp]),
     "srng_describe": (_int, [_vp, ctypes.POINTER(SetDesc)]),
@@ -223,6 +230,30 @@ def srng_create(gen: int, seed: int, n_streams: int, spacing: int = SRNG_SPACING
     h = _vp()
     _check(load().srng_create(ctypes.byref(h), gen, seed, n_streams, spacing, _stream(stream)), "srng_create")
     return h.value
+
+
+def srng_create_tinymt(params, group_size: int, seed: int, stream=None) -> int:
+    """params: (mat1, mat2, tmat) per parameter set (n x 3); each set serves
+    group_size consecutive streams."""
+    import numpy as np
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.uint32).reshape(-1, 3))
+    h = _vp()
+    _check(load().srng_create_tinymt(ctypes.byref(h), p.ctypes.data, p.shape[0], group_size, seed, _stream(stream)),
+           "srng_create_tinymt")
+    return h.value
+
+
+def srng_tinymt_find_params(seed: int, count: int):
+    import numpy as np
+    out = np.zeros((count, 3), dtype=np.uint32)
+    _check(load().srng_tinymt_find_params(seed, count, out.ctypes.data), "srng_tinymt_find_params")
+    return out
+
+
+def srng_tinymt_check_params(mat1: int, mat2: int) -> bool:
+    ok = _int()
+    _check(load().srng_tinymt_check_params(mat1, mat2, ctypes.byref(ok)), "srng_tinymt_check_params")
+    return bool(ok.value)
 
 
 def srng_create_from_state(state, n_streams: int, spacing: int = SRNG_SPACING_STREAM, stream=None) -> int:

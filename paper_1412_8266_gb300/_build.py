@@ -20,7 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsrng.so")
 
-SOURCES = ["api.cu", "jump.cu", "generate.cu", "batch.cu", "server.cu", "host_math.cpp"]
+SOURCES = ["api.cu", "jump.cu", "generate.cu", "batch.cu", "server.cu", "tinymt.cu", "host_math.cpp",
+           "tinymt_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

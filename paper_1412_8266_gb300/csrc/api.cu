@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <new>
@@ -61,8 +62,8 @@ srng_status current_device(DeviceInfo *out)
 // ------------------------------------------------------------------ tuning
 namespace {
 std::mutex g_tune_mu;
-srng_tune g_tune[2][3];
-bool g_tune_set[2][3];
+srng_tune g_tune[3][3];   // rows: MRG32k3a, counter-based (Philox, Threefry), TinyMT32
+bool g_tune_set[3][3];
 
 srng_tune builtin_tune(srng_gen gen, srng_out)
 {
@@ -82,10 +83,11 @@ srng_tune effective_tune(srng_gen gen, srng_out type, const srng_tune *user)
 {
     gen = (srng_gen)kernel_gen(gen);
     srng_tune t = builtin_tune(gen, type);
+    const int row = tune_row(gen);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        if (g_tune_set[gen][type]) {
-            const srng_tune &d = g_tune[gen][type];
+        if (g_tune_set[row][type]) {
+            const srng_tune &d = g_tune[row][type];
             if (d.block_threads) t.block_threads = d.block_threads;
             if (d.blocks_per_sm) t.blocks_per_sm = d.blocks_per_sm;
             if (d.chunk) t.chunk = d.chunk;
@@ -151,7 +153,8 @@ size_t out_size(srng_out t) { return t == SRNG_OUT_F64 ? 8 : 4; }
 
 bool valid_gen(int g)
 {
-    return g == SRNG_MRG32K3A || g == SRNG_PHILOX4X32_10 || g == SRNG_PHILOX4X32_10_KEYED || g == SRNG_THREEFRY4X32_20;
+    return g == SRNG_MRG32K3A || g == SRNG_PHILOX4X32_10 || g == SRNG_PHILOX4X32_10_KEYED ||
+           g == SRNG_THREEFRY4X32_20 || g == SRNG_TINYMT32;
 }
 bool valid_out(int t) { return t == SRNG_OUT_U32 || t == SRNG_OUT_F32 || t == SRNG_OUT_F64; }
 
@@ -172,6 +175,171 @@ static srng_status place_streams(srng_set *s, uint64_t first, uint64_t count, cu
     return SRNG_OK;
 }
 
+// ------------------------------------------------------------ TinyMT32 sets
+constexpr uint64_t kTmtMaxParams = 1ull << 20;
+
+// The device polynomial table of set s under `key`, built on the host by
+// `build` on first use and kept until srng_destroy (a launch in flight on any
+// stream may still read an older table).
+static srng_status tmt_table(srng_set *s, const std::array<uint64_t, 6> &key,
+                             const std::function<void(std::vector<uint4> &)> &build, const uint4 **out)
+{
+    std::lock_guard<std::mutex> lk(s->tmt_mu);
+    auto it = s->tmt_tables.find(key);
+    if (it != s->tmt_tables.end()) {
+        *out = it->second;
+        return SRNG_OK;
+    }
+    if (s->tmt_tables.size() >= 64) {  // bound the cache: drop it once the device is idle
+        SRNG_CUDA_TRY(cudaDeviceSynchronize());
+        for (auto &kv : s->tmt_tables) cudaFree(kv.second);
+        s->tmt_tables.clear();
+    }
+    std::vector<uint4> h;
+    try { build(h); } catch (...) { return fail(SRNG_ERR_OOM, "host allocation failed"); }
+    uint4 *d = nullptr;
+    SRNG_CUDA_TRY(cudaMalloc(&d, std::max<size_t>(1, h.size()) * sizeof(uint4)));
+    const cudaError_t e = cudaMemcpy(d, h.data(), h.size() * sizeof(uint4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "cudaMemcpy(TinyMT32 table)");
+    }
+    s->tmt_tables.emplace(key, d);
+    *out = d;
+    return SRNG_OK;
+}
+
+// x^(e_hi 2^64 + e_lo) mod p_g for the groups [g0, g0 + ng) (table kind `kind`).
+static srng_status tmt_poly_table(srng_set *s, uint64_t kind, uint64_t e_hi, uint64_t e_lo, uint64_t g0,
+                                  uint64_t ng, const uint4 **out)
+{
+    return tmt_table(s, {kind, e_hi, e_lo, g0, ng, 0},
+                     [&](std::vector<uint4> &h) {
+                         h.resize(ng);
+                         for (uint64_t g = 0; g < ng; ++g) h[g] = poly_words(tmt_xpow(s->tmt_poly[g0 + g], e_hi, e_lo));
+                     },
+                     out);
+}
+
+// (x^(base))^(2^k) mod p_g, k < nbits, for the groups [g0, g0 + ng): the
+// jump tables of chunk starts (base = chunk) and stream placement (2^64).
+static srng_status tmt_pow2_table(srng_set *s, uint64_t kind, uint64_t e_hi, uint64_t e_lo, uint64_t g0,
+                                  uint64_t ng, int nbits, const uint4 **out)
+{
+    return tmt_table(s, {kind, e_hi, e_lo, g0, ng, (uint64_t)nbits},
+                     [&](std::vector<uint4> &h) {
+                         h.resize(ng * nbits);
+                         for (uint64_t g = 0; g < ng; ++g) {
+                             const u128 p = s->tmt_poly[g0 + g];
+                             u128 r = tmt_xpow(p, e_hi, e_lo);
+                             for (int k = 0; k < nbits; ++k) {
+                                 h[g * nbits + k] = poly_words(r);
+                                 r = tmt_square_mod(p, r);
+                             }
+                         }
+                     },
+                     out);
+}
+
+// Every stream to its start: T^(j 2^64) of its group's seed state.
+static srng_status tmt_place(srng_set *s, cudaStream_t stream)
+{
+    DeviceInfo dev;
+    srng_status st = current_device(&dev);
+    if (st) return st;
+    const uint64_t ng = s->tmt_n_groups, gs = s->tmt_group_size;
+    const int nbits = bit_length(std::min(gs, s->n_streams) - 1);
+    const uint4 *seeds = nullptr, *jt = nullptr;
+    st = tmt_table(s, {1, 0, 0, 0, ng, 0},
+                   [&](std::vector<uint4> &h) {
+                       h.resize(ng);
+                       for (uint64_t g = 0; g < ng; ++g) {
+                           uint32_t w[4];
+                           const uint32_t *p = &s->tmt_params[3 * g];
+                           tmt_seed_state(s->tmt_seed32, p[0], p[1], p[2], w);
+                           h[g] = make_uint4(w[0], w[1], w[2], w[3]);
+                       }
+                   },
+                   &seeds);
+    if (st) return st;
+    if (nbits > 0 && (st = tmt_pow2_table(s, 2, 1, 0, 0, ng, nbits, &jt))) return st;
+    SRNG_CUDA_TRY(launch_tmt_place(s->d_tstate, s->n_streams, s->d_tparams, gs, seeds, jt, nbits, stream, dev));
+    return SRNG_OK;
+}
+
+static void free_set(srng_set *s)
+{
+    if (s->d_state) cudaFree(s->d_state);
+    if (s->d_pos) cudaFree(s->d_pos);
+    if (s->d_tstate) cudaFree(s->d_tstate);
+    if (s->d_tparams) cudaFree(s->d_tparams);
+    for (auto &kv : s->tmt_tables) cudaFree(kv.second);
+    delete s;
+}
+
+// polys: the parameter sets' characteristic polynomials when already known.
+static srng_status tmt_create(srng_set **out, const uint32_t *params, const std::vector<u128> *polys,
+                              uint64_t n_params, uint64_t group_size, uint64_t n_streams, uint64_t seed,
+                              cudaStream_t stream)
+{
+    srng_set *s = new (std::nothrow) srng_set();
+    if (!s) return fail(SRNG_ERR_OOM, "host allocation failed");
+    s->gen = SRNG_TINYMT32;
+    s->keyed = s->threefry = false;
+    s->spacing = SRNG_SPACING_STREAM;
+    s->n_streams = n_streams;
+    s->stream_base = 0;
+    s->seed = seed;
+    s->key0 = (uint32_t)seed;
+    s->key1 = (uint32_t)(seed >> 32);
+    memset(s->y0, 0, sizeof s->y0);
+    s->d_state = nullptr;
+    s->d_pos = nullptr;
+    s->max_pos = 0;
+    s->d_stage[0] = s->d_stage[1] = nullptr;
+    s->stage_bytes = 0;
+    s->copy_stream = nullptr;
+    s->tmt_group_size = group_size;
+    s->tmt_n_groups = n_params;
+    s->tmt_seed32 = (uint32_t)seed;
+    cudaGetDevice(&s->device);
+    srng_status st = SRNG_OK;
+    try {
+        s->tmt_params.assign(params, params + 3 * n_params);
+        s->tmt_poly.resize(n_params);
+    } catch (...) {
+        free_set(s);
+        return fail(SRNG_ERR_OOM, "host allocation failed");
+    }
+    for (uint64_t g = 0; g < n_params; ++g) {
+        if (polys) {
+            s->tmt_poly[g] = (*polys)[g];
+        } else if (!tmt_max_period(params[3 * g], params[3 * g + 1], &s->tmt_poly[g])) {
+            free_set(s);
+            return fail(SRNG_ERR_ARG, "parameter set " + std::to_string(g) + " does not have period 2^127 - 1");
+        }
+    }
+    std::vector<uint4> hp(n_params);
+    for (uint64_t g = 0; g < n_params; ++g) hp[g] = make_uint4(params[3 * g], params[3 * g + 1], params[3 * g + 2], 0);
+    cudaError_t e = cudaMalloc(&s->d_tstate, 4 * n_streams * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_tparams, n_params * sizeof(uint4));
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_tparams, hp.data(), n_params * sizeof(uint4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_set(s);
+        return cuda_fail(e, "TinyMT32 set allocation");
+    }
+    if ((st = tmt_place(s, stream))) {
+        free_set(s);
+        return st;
+    }
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) {
+        free_set(s);
+        return cuda_fail(e, "cudaStreamSynchronize(create)");
+    }
+    *out = s;
+    return SRNG_OK;
+}
+
 static srng_status create_common(srng_set **out, srng_gen gen, uint64_t seed, const uint32_t *state,
                                  uint64_t stream_base, uint64_t n_streams, srng_spacing spacing, void *cuda_stream)
 {
@@ -183,6 +351,21 @@ static srng_status create_common(srng_set **out, srng_gen gen, uint64_t seed, co
     if (n_streams == 0 || n_streams > (1ull << 40)) return fail(SRNG_ERR_ARG, "n_streams must be in [1, 2^40]");
     if (stream_base > UINT64_MAX - (n_streams - 1)) return fail(SRNG_ERR_RANGE, "stream numbers would pass 2^64 - 1");
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    if (gen == SRNG_TINYMT32) {
+        if (stream_base || state) return fail(SRNG_ERR_UNSUPPORTED, "TinyMT32 sets start at stream 0 from a seed");
+        const uint64_t gs = 256, ng = (n_streams + gs - 1) / gs;
+        if (ng > kTmtMaxParams) return fail(SRNG_ERR_ARG, "TinyMT32: at most 2^20 parameter sets (2^28 streams)");
+        std::vector<uint32_t> prm;
+        std::vector<u128> polys;
+        try {
+            prm.resize(3 * ng);
+            polys.resize(ng);
+        } catch (...) {
+            return fail(SRNG_ERR_OOM, "host allocation failed");
+        }
+        tmt_find_params(seed, (uint32_t)ng, prm.data(), polys.data());
+        return tmt_create(out, prm.data(), &polys, ng, gs, n_streams, seed, stream);
+    }
     srng_set *s = new (std::nothrow) srng_set();
     if (!s) return fail(SRNG_ERR_OOM, "host allocation failed");
     s->keyed = gen == SRNG_PHILOX4X32_10_KEYED || gen == SRNG_THREEFRY4X32_20;
@@ -269,6 +452,43 @@ static srng_status generate_dev(srng_set *s, uint64_t b, uint64_t c, uint64_t n,
         const JumpTable &tab = jump_table(0, chunk);
         SRNG_CUDA_TRY(launch_mrg_generate(a, type, tab, t, stream, dev));
         SRNG_CUDA_TRY(launch_mrg_apply(s->d_state, s->n_streams, b, c, mat_pow_shifted(0, n, 0), stream, dev));
+    } else if (s->gen == SRNG_TINYMT32) {
+        const uint64_t gs = s->tmt_group_size;
+        TmtGenArgs a;
+        a.state = s->d_tstate;
+        a.n_streams = s->n_streams;
+        a.params = s->d_tparams;
+        a.group_size = gs;
+        a.s_begin = b;
+        a.s_count = c;
+        a.n = n;
+        a.out = out;
+        uint64_t chunk = t.chunk;
+        if (!chunk) {
+            // about four waves of resident threads; a chunk start costs ~2,000
+            // instructions per set bit of its index, so chunks stay >= 4096 draws
+            const uint64_t resident = (uint64_t)dev.sm_count * (t.blocks_per_sm ? t.blocks_per_sm : 8) * 256;
+            const uint64_t want = 4 * resident;
+            const uint64_t splits = c >= want ? 1 : (want + c - 1) / c;
+            chunk = (n + splits - 1) / splits;
+            chunk = std::max<uint64_t>(4096, ((chunk + 31) / 32) * 32);
+        }
+        if (chunk > n) chunk = n;
+        a.chunk = chunk;
+        a.cps = (n + chunk - 1) / chunk;
+        a.nbits = bit_length(a.cps - 1);
+        a.write_back = a.cps == 1 ? 1 : 0;
+        const uint64_t g0 = b / gs, ng = (b + c - 1) / gs - g0 + 1;
+        a.g0 = g0;
+        a.jtab = nullptr;
+        srng_status st;
+        if (a.nbits > 0 && (st = tmt_pow2_table(s, 3, 0, chunk, g0, ng, a.nbits, &a.jtab))) return st;
+        SRNG_CUDA_TRY(launch_tmt_generate(a, type, t, stream, dev));
+        if (!a.write_back) {  // advance every stream by n (the chunks read the start state)
+            const uint4 *adv = nullptr;
+            if ((st = tmt_poly_table(s, 4, 0, n, g0, ng, &adv))) return st;
+            SRNG_CUDA_TRY(launch_tmt_apply(s->d_tstate, s->n_streams, s->d_tparams, gs, b, c, adv, g0, stream, dev));
+        }
     } else {
         PhiloxGenArgs a;
         a.stream_base = s->stream_base;
@@ -361,6 +581,36 @@ srng_status srng_create_from_state(srng_set **out, const uint32_t state[6], uint
     return create_common(out, SRNG_MRG32K3A, 0, state, 0, n_streams, spacing, cuda_stream);
 }
 
+srng_status srng_create_tinymt(srng_set **out, const uint32_t *params, uint64_t n_params, uint64_t group_size,
+                               uint64_t seed, void *cuda_stream)
+{
+    clear_error();
+    if (!out || !params) return fail(SRNG_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (n_params == 0 || n_params > kTmtMaxParams) return fail(SRNG_ERR_ARG, "n_params must be in [1, 2^20]");
+    if (group_size == 0 || group_size > (1ull << 40) / n_params)
+        return fail(SRNG_ERR_ARG, "group_size must be >= 1 and n_params * group_size <= 2^40");
+    return tmt_create(out, params, nullptr, n_params, group_size, n_params * group_size, seed,
+                      static_cast<cudaStream_t>(cuda_stream));
+}
+
+srng_status srng_tinymt_find_params(uint64_t seed, uint32_t count, uint32_t *params_out)
+{
+    clear_error();
+    if (count && !params_out) return fail(SRNG_ERR_ARG, "params_out is NULL");
+    if (count > kTmtMaxParams) return fail(SRNG_ERR_ARG, "at most 2^20 parameter sets per call");
+    tmt_find_params(seed, count, params_out, nullptr);
+    return SRNG_OK;
+}
+
+srng_status srng_tinymt_check_params(uint32_t mat1, uint32_t mat2, int *max_period)
+{
+    clear_error();
+    if (!max_period) return fail(SRNG_ERR_ARG, "max_period is NULL");
+    *max_period = tmt_max_period(mat1, mat2, nullptr) ? 1 : 0;
+    return SRNG_OK;
+}
+
 srng_status srng_destroy(srng_set *set)
 {
     clear_error();
@@ -371,6 +621,9 @@ srng_status srng_destroy(srng_set *set)
     cudaDeviceSynchronize();
     if (set->d_state) cudaFree(set->d_state);
     if (set->d_pos) cudaFree(set->d_pos);
+    if (set->d_tstate) cudaFree(set->d_tstate);
+    if (set->d_tparams) cudaFree(set->d_tparams);
+    for (auto &kv : set->tmt_tables) cudaFree(kv.second);
     for (int i = 0; i < 2; ++i) {
         if (set->d_stage[i]) cudaFree(set->d_stage[i]);
     }
@@ -392,6 +645,7 @@ srng_status srng_reset(srng_set *set, void *cuda_stream)
     if (!set) return fail(SRNG_ERR_ARG, "set is NULL");
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     if (set->gen == SRNG_MRG32K3A) return place_streams(set, 0, set->n_streams, stream);
+    if (set->gen == SRNG_TINYMT32) return tmt_place(set, stream);
     SRNG_CUDA_TRY(cudaMemsetAsync(set->d_pos, 0, set->n_streams * sizeof(uint64_t), stream));
     set->max_pos = 0;
     return SRNG_OK;
@@ -402,7 +656,7 @@ srng_status srng_describe(const srng_set *set, srng_set_desc *out)
     clear_error();
     if (!set || !out) return fail(SRNG_ERR_ARG, "NULL argument");
     memset(out, 0, sizeof *out);
-    out->gen = set->threefry ? SRNG_THREEFRY4X32_20 : set->keyed ? SRNG_PHILOX4X32_10_KEYED : set->gen;
+    out->gen = set->threefry ? SRNG_THREEFRY4X32_20 : set->keyed ? SRNG_PHILOX4X32_10_KEYED : set->gen;  // TinyMT32 too
     out->spacing = set->spacing;
     out->n_streams = set->n_streams;
     out->seed = set->seed;
@@ -421,6 +675,9 @@ srng_status srng_get_device_view(const srng_set *set, srng_dev_view *out)
     out->key0 = set->key0;
     out->key1 = set->key1;
     out->flags = set->keyed && !set->threefry ? 1u : 0u;
+    out->tinymt_state = set->d_tstate;
+    out->tinymt_params = reinterpret_cast<const uint32_t *>(set->d_tparams);
+    out->tinymt_group_size = set->tmt_group_size;
     out->n_streams = set->n_streams;
     out->mrg_state = set->d_state;
     out->philox_pos = set->d_pos;
@@ -444,6 +701,15 @@ srng_status srng_jump(srng_set *set, uint64_t stream_begin, uint64_t count, srng
         const int shift = unit == SRNG_JUMP_DRAWS ? 0 : unit == SRNG_JUMP_SUBSTREAMS ? 76 : 127;
         SRNG_CUDA_TRY(launch_mrg_apply(set->d_state, set->n_streams, stream_begin, count,
                                        mat_pow_shifted(n_hi, n_lo, shift), stream, dev));
+        return SRNG_OK;
+    }
+    if (set->gen == SRNG_TINYMT32) {
+        if (unit != SRNG_JUMP_DRAWS) return fail(SRNG_ERR_UNSUPPORTED, "TinyMT32 streams jump by draws only");
+        const uint64_t gs = set->tmt_group_size, g0 = stream_begin / gs, ng = (stream_begin + count - 1) / gs - g0 + 1;
+        const uint4 *poly = nullptr;
+        if ((st = tmt_poly_table(set, 5, n_hi, n_lo, g0, ng, &poly))) return st;
+        SRNG_CUDA_TRY(launch_tmt_apply(set->d_tstate, set->n_streams, set->d_tparams, gs, stream_begin, count, poly, g0,
+                                       stream, dev));
         return SRNG_OK;
     }
     if (unit != SRNG_JUMP_DRAWS) return fail(SRNG_ERR_UNSUPPORTED, "Philox streams jump by draws only");
@@ -556,6 +822,18 @@ srng_status srng_get_state(const srng_set *set, uint64_t stream_begin, uint64_t 
     if (count == 0) return SRNG_OK;
     if (!state_host) return fail(SRNG_ERR_ARG, "state_host is NULL");
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    if (set->gen == SRNG_TINYMT32) {
+        std::vector<uint32_t> soa;
+        try { soa.resize(4 * count); } catch (...) { return fail(SRNG_ERR_OOM, "host allocation failed"); }
+        SRNG_CUDA_TRY(cudaMemcpy2DAsync(soa.data(), count * sizeof(uint32_t), set->d_tstate + stream_begin,
+                                        set->n_streams * sizeof(uint32_t), count * sizeof(uint32_t), 4,
+                                        cudaMemcpyDeviceToHost, stream));
+        SRNG_CUDA_TRY(cudaStreamSynchronize(stream));
+        uint32_t *h = static_cast<uint32_t *>(state_host);
+        for (uint64_t i = 0; i < count; ++i)
+            for (int j = 0; j < 4; ++j) h[4 * i + j] = soa[j * count + i];
+        return SRNG_OK;
+    }
     if (set->gen == SRNG_PHILOX4X32_10) {
         SRNG_CUDA_TRY(cudaMemcpyAsync(state_host, set->d_pos + stream_begin, count * sizeof(uint64_t),
                                       cudaMemcpyDeviceToHost, stream));
@@ -583,6 +861,21 @@ srng_status srng_set_state(srng_set *set, uint64_t stream_begin, uint64_t count,
     if (count == 0) return SRNG_OK;
     if (!state_host) return fail(SRNG_ERR_ARG, "state_host is NULL");
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    if (set->gen == SRNG_TINYMT32) {
+        const uint32_t *h = static_cast<const uint32_t *>(state_host);
+        std::vector<uint32_t> soa;
+        try { soa.resize(4 * count); } catch (...) { return fail(SRNG_ERR_OOM, "host allocation failed"); }
+        for (uint64_t i = 0; i < count; ++i) {
+            if ((h[4 * i] & 0x7fffffffu) == 0 && h[4 * i + 1] == 0 && h[4 * i + 2] == 0 && h[4 * i + 3] == 0)
+                return fail(SRNG_ERR_STATE, "TinyMT32 state " + std::to_string(i) + " is all zero");
+            for (int j = 0; j < 4; ++j) soa[j * count + i] = h[4 * i + j];
+        }
+        SRNG_CUDA_TRY(cudaMemcpy2DAsync(set->d_tstate + stream_begin, set->n_streams * sizeof(uint32_t), soa.data(),
+                                        count * sizeof(uint32_t), count * sizeof(uint32_t), 4, cudaMemcpyHostToDevice,
+                                        stream));
+        SRNG_CUDA_TRY(cudaStreamSynchronize(stream));
+        return SRNG_OK;
+    }
     if (set->gen == SRNG_PHILOX4X32_10) {
         const uint64_t *p = static_cast<const uint64_t *>(state_host);
         uint64_t mx = 0;
@@ -615,7 +908,7 @@ srng_status srng_set_tune(srng_gen gen, srng_out type, const srng_tune *tune)
     srng_status st = check_tune(tune);
     if (st) return st;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    const int g = kernel_gen(gen);
+    const int g = tune_row(kernel_gen(gen));
     if (tune) {
         g_tune[g][type] = *tune;
         g_tune_set[g][type] = true;

@@ -425,6 +425,7 @@ srng_status batch_build(srng_set *const *sets, uint32_t n_sets, const srng_insta
         if (x.set_index >= n_sets || !sets[x.set_index])
             return fail(SRNG_ERR_ARG, "instance " + std::to_string(i) + ": bad set index");
         const srng_set *s = sets[x.set_index];
+        if (s->gen == SRNG_TINYMT32) return fail(SRNG_ERR_UNSUPPORTED, "TinyMT32 sets are not batched");
         if (x.stream >= s->n_streams) return fail(SRNG_ERR_RANGE, "instance " + std::to_string(i) + ": stream outside its set");
         if (x.length > (1ull << 48)) return fail(SRNG_ERR_ARG, "instance " + std::to_string(i) + ": length above 2^48");
         if (s->gen == SRNG_PHILOX4X32_10 && (x.offset > UINT64_MAX - s->max_pos ||
@@ -851,6 +852,7 @@ extern "C" srng_status srng_batch_run_static(srng_set *const *sets, uint32_t n_s
     for (uint32_t k = 0; k < n_sets; ++k) {
         const srng_set *s = sets[k];
         if (!s) return fail(SRNG_ERR_ARG, "NULL set");
+        if (s->gen == SRNG_TINYMT32) return fail(SRNG_ERR_UNSUPPORTED, "TinyMT32 sets are not batched");
         ss.gen[k] = inst_gen(s);
         ss.key0[k] = s->key0;
         ss.key1[k] = s->key1;

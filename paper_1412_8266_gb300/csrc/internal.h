@@ -4,8 +4,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
+#include <map>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "srng.h"
 
@@ -51,7 +54,12 @@ srng_status current_device(DeviceInfo *out);
 
 // The kernels (and tuning tables) of a generator value: the keyed Philox
 // layout runs the Philox kernels.
-inline int kernel_gen(int g) { return g == SRNG_MRG32K3A ? SRNG_MRG32K3A : SRNG_PHILOX4X32_10; }
+inline int kernel_gen(int g)
+{
+    return g == SRNG_MRG32K3A ? SRNG_MRG32K3A : g == SRNG_TINYMT32 ? SRNG_TINYMT32 : SRNG_PHILOX4X32_10;
+}
+// Row of the tuning tables of a kernel family.
+inline int tune_row(int g) { return g == SRNG_MRG32K3A ? 0 : g == SRNG_TINYMT32 ? 2 : 1; }
 
 // ---------------------------------------------------------------- tuning
 srng_tune effective_tune(srng_gen gen, srng_out type, const srng_tune *user);
@@ -148,6 +156,51 @@ int batch_blocks_per_sm(srng_out type);
 void chunk_jump_table(uint64_t chunk, JumpTable *out);
 constexpr int kBatchThreads = 256;
 
+// ------------------------------------------------ TinyMT32 (tinymt.cu, tinymt_host.cpp)
+typedef unsigned __int128 u128;
+// Seed state of a parameter set from a 32-bit seed (the TinyMT32 seeding).
+void tmt_seed_state(uint32_t seed32, uint32_t mat1, uint32_t mat2, uint32_t tmat, uint32_t s[4]);
+// True when (mat1, mat2) has period 2^127 - 1; *charpoly = the step's
+// characteristic polynomial (degree 127).
+bool tmt_max_period(uint32_t mat1, uint32_t mat2, u128 *charpoly);
+// x^(e_hi 2^64 + e_lo) mod p.
+u128 tmt_xpow(u128 p, uint64_t e_hi, uint64_t e_lo);
+// a^2 mod p.
+u128 tmt_square_mod(u128 p, u128 a);
+// `count` parameter sets (mat1, mat2, tmat) from SplitMix64(seed), with
+// their characteristic polynomials when polys is not NULL.
+void tmt_find_params(uint64_t seed, uint32_t count, uint32_t *out, u128 *polys);
+
+inline uint4 poly_words(u128 r)
+{
+    return make_uint4((uint32_t)r, (uint32_t)(r >> 32), (uint32_t)(r >> 64), (uint32_t)(r >> 96));
+}
+
+struct TmtGenArgs {
+    uint32_t *state;           // SoA 4 x n_streams
+    uint64_t n_streams;
+    const uint4 *params;       // (mat1, mat2, tmat, 0) per group
+    uint64_t group_size;
+    uint64_t s_begin, s_count, n;
+    uint64_t chunk, cps;       // draws per item, items per stream
+    int nbits;                 // bits of the chunk index
+    const uint4 *jtab;         // [group - g0][k] = x^(chunk 2^k) mod p_group, k < nbits
+    uint64_t g0;
+    int write_back;            // 1: one item per stream, its thread stores the advanced state
+    void *out;
+};
+// Stream placement: stream i of group g = T^(j 2^64) seed[g], j = i - g group_size,
+// jt[g][k] = x^(2^(64 + k)) mod p_g, k < nbits.
+cudaError_t launch_tmt_place(uint32_t *state, uint64_t n_streams, const uint4 *params, uint64_t group_size,
+                             const uint4 *seed_states, const uint4 *jt, int nbits, cudaStream_t stream,
+                             const DeviceInfo &dev);
+// state <- poly[group - g0](T) state for streams [first, first + count).
+cudaError_t launch_tmt_apply(uint32_t *state, uint64_t n_streams, const uint4 *params, uint64_t group_size,
+                             uint64_t first, uint64_t count, const uint4 *poly, uint64_t g0, cudaStream_t stream,
+                             const DeviceInfo &dev);
+cudaError_t launch_tmt_generate(const TmtGenArgs &a, srng_out type, const srng_tune &t, cudaStream_t stream,
+                                const DeviceInfo &dev);
+
 }  // namespace srng_impl
 
 // The stream set object behind the opaque srng_set handle.
@@ -161,6 +214,17 @@ struct srng_set {
     uint32_t key0, key1;     // Philox / Threefry seed words (Philox key, or counter words 2-3 when keyed)
     bool keyed;              // key = the stream (keyed Philox, Threefry)
     bool threefry;           // Threefry4x32-20 (counter-based family, kernels as Philox)
+    // TinyMT32: states, parameter sets and their characteristic polynomials
+    uint64_t tmt_group_size = 0, tmt_n_groups = 0;
+    uint32_t tmt_seed32 = 0;
+    uint32_t *d_tstate = nullptr;            // SoA 4 x n_streams
+    uint4 *d_tparams = nullptr;              // (mat1, mat2, tmat, 0) per group
+    std::vector<uint32_t> tmt_params;        // host copy, 3 per group
+    std::vector<srng_impl::u128> tmt_poly;   // per group
+    // device polynomial tables by (kind, exponent words, first group, groups, bits);
+    // kept until destroy (at most a few dozen) so no launch in flight loses its table
+    std::map<std::array<uint64_t, 6>, uint4 *> tmt_tables;
+    std::mutex tmt_mu;
     int device;
     uint32_t *d_state;       // MRG32k3a SoA states (6 x n_streams)
     uint64_t *d_pos;         // Philox positions

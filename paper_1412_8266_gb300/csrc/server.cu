@@ -397,6 +397,7 @@ srng_status srng_server_create(srng_server **out, srng_set *set, const srng_serv
     clear_error();
     if (!out || !set) return fail(SRNG_ERR_ARG, "NULL argument");
     *out = nullptr;
+    if (set->gen == SRNG_TINYMT32) return fail(SRNG_ERR_UNSUPPORTED, "TinyMT32 sets are not served");
     srng_server_config c;
     memset(&c, 0, sizeof c);
     if (cfg) c = *cfg;

@@ -30,6 +30,14 @@ __global__ void bazKernel(double *ddata)
     ddata[blockDim.x * blockIdx.x + threadIdx.x] = rng.next();
 }
 
+__global__ void quxKernel(float *ddata)
+{
+    RNG<float, srng::TinyMT32> rng;   // the block's threads share one parameter set
+    const uint64_t i = (uint64_t)blockDim.x * blockIdx.x + threadIdx.x;
+    ddata[2 * i] = rng.next();
+    ddata[2 * i + 1] = rng.next();
+}
+
 // launches = number of fooKernel launches (each continues every stream).
 extern "C" int run_paper_listing1(float *d_data, int block_num, int thread_num, int launches, uint64_t seed)
 {
@@ -56,5 +64,14 @@ extern "C" int run_threefry_form(double *d_data, int block_num, int thread_num, 
     bazKernel<<<block_num, thread_num>>>(d_data);
     const int rc = cudaDeviceSynchronize() == cudaSuccess ? 0 : 2;
     RNG<double, srng::Threefry4x32_20>::release();
+    return rc;
+}
+
+extern "C" int run_tinymt_form(float *d_data, int block_num, int thread_num, uint64_t seed)
+{
+    if (RNG<float, srng::TinyMT32>::init((uint64_t)block_num * thread_num, seed) != SRNG_OK) return 1;
+    quxKernel<<<block_num, thread_num>>>(d_data);
+    const int rc = cudaDeviceSynchronize() == cudaSuccess ? 0 : 2;
+    RNG<float, srng::TinyMT32>::release();
     return rc;
 }

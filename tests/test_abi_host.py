@@ -50,7 +50,7 @@ def test_python_binding_covers_every_entry_point(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert srng.srng_abi_version() == 1
+    assert srng.srng_abi_version() == 2
     assert srng.srng_status_string(0) == "SRNG_OK"
     assert srng.srng_status_string(3) == "SRNG_ERR_STATE"
 
@@ -133,3 +133,26 @@ def test_range_set_argument_errors(lib):
     with pytest.raises(srng.SrngError) as e:
         srng.srng_create_range(srng.SRNG_MRG32K3A, 1, 0, 5, state=[0, 0, 0, 4, 5, 6])
     assert e.value.name == "SRNG_ERR_STATE"
+
+
+def test_tinymt_parameter_search_matches_oracle(lib):
+    """The library's host parameter search (its own Berlekamp-Massey and GF(2)
+    arithmetic, threaded) finds the same sets, in the same order, as the
+    oracle's plain search."""
+    for seed in (0, 0x5EED, 2**64 - 1):
+        got = srng.srng_tinymt_find_params(seed, 5)
+        assert np.array_equal(got, O.tinymt32_find_params(seed, 5)), seed
+    assert srng.srng_tinymt_check_params(0x8F7011EE, 0xFC78FF1F)
+    assert not srng.srng_tinymt_check_params(0x8F7011EE, 0xFC78FF1E) or O.tinymt32_max_period(0x8F7011EE, 0xFC78FF1E)
+    rng = np.random.default_rng(9)
+    for mat1, mat2 in rng.integers(0, 2**32, (64, 2), dtype=np.uint64):
+        assert srng.srng_tinymt_check_params(int(mat1), int(mat2)) == O.tinymt32_max_period(int(mat1), int(mat2))
+
+
+def test_tinymt_arguments_need_no_gpu(lib):
+    with pytest.raises(srng.SrngError) as e:
+        srng.srng_create_tinymt(np.zeros((0, 3), dtype=np.uint32), 4, 1)
+    assert e.value.name == "SRNG_ERR_ARG"
+    with pytest.raises(srng.SrngError) as e:
+        srng.srng_create_tinymt([[1, 2, 3]], 0, 1)
+    assert e.value.name == "SRNG_ERR_ARG"

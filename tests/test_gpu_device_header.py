@@ -129,6 +129,8 @@ def paper_form_lib(tmp_path_factory):
     lib.run_paper_listing1.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
     lib.run_philox_form.restype = ctypes.c_int
     lib.run_philox_form.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
+    lib.run_tinymt_form.restype = ctypes.c_int
+    lib.run_tinymt_form.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
     lib.run_threefry_form.restype = ctypes.c_int
     lib.run_threefry_form.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
     return lib
@@ -165,3 +167,18 @@ def test_paper_form_threefry(paper_form_lib):
     assert paper_form_lib.run_threefry_form(out.data_ptr(), block_num, thread_num, seed) == 0
     ref, _ = O.threefry_bulk(seed, 0, [0] * n, 1, O.OUT_F64)
     assert np.array_equal(out.cpu().numpy(), ref.ravel())
+
+
+def test_paper_form_tinymt(paper_form_lib):
+    """RNG<float, TinyMT32> with 256-thread blocks: block b's threads share
+    parameter set b (the paper's Sec. 4.2 hybrid) and thread t of the block
+    takes substream t."""
+    block_num, thread_num, seed = 3, 256, 0xFEED
+    n = block_num * thread_num
+    out = torch.empty(2 * n, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    assert paper_form_lib.run_tinymt_form(out.data_ptr(), block_num, thread_num, seed) == 0
+    prm = O.tinymt32_find_params(seed, block_num)
+    st = O.tinymt32_stream_starts(seed & 0xFFFFFFFF, prm, 256, n)
+    ref, _ = O.tinymt32_bulk(st, prm, 256, 2, O.OUT_F32)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32).reshape(n, 2), ref.view(np.uint32))
