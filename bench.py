@@ -315,8 +315,17 @@ def run_ours(args):
         e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dev)
         # the host copy must equal the device output of the same step
         same = bool(np.array_equal(host_u[:1 << 20].numpy(), out_u[:1 << 20].cpu().numpy()))
+        # the host link alone: one 1 GiB device -> pinned host copy (best of 3)
+        src = torch.empty(1 << 28, dtype=torch.float32, device=dev)
+        dst = torch.empty(1 << 28, dtype=torch.float32, pin_memory=True)
+        link_ms, _ = _time(torch, stream, lambda: dst.copy_(src, non_blocking=True), reps=3, warm=1)
+        link = (1 << 30) / link_ms / 1e6
+        del src, dst
+        e2e_gbs = (bytes_u + bytes_f) / e2e_s / 1e9
         e2e = {"value": world * numbers / e2e_s / 1e9, "unit": "Guniforms/s", "h2d_bytes_per_step": 0,
-               "d2h_bytes_per_step": bytes_u + bytes_f, "ms_per_step": e2e_s * 1e3, "matches_device_output": same}
+               "d2h_bytes_per_step": bytes_u + bytes_f, "ms_per_step": e2e_s * 1e3, "matches_device_output": same,
+               "GB_s": e2e_gbs, "host_link_GB_s": link, "frac_of_host_link": e2e_gbs / link,
+               "bound": "host link (device -> pinned host copy measured in this run)"}
         del host_u, host_f
 
     srng.srng_destroy(h)
