@@ -436,6 +436,15 @@ def extras(torch, srng, dev, stream, peak):
         best, med = _time(torch, stream, lambda: srng.srng_transform(d, u, n, z, stream))
         var[name] = {"ms_best": best, "ms_median": med, "Gvariates_s": n / best / 1e6, "GB_s": n * 8 / best / 1e6,
                      "frac_of_copy_peak": n * 8 / best / 1e6 / peak}
+    # the same normals fused into generation (SRNG_OUT_NORMAL_F32: 4 bytes written per value)
+    for name, t in (("fused_exponential", srng.SRNG_OUT_EXP_F32), ("fused_normal", srng.SRNG_OUT_NORMAL_F32)):
+        tt = autotune.tune_generate(srng.SRNG_PHILOX4X32_10, t, 1, n, use_cache=False, install=False)[0]
+        best, med = _time(torch, stream, lambda: (srng.srng_reset(h, stream),
+                                                  srng.srng_generate_tuned(h, 0, 1, n, t, z, tt, stream)))
+        var[name] = {"ms_best": best, "ms_median": med, "Gvariates_s": n / best / 1e6, "GB_s": n * 4 / best / 1e6,
+                     "frac_of_copy_peak": n * 4 / best / 1e6 / peak,
+                     "vs_generate_then_transform": (ph["f32"]["ms_best"] + var[name[6:]]["ms_best"]) / best,
+                     "tune": tt}
     del u, z
     srng.srng_destroy(h)
     res["philox_bulk_2^30"] = ph

@@ -73,7 +73,17 @@ typedef enum srng_gen {
 typedef enum srng_out {
     SRNG_OUT_U32 = 0,
     SRNG_OUT_F32 = 1,
-    SRNG_OUT_F64 = 2
+    SRNG_OUT_F64 = 2,
+    /* Fused non-uniform variates (bulk generation calls only; see srng_transform
+     * for the functions, which these outputs apply in the generation kernel):
+     *   SRNG_OUT_EXP_F32: exponential(FP32 uniform of draw k);
+     *   SRNG_OUT_NORMAL_F32: Box-Muller on pairs of draws.  Philox / Threefry:
+     *     the pairs are the stream positions (2j, 2j + 1) -- value at position
+     *     P is component P mod 2 (0: r cos t, 1: r sin t) of pair P / 2, any
+     *     start and length.  MRG32k3a / TinyMT32: the pairs are draws
+     *     (2i, 2i + 1) of the call; n must be even.                          */
+    SRNG_OUT_EXP_F32 = 3,
+    SRNG_OUT_NORMAL_F32 = 4
 } srng_out;
 
 /* Spacing of consecutive streams of an MRG32k3a set (paper Sec. 4.1). */

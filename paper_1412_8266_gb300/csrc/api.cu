@@ -65,14 +65,16 @@ std::mutex g_tune_mu;
 srng_tune g_tune[3][3];   // rows: MRG32k3a, counter-based (Philox, Threefry), TinyMT32
 bool g_tune_set[3][3];
 
-srng_tune builtin_tune(srng_gen gen, srng_out)
+srng_tune builtin_tune(srng_gen gen, srng_out type)
 {
     srng_tune t;
     memset(&t, 0, sizeof t);
     t.block_threads = 256;
     t.blocks_per_sm = 8;
     t.chunk = 0;  // chosen from the problem shape
-    t.unroll = 4;
+    // the fused variates carry long single-precision sequences: one block pair
+    // per lane keeps the registers (and the resident warps) of the uniforms
+    t.unroll = type == SRNG_OUT_EXP_F32 || type == SRNG_OUT_NORMAL_F32 ? 1 : 4;
     t.vector_store = 1;
     t.lane_blocks = 64;
     return t;
@@ -84,10 +86,11 @@ srng_tune effective_tune(srng_gen gen, srng_out type, const srng_tune *user)
     gen = (srng_gen)kernel_gen(gen);
     srng_tune t = builtin_tune(gen, type);
     const int row = tune_row(gen);
-    {
+    const int col = type == SRNG_OUT_F64 ? SRNG_OUT_F64 : type == SRNG_OUT_U32 ? SRNG_OUT_U32 : SRNG_OUT_F32;
+    {   // the fused variate outputs take the FP32 entries
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        if (g_tune_set[row][type]) {
-            const srng_tune &d = g_tune[row][type];
+        if (g_tune_set[row][col]) {
+            const srng_tune &d = g_tune[row][col];
             if (d.block_threads) t.block_threads = d.block_threads;
             if (d.blocks_per_sm) t.blocks_per_sm = d.blocks_per_sm;
             if (d.chunk) t.chunk = d.chunk;
@@ -157,6 +160,8 @@ bool valid_gen(int g)
            g == SRNG_THREEFRY4X32_20 || g == SRNG_TINYMT32;
 }
 bool valid_out(int t) { return t == SRNG_OUT_U32 || t == SRNG_OUT_F32 || t == SRNG_OUT_F64; }
+// Output types of the bulk generation calls (the uniforms and the fused variates).
+bool valid_gen_out(int t) { return valid_out(t) || t == SRNG_OUT_EXP_F32 || t == SRNG_OUT_NORMAL_F32; }
 
 int spacing_shift(srng_spacing sp) { return sp == SRNG_SPACING_SUBSTREAM ? 76 : 127; }
 
@@ -513,7 +518,9 @@ static srng_status generate_checks(srng_set *s, uint64_t b, uint64_t c, uint64_t
 {
     srng_status st = check_range(s, b, c);
     if (st) return st;
-    if (!valid_out(type)) return fail(SRNG_ERR_ARG, "unknown output type");
+    if (!valid_gen_out(type)) return fail(SRNG_ERR_ARG, "unknown output type");
+    if (type == SRNG_OUT_NORMAL_F32 && (n & 1) && (s->gen == SRNG_MRG32K3A || s->gen == SRNG_TINYMT32))
+        return fail(SRNG_ERR_ARG, "normal output of a state-based generator takes draws in pairs: n must be even");
     if (c == 0 || n == 0) return SRNG_OK;
     if (!out) return fail(SRNG_ERR_ARG, "output pointer is NULL");
     if (reinterpret_cast<uintptr_t>(out) % out_size(type))

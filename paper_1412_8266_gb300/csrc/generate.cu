@@ -32,14 +32,34 @@ template <int OUT> struct OutType;
 template <> struct OutType<SRNG_OUT_U32> { using T = uint32_t; };
 template <> struct OutType<SRNG_OUT_F32> { using T = float; };
 template <> struct OutType<SRNG_OUT_F64> { using T = double; };
+template <> struct OutType<SRNG_OUT_EXP_F32> { using T = float; };
+template <> struct OutType<SRNG_OUT_NORMAL_F32> { using T = float; };
 
 template <int GEN, int OUT>
 __device__ __forceinline__ typename OutType<OUT>::T convert(uint32_t v)
 {
     if constexpr (OUT == SRNG_OUT_U32) return v;
     else if constexpr (OUT == SRNG_OUT_F32) return srng::to_f32(v);
+    else if constexpr (OUT == SRNG_OUT_EXP_F32) return srng::dist::exponential(srng::to_f32(v));
     else if constexpr (GEN == SRNG_MRG32K3A) return srng::mrg::to_f64(v);
     else return srng::philox::to_f64(v);
+}
+
+// K output values from K consecutive words (K even).  The normal output pairs
+// words (2i, 2i + 1) of the group (Box-Muller on their FP32 uniforms); every
+// caller passes groups that start at an even draw of the stream (an even
+// position for the counter-based generators, an even index of the call for
+// the others).
+template <int GEN, int OUT, int K>
+__device__ __forceinline__ void convert_k(const uint32_t *w, typename OutType<OUT>::T *v)
+{
+    if constexpr (OUT == SRNG_OUT_NORMAL_F32) {
+#pragma unroll
+        for (int i = 0; i < K; i += 2) srng::dist::normal_pair(srng::to_f32(w[i]), srng::to_f32(w[i + 1]), &v[i], &v[i + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < K; ++i) v[i] = convert<GEN, OUT>(w[i]);
+    }
 }
 
 // ------------------------------------------------------------------ K2
@@ -87,16 +107,12 @@ __global__ void __launch_bounds__(WARPS * 32)
             row_len[warp][lane] = rl;
             for (uint32_t j = 0; j < rl; j += VPL) {
                 if constexpr (sizeof(T) == 4) {
-                    uint4 v;
-                    T x0 = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
-                    T x1 = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
-                    T x2 = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
-                    T x3 = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
-                    v.x = *reinterpret_cast<uint32_t *>(&x0);
-                    v.y = *reinterpret_cast<uint32_t *>(&x1);
-                    v.z = *reinterpret_cast<uint32_t *>(&x2);
-                    v.w = *reinterpret_cast<uint32_t *>(&x3);
-                    *reinterpret_cast<uint4 *>(&my[j]) = v;
+                    uint32_t w[4];
+                    T x[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) w[e] = srng::mrg::step(s0, s1, s2, s3, s4, s5);
+                    convert_k<SRNG_MRG32K3A, OUT, 4>(w, x);
+                    *reinterpret_cast<uint4 *>(&my[j]) = *reinterpret_cast<const uint4 *>(x);
                 } else {
                     double2 v;
                     v.x = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
@@ -177,10 +193,11 @@ __global__ void __launch_bounds__(WARPS * 32)
 #pragma unroll
                 for (int j = 0; j < G; j += VPL) {
                     if constexpr (sizeof(T) == 4) {
+                        uint32_t w[4];
                         T x[4];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            x[e] = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+                        for (int e = 0; e < 4; ++e) w[e] = srng::mrg::step(s0, s1, s2, s3, s4, s5);
+                        convert_k<SRNG_MRG32K3A, OUT, 4>(w, x);
                         *reinterpret_cast<uint4 *>(&my[j]) = *reinterpret_cast<uint4 *>(x);
                     } else {
                         double2 v;
@@ -229,9 +246,11 @@ __global__ void __launch_bounds__(WARPS * 32)
             if ((t >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
         T *dst = out + item * a.chunk;
         for (uint64_t j = 0; j < a.chunk; j += EPQ) {
+            uint32_t w[EPQ];
             T v[EPQ];
 #pragma unroll
-            for (int e = 0; e < EPQ; ++e) v[e] = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+            for (int e = 0; e < EPQ; ++e) w[e] = srng::mrg::step(s0, s1, s2, s3, s4, s5);
+            convert_k<SRNG_MRG32K3A, OUT, EPQ>(w, v);
             const uint4 *p = reinterpret_cast<const uint4 *>(v);
             st256(dst + j, p[0], p[1]);
         }
@@ -240,12 +259,12 @@ __global__ void __launch_bounds__(WARPS * 32)
 
 // ------------------------------------------------------------------ K3
 template <int GEN, int OUT, bool VEC>
-__device__ __forceinline__ void store4(typename OutType<OUT>::T *row, int64_t k0, uint64_t n, uint32_t w0,
-                                       uint32_t w1, uint32_t w2, uint32_t w3)
+__device__ __forceinline__ void store4(typename OutType<OUT>::T *row, int64_t k0, uint64_t n, const uint32_t *w)
 {
     using T = typename OutType<OUT>::T;
-    const T v0 = convert<GEN, OUT>(w0), v1 = convert<GEN, OUT>(w1);
-    const T v2 = convert<GEN, OUT>(w2), v3 = convert<GEN, OUT>(w3);
+    T vv[4];
+    convert_k<GEN, OUT, 4>(w, vv);  // one block: its pairs are at even positions
+    const T v0 = vv[0], v1 = vv[1], v2 = vv[2], v3 = vv[3];
     if (VEC && k0 >= 0 && (uint64_t)k0 + 4 <= n && ((reinterpret_cast<uintptr_t>(row + k0) & 15) == 0)) {
         if constexpr (sizeof(T) == 4) {
             uint4 v;
@@ -277,8 +296,7 @@ __device__ __forceinline__ void store8(typename OutType<OUT>::T *row, int64_t k0
     using T = typename OutType<OUT>::T;
     if (VEC && k0 >= 0 && (uint64_t)k0 + 8 <= n && ((reinterpret_cast<uintptr_t>(row + k0) & 31) == 0)) {
         T v[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = convert<GEN, OUT>(w[j]);
+        convert_k<GEN, OUT, 8>(w, v);
         const uint4 *p = reinterpret_cast<const uint4 *>(v);
         if constexpr (sizeof(T) == 4) {
             st256(row + k0, p[0], p[1]);
@@ -287,8 +305,8 @@ __device__ __forceinline__ void store8(typename OutType<OUT>::T *row, int64_t k0
             st256(row + k0 + 4, p[2], p[3]);
         }
     } else {
-        store4<GEN, OUT, VEC>(row, k0, n, w[0], w[1], w[2], w[3]);
-        store4<GEN, OUT, VEC>(row, k0 + 4, n, w[4], w[5], w[6], w[7]);
+        store4<GEN, OUT, VEC>(row, k0, n, w);
+        store4<GEN, OUT, VEC>(row, k0 + 4, n, w + 4);
     }
 }
 
@@ -613,6 +631,8 @@ cudaError_t launch_mrg_generate(const MrgGenArgs &a, srng_out type, const JumpTa
     switch (type) {
     case SRNG_OUT_U32: return mrg_dispatch<SRNG_OUT_U32>(a, tab, t, stream, dev);
     case SRNG_OUT_F32: return mrg_dispatch<SRNG_OUT_F32>(a, tab, t, stream, dev);
+    case SRNG_OUT_EXP_F32: return mrg_dispatch<SRNG_OUT_EXP_F32>(a, tab, t, stream, dev);
+    case SRNG_OUT_NORMAL_F32: return mrg_dispatch<SRNG_OUT_NORMAL_F32>(a, tab, t, stream, dev);
     default: return mrg_dispatch<SRNG_OUT_F64>(a, tab, t, stream, dev);
     }
 }
@@ -624,12 +644,16 @@ cudaError_t launch_philox_generate(const PhiloxGenArgs &a, srng_out type, const 
         switch (type) {
         case SRNG_OUT_U32: return philox_dispatch<SRNG_OUT_U32, kCipherThreefry>(a, t, stream, dev);
         case SRNG_OUT_F32: return philox_dispatch<SRNG_OUT_F32, kCipherThreefry>(a, t, stream, dev);
+        case SRNG_OUT_EXP_F32: return philox_dispatch<SRNG_OUT_EXP_F32, kCipherThreefry>(a, t, stream, dev);
+        case SRNG_OUT_NORMAL_F32: return philox_dispatch<SRNG_OUT_NORMAL_F32, kCipherThreefry>(a, t, stream, dev);
         default: return philox_dispatch<SRNG_OUT_F64, kCipherThreefry>(a, t, stream, dev);
         }
     }
     switch (type) {
     case SRNG_OUT_U32: return philox_dispatch<SRNG_OUT_U32, kCipherPhilox>(a, t, stream, dev);
     case SRNG_OUT_F32: return philox_dispatch<SRNG_OUT_F32, kCipherPhilox>(a, t, stream, dev);
+    case SRNG_OUT_EXP_F32: return philox_dispatch<SRNG_OUT_EXP_F32, kCipherPhilox>(a, t, stream, dev);
+    case SRNG_OUT_NORMAL_F32: return philox_dispatch<SRNG_OUT_NORMAL_F32, kCipherPhilox>(a, t, stream, dev);
     default: return philox_dispatch<SRNG_OUT_F64, kCipherPhilox>(a, t, stream, dev);
     }
 }

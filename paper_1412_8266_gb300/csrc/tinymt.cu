@@ -33,11 +33,14 @@ template <int OUT> struct TOut;
 template <> struct TOut<SRNG_OUT_U32> { using T = uint32_t; };
 template <> struct TOut<SRNG_OUT_F32> { using T = float; };
 template <> struct TOut<SRNG_OUT_F64> { using T = double; };
+template <> struct TOut<SRNG_OUT_EXP_F32> { using T = float; };
+template <> struct TOut<SRNG_OUT_NORMAL_F32> { using T = float; };
 
 template <int OUT> __device__ __forceinline__ typename TOut<OUT>::T tconv(uint32_t v)
 {
     if constexpr (OUT == SRNG_OUT_U32) return v;
     else if constexpr (OUT == SRNG_OUT_F32) return srng::to_f32(v);
+    else if constexpr (OUT == SRNG_OUT_EXP_F32) return srng::dist::exponential(srng::to_f32(v));
     else return srng::philox::to_f64(v);
 }
 
@@ -95,6 +98,32 @@ __global__ void __launch_bounds__(kThreads) k_tmt_generate(const TmtGenArgs a)
         const uint64_t k0 = t * a.chunk;
         const uint64_t len = min(a.chunk, a.n - k0);
         T *row = static_cast<T *>(a.out) + s_rel * a.n + k0;
+        if constexpr (OUT == SRNG_OUT_NORMAL_F32) {
+            // pairs of draws (2i, 2i + 1) of the item (the chunk and n are even):
+            // groups of eight values, 32-byte stores when aligned
+            for (uint64_t done = 0; done < len; done += 8) {
+                const uint32_t cnt = (uint32_t)min((uint64_t)8, len - done);
+                uint32_t w[8];
+                float v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    if ((uint32_t)e < cnt) srng::tinymt::step(s0, s1, s2, s3, p.x, p.y);
+                    w[e] = srng::tinymt::temper(s0, s2, s3, p.z);
+                }
+#pragma unroll
+                for (int e = 0; e < 8; e += 2)
+                    srng::dist::normal_pair(srng::to_f32(w[e]), srng::to_f32(w[e + 1]), &v[e], &v[e + 1]);
+                if (cnt == 8 && (reinterpret_cast<uintptr_t>(row + done) & 31u) == 0) {
+                    tst256(row + done, reinterpret_cast<const uint32_t *>(v));
+                } else {
+                    for (uint32_t e = 0; e < cnt; ++e) row[done + e] = v[e];
+                }
+            }
+            if (a.write_back) {
+                a.state[s] = s0; a.state[ns + s] = s1; a.state[2 * ns + s] = s2; a.state[3 * ns + s] = s3;
+            }
+            continue;
+        }
         uint64_t head = ((32u - (reinterpret_cast<uintptr_t>(row) & 31u)) & 31u) / sizeof(T);
         if (head > len) head = len;
         uint64_t done = 0;
@@ -159,6 +188,8 @@ cudaError_t launch_tmt_generate(const TmtGenArgs &a, srng_out type, const srng_t
     switch (type) {
     case SRNG_OUT_U32: k_tmt_generate<SRNG_OUT_U32><<<g, kThreads, 0, stream>>>(a); break;
     case SRNG_OUT_F32: k_tmt_generate<SRNG_OUT_F32><<<g, kThreads, 0, stream>>>(a); break;
+    case SRNG_OUT_EXP_F32: k_tmt_generate<SRNG_OUT_EXP_F32><<<g, kThreads, 0, stream>>>(a); break;
+    case SRNG_OUT_NORMAL_F32: k_tmt_generate<SRNG_OUT_NORMAL_F32><<<g, kThreads, 0, stream>>>(a); break;
     default: k_tmt_generate<SRNG_OUT_F64><<<g, kThreads, 0, stream>>>(a); break;
     }
     return cudaGetLastError();
