@@ -586,7 +586,7 @@ def run_case(args):
         nbytes, nvals = o.numel() * o.element_size(), o.numel()
     elif c.startswith("philox") or c.startswith("threefry"):
         n = (1 << 30) // k
-        t = srng.SRNG_OUT_U32 if c.endswith("u32") else srng.SRNG_OUT_F32
+        t = {"u32": srng.SRNG_OUT_U32, "f32": srng.SRNG_OUT_F32, "normal": srng.SRNG_OUT_NORMAL_F32}[c.split("_")[1]]
         g = srng.SRNG_PHILOX4X32_10 if c.startswith("philox") else srng.SRNG_THREEFRY4X32_20
         h = srng.srng_create(g, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
         o = torch.empty(n, dtype=torch.int32 if t == 0 else torch.float32, device=dev)
@@ -629,7 +629,8 @@ def run_case(args):
     return 0
 
 
-CASES = {"mrg_u32", "mrg_f64", "philox_u32", "philox_f32", "threefry_u32", "threefry_f32", "tinymt_u32", "tinymt_f64",
+CASES = {"mrg_u32", "mrg_f64", "philox_u32", "philox_f32", "philox_normal", "threefry_u32", "threefry_f32",
+         "tinymt_u32", "tinymt_f64",
          "batch_write", "batch_pi", "transform_exponential", "transform_normal"}
 
 
