@@ -10,6 +10,12 @@
  *     substreams of 2^76 draws, placed by sequence splitting (Sec. 2.3) with
  *     3x3 jump-ahead matrix powers modulo m1 = 2^32-209 and m2 = 2^32-22853.
  *   - Philox4x32-10 (paper Sec. 4.3): counter-based; the parameter is a key.
+ *   - Threefry4x32-20 (named beside Philox in Sec. 4.3): counter-based,
+ *     add / rotate / xor rounds, key = (stream, seed).
+ *   - TinyMT32 (Sec. 4.2): a parameter set shared by a group of streams,
+ *     substreams 2^64 apart by polynomial jump-ahead.
+ *   - Exponential and normal variates from the FP32 uniforms (srng_transform,
+ *     and fused into generation as SRNG_OUT_EXP_F32 / SRNG_OUT_NORMAL_F32).
  *
  * Host set-up (paper Sec. 5.1: one host call allocates and places the streams
  * before the kernels run) maps to srng_create; release (Sec. 5, Listing 1)
@@ -29,13 +35,14 @@
  *     out[(s - stream_begin) * n_per_stream + k] = draw k of stream s, counted
  *     from the stream's position when the call is made.  Values never depend
  *     on launch configuration or tuning.
- *   - Output of the three types (fixed conversions):
+ *   - Output of the uniform types (fixed conversions):
  *       SRNG_OUT_U32: MRG32k3a z = (x1 - x2) mod m1 taken in [1, m1]
- *                     (0 and values above m1 never occur); Philox: the word.
- *       SRNG_OUT_F32: (v >> 8) * 2^-24, exact, in [0, 1) (both generators).
+ *                     (0 and values above m1 never occur); Philox, Threefry,
+ *                     TinyMT32: the 32-bit word.
+ *       SRNG_OUT_F32: (v >> 8) * 2^-24, exact, in [0, 1) (every generator).
  *       SRNG_OUT_F64: MRG32k3a: z * norm rounded to nearest even, norm the
  *                     double nearest 1/(m1+1), in (0, 1);
- *                     Philox: (2w + 1) * 2^-33, exact, in (0, 1).
+ *                     the others: (2w + 1) * 2^-33, exact, in (0, 1).
  */
 #ifndef SRNG_H
 #define SRNG_H

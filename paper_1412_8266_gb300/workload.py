@@ -3,7 +3,7 @@
 Both the CUDA path and the CPU oracle receive the lists built here; neither
 side draws its inputs itself.  The random draws use numpy's PCG64
 (``numpy.random.default_rng``) with fixed seeds, a generator unrelated to the
-two generators under test.
+generators under test.
 
 Workloads (sizes as in the configurations this library is measured on):
   mrg_plain    MRG32k3a, seed state all 12345, 64 streams 2^127 apart,
