@@ -154,7 +154,7 @@ __device__ __forceinline__ void st256(void *p, uint4 a, uint4 b)
                  : "memory");
 }
 
-template <int OUT, int WARPS>
+template <int OUT, int WARPS, bool JUMP>
 __global__ void __launch_bounds__(WARPS * 32)
     k_mrg_generate_rows(const MrgGenArgs a, const __grid_constant__ JumpTable tab)
 {
@@ -178,14 +178,15 @@ __global__ void __launch_bounds__(WARPS * 32)
         const uint32_t rows = (uint32_t)min((uint64_t)32, n_items - base);
         uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
         if (active) {
-            const uint64_t s_rel = item / a.cps;
-            const uint64_t t = item - s_rel * a.cps;
+            const uint64_t s_rel = JUMP ? item / a.cps : item;
+            const uint64_t t = JUMP ? item - s_rel * a.cps : 0;
             const uint64_t s = a.s_begin + s_rel;
             const uint64_t ns = a.n_streams;
             s0 = a.state[s]; s1 = a.state[ns + s]; s2 = a.state[2 * ns + s];
             s3 = a.state[3 * ns + s]; s4 = a.state[4 * ns + s]; s5 = a.state[5 * ns + s];
-            for (int k = 0; k < a.nbits; ++k)
-                if ((t >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
+            if (JUMP)
+                for (int k = 0; k < a.nbits; ++k)
+                    if ((t >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
         }
         T *dst0 = out + base * a.chunk + (uint64_t)q * EPQ;
         for (uint64_t done = 0; done < a.chunk; done += G) {
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(WARPS * 32)
 // straight from registers -- every store fills one whole 32-byte sector, 32
 // sectors per warp instruction, no shared-memory transpose.  Same preconditions
 // as k_mrg_generate_rows.
-template <int OUT, int WARPS>
+template <int OUT, int WARPS, bool JUMP>
 __global__ void __launch_bounds__(WARPS * 32)
     k_mrg_generate_direct(const MrgGenArgs a, const __grid_constant__ JumpTable tab)
 {
@@ -236,14 +237,15 @@ __global__ void __launch_bounds__(WARPS * 32)
     const uint64_t n_items = a.s_count * a.cps;
     const uint64_t stride = (uint64_t)gridDim.x * WARPS * 32;
     for (uint64_t item = (uint64_t)blockIdx.x * WARPS * 32 + threadIdx.x; item < n_items; item += stride) {
-        const uint64_t s_rel = item / a.cps;
-        const uint64_t t = item - s_rel * a.cps;
+        const uint64_t s_rel = JUMP ? item / a.cps : item;
+        const uint64_t t = JUMP ? item - s_rel * a.cps : 0;
         const uint64_t s = a.s_begin + s_rel;
         const uint64_t ns = a.n_streams;
         uint32_t s0 = a.state[s], s1 = a.state[ns + s], s2 = a.state[2 * ns + s];
         uint32_t s3 = a.state[3 * ns + s], s4 = a.state[4 * ns + s], s5 = a.state[5 * ns + s];
-        for (int k = 0; k < a.nbits; ++k)
-            if ((t >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
+        if (JUMP)
+            for (int k = 0; k < a.nbits; ++k)
+                if ((t >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
         T *dst = out + item * a.chunk;
         for (uint64_t j = 0; j < a.chunk; j += EPQ) {
             uint32_t w[EPQ];
@@ -545,12 +547,25 @@ cudaError_t mrg_dispatch_rows(const MrgGenArgs &a, const JumpTable &tab, const s
     uint64_t cap = (uint64_t)dev.sm_count * (t.blocks_per_sm ? t.blocks_per_sm : 5);
     if (blocks > cap) blocks = cap;
     if (blocks == 0) blocks = 1;
+    // one item per stream (no chunk starts to reach): kernels without the jump code
+    const bool jump = a.cps > 1;
+    const unsigned g = (unsigned)blocks;
     if (t.vector_store == 3) {
-        if (warps == 8) k_mrg_generate_direct<OUT, 8><<<(unsigned)blocks, 256, 0, stream>>>(a, tab);
-        else k_mrg_generate_direct<OUT, 4><<<(unsigned)blocks, 128, 0, stream>>>(a, tab);
+        if (warps == 8) {
+            if (jump) k_mrg_generate_direct<OUT, 8, true><<<g, 256, 0, stream>>>(a, tab);
+            else k_mrg_generate_direct<OUT, 8, false><<<g, 256, 0, stream>>>(a, tab);
+        } else {
+            if (jump) k_mrg_generate_direct<OUT, 4, true><<<g, 128, 0, stream>>>(a, tab);
+            else k_mrg_generate_direct<OUT, 4, false><<<g, 128, 0, stream>>>(a, tab);
+        }
     } else {
-        if (warps == 8) k_mrg_generate_rows<OUT, 8><<<(unsigned)blocks, 256, 0, stream>>>(a, tab);
-        else k_mrg_generate_rows<OUT, 4><<<(unsigned)blocks, 128, 0, stream>>>(a, tab);
+        if (warps == 8) {
+            if (jump) k_mrg_generate_rows<OUT, 8, true><<<g, 256, 0, stream>>>(a, tab);
+            else k_mrg_generate_rows<OUT, 8, false><<<g, 256, 0, stream>>>(a, tab);
+        } else {
+            if (jump) k_mrg_generate_rows<OUT, 4, true><<<g, 128, 0, stream>>>(a, tab);
+            else k_mrg_generate_rows<OUT, 4, false><<<g, 128, 0, stream>>>(a, tab);
+        }
     }
     return cudaGetLastError();
 }
