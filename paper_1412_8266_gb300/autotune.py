@@ -27,7 +27,8 @@ MRG_SPACE = [dict(block_threads=bt, blocks_per_sm=b, chunk=c, vector_store=v)
              for bt, b, c, v in itertools.product((128, 256), (4, 8), (512, 1024, 2048, 4096), (1, 3))]
 PHILOX_SPACE = [dict(block_threads=bt, unroll=u, blocks_per_sm=b)
                 for bt, u, b in itertools.product((128, 256), (1, 2, 4), (4, 8))]
-BATCH_SPACE = [dict(chunk=c, lane_blocks=lb) for c, lb in itertools.product((256, 512, 1024), (32, 64, 128))]
+BATCH_SPACE = [dict(chunk=c, lane_blocks=lb) for c, lb in itertools.product((256, 512, 1024, 2048, 4096),
+                                                                              (32, 64, 128, 256))]
 
 
 def cache_path() -> str:
