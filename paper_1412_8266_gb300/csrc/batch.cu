@@ -129,7 +129,7 @@ __device__ void mrg_item(const BatchArgs &a, const JumpTable &tab, uint32_t ii, 
     for (uint32_t g = 0; g < max_tiles; ++g) {
         const uint64_t done = (uint64_t)g * G;
         const uint32_t rl = len > done ? (uint32_t)min((uint64_t)G, len - done) : 0u;
-        for (uint32_t j = 0; j < rl; j += VPL) {
+        auto fill = [&](uint32_t j) {  // VPL values of this lane's row into the tile
             if constexpr (sizeof(T) == 4) {
                 T x[4];
 #pragma unroll
@@ -141,6 +141,12 @@ __device__ void mrg_item(const BatchArgs &a, const JumpTable &tab, uint32_t ii, 
                 v.y = bconvert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
                 *reinterpret_cast<double2 *>(&my[j]) = v;
             }
+        };
+        if (rl == (uint32_t)G) {  // a full tile row: unrolled, so steps and stores interleave
+#pragma unroll
+            for (int j = 0; j < G; j += VPL) fill((uint32_t)j);
+        } else {
+            for (uint32_t j = 0; j < rl; j += VPL) fill(j);
         }
         __syncwarp();
         if (vec) {
@@ -234,16 +240,7 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
     // draws this item may write: its own blocks only (an odd lane_blocks leaves
     // the last pair half outside), and the instance's length
     const int64_t lim = min((int64_t)L, (int64_t)(4 * (b0 + 32ull * a.lane_blocks)) - (int64_t)al);
-    for (uint32_t u = 0; u < a.lane_blocks; u += 2) {
-        const uint64_t b = b0 + (uint64_t)u * 32 + 2 * lane;  // this lane's pair: blocks b, b + 1
-        if (b >= nb) break;
-        uint32_t w[8];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint64_t q = q0 + b + h;
-            w[4 * h] = (uint32_t)q; w[4 * h + 1] = (uint32_t)(q >> 32);
-            item_block(tf, w[4 * h], w[4 * h + 1], w[4 * h + 2], w[4 * h + 3], in.key0, in.key1, c2, c3);
-        }
+    auto store_pair = [&](uint64_t b, const uint32_t *w) {  // the eight values of blocks b, b + 1
         const int64_t k0 = (int64_t)(b * 4) - al;
         T v[8];
 #pragma unroll
@@ -259,6 +256,23 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
                 if (k >= 0 && k < lim) row[k] = v[j];
             }
         }
+    };
+    // two pairs per lane in flight (four independent blocks); the second pair is
+    // computed even past the end of the item and then not stored
+    for (uint32_t u = 0; u < a.lane_blocks; u += 4) {
+        const uint64_t b = b0 + (uint64_t)u * 32 + 2 * lane;  // this lane's pairs: b, b + 1 and b + 64, b + 65
+        if (b >= nb) break;
+        uint32_t w[2][8];
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint64_t q = q0 + b + 64 * p + h;
+                w[p][4 * h] = (uint32_t)q; w[p][4 * h + 1] = (uint32_t)(q >> 32);
+                item_block(tf, w[p][4 * h], w[p][4 * h + 1], w[p][4 * h + 2], w[p][4 * h + 3], in.key0, in.key1, c2, c3);
+            }
+        store_pair(b, w[0]);
+        if (u + 2 < a.lane_blocks && b + 64 < nb) store_pair(b + 64, w[1]);
     }
 }
 
