@@ -401,7 +401,9 @@ srng_status srng_batch_plan_create(srng_batch_plan **out, srng_set *const *sets,
                                    void *cuda_stream);
 /* Launch the captured graph once on cuda_stream (asynchronous). */
 srng_status srng_batch_plan_launch(srng_batch_plan *plan, void *cuda_stream);
-/* Number of kernel launches one srng_batch_plan_launch performs. */
+/* Number of kernel launches one srng_batch_plan_launch performs: one
+ * persistent kernel per generator family present (MRG32k3a items; Philox and
+ * Threefry items), both nodes of the one captured graph. */
 srng_status srng_batch_plan_info(const srng_batch_plan *plan, uint64_t *n_work_items,
                                  uint32_t *kernels_per_launch);
 srng_status srng_batch_plan_destroy(srng_batch_plan *plan);

@@ -276,7 +276,13 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
     }
 }
 
-template <int OUT>
+// FAM: which work items the kernel holds code for -- 0 both kinds (the server's
+// steps), 1 MRG32k3a items only, 2 counter-based items only.  A plan launches one
+// kernel per family present: each carries half the code, so fewer instruction
+// cache misses, and its own register count and occupancy.
+enum { kFamAll = 0, kFamMrg = 1, kFamCounter = 2 };
+
+template <int OUT, int FAM>
 __global__ void __launch_bounds__(kWarps * 32) k_batch(const BatchArgs a, const __grid_constant__ JumpTable tab)
 {
     __shared__ __align__(16) Smem<OUT> sm;
@@ -287,8 +293,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_batch(const BatchArgs a, const 
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= a.n_items) break;
         const uint2 item = a.items[it];
-        if (a.inst[item.x].gen == SRNG_MRG32K3A) mrg_item<OUT>(a, tab, item.x, item.y, sm, warp, lane);
-        else philox_item<OUT>(a, item.x, item.y, lane);
+        if constexpr (FAM == kFamMrg) {
+            mrg_item<OUT>(a, tab, item.x, item.y, sm, warp, lane);
+        } else if constexpr (FAM == kFamCounter) {
+            philox_item<OUT>(a, item.x, item.y, lane);
+        } else {
+            if (a.inst[item.x].gen == SRNG_MRG32K3A) mrg_item<OUT>(a, tab, item.x, item.y, sm, warp, lane);
+            else philox_item<OUT>(a, item.x, item.y, lane);
+        }
     }
 }
 
@@ -321,13 +333,16 @@ struct BatchPlanImpl {
     uint64_t n_inst, n_items;
     BatchInst *d_inst = nullptr;
     uint2 *d_items = nullptr;
-    uint32_t *d_counter = nullptr;
+    uint32_t *d_counter = nullptr;           // one per family kernel
     void *out = nullptr;
-    BatchArgs args;
+    BatchArgs args[2];                       // [0] MRG32k3a items, [1] counter-based items
     JumpTable chunk_tab;
-    unsigned grid = 0;
+    unsigned grid[2] = {0, 0};
+    cudaStream_t side = nullptr;             // capture fork for the second kernel
+    cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    uint32_t kernels() const { return (args[0].n_items ? 1u : 0u) + (args[1].n_items ? 1u : 0u); }
 };
 
 }  // namespace srng_impl
@@ -349,36 +364,61 @@ static void plan_free(srng_batch_plan *pl)
     if (p.d_inst) cudaFree(p.d_inst);
     if (p.d_items) cudaFree(p.d_items);
     if (p.d_counter) cudaFree(p.d_counter);
+    if (p.side) cudaStreamDestroy(p.side);
+    if (p.fork) cudaEventDestroy(p.fork);
+    if (p.join) cudaEventDestroy(p.join);
     delete pl;
 }
 
+template <int FAM>
+static void launch_fam(srng_out type, unsigned grid, const BatchArgs &a, const JumpTable &tab, cudaStream_t s)
+{
+    switch (type) {
+    case SRNG_OUT_U32: k_batch<SRNG_OUT_U32, FAM><<<grid, kWarps * 32, 0, s>>>(a, tab); break;
+    case SRNG_OUT_F32: k_batch<SRNG_OUT_F32, FAM><<<grid, kWarps * 32, 0, s>>>(a, tab); break;
+    default: k_batch<SRNG_OUT_F64, FAM><<<grid, kWarps * 32, 0, s>>>(a, tab); break;
+    }
+}
+
+// {reset counters, zero counts} then the family kernels; with both families the
+// counter-based kernel goes on a forked stream so the two are independent graph
+// nodes (its blocks take SMs as the MRG32k3a kernel's blocks finish).
 static cudaError_t enqueue_batch(const BatchPlanImpl &p, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(p.d_counter, 0, sizeof(uint32_t), s);
+    cudaError_t e = cudaMemsetAsync(p.d_counter, 0, 2 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     if (p.mode == SRNG_BATCH_FUSED_PI && p.n_inst) {
         e = cudaMemsetAsync(p.out, 0, p.n_inst * sizeof(int64_t), s);
         if (e != cudaSuccess) return e;
     }
-    if (p.n_items == 0) return cudaSuccess;
-    switch (p.type) {
-    case SRNG_OUT_U32: k_batch<SRNG_OUT_U32><<<p.grid, kWarps * 32, 0, s>>>(p.args, p.chunk_tab); break;
-    case SRNG_OUT_F32: k_batch<SRNG_OUT_F32><<<p.grid, kWarps * 32, 0, s>>>(p.args, p.chunk_tab); break;
-    default: k_batch<SRNG_OUT_F64><<<p.grid, kWarps * 32, 0, s>>>(p.args, p.chunk_tab); break;
+    const bool m = p.args[0].n_items > 0, c = p.args[1].n_items > 0;
+    if (m && c) {
+        if ((e = cudaEventRecord(p.fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(p.side, p.fork, 0)) != cudaSuccess) return e;
+        launch_fam<kFamMrg>(p.type, p.grid[0], p.args[0], p.chunk_tab, s);
+        launch_fam<kFamCounter>(p.type, p.grid[1], p.args[1], p.chunk_tab, p.side);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(p.join, p.side)) != cudaSuccess) return e;
+        return cudaStreamWaitEvent(s, p.join, 0);
     }
+    if (m) launch_fam<kFamMrg>(p.type, p.grid[0], p.args[0], p.chunk_tab, s);
+    if (c) launch_fam<kFamCounter>(p.type, p.grid[1], p.args[1], p.chunk_tab, s);
     return cudaGetLastError();
 }
 
-static int occupancy_blocks(srng_out type)
+template <int FAM>
+static int occupancy_blocks_fam(srng_out type)
 {
     int nb = 0;
     switch (type) {
-    case SRNG_OUT_U32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<SRNG_OUT_U32>, kWarps * 32, 0); break;
-    case SRNG_OUT_F32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<SRNG_OUT_F32>, kWarps * 32, 0); break;
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<SRNG_OUT_F64>, kWarps * 32, 0); break;
+    case SRNG_OUT_U32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<SRNG_OUT_U32, FAM>, kWarps * 32, 0); break;
+    case SRNG_OUT_F32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<SRNG_OUT_F32, FAM>, kWarps * 32, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<SRNG_OUT_F64, FAM>, kWarps * 32, 0); break;
     }
     return nb > 0 ? nb : 1;
 }
+
+static int occupancy_blocks(srng_out type) { return occupancy_blocks_fam<kFamAll>(type); }
 
 cudaError_t launch_batch_setup(BatchInst *d_inst, uint64_t n, cudaStream_t s)
 {
@@ -396,11 +436,7 @@ cudaError_t launch_batch(const BatchArgs &a, srng_out type, const JumpTable &chu
                          cudaStream_t s)
 {
     if (a.n_items == 0) return cudaSuccess;
-    switch (type) {
-    case SRNG_OUT_U32: k_batch<SRNG_OUT_U32><<<grid, kWarps * 32, 0, s>>>(a, chunk_tab); break;
-    case SRNG_OUT_F32: k_batch<SRNG_OUT_F32><<<grid, kWarps * 32, 0, s>>>(a, chunk_tab); break;
-    default: k_batch<SRNG_OUT_F64><<<grid, kWarps * 32, 0, s>>>(a, chunk_tab); break;
-    }
+    launch_fam<kFamAll>(type, grid, a, chunk_tab, s);
     return cudaGetLastError();
 }
 
@@ -418,8 +454,10 @@ void chunk_jump_table(uint64_t chunk, JumpTable *out)
 // Validate, build instance descriptors and the item list on the host.
 srng_status batch_build(srng_set *const *sets, uint32_t n_sets, const srng_instance *inst, uint64_t n_inst,
                         srng_batch_mode mode, srng_out type, void *out_dev, const srng_tune &t,
-                        std::vector<BatchInst> &hin, std::vector<uint2> &items, uint64_t &chunk)
+                        std::vector<BatchInst> &hin, std::vector<uint2> &items, uint64_t &chunk,
+                        uint64_t *n_mrg_items)
 {
+    std::vector<uint2> cb_items;  // counter-based items, placed after the MRG32k3a ones
     if (mode != SRNG_BATCH_WRITE && mode != SRNG_BATCH_FUSED_PI) return fail(SRNG_ERR_ARG, "unknown batch mode");
     if (type != SRNG_OUT_U32 && type != SRNG_OUT_F32 && type != SRNG_OUT_F64)
         return fail(SRNG_ERR_ARG, "unknown output type");
@@ -470,9 +508,11 @@ srng_status batch_build(srng_set *const *sets, uint32_t n_sets, const srng_insta
             const uint64_t per = 32 * lane_blocks;
             const uint64_t nseg = (nb + per - 1) / per;
             if (nseg > (1ull << 32)) return fail(SRNG_ERR_ARG, "instance too long");
-            for (uint64_t g = 0; g < nseg; ++g) items.push_back(make_uint2((uint32_t)i, (uint32_t)g));
+            for (uint64_t g = 0; g < nseg; ++g) cb_items.push_back(make_uint2((uint32_t)i, (uint32_t)g));
         }
     }
+    if (n_mrg_items) *n_mrg_items = items.size();
+    items.insert(items.end(), cb_items.begin(), cb_items.end());
     if (items.size() >= (1ull << 32)) return fail(SRNG_ERR_ARG, "too many work items");
     return SRNG_OK;
 }
@@ -495,8 +535,8 @@ srng_status srng_batch_plan_create(srng_batch_plan **out, srng_set *const *sets,
     const srng_tune t = effective_tune(SRNG_MRG32K3A, type == SRNG_OUT_F64 ? SRNG_OUT_F64 : type, tune);
     std::vector<BatchInst> hin;
     std::vector<uint2> items;
-    uint64_t chunk = 0;
-    if ((st = batch_build(sets, n_sets, inst, n_inst, mode, type, out_dev, t, hin, items, chunk))) return st;
+    uint64_t chunk = 0, n_mrg = 0;
+    if ((st = batch_build(sets, n_sets, inst, n_inst, mode, type, out_dev, t, hin, items, chunk, &n_mrg))) return st;
 
     srng_batch_plan *pl = new (std::nothrow) srng_batch_plan();
     if (!pl) return fail(SRNG_ERR_OOM, "host allocation failed");
@@ -515,7 +555,10 @@ srng_status srng_batch_plan_create(srng_batch_plan **out, srng_set *const *sets,
         e = (expr);                                                      \
         if (e != cudaSuccess) { st = cuda_fail(e, #expr); goto bad; }    \
     } while (0)
-    PLAN_TRY(cudaMalloc(&p.d_counter, sizeof(uint32_t)));
+    PLAN_TRY(cudaMalloc(&p.d_counter, 2 * sizeof(uint32_t)));
+    PLAN_TRY(cudaStreamCreateWithFlags(&p.side, cudaStreamNonBlocking));
+    PLAN_TRY(cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming));
+    PLAN_TRY(cudaEventCreateWithFlags(&p.join, cudaEventDisableTiming));
     if (n_inst) {
         PLAN_TRY(cudaMalloc(&p.d_inst, n_inst * sizeof(BatchInst)));
         PLAN_TRY(cudaMemcpyAsync(p.d_inst, hin.data(), n_inst * sizeof(BatchInst), cudaMemcpyHostToDevice, stream));
@@ -538,21 +581,22 @@ srng_status srng_batch_plan_create(srng_batch_plan **out, srng_set *const *sets,
             m = mat_mul(m, m);
         }
     }
-    p.args.inst = p.d_inst;
-    p.args.items = p.d_items;
-    p.args.counter = p.d_counter;
-    p.args.n_items = p.n_items;
-    p.args.chunk = chunk;
-    p.args.lane_blocks = t.lane_blocks ? t.lane_blocks : 64;
-    p.args.mode = mode;
-    p.args.out = out_dev;
-    {
-        int per_sm = occupancy_blocks(type);
+    for (int f = 0; f < 2; ++f) {  // [0] MRG32k3a items, [1] counter-based items
+        BatchArgs &a = p.args[f];
+        a.inst = p.d_inst;
+        a.items = p.d_items ? p.d_items + (f ? n_mrg : 0) : nullptr;
+        a.counter = p.d_counter + f;
+        a.n_items = f ? p.n_items - n_mrg : n_mrg;
+        a.chunk = chunk;
+        a.lane_blocks = t.lane_blocks ? t.lane_blocks : 64;
+        a.mode = mode;
+        a.out = out_dev;
+        int per_sm = f ? occupancy_blocks_fam<kFamCounter>(type) : occupancy_blocks_fam<kFamMrg>(type);
         if (tune && tune->blocks_per_sm) per_sm = std::min<int>(per_sm, (int)tune->blocks_per_sm);
-        const uint64_t want = (p.n_items + kWarps - 1) / kWarps;
+        const uint64_t want = (a.n_items + kWarps - 1) / kWarps;
         uint64_t g = (uint64_t)dev.sm_count * per_sm;
         if (g > want) g = want;
-        p.grid = (unsigned)std::max<uint64_t>(1, g);
+        p.grid[f] = (unsigned)std::max<uint64_t>(1, g);
     }
     PLAN_TRY(cudaStreamSynchronize(stream));
     // Capture {reset counter, zero counts, persistent kernel} once.
@@ -588,7 +632,7 @@ srng_status srng_batch_plan_info(const srng_batch_plan *plan, uint64_t *n_work_i
     clear_error();
     if (!plan) return fail(SRNG_ERR_ARG, "plan is NULL");
     if (n_work_items) *n_work_items = plan->p.n_items;
-    if (kernels_per_launch) *kernels_per_launch = plan->p.n_items ? 1u : 0u;
+    if (kernels_per_launch) *kernels_per_launch = plan->p.kernels();
     return SRNG_OK;
 }
 
