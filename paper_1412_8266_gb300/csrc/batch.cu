@@ -276,11 +276,11 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
     }
 }
 
-// FAM: which work items the kernel holds code for -- 0 both kinds (the server's
-// steps), 1 MRG32k3a items only, 2 counter-based items only.  A plan launches one
-// kernel per family present: each carries half the code, so fewer instruction
-// cache misses, and its own register count and occupancy.
-enum { kFamAll = 0, kFamMrg = 1, kFamCounter = 2 };
+// FAM: which work items the kernel holds code for -- MRG32k3a items or
+// counter-based (Philox, Threefry) items.  A plan launches one kernel per family
+// present: each carries half the code, so fewer instruction-cache misses, and
+// its own register count and occupancy.
+enum { kFamMrg = 1, kFamCounter = 2 };
 
 template <int OUT, int FAM>
 __global__ void __launch_bounds__(kWarps * 32) k_batch(const BatchArgs a, const __grid_constant__ JumpTable tab)
@@ -293,14 +293,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_batch(const BatchArgs a, const 
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= a.n_items) break;
         const uint2 item = a.items[it];
-        if constexpr (FAM == kFamMrg) {
-            mrg_item<OUT>(a, tab, item.x, item.y, sm, warp, lane);
-        } else if constexpr (FAM == kFamCounter) {
-            philox_item<OUT>(a, item.x, item.y, lane);
-        } else {
-            if (a.inst[item.x].gen == SRNG_MRG32K3A) mrg_item<OUT>(a, tab, item.x, item.y, sm, warp, lane);
-            else philox_item<OUT>(a, item.x, item.y, lane);
-        }
+        if constexpr (FAM == kFamMrg) mrg_item<OUT>(a, tab, item.x, item.y, sm, warp, lane);
+        else philox_item<OUT>(a, item.x, item.y, lane);
     }
 }
 
@@ -418,7 +412,6 @@ static int occupancy_blocks_fam(srng_out type)
     return nb > 0 ? nb : 1;
 }
 
-static int occupancy_blocks(srng_out type) { return occupancy_blocks_fam<kFamAll>(type); }
 
 cudaError_t launch_batch_setup(BatchInst *d_inst, uint64_t n, cudaStream_t s)
 {
@@ -432,15 +425,19 @@ cudaError_t launch_batch_setup(BatchInst *d_inst, uint64_t n, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch(const BatchArgs &a, srng_out type, const JumpTable &chunk_tab, unsigned grid,
+cudaError_t launch_batch(const BatchArgs &a, srng_out type, bool mrg, const JumpTable &chunk_tab, unsigned grid,
                          cudaStream_t s)
 {
     if (a.n_items == 0) return cudaSuccess;
-    launch_fam<kFamAll>(type, grid, a, chunk_tab, s);
+    if (mrg) launch_fam<kFamMrg>(type, grid, a, chunk_tab, s);
+    else launch_fam<kFamCounter>(type, grid, a, chunk_tab, s);
     return cudaGetLastError();
 }
 
-int batch_blocks_per_sm(srng_out type) { return occupancy_blocks(type); }
+int batch_blocks_per_sm(srng_out type, bool mrg)
+{
+    return mrg ? occupancy_blocks_fam<kFamMrg>(type) : occupancy_blocks_fam<kFamCounter>(type);
+}
 
 void chunk_jump_table(uint64_t chunk, JumpTable *out)
 {

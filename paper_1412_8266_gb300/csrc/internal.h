@@ -147,11 +147,12 @@ struct BatchArgs {
 // Instance start states: MRG32k3a = A^offset applied to the stream state;
 // Philox = stream position + offset (reads src_* fields, writes st / pos).
 cudaError_t launch_batch_setup(BatchInst *d_inst, uint64_t n, cudaStream_t s);
-// The persistent batch kernel over a.n_items items; a.counter must be zero.
-cudaError_t launch_batch(const BatchArgs &a, srng_out type, const JumpTable &chunk_tab, unsigned grid,
+// The persistent batch kernel over a.n_items items, all MRG32k3a (mrg) or all
+// counter-based (!mrg); a.counter must be zero.
+cudaError_t launch_batch(const BatchArgs &a, srng_out type, bool mrg, const JumpTable &chunk_tab, unsigned grid,
                          cudaStream_t s);
 // Resident blocks per SM of the batch kernel for `type`.
-int batch_blocks_per_sm(srng_out type);
+int batch_blocks_per_sm(srng_out type, bool mrg);
 // J_k = A^(chunk 2^k), k < 64.
 void chunk_jump_table(uint64_t chunk, JumpTable *out);
 constexpr int kBatchThreads = 256;
