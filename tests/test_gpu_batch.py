@@ -170,3 +170,36 @@ def test_full_size_batched_vs_plain_and_oracle():
     finally:
         srng.srng_destroy(hm)
         srng.srng_destroy(hp)
+
+
+@pytest.mark.parametrize("gen", [srng.SRNG_MRG32K3A, srng.SRNG_PHILOX4X32_10])
+def test_single_family_plan_has_one_kernel(gen):
+    """A batch of one generator family captures one persistent kernel; its
+    output equals the oracle's."""
+    seed = MRG_SEED if gen == srng.SRNG_MRG32K3A else PHX_SEED
+    h = srng.srng_create(gen, seed, 16)
+    try:
+        lengths = [5, 0, 4097, 70001, 33]
+        outoff = np.concatenate([[0], np.cumsum(lengths[:-1])]).astype(int)
+        inst = [srng.Instance(set_index=0, stream=i, offset=0, length=L, out_offset=int(outoff[i]))
+                for i, L in enumerate(lengths)]
+        out = torch.zeros(sum(lengths), dtype=torch.int32, device="cuda")
+        plan = srng.srng_batch_plan_create([h], inst, srng.SRNG_BATCH_WRITE, srng.SRNG_OUT_U32, out)
+        try:
+            srng.srng_batch_plan_launch(plan)
+            torch.cuda.synchronize()
+            items, kernels = srng.srng_batch_plan_info(plan)
+            assert items > 0 and kernels == 1
+        finally:
+            srng.srng_batch_plan_destroy(plan)
+        got = out.cpu().numpy().view(np.uint32)
+        if gen == srng.SRNG_MRG32K3A:
+            st = _states(h, 16)
+            for i, L in enumerate(lengths):
+                ref, _ = O.mrg_generate(st[i], L)
+                assert np.array_equal(got[outoff[i]:outoff[i] + L], ref), i
+        else:
+            for i, L in enumerate(lengths):
+                assert np.array_equal(got[outoff[i]:outoff[i] + L], O.philox_generate(key_of(PHX_SEED), i, 0, L)), i
+    finally:
+        srng.srng_destroy(h)
