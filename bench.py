@@ -584,6 +584,14 @@ def run_case(args):
         tune = json.loads(args.case_tune) if args.case_tune else None
         fn = lambda: srng.srng_generate_tuned(h, 0, S, N_DRAWS, t, o, tune, stream)
         nbytes, nvals = o.numel() * o.element_size(), o.numel()
+    elif c in ("philox_many_u32", "philox_keyed_many_u32"):
+        g = srng.SRNG_PHILOX4X32_10 if c == "philox_many_u32" else srng.SRNG_PHILOX4X32_10_KEYED
+        S = S_STREAMS // k
+        h = srng.srng_create(g, 0xC0FFEE, S, srng.SRNG_SPACING_STREAM, stream)
+        o = torch.empty(S * N_DRAWS, dtype=torch.int32, device=dev)
+        tune = json.loads(args.case_tune) if args.case_tune else None
+        fn = lambda: srng.srng_generate_tuned(h, 0, S, N_DRAWS, srng.SRNG_OUT_U32, o, tune, stream)
+        nbytes, nvals = o.numel() * 4, o.numel()
     elif c.startswith("philox") or c.startswith("threefry"):
         n = (1 << 30) // k
         t = {"u32": srng.SRNG_OUT_U32, "f32": srng.SRNG_OUT_F32, "normal": srng.SRNG_OUT_NORMAL_F32}[c.split("_")[1]]
@@ -629,7 +637,8 @@ def run_case(args):
     return 0
 
 
-CASES = {"mrg_u32", "mrg_f64", "philox_u32", "philox_f32", "philox_normal", "threefry_u32", "threefry_f32",
+CASES = {"mrg_u32", "mrg_f64", "philox_u32", "philox_f32", "philox_normal", "philox_many_u32", "philox_keyed_many_u32",
+         "threefry_u32", "threefry_f32",
          "tinymt_u32", "tinymt_f64",
          "batch_write", "batch_pi", "transform_exponential", "transform_normal"}
 

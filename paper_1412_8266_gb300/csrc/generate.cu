@@ -625,6 +625,9 @@ cudaError_t philox_dispatch(const PhiloxGenArgs &a, const srng_tune &t, cudaStre
         if (t.unroll == 1) {
             if (vec) k_philox_generate_flat<OUT, 1, true, CIPHER><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
             else k_philox_generate_flat<OUT, 1, false, CIPHER><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
+        } else if (t.unroll == 4) {
+            if (vec) k_philox_generate_flat<OUT, 4, true, CIPHER><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
+            else k_philox_generate_flat<OUT, 4, false, CIPHER><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
         } else {
             if (vec) k_philox_generate_flat<OUT, 2, true, CIPHER><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
             else k_philox_generate_flat<OUT, 2, false, CIPHER><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
