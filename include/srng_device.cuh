@@ -336,14 +336,15 @@ __device__ __forceinline__ void jump(const uint4 r, uint32_t &s0, uint32_t &s1, 
 }  // namespace tinymt
 
 /* (v >> 8) 2^-24 as a float, exact, without an integer-to-float conversion:
- * with a = v >> 8 = 2k + b, the bit pattern 0x3F800000 | k is 1 + k 2^-23, so
- * subtracting 1 gives k 2^-23 exactly, and adding b 2^-24 (bit pattern
- * 0x33800000 when b = 1) is exact because 2k + b < 2^24. */
+ * with a = v >> 8 = 2k + b, the bit pattern 0x3F800000 | k is 1 + k 2^-23;
+ * adding -1 (b = 0) or -(1 - 2^-24) (b = 1, the float 0x3F7FFFFF) leaves
+ * (2k + b) 2^-24, which has at most 24 significant bits, so the one rounded
+ * addition is exact. */
 __device__ __forceinline__ float to_f32(uint32_t v)
 {
-    const float hi = __uint_as_float(0x3F800000u | (v >> 9)) - 1.0f;
-    const float lo = __uint_as_float((v & 0x100u) ? 0x33800000u : 0u);
-    return hi + lo;
+    const float one_k = __uint_as_float(0x3F800000u | (v >> 9));
+    const float minus = __uint_as_float((v & 0x100u) ? 0xBF7FFFFFu : 0xBF800000u);
+    return __fadd_rn(one_k, minus);
 }
 
 /* ------------------------------------------------------- generator objects */
