@@ -19,7 +19,8 @@ Parity status per function (what pins it is in tests/test_oracle_pins.py):
   dist_constants / ln_unit_f32 / sincos_2pi_f32 / transform  pinned (exhaustive
       over the 2^24 FP32 uniforms against float64 libm, constants against
       exact rationals, distribution tests)
-  threefry4x32_20 / threefry_word / threefry_*            parity unpinned: the
+  threefry4x32_20 / threefry_word / threefry_*, and the
+  threefry4x64_20 / threefry64_* counterparts              parity unpinned: the
       rotation counts and parity constant of Salmon et al. 2011 have no
       independent implementation here; structure pinned (bijection, key and
       counter use, the block-to-word layout, avalanche)
@@ -95,6 +96,10 @@ def _load(path: str | None = None):
             "oracle_threefry_generate": (None, [u64, u64, u64, u64, i32, vp]),
             "oracle_threefry_bulk": (None, [u64, u64, u64p, u64, u64, i32, vp, i32]),
             "oracle_threefry_pi_count": (ctypes.c_int64, [u64, u64, u64, u64]),
+            "oracle_threefry4x64_20": (None, [u64p, u64p, u64p]),
+            "oracle_threefry64_word": (u32, [u64, u64, u64]),
+            "oracle_threefry64_generate": (None, [u64, u64, u64, u64, i32, vp]),
+            "oracle_threefry64_pi_count": (ctypes.c_int64, [u64, u64, u64, u64]),
             "oracle_tinymt32_next": (None, [u32p, u32, u32]),
             "oracle_tinymt32_temper": (u32, [u32p, u32]),
             "oracle_tinymt32_init": (None, [u32, u32, u32, u32, u32p]),
@@ -294,6 +299,28 @@ def threefry_bulk(seed: int, stream0: int, positions, n: int, out_type: int = OU
 
 def threefry_pi_count(seed: int, stream: int, pos: int, length: int) -> int:
     return int(_load().oracle_threefry_pi_count(seed, stream, pos, length))
+
+
+def threefry4x64_20(ctr, key) -> np.ndarray:
+    c = np.array(ctr, dtype=np.uint64)
+    k = np.array(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    _load().oracle_threefry4x64_20(_u64p(c), _u64p(k), _u64p(out))
+    return out
+
+
+def threefry64_word(seed: int, stream: int, pos: int) -> int:
+    return int(_load().oracle_threefry64_word(seed, stream, pos))
+
+
+def threefry64_generate(seed: int, stream: int, pos: int, n: int, out_type: int = OUT_U32) -> np.ndarray:
+    out = np.empty(n, dtype=_DTYPES[out_type])
+    _load().oracle_threefry64_generate(seed, stream, pos, n, out_type, out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def threefry64_pi_count(seed: int, stream: int, pos: int, length: int) -> int:
+    return int(_load().oracle_threefry64_pi_count(seed, stream, pos, length))
 
 
 # ---------------------------------------------------------------- TinyMT32

@@ -319,6 +319,56 @@ uint32_t oracle_threefry_word(uint64_t seed, uint64_t s, uint64_t p)
     return out[p % 4];
 }
 
+/* Threefry4x64-20: the same construction on four 64-bit words (the Threefish-
+ * 256 block shape), parity constant 0x1BD11BDAA9FC1A22, the eight rotation
+ * pairs below, twenty rounds.  PARITY UNPINNED for the constants, as for
+ * Threefry4x32.  Stream layout: key = (s, seed, 0, 0), counter = (q, 0, 0, 0)
+ * for block q; a block gives eight 32-bit draws, the low then the high half
+ * of each word in order, so draw p is 32-bit word p mod 8 of block p / 8. */
+static const int ORC_THREEFRY64_ROT[8][2] = {
+    {14, 16}, {52, 57}, {23, 40}, {5, 37}, {25, 33}, {46, 12}, {58, 22}, {32, 32}};
+#define ORC_THREEFRY64_PARITY 0x1BD11BDAA9FC1A22ULL
+
+static uint64_t orc_rotl64(uint64_t x, int r) { return (x << r) | (x >> (64 - r)); }
+
+void oracle_threefry4x64_20(const uint64_t ctr[4], const uint64_t key[4], uint64_t out[4])
+{
+    uint64_t ks[5];
+    ks[4] = ORC_THREEFRY64_PARITY;
+    for (int i = 0; i < 4; ++i) {
+        ks[i] = key[i];
+        ks[4] ^= key[i];
+    }
+    uint64_t v[4];
+    for (int i = 0; i < 4; ++i) v[i] = ctr[i] + ks[i];
+    for (int d = 0; d < 20; ++d) {
+        for (int pair = 0; pair < 2; ++pair) {
+            uint64_t *a = &v[2 * pair], *b = &v[2 * pair + 1];
+            *a = *a + *b;
+            *b = orc_rotl64(*b, ORC_THREEFRY64_ROT[d % 8][pair]) ^ *a;
+        }
+        uint64_t t = v[1];
+        v[1] = v[3];
+        v[3] = t;
+        if (d % 4 == 3) {
+            uint64_t j = (uint64_t)(d + 1) / 4;
+            for (int i = 0; i < 4; ++i) v[i] += ks[(j + i) % 5];
+            v[3] += j;
+        }
+    }
+    for (int i = 0; i < 4; ++i) out[i] = v[i];
+}
+
+uint32_t oracle_threefry64_word(uint64_t seed, uint64_t s, uint64_t p)
+{
+    uint64_t ctr[4] = {p / 8, 0, 0, 0};
+    uint64_t key[4] = {s, seed, 0, 0};
+    uint64_t out[4];
+    oracle_threefry4x64_20(ctr, key, out);
+    uint64_t w = out[(p % 8) / 2];
+    return (p % 2) ? (uint32_t)(w >> 32) : (uint32_t)w;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Integer -> uniform conversions (fixed readings)                          */
 /* ---------------------------------------------------------------------- */
@@ -367,6 +417,12 @@ void oracle_philox_generate(uint32_t k0, uint32_t k1, uint64_t s, uint64_t p, ui
 void oracle_threefry_generate(uint64_t seed, uint64_t s, uint64_t p, uint64_t n, int out_type, void *out)
 {
     for (uint64_t k = 0; k < n; ++k) store_value(out_type, out, k, oracle_threefry_word(seed, s, p + k), 0);
+}
+
+/* n draws of Threefry4x64 stream s starting at position p (conversions as Philox). */
+void oracle_threefry64_generate(uint64_t seed, uint64_t s, uint64_t p, uint64_t n, int out_type, void *out)
+{
+    for (uint64_t k = 0; k < n; ++k) store_value(out_type, out, k, oracle_threefry64_word(seed, s, p + k), 0);
 }
 
 /* Stream-major bulk output of many streams:
@@ -454,6 +510,14 @@ int64_t oracle_philox_pi_count(uint32_t k0, uint32_t k1, uint64_t s, uint64_t p,
     for (uint64_t k = 0; k + 1 < length; k += 2)
         hits += oracle_pi_hit_philox(oracle_philox_word(k0, k1, s, p + k),
                                      oracle_philox_word(k0, k1, s, p + k + 1));
+    return hits;
+}
+
+int64_t oracle_threefry64_pi_count(uint64_t seed, uint64_t s, uint64_t p, uint64_t length)
+{
+    int64_t hits = 0;
+    for (uint64_t k = 0; k + 1 < length; k += 2)
+        hits += oracle_pi_hit_philox(oracle_threefry64_word(seed, s, p + k), oracle_threefry64_word(seed, s, p + k + 1));
     return hits;
 }
 

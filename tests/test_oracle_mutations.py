@@ -50,6 +50,10 @@ MUTATIONS = {
     "reflection": ("if (exchanged) r = 1.0f - r;", "if (exchanged) r = r - 0.5f;"),
     "threefry permutation": ("        v[1] = v[3];\n        v[3] = t;\n", "        (void)t;\n"),
     "threefry rounds": ("for (int d = 0; d < 20; ++d) {", "for (int d = 0; d < 3; ++d) {"),
+    "threefry64 permutation": ("        uint64_t t = v[1];\n        v[1] = v[3];\n        v[3] = t;\n",
+                               "        uint64_t t = v[1];\n        (void)t;\n"),
+    "threefry64 rounds": ("    for (int d = 0; d < 20; ++d) {\n        for (int pair = 0; pair < 2; ++pair) {\n            uint64_t",
+                          "    for (int d = 0; d < 3; ++d) {\n        for (int pair = 0; pair < 2; ++pair) {\n            uint64_t"),
     "tinymt shift": ("    s[2] = x ^ (y << 10);", "    s[2] = x ^ (y << 11);"),
     "tinymt feedback": ("    x ^= x << 1;\n    uint32_t y", "    x ^= x << 2;\n    uint32_t y"),
     "tinymt mask": ("uint32_t x = (s[0] & ORC_TMT_MASK) ^ s[1] ^ s[2];", "uint32_t x = s[0] ^ s[1] ^ s[2];"),
@@ -189,6 +193,17 @@ def _pins_fail(ref):
                 c2[b // 32] ^= np.uint32(1 << (b % 32))
                 flips[b] += np.unpackbits(O.threefry4x32_20(c2, key).view(np.uint8)) != base
         if np.abs(flips / 48 - 0.5).max() > 0.33:
+            return True
+        flips = np.zeros((256, 256))
+        for _ in range(32):
+            ctr = rng.integers(0, 2**63, 4, dtype=np.uint64)
+            key = rng.integers(0, 2**63, 4, dtype=np.uint64)
+            base = np.unpackbits(O.threefry4x64_20(ctr, key).view(np.uint8))
+            for b in range(256):
+                c2 = ctr.copy()
+                c2[b // 64] ^= np.uint64(1 << (b % 64))
+                flips[b] += np.unpackbits(O.threefry4x64_20(c2, key).view(np.uint8)) != base
+        if np.abs(flips / 32 - 0.5).max() > 0.38:
             return True
         # TinyMT32: the authors' default parameter set has period 2^127 - 1
         # under the step; jumps equal stepping
