@@ -449,19 +449,22 @@ def extras(torch, srng, dev, stream, peak):
     srng.srng_destroy(h)
     res["philox_bulk_2^30"] = ph
     res["variates_2^30_f32"] = var
-    # Threefry4x32-20 bulk: 2^30 words of one stream, u32 and f32 (ALU bound: 20 add/rotate/xor rounds)
-    tf = {}
-    h = srng.srng_create(srng.SRNG_THREEFRY4X32_20, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
-    for name, t, dt in (("u32", srng.SRNG_OUT_U32, torch.int32), ("f32", srng.SRNG_OUT_F32, torch.float32)):
-        tt = autotune.tune_generate(srng.SRNG_THREEFRY4X32_20, t, 1, n, use_cache=False, install=False)[0]
-        o = torch.empty(n, dtype=dt, device=dev)
-        best, med = _time(torch, stream, lambda: (srng.srng_reset(h, stream),
-                                                  srng.srng_generate_tuned(h, 0, 1, n, t, o, tt, stream)))
-        tf[name] = {"ms_best": best, "ms_median": med, "Guniforms_s": n / best / 1e6, "GB_s": n * 4 / best / 1e6,
-                    "frac_of_copy_peak": n * 4 / best / 1e6 / peak, "tune": tt}
-        del o
-    srng.srng_destroy(h)
-    res["threefry_bulk_2^30"] = tf
+    # Threefry bulk: 2^30 words of one stream, u32 and f32, both word sizes (ALU bound: 20 rounds of
+    # add / rotate / xor per block; the 4x64 block gives eight words)
+    for key, g in (("threefry_bulk_2^30", srng.SRNG_THREEFRY4X32_20),
+                   ("threefry4x64_bulk_2^30", srng.SRNG_THREEFRY4X64_20)):
+        tf = {}
+        h = srng.srng_create(g, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
+        for name, t, dt in (("u32", srng.SRNG_OUT_U32, torch.int32), ("f32", srng.SRNG_OUT_F32, torch.float32)):
+            tt = autotune.tune_generate(g, t, 1, n, use_cache=False, install=False)[0]
+            o = torch.empty(n, dtype=dt, device=dev)
+            best, med = _time(torch, stream, lambda: (srng.srng_reset(h, stream),
+                                                      srng.srng_generate_tuned(h, 0, 1, n, t, o, tt, stream)))
+            tf[name] = {"ms_best": best, "ms_median": med, "Guniforms_s": n / best / 1e6, "GB_s": n * 4 / best / 1e6,
+                        "frac_of_copy_peak": n * 4 / best / 1e6 / peak, "tune": tt}
+            del o
+        srng.srng_destroy(h)
+        res[key] = tf
     # TinyMT32 bulk at the MRG32k3a bulk shape: 2^18 streams (1024 parameter sets of 256) x 4096, u32 and FP64
     tm = {}
     t0 = time.perf_counter()
@@ -595,7 +598,8 @@ def run_case(args):
     elif c.startswith("philox") or c.startswith("threefry"):
         n = (1 << 30) // k
         t = {"u32": srng.SRNG_OUT_U32, "f32": srng.SRNG_OUT_F32, "normal": srng.SRNG_OUT_NORMAL_F32}[c.split("_")[1]]
-        g = srng.SRNG_PHILOX4X32_10 if c.startswith("philox") else srng.SRNG_THREEFRY4X32_20
+        g = (srng.SRNG_PHILOX4X32_10 if c.startswith("philox") else
+             srng.SRNG_THREEFRY4X64_20 if c.startswith("threefry64") else srng.SRNG_THREEFRY4X32_20)
         h = srng.srng_create(g, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
         o = torch.empty(n, dtype=torch.int32 if t == 0 else torch.float32, device=dev)
         fn = lambda: srng.srng_generate(h, 0, 1, n, t, o, stream)
@@ -638,7 +642,7 @@ def run_case(args):
 
 
 CASES = {"mrg_u32", "mrg_f64", "philox_u32", "philox_f32", "philox_normal", "philox_many_u32", "philox_keyed_many_u32",
-         "threefry_u32", "threefry_f32",
+         "threefry_u32", "threefry_f32", "threefry64_u32", "threefry64_f32",
          "tinymt_u32", "tinymt_f64",
          "batch_write", "batch_pi", "transform_exponential", "transform_normal"}
 

@@ -74,7 +74,8 @@ typedef enum srng_gen {
     SRNG_PHILOX4X32_10 = 1,      /* streams split the counter, one key per set        */
     SRNG_PHILOX4X32_10_KEYED = 2, /* one key per stream (paper Sec. 4.3): see srng_create */
     SRNG_THREEFRY4X32_20 = 3,     /* Threefry4x32, 20 rounds (Sec. 4.3): see srng_create  */
-    SRNG_TINYMT32 = 4             /* TinyMT32 (Sec. 4.2): see srng_create_tinymt          */
+    SRNG_TINYMT32 = 4,            /* TinyMT32 (Sec. 4.2): see srng_create_tinymt          */
+    SRNG_THREEFRY4X64_20 = 5      /* Threefry4x64, 20 rounds (Sec. 4.3): see srng_create  */
 } srng_gen;
 
 typedef enum srng_out {
@@ -171,6 +172,10 @@ int srng_abi_version(void);
  *     and counter (position / 4 low, high, 0, 0), draw = word position % 4;
  *     conversions, positions and limits as Philox.  Tuning entries are
  *     shared with Philox (srng_set_tune of either applies to both).
+ *   Threefry4x64-20 (SRNG_THREEFRY4X64_20; the 64-bit-word form): stream s
+ *     uses key (s, seed, 0, 0) and counter (position / 8, 0, 0, 0) as 64-bit
+ *     words; a block gives eight 32-bit draws, the low then the high half of
+ *     each word, draw = 32-bit word position % 8.  Otherwise as Threefry4x32.
  * n_streams: 1 .. 2^40 (MRG32k3a with SRNG_SPACING_STREAM: at most 2^64 by
  * the paper, here limited by device memory: 24 bytes per stream; Philox and
  * Threefry: 8).

@@ -285,6 +285,53 @@ __device__ __forceinline__ void block(uint32_t &c0, uint32_t &c1, uint32_t &c2, 
 }
 }  // namespace threefry
 
+namespace threefry64 {
+/* Threefry-4x64 (Salmon et al. 2011): the same construction on four 64-bit
+ * words (the Threefish-256 shape) with parity constant kParity64 and the
+ * rotation pairs of rot64; twenty rounds.  64-bit adds and rotates run as
+ * pairs of 32-bit operations on this GPU. */
+constexpr uint64_t kParity64 = 0x1BD11BDAA9FC1A22ull;
+__host__ __device__ constexpr int rot64(int r, int half)
+{
+    return r == 0 ? (half ? 16 : 14) : r == 1 ? (half ? 57 : 52) : r == 2 ? (half ? 40 : 23)
+         : r == 3 ? (half ? 37 : 5) : r == 4 ? (half ? 33 : 25) : r == 5 ? (half ? 12 : 46)
+         : r == 6 ? (half ? 22 : 58) : (half ? 32 : 32);
+}
+__device__ __forceinline__ uint64_t rotl64(uint64_t x, int r) { return (x << r) | (x >> (64 - r)); }
+
+/* Twenty rounds on counter (c0..c3) with key (k0..k3), in place. */
+__device__ __forceinline__ void block(uint64_t &c0, uint64_t &c1, uint64_t &c2, uint64_t &c3, uint64_t k0,
+                                      uint64_t k1, uint64_t k2, uint64_t k3)
+{
+    const uint64_t ks[5] = {k0, k1, k2, k3, kParity64 ^ k0 ^ k1 ^ k2 ^ k3};
+    c0 += ks[0]; c1 += ks[1]; c2 += ks[2]; c3 += ks[3];
+#pragma unroll
+    for (int r = 0; r < 20; ++r) {
+        if ((r & 1) == 0) {
+            c0 += c1; c1 = rotl64(c1, rot64(r & 7, 0)) ^ c0;
+            c2 += c3; c3 = rotl64(c3, rot64(r & 7, 1)) ^ c2;
+        } else {
+            c0 += c3; c3 = rotl64(c3, rot64(r & 7, 0)) ^ c0;
+            c2 += c1; c1 = rotl64(c1, rot64(r & 7, 1)) ^ c2;
+        }
+        if ((r & 3) == 3) {
+            const int j = (r + 1) >> 2;
+            c0 += ks[j % 5]; c1 += ks[(j + 1) % 5]; c2 += ks[(j + 2) % 5]; c3 += ks[(j + 3) % 5] + (uint64_t)j;
+        }
+    }
+}
+
+/* The eight 32-bit draws of block q of stream s under `seed`: key (s, seed, 0, 0),
+ * counter (q, 0, 0, 0); the low then the high half of each 64-bit word. */
+__device__ __forceinline__ void words(uint64_t q, uint64_t s, uint64_t seed, uint32_t *w)
+{
+    uint64_t c0 = q, c1 = 0, c2 = 0, c3 = 0;
+    block(c0, c1, c2, c3, s, seed, 0, 0);
+    w[0] = (uint32_t)c0; w[1] = (uint32_t)(c0 >> 32); w[2] = (uint32_t)c1; w[3] = (uint32_t)(c1 >> 32);
+    w[4] = (uint32_t)c2; w[5] = (uint32_t)(c2 >> 32); w[6] = (uint32_t)c3; w[7] = (uint32_t)(c3 >> 32);
+}
+}  // namespace threefry64
+
 namespace tinymt {
 /* TinyMT32 (Saito & Matsumoto 2011; the paper's Sec. 4.2): one step of the
  * 127-bit GF(2)-linear state (bit 31 of s0 unused) with parameters
@@ -390,9 +437,9 @@ class Philox4x32_10 {
         : k0((v.flags & 1u) ? (uint32_t)(v.stream_base + stream) : v.key0),
           k1((v.flags & 1u) ? (uint32_t)((v.stream_base + stream) >> 32) : v.key1), stream_(stream),
           ctr_hi_((v.flags & 1u) ? ((uint64_t)v.key1 << 32 | v.key0) : v.stream_base + stream),
-          pos_(v.philox_pos[stream]) {}
+          pos_(v.philox_pos[stream]), bq_(~0ull) {}
     __device__ Philox4x32_10(uint32_t key0, uint32_t key1, uint64_t stream, uint64_t position)
-        : k0(key0), k1(key1), stream_(stream), ctr_hi_(stream), pos_(position) {}
+        : k0(key0), k1(key1), stream_(stream), ctr_hi_(stream), pos_(position), bq_(~0ull) {}
 
     /* The four words of block q of this stream. */
     __device__ __forceinline__ uint4 block(uint64_t q) const
@@ -402,12 +449,18 @@ class Philox4x32_10 {
         philox::block(c0, c1, c2, c3, k0, k1);
         return make_uint4(c0, c1, c2, c3);
     }
+    /* Draw pos: the block of the previous draw is kept, so four consecutive
+     * draws cost one block. */
     __device__ __forceinline__ uint32_t next_u32()
     {
-        uint4 b = block(pos_ >> 2);
-        uint32_t j = (uint32_t)pos_ & 3u;
+        const uint64_t q = pos_ >> 2;
+        if (q != bq_) {
+            b_ = block(q);
+            bq_ = q;
+        }
+        const uint32_t j = (uint32_t)pos_ & 3u;
         ++pos_;
-        return j == 0 ? b.x : j == 1 ? b.y : j == 2 ? b.z : b.w;
+        return j == 0 ? b_.x : j == 1 ? b_.y : j == 2 ? b_.z : b_.w;
     }
     __device__ __forceinline__ float next_f32() { return to_f32(next_u32()); }
     __device__ __forceinline__ double next_f64() { return philox::to_f64(next_u32()); }
@@ -416,6 +469,10 @@ class Philox4x32_10 {
 
     uint32_t k0, k1;
     uint64_t stream_, ctr_hi_, pos_;
+
+  private:
+    uint64_t bq_;  // block held in b_ (~0: none; block numbers are below 2^62)
+    uint4 b_;
 };
 
 /* Threefry4x32-20 stream handle (the paper's per-thread key, Sec. 4.3):
@@ -428,10 +485,10 @@ class Threefry4x32_20 {
      * v.stream_base + stream and the set's seed words v.key0, v.key1. */
     __device__ Threefry4x32_20(const srng_dev_view &v, uint64_t stream)
         : k0((uint32_t)(v.stream_base + stream)), k1((uint32_t)((v.stream_base + stream) >> 32)), k2(v.key0),
-          k3(v.key1), stream_(stream), pos_(v.philox_pos[stream]) {}
+          k3(v.key1), stream_(stream), pos_(v.philox_pos[stream]), bq_(~0ull) {}
     __device__ Threefry4x32_20(uint64_t seed, uint64_t stream, uint64_t position)
         : k0((uint32_t)stream), k1((uint32_t)(stream >> 32)), k2((uint32_t)seed), k3((uint32_t)(seed >> 32)),
-          stream_(stream), pos_(position) {}
+          stream_(stream), pos_(position), bq_(~0ull) {}
 
     __device__ __forceinline__ uint4 block(uint64_t q) const
     {
@@ -441,10 +498,14 @@ class Threefry4x32_20 {
     }
     __device__ __forceinline__ uint32_t next_u32()
     {
-        uint4 b = block(pos_ >> 2);
-        uint32_t j = (uint32_t)pos_ & 3u;
+        const uint64_t q = pos_ >> 2;
+        if (q != bq_) {
+            b_ = block(q);
+            bq_ = q;
+        }
+        const uint32_t j = (uint32_t)pos_ & 3u;
         ++pos_;
-        return j == 0 ? b.x : j == 1 ? b.y : j == 2 ? b.z : b.w;
+        return j == 0 ? b_.x : j == 1 ? b_.y : j == 2 ? b_.z : b_.w;
     }
     __device__ __forceinline__ float next_f32() { return to_f32(next_u32()); }
     __device__ __forceinline__ double next_f64() { return philox::to_f64(next_u32()); }
@@ -453,6 +514,47 @@ class Threefry4x32_20 {
 
     uint32_t k0, k1, k2, k3;
     uint64_t stream_, pos_;
+
+  private:
+    uint64_t bq_;  // block held in b_ (~0: none)
+    uint4 b_;
+};
+
+/* Threefry4x64-20 stream handle: key = (stream, seed, 0, 0), counter
+ * (q, 0, 0, 0) for block q; draw p is 32-bit word p mod 8 of block p / 8. */
+class Threefry4x64_20 {
+  public:
+    __device__ Threefry4x64_20(const srng_dev_view &v, uint64_t stream)
+        : s_(v.stream_base + stream), seed_((uint64_t)v.key1 << 32 | v.key0), stream_(stream),
+          pos_(v.philox_pos[stream]), bq_(~0ull) {}
+    __device__ Threefry4x64_20(uint64_t seed, uint64_t stream, uint64_t position)
+        : s_(stream), seed_(seed), stream_(stream), pos_(position), bq_(~0ull) {}
+
+    /* Eight consecutive draws cost one block (the last block is kept). */
+    __device__ __forceinline__ uint32_t next_u32()
+    {
+        const uint64_t q = pos_ >> 3;
+        if (q != bq_) {
+            threefry64::words(q, s_, seed_, w_);
+            bq_ = q;
+        }
+        const uint32_t j = (uint32_t)pos_ & 7u;
+        ++pos_;
+        uint32_t r = w_[0];
+#pragma unroll
+        for (int i = 1; i < 8; ++i) r = j == (uint32_t)i ? w_[i] : r;
+        return r;
+    }
+    __device__ __forceinline__ float next_f32() { return to_f32(next_u32()); }
+    __device__ __forceinline__ double next_f64() { return philox::to_f64(next_u32()); }
+    __device__ void store(const srng_dev_view &v) const { v.philox_pos[stream_] = pos_; }
+    __device__ uint64_t position() const { return pos_; }
+
+    uint64_t s_, seed_, stream_, pos_;
+
+  private:
+    uint64_t bq_;  // block held in w_ (~0: none; block numbers are below 2^61)
+    uint32_t w_[8];
 };
 
 /* TinyMT32 stream handle (the paper's Sec. 4.2 hybrid: the parameter set of
@@ -605,6 +707,7 @@ static_assert(is_generator<Mrg32k3a>::value, "Mrg32k3a must provide next_u32/nex
 static_assert(is_generator<Philox4x32_10>::value, "Philox4x32_10 must provide next_u32/next_f32/next_f64");
 static_assert(is_generator<Threefry4x32_20>::value, "Threefry4x32_20 must provide next_u32/next_f32/next_f64");
 static_assert(is_generator<TinyMT32>::value, "TinyMT32 must provide next_u32/next_f32/next_f64");
+static_assert(is_generator<Threefry4x64_20>::value, "Threefry4x64_20 must provide next_u32/next_f32/next_f64");
 #if __cplusplus >= 202002L
 template <class G>
 concept DeviceGenerator = requires(G g) {
@@ -613,7 +716,7 @@ concept DeviceGenerator = requires(G g) {
     { g.next_f64() } -> std::same_as<double>;
 };
 static_assert(DeviceGenerator<Mrg32k3a> && DeviceGenerator<Philox4x32_10> && DeviceGenerator<Threefry4x32_20> &&
-              DeviceGenerator<TinyMT32>);
+              DeviceGenerator<Threefry4x64_20> && DeviceGenerator<TinyMT32>);
 #endif
 
 namespace detail {
@@ -638,6 +741,7 @@ template <> struct gen_id<Mrg32k3a> { static constexpr int value = SRNG_MRG32K3A
 template <> struct gen_id<Philox4x32_10> { static constexpr int value = SRNG_PHILOX4X32_10; };
 template <> struct gen_id<Threefry4x32_20> { static constexpr int value = SRNG_THREEFRY4X32_20; };
 template <> struct gen_id<TinyMT32> { static constexpr int value = SRNG_TINYMT32; };
+template <> struct gen_id<Threefry4x64_20> { static constexpr int value = SRNG_THREEFRY4X64_20; };
 }  // namespace detail
 
 /* The paper's device object (Listing 1): constructed inside a kernel with no

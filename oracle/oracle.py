@@ -100,6 +100,7 @@ def _load(path: str | None = None):
             "oracle_threefry64_word": (u32, [u64, u64, u64]),
             "oracle_threefry64_generate": (None, [u64, u64, u64, u64, i32, vp]),
             "oracle_threefry64_pi_count": (ctypes.c_int64, [u64, u64, u64, u64]),
+            "oracle_threefry64_bulk": (None, [u64, u64, u64p, u64, u64, i32, vp, i32]),
             "oracle_tinymt32_next": (None, [u32p, u32, u32]),
             "oracle_tinymt32_temper": (u32, [u32p, u32]),
             "oracle_tinymt32_init": (None, [u32, u32, u32, u32, u32p]),
@@ -317,6 +318,14 @@ def threefry64_generate(seed: int, stream: int, pos: int, n: int, out_type: int 
     out = np.empty(n, dtype=_DTYPES[out_type])
     _load().oracle_threefry64_generate(seed, stream, pos, n, out_type, out.ctypes.data_as(ctypes.c_void_p))
     return out
+
+
+def threefry64_bulk(seed: int, stream0: int, positions, n: int, out_type: int = OUT_U32, threads: int = 0):
+    pos = np.ascontiguousarray(np.array(positions, dtype=np.uint64))
+    out = np.empty((pos.shape[0], n), dtype=_DTYPES[out_type])
+    _load().oracle_threefry64_bulk(seed, stream0, _u64p(pos), pos.shape[0], n, out_type,
+                                   out.ctypes.data_as(ctypes.c_void_p), threads)
+    return out, pos
 
 
 def threefry64_pi_count(seed: int, stream: int, pos: int, length: int) -> int:

@@ -471,6 +471,21 @@ void oracle_threefry_bulk(uint64_t seed, uint64_t stream0, uint64_t *positions, 
     }
 }
 
+void oracle_threefry64_bulk(uint64_t seed, uint64_t stream0, uint64_t *positions, uint64_t n_streams,
+                            uint64_t n, int out_type, void *out, int threads)
+{
+    size_t esz = out_type == ORC_OUT_F64 ? 8 : 4;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t i = 0; i < (int64_t)n_streams; ++i) {
+        oracle_threefry64_generate(seed, stream0 + (uint64_t)i, positions[i], n, out_type,
+                                   (char *)out + (size_t)i * n * esz);
+        positions[i] += n;
+    }
+}
+
 /* ---------------------------------------------------------------------- */
 /* Monte Carlo quarter-circle hit count (fused consumer reading).          */
 /* Draws are taken in pairs (2k, 2k+1), k < floor(L/2); a pair hits when    */

@@ -21,7 +21,7 @@ import threading
 __all__ = [
     "SrngError", "Tune", "Instance", "SetDesc", "DevView", "ServerConfig", "ServerStats", "Request",
     "lib_path", "load",
-    "SRNG_MRG32K3A", "SRNG_PHILOX4X32_10", "SRNG_PHILOX4X32_10_KEYED", "SRNG_THREEFRY4X32_20", "SRNG_TINYMT32",
+    "SRNG_MRG32K3A", "SRNG_PHILOX4X32_10", "SRNG_PHILOX4X32_10_KEYED", "SRNG_THREEFRY4X32_20", "SRNG_THREEFRY4X64_20", "SRNG_TINYMT32",
     "SRNG_OUT_U32", "SRNG_OUT_F32", "SRNG_OUT_F64", "SRNG_OUT_EXP_F32", "SRNG_OUT_NORMAL_F32",
     "SRNG_SPACING_STREAM", "SRNG_SPACING_SUBSTREAM", "SRNG_JUMP_DRAWS", "SRNG_JUMP_SUBSTREAMS",
     "SRNG_JUMP_STREAMS", "SRNG_BATCH_WRITE", "SRNG_BATCH_FUSED_PI", "SRNG_DIST_EXPONENTIAL", "SRNG_DIST_NORMAL",
@@ -29,6 +29,7 @@ __all__ = [
 
 SRNG_ABI_VERSION = 2  # the struct layouts below follow this version of include/srng.h
 SRNG_MRG32K3A, SRNG_PHILOX4X32_10, SRNG_PHILOX4X32_10_KEYED, SRNG_THREEFRY4X32_20, SRNG_TINYMT32 = 0, 1, 2, 3, 4
+SRNG_THREEFRY4X64_20 = 5
 SRNG_OUT_U32, SRNG_OUT_F32, SRNG_OUT_F64 = 0, 1, 2
 SRNG_OUT_EXP_F32, SRNG_OUT_NORMAL_F32 = 3, 4
 SRNG_SPACING_STREAM, SRNG_SPACING_SUBSTREAM = 0, 1

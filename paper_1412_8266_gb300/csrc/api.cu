@@ -157,7 +157,7 @@ size_t out_size(srng_out t) { return t == SRNG_OUT_F64 ? 8 : 4; }
 bool valid_gen(int g)
 {
     return g == SRNG_MRG32K3A || g == SRNG_PHILOX4X32_10 || g == SRNG_PHILOX4X32_10_KEYED ||
-           g == SRNG_THREEFRY4X32_20 || g == SRNG_TINYMT32;
+           g == SRNG_THREEFRY4X32_20 || g == SRNG_TINYMT32 || g == SRNG_THREEFRY4X64_20;
 }
 bool valid_out(int t) { return t == SRNG_OUT_U32 || t == SRNG_OUT_F32 || t == SRNG_OUT_F64; }
 // Output types of the bulk generation calls (the uniforms and the fused variates).
@@ -290,7 +290,7 @@ static srng_status tmt_create(srng_set **out, const uint32_t *params, const std:
     srng_set *s = new (std::nothrow) srng_set();
     if (!s) return fail(SRNG_ERR_OOM, "host allocation failed");
     s->gen = SRNG_TINYMT32;
-    s->keyed = s->threefry = false;
+    s->keyed = s->threefry = s->threefry64 = false;
     s->spacing = SRNG_SPACING_STREAM;
     s->n_streams = n_streams;
     s->stream_base = 0;
@@ -373,8 +373,9 @@ static srng_status create_common(srng_set **out, srng_gen gen, uint64_t seed, co
     }
     srng_set *s = new (std::nothrow) srng_set();
     if (!s) return fail(SRNG_ERR_OOM, "host allocation failed");
-    s->keyed = gen == SRNG_PHILOX4X32_10_KEYED || gen == SRNG_THREEFRY4X32_20;
-    s->threefry = gen == SRNG_THREEFRY4X32_20;
+    s->keyed = gen == SRNG_PHILOX4X32_10_KEYED || gen == SRNG_THREEFRY4X32_20 || gen == SRNG_THREEFRY4X64_20;
+    s->threefry = gen == SRNG_THREEFRY4X32_20 || gen == SRNG_THREEFRY4X64_20;
+    s->threefry64 = gen == SRNG_THREEFRY4X64_20;
     s->gen = (srng_gen)kernel_gen(gen);
     s->spacing = spacing;
     s->n_streams = n_streams;
@@ -500,7 +501,7 @@ static srng_status generate_dev(srng_set *s, uint64_t b, uint64_t c, uint64_t n,
         a.k0 = s->key0;
         a.k1 = s->key1;
         a.keyed = s->keyed ? 1 : 0;
-        a.threefry = s->threefry ? 1 : 0;
+        a.threefry = s->threefry64 ? 2 : s->threefry ? 1 : 0;
         a.pos = s->d_pos;
         a.s_begin = b;
         a.s_count = c;
@@ -663,7 +664,7 @@ srng_status srng_describe(const srng_set *set, srng_set_desc *out)
     clear_error();
     if (!set || !out) return fail(SRNG_ERR_ARG, "NULL argument");
     memset(out, 0, sizeof *out);
-    out->gen = set->threefry ? SRNG_THREEFRY4X32_20 : set->keyed ? SRNG_PHILOX4X32_10_KEYED : set->gen;  // TinyMT32 too
+    out->gen = set->threefry ? (srng_gen)inst_gen(set) : set->keyed ? SRNG_PHILOX4X32_10_KEYED : set->gen;  // TinyMT32 too
     out->spacing = set->spacing;
     out->n_streams = set->n_streams;
     out->seed = set->seed;

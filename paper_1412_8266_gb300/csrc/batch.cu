@@ -184,12 +184,21 @@ __device__ void mrg_item(const BatchArgs &a, const JumpTable &tab, uint32_t ii, 
 }
 
 // ------------------------------------------------------- Philox work item
-// Block q of an instance's stream (x0, x1 = q on entry), Philox or Threefry.
-__device__ __forceinline__ void item_block(bool tf, uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x3,
+// Block q of an instance's stream (x0, x1 = q on entry), and the block pair
+// (q, q + 1), for the instance's cipher (uniform over the warp).
+__device__ __forceinline__ void item_block(int cipher, uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x3,
                                            uint32_t kk0, uint32_t kk1, uint32_t c2, uint32_t c3)
 {
-    if (tf) cb_block<kCipherThreefry>(x0, x1, x2, x3, kk0, kk1, c2, c3);
+    if (cipher == kCipherThreefry) cb_block<kCipherThreefry>(x0, x1, x2, x3, kk0, kk1, c2, c3);
+    else if (cipher == kCipherThreefry64) cb_block<kCipherThreefry64>(x0, x1, x2, x3, kk0, kk1, c2, c3);
     else cb_block<kCipherPhilox>(x0, x1, x2, x3, kk0, kk1, c2, c3);
+}
+__device__ __forceinline__ void item_pair(int cipher, uint64_t q, uint32_t *w, uint32_t kk0, uint32_t kk1, uint32_t c2,
+                                          uint32_t c3)
+{
+    if (cipher == kCipherThreefry) cb_pair<kCipherThreefry>(q, w, kk0, kk1, c2, c3);
+    else if (cipher == kCipherThreefry64) cb_pair<kCipherThreefry64>(q, w, kk0, kk1, c2, c3);
+    else cb_pair<kCipherPhilox>(q, w, kk0, kk1, c2, c3);
 }
 
 // Lane l computes pairs of adjacent blocks; eight values per pair go out as
@@ -205,7 +214,8 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
     const uint64_t nb = (al + in.length + 3) >> 2;
     const uint64_t b0 = (uint64_t)seg * 32 * a.lane_blocks;
     const uint32_t c2 = (uint32_t)in.ctr_hi, c3 = (uint32_t)(in.ctr_hi >> 32);
-    const bool tf = in.gen == SRNG_THREEFRY4X32_20;  // uniform over the warp
+    const int tf = in.gen == SRNG_THREEFRY4X32_20 ? kCipherThreefry
+                 : in.gen == SRNG_THREEFRY4X64_20 ? kCipherThreefry64 : kCipherPhilox;  // uniform over the warp
     const uint64_t L = in.length;
     if (a.mode == SRNG_BATCH_FUSED_PI) {
         uint32_t hits = 0;
@@ -264,13 +274,7 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
         if (b >= nb) break;
         uint32_t w[2][8];
 #pragma unroll
-        for (int p = 0; p < 2; ++p)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint64_t q = q0 + b + 64 * p + h;
-                w[p][4 * h] = (uint32_t)q; w[p][4 * h + 1] = (uint32_t)(q >> 32);
-                item_block(tf, w[p][4 * h], w[p][4 * h + 1], w[p][4 * h + 2], w[p][4 * h + 3], in.key0, in.key1, c2, c3);
-            }
+        for (int p = 0; p < 2; ++p) item_pair(tf, q0 + b + 64 * p, w[p], in.key0, in.key1, c2, c3);
         store_pair(b, w[0]);
         if (u + 2 < a.lane_blocks && b + 64 < nb) store_pair(b + 64, w[1]);
     }

@@ -350,13 +350,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint64_t b = tt * tb + (uint64_t)u * 2 * blockDim.x + 2 * threadIdx.x;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint64_t q = q0 + b + h;
-                uint32_t *y = &x[u][4 * h];
-                y[0] = (uint32_t)q; y[1] = (uint32_t)(q >> 32);
-                cb_block<CIPHER>(y[0], y[1], y[2], y[3], kk0, kk1, c2, c3);
-            }
+            cb_pair<CIPHER>(q0 + b, x[u], kk0, kk1, c2, c3);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -425,12 +419,7 @@ __global__ void __launch_bounds__(256)
             uint32_t kk0 = a.k0, kk1 = a.k1, c2, c3;
             if (a.keyed) { kk0 = (uint32_t)s; kk1 = (uint32_t)(s >> 32); c2 = a.k0; c3 = a.k1; }
             else { c2 = (uint32_t)s; c3 = (uint32_t)(s >> 32); }
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint64_t q = (pos >> 2) + b + h;
-                x[u][4 * h] = (uint32_t)q; x[u][4 * h + 1] = (uint32_t)(q >> 32);
-                cb_block<CIPHER>(x[u][4 * h], x[u][4 * h + 1], x[u][4 * h + 2], x[u][4 * h + 3], kk0, kk1, c2, c3);
-            }
+            cb_pair<CIPHER>((pos >> 2) + b, x[u], kk0, kk1, c2, c3);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -658,6 +647,15 @@ cudaError_t launch_mrg_generate(const MrgGenArgs &a, srng_out type, const JumpTa
 cudaError_t launch_philox_generate(const PhiloxGenArgs &a, srng_out type, const srng_tune &t,
                                    cudaStream_t stream, const DeviceInfo &dev)
 {
+    if (a.threefry == 2) {
+        switch (type) {
+        case SRNG_OUT_U32: return philox_dispatch<SRNG_OUT_U32, kCipherThreefry64>(a, t, stream, dev);
+        case SRNG_OUT_F32: return philox_dispatch<SRNG_OUT_F32, kCipherThreefry64>(a, t, stream, dev);
+        case SRNG_OUT_EXP_F32: return philox_dispatch<SRNG_OUT_EXP_F32, kCipherThreefry64>(a, t, stream, dev);
+        case SRNG_OUT_NORMAL_F32: return philox_dispatch<SRNG_OUT_NORMAL_F32, kCipherThreefry64>(a, t, stream, dev);
+        default: return philox_dispatch<SRNG_OUT_F64, kCipherThreefry64>(a, t, stream, dev);
+        }
+    }
     if (a.threefry) {
         switch (type) {
         case SRNG_OUT_U32: return philox_dispatch<SRNG_OUT_U32, kCipherThreefry>(a, t, stream, dev);

@@ -101,7 +101,8 @@ struct PhiloxGenArgs {
     uint64_t stream_base; // stream number of the set's slot 0
     uint32_t k0, k1;      // the set's seed words
     int keyed;            // 0: key = (k0, k1), counter words 2-3 = stream; 1: key = stream, words 2-3 = (k0, k1)
-    int threefry;         // 1: Threefry4x32-20, key = (stream, k0, k1), counter words 2-3 = 0
+    int threefry;         // 1: Threefry4x32-20, key = (stream, k0, k1), counter words 2-3 = 0;
+                          // 2: Threefry4x64-20, 64-bit key = (stream, k1:k0, 0, 0)
     const uint64_t *pos;
     uint64_t s_begin, s_count, n;
     void *out;
@@ -214,7 +215,8 @@ struct srng_set {
     uint32_t y0[6];          // MRG32k3a seed state
     uint32_t key0, key1;     // Philox / Threefry seed words (Philox key, or counter words 2-3 when keyed)
     bool keyed;              // key = the stream (keyed Philox, Threefry)
-    bool threefry;           // Threefry4x32-20 (counter-based family, kernels as Philox)
+    bool threefry;           // Threefry (counter-based family, kernels as Philox)
+    bool threefry64;         // the Threefry4x64-20 form
     // TinyMT32: states, parameter sets and their characteristic polynomials
     uint64_t tmt_group_size = 0, tmt_n_groups = 0;
     uint32_t tmt_seed32 = 0;
@@ -240,6 +242,9 @@ struct srng_set {
 
 namespace srng_impl {
 // Generator value of a set's work descriptors: the kernels' choice of block function.
-inline uint32_t inst_gen(const srng_set *s) { return s->threefry ? SRNG_THREEFRY4X32_20 : (uint32_t)s->gen; }
+inline uint32_t inst_gen(const srng_set *s)
+{
+    return s->threefry64 ? SRNG_THREEFRY4X64_20 : s->threefry ? SRNG_THREEFRY4X32_20 : (uint32_t)s->gen;
+}
 }  // namespace srng_impl
 

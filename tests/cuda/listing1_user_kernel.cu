@@ -59,6 +59,24 @@ extern "C" int run_user_threefry(const srng_dev_view *v, uint32_t *out, int per_
     return cudaDeviceSynchronize() == cudaSuccess ? 0 : 2;
 }
 
+// The 64-bit-word Threefry form: one cipher block serves eight draws.
+__global__ void user_threefry64(uint32_t *ddata, srng_dev_view v, int per_thread)
+{
+    const uint64_t s = (uint64_t)blockDim.x * blockIdx.x + threadIdx.x;
+    if (s >= v.n_streams) return;
+    srng::Threefry4x64_20 rng(v, s);
+    for (int k = 0; k < per_thread; ++k) ddata[s * per_thread + k] = rng.next_u32();
+    rng.store(v);
+}
+
+extern "C" int run_user_threefry64(const srng_dev_view *v, uint32_t *out, int per_thread)
+{
+    const unsigned threads = 128, blocks = (unsigned)((v->n_streams + threads - 1) / threads);
+    user_threefry64<<<blocks, threads>>>(out, *v, per_thread);
+    if (cudaGetLastError() != cudaSuccess) return 1;
+    return cudaDeviceSynchronize() == cudaSuccess ? 0 : 2;
+}
+
 extern "C" int run_user_normals(const srng_dev_view *v, float *out, int pairs)
 {
     const unsigned threads = 128, blocks = (unsigned)((v->n_streams + threads - 1) / threads);

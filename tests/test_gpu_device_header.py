@@ -32,6 +32,8 @@ def user_lib(tmp_path_factory):
     lib.run_listing1.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
     lib.run_user_threefry.restype = ctypes.c_int
     lib.run_user_threefry.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
+    lib.run_user_threefry64.restype = ctypes.c_int
+    lib.run_user_threefry64.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
     lib.run_user_normals.restype = ctypes.c_int
     lib.run_user_normals.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
     return lib
@@ -76,18 +78,25 @@ def test_philox_listing1_kernel(user_lib):
         srng.srng_destroy(h)
 
 
-def test_user_kernel_threefry(user_lib):
-    """srng::Threefry4x32_20 in a user kernel: draws equal the oracle's and the
-    stored positions let the library continue the streams."""
+@pytest.mark.parametrize("gen,start", [(srng.SRNG_THREEFRY4X32_20, 3), (srng.SRNG_THREEFRY4X64_20, 3),
+                                       (srng.SRNG_THREEFRY4X64_20, 6)])
+def test_user_kernel_threefry(user_lib, gen, start):
+    """srng::Threefry4x32_20 / Threefry4x64_20 in a user kernel: draws equal
+    the oracle's and the stored positions let the library continue the
+    streams."""
     n_streams, per, seed = 300, 9, 0xC0FFEE
-    h = srng.srng_create(srng.SRNG_THREEFRY4X32_20, seed, n_streams)
+    h = srng.srng_create(gen, seed, n_streams)
     try:
-        srng.srng_jump(h, 0, n_streams, srng.SRNG_JUMP_DRAWS, 3)
+        srng.srng_jump(h, 0, n_streams, srng.SRNG_JUMP_DRAWS, start)
         v = srng.srng_get_device_view(h)
         out = torch.empty(n_streams * per, dtype=torch.int32, device="cuda")
         torch.cuda.synchronize()
-        assert user_lib.run_user_threefry(ctypes.byref(v), out.data_ptr(), per) == 0
-        ref, _ = O.threefry_bulk(seed, 0, [3] * n_streams, 2 * per)
+        if gen == srng.SRNG_THREEFRY4X32_20:
+            assert user_lib.run_user_threefry(ctypes.byref(v), out.data_ptr(), per) == 0
+            ref, _ = O.threefry_bulk(seed, 0, [start] * n_streams, 2 * per)
+        else:
+            assert user_lib.run_user_threefry64(ctypes.byref(v), out.data_ptr(), per) == 0
+            ref, _ = O.threefry64_bulk(seed, 0, [start] * n_streams, 2 * per)
         assert np.array_equal(out.cpu().numpy().view(np.uint32).reshape(n_streams, per), ref[:, :per])
         nxt = torch.empty(n_streams * per, dtype=torch.int32, device="cuda")
         srng.srng_generate(h, 0, n_streams, per, srng.SRNG_OUT_U32, nxt)

@@ -35,7 +35,8 @@ def _counter_ref(gen_fn, stream, p, n, out_type):
     return v[p - p0:p - p0 + n].view(np.uint32)
 
 
-@pytest.mark.parametrize("gen", [srng.SRNG_PHILOX4X32_10, srng.SRNG_PHILOX4X32_10_KEYED, srng.SRNG_THREEFRY4X32_20])
+@pytest.mark.parametrize("gen", [srng.SRNG_PHILOX4X32_10, srng.SRNG_PHILOX4X32_10_KEYED, srng.SRNG_THREEFRY4X32_20,
+                                 srng.SRNG_THREEFRY4X64_20])
 @pytest.mark.parametrize("out_type", [EXP, NORM])
 @pytest.mark.parametrize("S,n,start", [(3, 1000, 0), (4, 1027, 1), (2, 4097, 2), (5, 33, 3), (600, 64, 5),
                                        (1, 70001, 0)])
@@ -50,8 +51,10 @@ def test_counter_based(gen, out_type, S, n, start, tune):
             fn = lambda s, p, m: O.philox_generate(key_of(SEED), s, p, m, O.OUT_F32)
         elif gen == srng.SRNG_PHILOX4X32_10_KEYED:
             fn = lambda s, p, m: O.philox_keyed_generate(SEED, s, p, m, O.OUT_F32)
-        else:
+        elif gen == srng.SRNG_THREEFRY4X32_20:
             fn = lambda s, p, m: O.threefry_generate(SEED, s, p, m, O.OUT_F32)
+        else:
+            fn = lambda s, p, m: O.threefry64_generate(SEED, s, p, m, O.OUT_F32)
         for i in range(S):
             assert np.array_equal(got[i], _counter_ref(fn, i, start, n, out_type)), i
     finally:
