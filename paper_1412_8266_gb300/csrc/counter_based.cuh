@@ -18,6 +18,11 @@ namespace srng_impl {
 
 enum { kCipherPhilox = 0, kCipherThreefry = 1, kCipherThreefry64 = 2 };
 
+// The generation kernels start a stream's run at the cipher block that holds
+// its position: words per block minus one is the largest offset of the first
+// draw inside that block (3 for the 4-word blocks, 7 for Threefry4x64).
+template <int CIPHER> constexpr uint32_t cb_align_mask() { return CIPHER == kCipherThreefry64 ? 7u : 3u; }
+
 // 4-word block q (x0, x1 = q on entry).
 template <int CIPHER>
 __device__ __forceinline__ void cb_block(uint32_t &x0, uint32_t &x1, uint32_t &x2, uint32_t &x3, uint32_t kk0,
@@ -44,12 +49,13 @@ __device__ __forceinline__ void cb_block(uint32_t &x0, uint32_t &x1, uint32_t &x
 }
 
 // 4-word blocks q and q + 1 into w[0..7].  For Threefry4x64 an even q is one
-// 64-bit block (computed once); an odd q straddles two.
-template <int CIPHER>
+// 64-bit block (computed once); an odd q straddles two.  EVEN: the caller
+// guarantees an even q (no code for the straddling case).
+template <int CIPHER, bool EVEN = false>
 __device__ __forceinline__ void cb_pair(uint64_t q, uint32_t *w, uint32_t kk0, uint32_t kk1, uint32_t c2, uint32_t c3)
 {
     if constexpr (CIPHER == kCipherThreefry64) {
-        if ((q & 1) == 0) {
+        if (EVEN || (q & 1) == 0) {
             srng::threefry64::words(q >> 1, (uint64_t)kk1 << 32 | kk0, (uint64_t)c3 << 32 | c2, w);
             return;
         }

@@ -336,8 +336,8 @@ __global__ void __launch_bounds__(256)
             const uint64_t slot = a.s_begin + s_rel;
             const uint64_t p0 = a.pos[slot];
             const uint64_t s = a.stream_base + slot;  // stream number
-            al = (uint32_t)p0 & 3u;
-            q0 = p0 >> 2;
+            al = (uint32_t)p0 & cb_align_mask<CIPHER>();  // q0 even for Threefry4x64: one block per pair
+            q0 = (p0 - al) >> 2;
             nb = (al + a.n + 3) >> 2;
             row = static_cast<T *>(a.out) + s_rel * a.n;
             if (a.keyed) {  // key = the stream, counter words 2-3 = the seed
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint64_t b = tt * tb + (uint64_t)u * 2 * blockDim.x + 2 * threadIdx.x;
-            cb_pair<CIPHER>(q0 + b, x[u], kk0, kk1, c2, c3);
+            cb_pair<CIPHER, true>(q0 + b, x[u], kk0, kk1, c2, c3);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(256)
             const uint64_t b = 2ull * (p - s_rel * pps.d);  // first block of the pair
             const uint64_t slot = a.s_begin + s_rel;
             const uint64_t pos = a.pos[slot];
-            al[u] = (uint32_t)pos & 3u;
+            al[u] = (uint32_t)pos & cb_align_mask<CIPHER>();
             ok[u] = p < total_pairs && b < ((al[u] + a.n + 3) >> 2);
             srel[u] = s_rel;
             bb[u] = b;
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(256)
             uint32_t kk0 = a.k0, kk1 = a.k1, c2, c3;
             if (a.keyed) { kk0 = (uint32_t)s; kk1 = (uint32_t)(s >> 32); c2 = a.k0; c3 = a.k1; }
             else { c2 = (uint32_t)s; c3 = (uint32_t)(s >> 32); }
-            cb_pair<CIPHER>((pos >> 2) + b, x[u], kk0, kk1, c2, c3);
+            cb_pair<CIPHER, true>(((pos - al[u]) >> 2) + b, x[u], kk0, kk1, c2, c3);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -580,7 +580,7 @@ cudaError_t philox_dispatch_u(const PhiloxGenArgs &a, const srng_tune &t, cudaSt
                               const DeviceInfo &dev)
 {
     const uint32_t threads = t.block_threads ? t.block_threads : 256;
-    const uint64_t bps = (a.n + 3) / 4 + 1;  // blocks per stream, any start alignment
+    const uint64_t bps = (a.n + cb_align_mask<CIPHER>() + 3) / 4;  // blocks per stream, any start offset
     const uint64_t tb = 2ull * threads * U;
     const uint64_t tps = (bps + tb - 1) / tb;
     const uint64_t n_tiles = a.s_count * tps;
@@ -601,7 +601,7 @@ cudaError_t philox_dispatch(const PhiloxGenArgs &a, const srng_tune &t, cudaStre
 {
     // Many short streams: the flat kernel (no idle lanes at stream ends), when
     // the pair count fits 32 bits and a stream is shorter than one tile.
-    const uint64_t pps = ((a.n + 3) / 4 + 2) / 2;  // block pairs per stream, any start alignment
+    const uint64_t pps = ((a.n + cb_align_mask<CIPHER>() + 3) / 4 + 1) / 2;  // block pairs per stream, any start offset
     const uint32_t threads = t.block_threads ? t.block_threads : 256;
     const uint64_t tile_pairs = (uint64_t)threads * (t.unroll ? t.unroll : 4);
     if (a.s_count > 1 && pps < tile_pairs && a.s_count * pps < (1ull << 32)) {
