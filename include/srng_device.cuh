@@ -186,13 +186,18 @@ __device__ __forceinline__ double to_f64(uint32_t z)
     }
     /* m = zn 2^21 + ehi < 2^53 as (hi, lo); the exponent field (1021 - lz,
      * plus 1 from m's 2^52 bit) is added into hi; rounding to nearest even:
-     * remainder elo / 2 > 2^30, or = 2^30 with m odd, i.e. elo + (m & 1) > 2^31
-     * (elo is even, no overflow); the carries go through the add chain. */
+     * remainder elo / 2 > 2^30, or = 2^30 with m odd, i.e. elo + (m & 1) > 2^31,
+     * i.e. elo + 2^31 - 1 + (m & 1) carries out of 32 bits (elo is even and at
+     * most 2^32 - 2, so the sum is below 2^33); that carry runs into (hi, lo). */
     const uint32_t hi0 = (zn >> 11) + ((1021u - lz) << 20);
     uint32_t lo, hi;
     asm("add.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %4, 0;" : "=r"(lo), "=r"(hi) : "r"(zn << 21), "r"(ehi), "r"(hi0));
-    const uint32_t up = (elo + (lo & 1u)) > 0x80000000u ? 1u : 0u;
-    asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+r"(lo), "+r"(hi) : "r"(up));
+    asm("{\n\t.reg .u32 t;\n\t"
+        "add.cc.u32 t, %2, %3;\n\t"
+        "addc.cc.u32 %0, %0, 0;\n\t"
+        "addc.u32 %1, %1, 0;\n\t}"
+        : "+r"(lo), "+r"(hi)
+        : "r"(elo), "r"(0x7FFFFFFFu + (lo & 1u)));
     return __hiloint2double((int)hi, (int)lo);
 }
 
