@@ -597,19 +597,22 @@ def run_case(args):
         nbytes, nvals = o.numel() * 4, o.numel()
     elif c.startswith("philox") or c.startswith("threefry"):
         n = (1 << 30) // k
-        t = {"u32": srng.SRNG_OUT_U32, "f32": srng.SRNG_OUT_F32, "normal": srng.SRNG_OUT_NORMAL_F32}[c.split("_")[1]]
+        t = {"u32": srng.SRNG_OUT_U32, "f32": srng.SRNG_OUT_F32, "f64": srng.SRNG_OUT_F64,
+             "normal": srng.SRNG_OUT_NORMAL_F32}[c.split("_")[1]]
         g = (srng.SRNG_PHILOX4X32_10 if c.startswith("philox") else
              srng.SRNG_THREEFRY4X64_20 if c.startswith("threefry64") else srng.SRNG_THREEFRY4X32_20)
         h = srng.srng_create(g, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
-        o = torch.empty(n, dtype=torch.int32 if t == 0 else torch.float32, device=dev)
+        dt = torch.int32 if t == 0 else torch.float64 if t == srng.SRNG_OUT_F64 else torch.float32
+        o = torch.empty(n, dtype=dt, device=dev)
         fn = lambda: srng.srng_generate(h, 0, 1, n, t, o, stream)
-        nbytes, nvals = n * 4, n
+        nbytes, nvals = n * o.element_size(), n
     elif c.startswith("tinymt"):
         S = S_STREAMS // k
         t = srng.SRNG_OUT_U32 if c == "tinymt_u32" else srng.SRNG_OUT_F64
         h = srng.srng_create(srng.SRNG_TINYMT32, SEED, S, srng.SRNG_SPACING_STREAM, stream)
         o = torch.empty(S * N_DRAWS, dtype=torch.int32 if t == 0 else torch.float64, device=dev)
-        fn = lambda: srng.srng_generate(h, 0, S, N_DRAWS, t, o, stream)
+        tune = json.loads(args.case_tune) if args.case_tune else None
+        fn = lambda: srng.srng_generate_tuned(h, 0, S, N_DRAWS, t, o, tune, stream)
         nbytes, nvals = o.numel() * o.element_size(), o.numel()
     elif c.startswith("transform"):
         n = (1 << 30) // k
@@ -641,7 +644,7 @@ def run_case(args):
     return 0
 
 
-CASES = {"mrg_u32", "mrg_f64", "philox_u32", "philox_f32", "philox_normal", "philox_many_u32", "philox_keyed_many_u32",
+CASES = {"mrg_u32", "mrg_f64", "philox_u32", "philox_f32", "philox_f64", "philox_normal", "philox_many_u32", "philox_keyed_many_u32",
          "threefry_u32", "threefry_f32", "threefry64_u32", "threefry64_f32",
          "tinymt_u32", "tinymt_f64",
          "batch_write", "batch_pi", "transform_exponential", "transform_normal"}

@@ -238,14 +238,21 @@ __device__ __forceinline__ void block(uint32_t &c0, uint32_t &c1, uint32_t &c2, 
     }
 }
 
-/* (2w + 1) 2^-33 as a double, exact, built from integers. */
+/* (2w + 1) 2^-33 as a double, exact, built from 32-bit integer operations.
+ * With l = clz(w) (32 for w = 0), v = 2w + 1 has bit length 33 - l, and
+ * x = v 2^l has bit 32 set: its low 32 bits are (w 2^l) 2 + 2^l (the two
+ * terms share no bit).  The double is 2^(-l-1) (x / 2^32): its 52 fraction
+ * bits are those low 32 bits followed by zeros, and its exponent field is
+ * 1022 - l.  Shifts by 32 give 0 (PTX shl), which makes w = 0 come out as
+ * 2^-33. */
 __device__ __forceinline__ double to_f64(uint32_t w)
 {
-    uint64_t v = 2ull * w + 1;                          /* odd, < 2^33 */
-    int b = 64 - __clzll((long long)v);                 /* 1 .. 33     */
-    uint64_t mant = v << (53 - b);                      /* [2^52, 2^53) */
-    uint64_t bits = ((uint64_t)(b + 988) << 52) + mant; /* biased exponent b + 989 */
-    return __longlong_as_double((long long)bits);
+    const uint32_t l = (uint32_t)__clz(w);
+    uint32_t wn, bit;
+    asm("shl.b32 %0, %2, %3;\n\tshl.b32 %1, 1, %3;" : "=r"(wn), "=r"(bit) : "r"(w), "r"(l));
+    const uint32_t x = (wn << 1) + bit;
+    const uint32_t hi = ((1022u - l) << 20) + (x >> 12);
+    return __hiloint2double((int)hi, (int)(x << 20));
 }
 }  // namespace philox
 

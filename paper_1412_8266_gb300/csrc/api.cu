@@ -472,12 +472,14 @@ static srng_status generate_dev(srng_set *s, uint64_t b, uint64_t c, uint64_t n,
         uint64_t chunk = t.chunk;
         if (!chunk) {
             // about four waves of resident threads; a chunk start costs ~2,000
-            // instructions per set bit of its index, so chunks stay >= 4096 draws
+            // instructions per set bit of its index, so chunks stay >= 2048 draws
+            // (measured at 2^18 streams x 4096: two chunks per stream beat one,
+            // whose 2^18 items fill 1.1 waves of this kernel's resident threads)
             const uint64_t resident = (uint64_t)dev.sm_count * (t.blocks_per_sm ? t.blocks_per_sm : 8) * 256;
             const uint64_t want = 4 * resident;
             const uint64_t splits = c >= want ? 1 : (want + c - 1) / c;
             chunk = (n + splits - 1) / splits;
-            chunk = std::max<uint64_t>(4096, ((chunk + 31) / 32) * 32);
+            chunk = std::max<uint64_t>(2048, ((chunk + 31) / 32) * 32);
         }
         if (chunk > n) chunk = n;
         a.chunk = chunk;
