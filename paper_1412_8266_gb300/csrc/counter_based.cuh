@@ -21,7 +21,7 @@ enum { kCipherPhilox = 0, kCipherThreefry = 1, kCipherThreefry64 = 2 };
 // The generation kernels start a stream's run at the cipher block that holds
 // its position: words per block minus one is the largest offset of the first
 // draw inside that block (3 for the 4-word blocks, 7 for Threefry4x64).
-template <int CIPHER> constexpr uint32_t cb_align_mask() { return CIPHER == kCipherThreefry64 ? 7u : 3u; }
+template <int CIPHER> __host__ __device__ constexpr uint32_t cb_align_mask() { return CIPHER == kCipherThreefry64 ? 7u : 3u; }
 
 // 4-word block q (x0, x1 = q on entry).
 template <int CIPHER>
