@@ -30,6 +30,12 @@ __global__ void bazKernel(double *ddata)
     ddata[blockDim.x * blockIdx.x + threadIdx.x] = rng.next();
 }
 
+__global__ void bazKernel64(double *ddata)
+{
+    RNG<double, srng::Threefry4x64_20> rng;
+    ddata[blockDim.x * blockIdx.x + threadIdx.x] = rng.next();
+}
+
 __global__ void quxKernel(float *ddata)
 {
     RNG<float, srng::TinyMT32> rng;   // the block's threads share one parameter set
@@ -64,6 +70,15 @@ extern "C" int run_threefry_form(double *d_data, int block_num, int thread_num, 
     bazKernel<<<block_num, thread_num>>>(d_data);
     const int rc = cudaDeviceSynchronize() == cudaSuccess ? 0 : 2;
     RNG<double, srng::Threefry4x32_20>::release();
+    return rc;
+}
+
+extern "C" int run_threefry64_form(double *d_data, int block_num, int thread_num, uint64_t seed)
+{
+    if (RNG<double, srng::Threefry4x64_20>::init((uint64_t)block_num * thread_num, seed) != SRNG_OK) return 1;
+    bazKernel64<<<block_num, thread_num>>>(d_data);
+    const int rc = cudaDeviceSynchronize() == cudaSuccess ? 0 : 2;
+    RNG<double, srng::Threefry4x64_20>::release();
     return rc;
 }
 

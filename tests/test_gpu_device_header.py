@@ -138,6 +138,8 @@ def paper_form_lib(tmp_path_factory):
     lib.run_paper_listing1.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
     lib.run_philox_form.restype = ctypes.c_int
     lib.run_philox_form.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
+    lib.run_threefry64_form.restype = ctypes.c_int
+    lib.run_threefry64_form.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
     lib.run_tinymt_form.restype = ctypes.c_int
     lib.run_tinymt_form.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
     lib.run_threefry_form.restype = ctypes.c_int
@@ -175,6 +177,16 @@ def test_paper_form_threefry(paper_form_lib):
     torch.cuda.synchronize()
     assert paper_form_lib.run_threefry_form(out.data_ptr(), block_num, thread_num, seed) == 0
     ref, _ = O.threefry_bulk(seed, 0, [0] * n, 1, O.OUT_F64)
+    assert np.array_equal(out.cpu().numpy(), ref.ravel())
+
+
+def test_paper_form_threefry64(paper_form_lib):
+    block_num, thread_num, seed = 7, 64, 0xBEEF
+    n = block_num * thread_num
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    assert paper_form_lib.run_threefry64_form(out.data_ptr(), block_num, thread_num, seed) == 0
+    ref, _ = O.threefry64_bulk(seed, 0, [0] * n, 1, O.OUT_F64)
     assert np.array_equal(out.cpu().numpy(), ref.ravel())
 
 
