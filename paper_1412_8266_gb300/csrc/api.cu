@@ -75,7 +75,10 @@ srng_tune builtin_tune(srng_gen gen, srng_out type)
     // the fused variates carry long single-precision sequences: one block pair
     // per lane keeps the registers (and the resident warps) of the uniforms
     t.unroll = type == SRNG_OUT_EXP_F32 || type == SRNG_OUT_NORMAL_F32 ? 1 : 4;
-    t.vector_store = 1;
+    // MRG32k3a whole-row items: doubles from each lane's registers with 32-byte
+    // stores, 4-byte values through the shared-memory row stage (the measured
+    // best of each at 2^18 streams x 4096)
+    t.vector_store = gen == SRNG_MRG32K3A && type == SRNG_OUT_F64 ? 3 : 1;
     t.lane_blocks = 64;
     return t;
 }
@@ -439,10 +442,12 @@ static srng_status generate_dev(srng_set *s, uint64_t b, uint64_t c, uint64_t n,
         a.n = n;
         uint64_t chunk = t.chunk;
         if (!chunk) {
-            // enough items for about four waves of resident threads
+            // enough items for about four waves of resident threads; when the
+            // streams alone fill three quarters of a wave, one item per stream
+            // (the kernels without jump code)
             const uint64_t resident = (uint64_t)dev.sm_count * t.blocks_per_sm * t.block_threads;
             const uint64_t want = 4 * resident;
-            const uint64_t splits = c >= want ? 1 : (want + c - 1) / c;
+            const uint64_t splits = 4 * c >= 3 * resident || c >= want ? 1 : (want + c - 1) / c;
             chunk = (n + splits - 1) / splits;
             chunk = ((chunk + 31) / 32) * 32;
             if (chunk < 256) chunk = 256;
