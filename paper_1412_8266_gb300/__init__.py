@@ -191,6 +191,39 @@ def _ptr(x) -> int:
     raise TypeError(f"cannot take a pointer of {type(x)!r}")
 
 
+def _out_size(out_type: int) -> int:
+    return 8 if out_type == SRNG_OUT_F64 else 4
+
+
+def _buffer(x, nbytes: int, func: str, where: str = "any") -> int:
+    """Pointer of a caller-owned buffer after checking what the binding can see:
+    a torch tensor or numpy array must be contiguous, large enough for the
+    nbytes the call writes or reads, and on the side the call expects
+    ("cuda", "host" or "any").  Raw integer addresses pass unchecked."""
+    if x is None or isinstance(x, int):
+        return _ptr(x)
+    size = None
+    if hasattr(x, "data_ptr") and hasattr(x, "element_size"):  # torch
+        if not x.is_contiguous():
+            raise ValueError(f"{func}: the buffer must be contiguous")
+        if where == "cuda" and not x.is_cuda:
+            raise ValueError(f"{func}: expects a CUDA buffer, got one on {x.device}")
+        if where == "host" and x.is_cuda:
+            raise ValueError(f"{func}: expects a host buffer, got one on {x.device}")
+        size = x.numel() * x.element_size()
+    elif hasattr(x, "ctypes") and hasattr(x, "nbytes"):  # numpy
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{func}: the buffer must be contiguous")
+        if where == "cuda":
+            raise ValueError(f"{func}: expects a CUDA buffer, got a host array")
+        size = x.nbytes
+    elif isinstance(x, ctypes.Array):
+        size = ctypes.sizeof(x)
+    if size is not None and size < nbytes:
+        raise ValueError(f"{func}: the buffer holds {size} bytes, the call needs {nbytes}")
+    return _ptr(x)
+
+
 def _stream(s) -> int:
     if s is None:
         torch = sys.modules.get("torch")
@@ -302,28 +335,39 @@ def srng_jump(handle: int, stream_begin: int, count: int, unit: int, n: int, str
 
 def srng_generate(handle: int, stream_begin: int, stream_count: int, n_per_stream: int, out_type: int, out,
                   stream=None) -> None:
-    _check(load().srng_generate(handle, stream_begin, stream_count, n_per_stream, out_type, _ptr(out),
-                                _stream(stream)), "srng_generate")
+    p = _buffer(out, stream_count * n_per_stream * _out_size(out_type), "srng_generate", "cuda")
+    _check(load().srng_generate(handle, stream_begin, stream_count, n_per_stream, out_type, p, _stream(stream)),
+           "srng_generate")
 
 
 def srng_generate_tuned(handle: int, stream_begin: int, stream_count: int, n_per_stream: int, out_type: int, out,
                         tune=None, stream=None) -> None:
-    _check(load().srng_generate_tuned(handle, stream_begin, stream_count, n_per_stream, out_type, _ptr(out),
+    p = _buffer(out, stream_count * n_per_stream * _out_size(out_type), "srng_generate_tuned", "cuda")
+    _check(load().srng_generate_tuned(handle, stream_begin, stream_count, n_per_stream, out_type, p,
                                       _tune(tune), _stream(stream)), "srng_generate_tuned")
 
 
 def srng_generate_host(handle: int, stream_begin: int, stream_count: int, n_per_stream: int, out_type: int,
                        out_host, stream=None) -> None:
-    _check(load().srng_generate_host(handle, stream_begin, stream_count, n_per_stream, out_type, _ptr(out_host),
+    p = _buffer(out_host, stream_count * n_per_stream * _out_size(out_type), "srng_generate_host", "host")
+    _check(load().srng_generate_host(handle, stream_begin, stream_count, n_per_stream, out_type, p,
                                      _stream(stream)), "srng_generate_host")
 
 
+def _state_bytes(handle: int) -> int:
+    """Bytes of host state per stream (srng_get_state / srng_set_state)."""
+    gen = srng_describe(handle).gen
+    return 24 if gen == SRNG_MRG32K3A else 16 if gen == SRNG_TINYMT32 else 8
+
+
 def srng_get_state(handle: int, stream_begin: int, count: int, state_host, stream=None) -> None:
-    _check(load().srng_get_state(handle, stream_begin, count, _ptr(state_host), _stream(stream)), "srng_get_state")
+    p = _buffer(state_host, count * _state_bytes(handle), "srng_get_state", "host")
+    _check(load().srng_get_state(handle, stream_begin, count, p, _stream(stream)), "srng_get_state")
 
 
 def srng_set_state(handle: int, stream_begin: int, count: int, state_host, stream=None) -> None:
-    _check(load().srng_set_state(handle, stream_begin, count, _ptr(state_host), _stream(stream)), "srng_set_state")
+    p = _buffer(state_host, count * _state_bytes(handle), "srng_set_state", "host")
+    _check(load().srng_set_state(handle, stream_begin, count, p, _stream(stream)), "srng_set_state")
 
 
 def srng_set_tune(gen: int, out_type: int, tune=None) -> None:
@@ -337,11 +381,15 @@ def srng_get_tune(gen: int, out_type: int) -> Tune:
 
 
 def srng_convert(gen: int, out_type: int, in_dev, n: int, out_dev, stream=None) -> None:
-    _check(load().srng_convert(gen, out_type, _ptr(in_dev), n, _ptr(out_dev), _stream(stream)), "srng_convert")
+    pi = _buffer(in_dev, 4 * n, "srng_convert", "cuda")
+    po = _buffer(out_dev, n * _out_size(out_type), "srng_convert", "cuda")
+    _check(load().srng_convert(gen, out_type, pi, n, po, _stream(stream)), "srng_convert")
 
 
 def srng_transform(dist: int, in_dev, n: int, out_dev, stream=None) -> None:
-    _check(load().srng_transform(dist, _ptr(in_dev), n, _ptr(out_dev), _stream(stream)), "srng_transform")
+    pi = _buffer(in_dev, 4 * n, "srng_transform", "cuda")
+    po = _buffer(out_dev, 4 * n, "srng_transform", "cuda")
+    _check(load().srng_transform(dist, pi, n, po, _stream(stream)), "srng_transform")
 
 
 def srng_seed_expand(seed: int) -> list:
@@ -376,12 +424,19 @@ def _sets(sets):
     return arr, len(sets)
 
 
+def _batch_out_bytes(ia, ni: int, mode: int, out_type: int) -> int:
+    if mode == SRNG_BATCH_FUSED_PI:
+        return 8 * ni
+    return max((ia[i].out_offset + ia[i].length for i in range(ni)), default=0) * _out_size(out_type)
+
+
 def srng_batch_plan_create(sets, inst, mode: int, out_type: int, out_dev, tune=None, stream=None):
-    """Returns (plan handle, keep-alive tuple)."""
+    """Returns the plan handle; the plan keeps out_dev's address."""
     sa, ns = _sets(sets)
     ia, ni = _instances(inst)
+    p = _buffer(out_dev, _batch_out_bytes(ia, ni, mode, out_type), "srng_batch_plan_create", "cuda")
     h = _vp()
-    _check(load().srng_batch_plan_create(ctypes.byref(h), sa, ns, ia, ni, mode, out_type, _ptr(out_dev),
+    _check(load().srng_batch_plan_create(ctypes.byref(h), sa, ns, ia, ni, mode, out_type, p,
                                          _tune(tune), _stream(stream)), "srng_batch_plan_create")
     return h.value
 
@@ -404,7 +459,8 @@ def srng_batch_plan_destroy(plan: int) -> None:
 def srng_batch_run(sets, inst, mode: int, out_type: int, out_dev, stream=None) -> None:
     sa, ns = _sets(sets)
     ia, ni = _instances(inst)
-    _check(load().srng_batch_run(sa, ns, ia, ni, mode, out_type, _ptr(out_dev), _stream(stream)), "srng_batch_run")
+    p = _buffer(out_dev, _batch_out_bytes(ia, ni, mode, out_type), "srng_batch_run", "cuda")
+    _check(load().srng_batch_run(sa, ns, ia, ni, mode, out_type, p, _stream(stream)), "srng_batch_run")
 
 
 def srng_batch_run_static(sets, inst, mode: int, out_type: int, out_dev, stream=None) -> None:
@@ -412,7 +468,8 @@ def srng_batch_run_static(sets, inst, mode: int, out_type: int, out_dev, stream=
     at most 4096 instances and 8 sets; calls that overlap on the GPU race)."""
     sa, ns = _sets(sets)
     ia, ni = _instances(inst)
-    _check(load().srng_batch_run_static(sa, ns, ia, ni, mode, out_type, _ptr(out_dev), _stream(stream)),
+    p = _buffer(out_dev, _batch_out_bytes(ia, ni, mode, out_type), "srng_batch_run_static", "cuda")
+    _check(load().srng_batch_run_static(sa, ns, ia, ni, mode, out_type, p, _stream(stream)),
            "srng_batch_run_static")
 
 

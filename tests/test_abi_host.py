@@ -156,3 +156,28 @@ def test_tinymt_arguments_need_no_gpu(lib):
     with pytest.raises(srng.SrngError) as e:
         srng.srng_create_tinymt([[1, 2, 3]], 0, 1)
     assert e.value.name == "SRNG_ERR_ARG"
+
+
+def test_binding_checks_buffers_before_the_call():
+    """The binding refuses a buffer it can see is wrong (too small, strided, on
+    the wrong side) before any library call; raw addresses pass through."""
+    import torch
+    from paper_1412_8266_gb300 import _buffer
+    a = np.zeros(10, dtype=np.uint32)
+    assert _buffer(a, 40, "f", "host") == a.ctypes.data
+    with pytest.raises(ValueError, match="needs 44"):
+        _buffer(a, 44, "f", "host")
+    with pytest.raises(ValueError, match="contiguous"):
+        _buffer(np.zeros((4, 4), dtype=np.uint32)[:, 1], 4, "f", "host")
+    with pytest.raises(ValueError, match="CUDA buffer"):
+        _buffer(a, 4, "f", "cuda")
+    t = torch.zeros(8, dtype=torch.float64)
+    assert _buffer(t, 64, "f", "host") == t.data_ptr()
+    with pytest.raises(ValueError, match="needs 72"):
+        _buffer(t, 72, "f", "any")
+    with pytest.raises(ValueError, match="CUDA buffer"):
+        _buffer(t, 8, "f", "cuda")
+    with pytest.raises(ValueError, match="contiguous"):
+        _buffer(torch.zeros(4, 4)[:, 0], 4, "f", "host")
+    assert _buffer(12345, 1 << 40, "f", "cuda") == 12345
+    assert _buffer(None, 0, "f", "cuda") == 0
