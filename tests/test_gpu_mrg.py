@@ -159,8 +159,17 @@ def test_full_size_mrg_plain_f64():
         srng.srng_destroy(h)
 
 
-def test_full_size_mrg_bulk_sampled():
-    """Whole workload in the benchmark's launch configuration: seed
+@pytest.mark.parametrize("tune_u, tune_f", [
+    (None, None),  # the built-in shapes
+    # the shapes the benchmark's tuner picks at this size (uint32: staged rows,
+    # one item per stream; FP64: per-lane rows in items of 2048 draws)
+    (dict(block_threads=256, blocks_per_sm=8, chunk=4096, vector_store=1),
+     dict(block_threads=256, blocks_per_sm=8, chunk=2048, vector_store=3)),
+    (dict(block_threads=128, blocks_per_sm=16, chunk=1024, vector_store=3),
+     dict(block_threads=128, blocks_per_sm=16, chunk=4096, vector_store=1)),
+])
+def test_full_size_mrg_bulk_sampled(tune_u, tune_f):
+    """Whole workload in the benchmark's launch configurations: seed
     0x5EED5EED5EED5EED, 2^18 streams x 4096 draws, u32 then f64 after a reset.
     1024 sampled streams are compared in full with the oracle; every f64 value
     equals the conversion of the u32 value at the same place; all u32 values
@@ -171,9 +180,9 @@ def test_full_size_mrg_bulk_sampled():
         starts = get_states(h, 0, S)
         u = torch.empty(S * n, dtype=torch.int32, device="cuda")
         f = torch.empty(S * n, dtype=torch.float64, device="cuda")
-        srng.srng_generate(h, 0, S, n, srng.SRNG_OUT_U32, u)
+        srng.srng_generate_tuned(h, 0, S, n, srng.SRNG_OUT_U32, u, tune_u)
         srng.srng_reset(h)
-        srng.srng_generate(h, 0, S, n, srng.SRNG_OUT_F64, f)
+        srng.srng_generate_tuned(h, 0, S, n, srng.SRNG_OUT_F64, f, tune_f)
         torch.cuda.synchronize()
         rng = np.random.default_rng(11)
         pick = np.unique(np.concatenate([[0, 1, S - 1], rng.integers(0, S, 1021)]))
