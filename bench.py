@@ -162,14 +162,15 @@ def ncu_traffic(kernel_key: str):
 
 
 # --------------------------------------------------------------------- CPU oracle
-def oracle_sample(target_s: float):
+def oracle_sample(target_s: float, threads: int = 0):
     """Time the oracle on a bounded sample of the MRG32k3a bulk workload:
     the first s streams of the same set, 4096 draws each as uint32, then 4096
     more as FP64 (the shape of one step), s chosen so the run takes about
-    target_s seconds.  Returns (Guniforms/s, cores used, description)."""
+    target_s seconds, on `threads` host threads (0: all).  Returns
+    (Guniforms/s, cores used, description)."""
     from oracle import oracle as O
     y0 = O.seed_expand(SEED)
-    threads = O.max_threads()
+    threads = threads or O.max_threads()
 
     def run(s):
         starts = O.mrg_stream_starts(y0, 127, 0, s)
@@ -363,7 +364,9 @@ def run_ours(args):
             line["workloads"] = {"error": repr(ex)}
     if rank == 0:
         v, cores, desc = oracle_sample(args.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": "Guniforms/s", "cores": cores, "kind": "oracle", "sample": desc}
+        v1, _, desc1 = oracle_sample(args.cpu_seconds / 4, threads=1)
+        line["cpu_baseline"] = {"value": v, "unit": "Guniforms/s", "cores": cores, "kind": "oracle", "sample": desc,
+                                "single_core": {"value": v1, "sample": desc1}}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
