@@ -134,8 +134,8 @@ def paper_form_lib(tmp_path_factory):
                     os.path.join(HERE, "cuda", "listing1_paper_form.cu"), "-o", out,
                     "-L", pkg, "-lsrng", "-Xlinker", "-rpath=" + pkg], check=True)
     lib = ctypes.CDLL(out)
-    lib.run_paper_listing1.restype = ctypes.c_int
-    lib.run_paper_listing1.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
+    lib.run_listing1_form.restype = ctypes.c_int
+    lib.run_listing1_form.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
     lib.run_philox_form.restype = ctypes.c_int
     lib.run_philox_form.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
     lib.run_threefry64_form.restype = ctypes.c_int
@@ -148,13 +148,13 @@ def paper_form_lib(tmp_path_factory):
 
 
 def test_paper_listing1_form(paper_form_lib):
-    """RNG<float, MRG32k3a> rng; ddata[blockDim.x * blockIdx.x + threadIdx.x] = rng.next();
+    """RNG<float, Mrg32k3a> built without arguments, one draw per thread,
     launched three times: launch l holds draw l of every thread's stream."""
     block_num, thread_num, launches, seed = 37, 128, 3, 0x5EED
     n = block_num * thread_num
     out = torch.empty(launches * n, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
-    assert paper_form_lib.run_paper_listing1(out.data_ptr(), block_num, thread_num, launches, seed) == 0
+    assert paper_form_lib.run_listing1_form(out.data_ptr(), block_num, thread_num, launches, seed) == 0
     ref, _ = O.mrg_bulk(O.mrg_stream_starts(O.seed_expand(seed), 127, 0, n), launches, O.OUT_F32)
     got = out.cpu().numpy().reshape(launches, n).T
     assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
