@@ -67,6 +67,10 @@ def test_mixed_requests_equal_oracle_and_alone(mrg_set):
         st = srng.srng_server_get_stats(srv)
         assert st.completed == 300 and st.steps > 1 and st.p99_us >= st.p50_us > 0
         assert st.peak_pool_bytes <= 64 << 20
+        srng.srng_server_reset_stats(srv)  # counters restart; the pool holds nothing after the releases
+        st = srng.srng_server_get_stats(srv)
+        assert st.submitted == st.completed == st.steps == st.kernels == st.draws_completed == 0
+        assert st.p50_us == st.p99_us == 0 and st.peak_pool_bytes == 0
     finally:
         srng.srng_server_destroy(srv)
 
