@@ -2,8 +2,9 @@
 """Benchmark of the bulk uniform-generation hot path on GB300.
 
 One step = one pass of the MRG32k3a bulk workload through the C ABI:
-  srng_reset (stream placement by jump-ahead, K1) of 2^18 streams 2^127 apart
-  from the expanded seed 0x5EED5EED5EED5EED, then srng_generate of 4096 draws
+  srng_reset (back to the start states of 2^18 streams 2^127 apart from the
+  expanded seed 0x5EED5EED5EED5EED, placed by jump-ahead (K1) when the set was
+  created and kept beside the working states), then srng_generate of 4096 draws
   per stream as uint32 (2^30 values), then -- after moving on -- another 4096
   draws per stream as FP64 (2^30 values).  Metric: uniforms per second
   (2^31 per step), with every output resident in HBM (12.9 GB per step,
@@ -354,7 +355,7 @@ def run_ours(args):
         "clocks": clk,
         "tune": {"mrg_u32": tune_u, "mrg_f64": tune_f, "tuning_s": t_tune},
         "e2e": e2e,
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": 4 * args.steps,  # per step: generate + state advance, twice (the reset is a device copy)
     }
 
     if rank == 0 and not args.no_extras:

@@ -10,8 +10,8 @@
  *     substreams of 2^76 draws, placed by sequence splitting (Sec. 2.3) with
  *     3x3 jump-ahead matrix powers modulo m1 = 2^32-209 and m2 = 2^32-22853.
  *   - Philox4x32-10 (paper Sec. 4.3): counter-based; the parameter is a key.
- *   - Threefry4x32-20 (named beside Philox in Sec. 4.3): counter-based,
- *     add / rotate / xor rounds, key = (stream, seed).
+ *   - Threefry4x32-20 and Threefry4x64-20 (named beside Philox in Sec. 4.3):
+ *     counter-based, add / rotate / xor rounds, key = (stream, seed).
  *   - TinyMT32 (Sec. 4.2): a parameter set shared by a group of streams,
  *     substreams 2^64 apart by polynomial jump-ahead.
  *   - Exponential and normal variates from the FP32 uniforms (srng_transform,
@@ -247,7 +247,10 @@ srng_status srng_tinymt_check_params(uint32_t mat1, uint32_t mat2, int *max_peri
  * synchronises the device first).  NULL is accepted. */
 srng_status srng_destroy(srng_set *set);
 
-/* Put every stream of the set back at its start (re-runs the placement). */
+/* Put every stream of the set back at its start: MRG32k3a and TinyMT32 sets
+ * copy back the start states placed at creation (a copy of the states is
+ * kept for this: 24 or 16 bytes per stream), counter-based sets zero their
+ * positions. */
 srng_status srng_reset(srng_set *set, void *cuda_stream);
 
 /* Description of a set. */

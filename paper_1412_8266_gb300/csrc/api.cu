@@ -278,6 +278,7 @@ static srng_status tmt_place(srng_set *s, cudaStream_t stream)
 static void free_set(srng_set *s)
 {
     if (s->d_state) cudaFree(s->d_state);
+    if (s->d_start) cudaFree(s->d_start);
     if (s->d_pos) cudaFree(s->d_pos);
     if (s->d_tstate) cudaFree(s->d_tstate);
     if (s->d_tparams) cudaFree(s->d_tparams);
@@ -302,6 +303,8 @@ static srng_status tmt_create(srng_set **out, const uint32_t *params, const std:
     s->key1 = (uint32_t)(seed >> 32);
     memset(s->y0, 0, sizeof s->y0);
     s->d_state = nullptr;
+    s->d_start = nullptr;
+    s->start_bytes = 0;
     s->d_pos = nullptr;
     s->max_pos = 0;
     s->d_stage[0] = s->d_stage[1] = nullptr;
@@ -329,7 +332,9 @@ static srng_status tmt_create(srng_set **out, const uint32_t *params, const std:
     }
     std::vector<uint4> hp(n_params);
     for (uint64_t g = 0; g < n_params; ++g) hp[g] = make_uint4(params[3 * g], params[3 * g + 1], params[3 * g + 2], 0);
-    cudaError_t e = cudaMalloc(&s->d_tstate, 4 * n_streams * sizeof(uint32_t));
+    s->start_bytes = 4 * n_streams * sizeof(uint32_t);
+    cudaError_t e = cudaMalloc(&s->d_tstate, s->start_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_start, s->start_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_tparams, n_params * sizeof(uint4));
     if (e == cudaSuccess) e = cudaMemcpy(s->d_tparams, hp.data(), n_params * sizeof(uint4), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -339,6 +344,11 @@ static srng_status tmt_create(srng_set **out, const uint32_t *params, const std:
     if ((st = tmt_place(s, stream))) {
         free_set(s);
         return st;
+    }
+    if ((e = cudaMemcpyAsync(s->d_start, s->d_tstate, s->start_bytes, cudaMemcpyDeviceToDevice, stream)) !=
+        cudaSuccess) {
+        free_set(s);
+        return cuda_fail(e, "cudaMemcpyAsync(start states)");
     }
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) {
         free_set(s);
@@ -385,6 +395,8 @@ static srng_status create_common(srng_set **out, srng_gen gen, uint64_t seed, co
     s->stream_base = stream_base;
     s->seed = seed;
     s->d_state = nullptr;
+    s->d_start = nullptr;
+    s->start_bytes = 0;
     s->d_pos = nullptr;
     s->max_pos = 0;
     s->d_stage[0] = s->d_stage[1] = nullptr;
@@ -397,10 +409,14 @@ static srng_status create_common(srng_set **out, srng_gen gen, uint64_t seed, co
     if (gen == SRNG_MRG32K3A) {
         if (state) memcpy(s->y0, state, sizeof s->y0);
         else seed_expand(seed, s->y0);
-        e = cudaMalloc(&s->d_state, 6 * n_streams * sizeof(uint32_t));
+        s->start_bytes = 6 * n_streams * sizeof(uint32_t);
+        e = cudaMalloc(&s->d_state, s->start_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_start, s->start_bytes);
         if (e != cudaSuccess) { st = cuda_fail(e, "cudaMalloc(stream states)"); goto bad; }
         st = place_streams(s, 0, n_streams, stream);
         if (st) goto bad;
+        e = cudaMemcpyAsync(s->d_start, s->d_state, s->start_bytes, cudaMemcpyDeviceToDevice, stream);
+        if (e != cudaSuccess) { st = cuda_fail(e, "cudaMemcpyAsync(start states)"); goto bad; }
     } else {
         s->key0 = (uint32_t)seed;
         s->key1 = (uint32_t)(seed >> 32);
@@ -415,6 +431,7 @@ static srng_status create_common(srng_set **out, srng_gen gen, uint64_t seed, co
     return SRNG_OK;
 bad:
     if (s->d_state) cudaFree(s->d_state);
+    if (s->d_start) cudaFree(s->d_start);
     if (s->d_pos) cudaFree(s->d_pos);
     delete s;
     return st;
@@ -659,8 +676,12 @@ srng_status srng_reset(srng_set *set, void *cuda_stream)
     clear_error();
     if (!set) return fail(SRNG_ERR_ARG, "set is NULL");
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-    if (set->gen == SRNG_MRG32K3A) return place_streams(set, 0, set->n_streams, stream);
-    if (set->gen == SRNG_TINYMT32) return tmt_place(set, stream);
+    if (set->gen == SRNG_MRG32K3A || set->gen == SRNG_TINYMT32) {
+        // the start states placed at creation, kept beside the working states
+        SRNG_CUDA_TRY(cudaMemcpyAsync(set->gen == SRNG_MRG32K3A ? set->d_state : set->d_tstate, set->d_start,
+                                      set->start_bytes, cudaMemcpyDeviceToDevice, stream));
+        return SRNG_OK;
+    }
     SRNG_CUDA_TRY(cudaMemsetAsync(set->d_pos, 0, set->n_streams * sizeof(uint64_t), stream));
     set->max_pos = 0;
     return SRNG_OK;

@@ -230,6 +230,8 @@ struct srng_set {
     std::mutex tmt_mu;
     int device;
     uint32_t *d_state;       // MRG32k3a SoA states (6 x n_streams)
+    uint32_t *d_start;       // the placed start states of d_state or d_tstate (srng_reset copies them back)
+    size_t start_bytes;
     uint64_t *d_pos;         // Philox positions
     uint64_t max_pos;        // host-side upper bound on any Philox position
     // staging for srng_generate_host
