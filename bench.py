@@ -125,8 +125,9 @@ class ClockSampler:
 
 def source_hash(parts):
     """Hash of the kernel's source: whole files, or (file, first line, last
-    line) regions -- the generation file and the MRG32k3a device maths of the
-    header, so that additions elsewhere in the header keep the counters valid."""
+    line) regions -- the MRG32k3a generation kernels and their dispatch, and
+    the MRG32k3a device maths of the header, so that edits to the other
+    generators keep the counters valid."""
     h = hashlib.sha256()
     for part in parts:
         if isinstance(part, str):
@@ -142,9 +143,15 @@ def source_hash(parts):
     return h.hexdigest()[:16]
 
 
-KERNEL_SOURCES = ["paper_1412_8266_gb300/csrc/generate.cu",
-                  ("include/srng_device.cuh", "namespace mrg {", "}  // namespace mrg"),
-                  ("include/srng_device.cuh", "__device__ __forceinline__ float to_f32(uint32_t v)", "\n}\n")]
+KERNEL_SOURCES = [
+    # the MRG32k3a generation kernels with their conversions, and their launch-shape dispatch
+    ("paper_1412_8266_gb300/csrc/generate.cu", "template <int GEN, int OUT>\n__device__ __forceinline__",
+     "// ------------------------------------------------------------------ K3"),
+    ("paper_1412_8266_gb300/csrc/generate.cu", "template <int OUT, bool VEC>\ncudaError_t mrg_dispatch_warps",
+     "template <int OUT, int U, int CIPHER>"),
+    # the MRG32k3a device maths and the FP32 conversion of the header
+    ("include/srng_device.cuh", "namespace mrg {", "}  // namespace mrg"),
+    ("include/srng_device.cuh", "__device__ __forceinline__ float to_f32(uint32_t v)", "\n}\n")]
 
 
 def ncu_traffic(kernel_key: str):

@@ -38,13 +38,8 @@ namespace srng_impl {
 
 namespace {
 
-template <int OUT> struct OutT;
-template <> struct OutT<SRNG_OUT_U32> { using T = uint32_t; };
-template <> struct OutT<SRNG_OUT_F32> { using T = float; };
-template <> struct OutT<SRNG_OUT_F64> { using T = double; };
-
 template <int GEN, int OUT>
-__device__ __forceinline__ typename OutT<OUT>::T bconvert(uint32_t v)
+__device__ __forceinline__ typename OutType<OUT>::T bconvert(uint32_t v)
 {
     if constexpr (OUT == SRNG_OUT_U32) return v;
     else if constexpr (OUT == SRNG_OUT_F32) return srng::to_f32(v);
@@ -71,7 +66,7 @@ constexpr int kWarps = 8;
 
 template <int OUT>
 struct Smem {
-    using T = typename OutT<OUT>::T;
+    using T = typename OutType<OUT>::T;
     static constexpr int G = 128 / sizeof(T);
     static constexpr int VPL = 16 / sizeof(T);
     static constexpr int RS = G + VPL;
@@ -96,7 +91,7 @@ template <int OUT>
 __device__ void mrg_item(const BatchArgs &a, const JumpTable &tab, uint32_t ii, uint32_t first_chunk,
                          Smem<OUT> &sm, int warp, int lane)
 {
-    using T = typename OutT<OUT>::T;
+    using T = typename OutType<OUT>::T;
     constexpr int G = Smem<OUT>::G, VPL = Smem<OUT>::VPL, RS = Smem<OUT>::RS;
     constexpr int EPQ = 32 / sizeof(T);
     const BatchInst &in = a.inst[ii];
@@ -206,7 +201,7 @@ __device__ __forceinline__ void item_pair(int cipher, uint64_t q, uint32_t *w, u
 template <int OUT>
 __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int lane)
 {
-    using T = typename OutT<OUT>::T;
+    using T = typename OutType<OUT>::T;
     const BatchInst &in = a.inst[ii];
     const uint64_t p0 = in.pos;
     const uint32_t al = (uint32_t)p0 & 3u;

@@ -28,13 +28,6 @@ namespace srng_impl {
 
 namespace {
 
-template <int OUT> struct OutType;
-template <> struct OutType<SRNG_OUT_U32> { using T = uint32_t; };
-template <> struct OutType<SRNG_OUT_F32> { using T = float; };
-template <> struct OutType<SRNG_OUT_F64> { using T = double; };
-template <> struct OutType<SRNG_OUT_EXP_F32> { using T = float; };
-template <> struct OutType<SRNG_OUT_NORMAL_F32> { using T = float; };
-
 template <int GEN, int OUT>
 __device__ __forceinline__ typename OutType<OUT>::T convert(uint32_t v)
 {

@@ -14,6 +14,14 @@
 
 namespace srng_impl {
 
+// Element type of each output type (the fused variates are FP32).
+template <int OUT> struct OutType;
+template <> struct OutType<SRNG_OUT_U32> { using T = uint32_t; };
+template <> struct OutType<SRNG_OUT_F32> { using T = float; };
+template <> struct OutType<SRNG_OUT_F64> { using T = double; };
+template <> struct OutType<SRNG_OUT_EXP_F32> { using T = float; };
+template <> struct OutType<SRNG_OUT_NORMAL_F32> { using T = float; };
+
 // ------------------------------------------------------------------ errors
 // Record a failure message for srng_last_error() and return the status.
 srng_status fail(srng_status st, const std::string &msg);

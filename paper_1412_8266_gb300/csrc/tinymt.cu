@@ -29,14 +29,7 @@ namespace {
 
 constexpr int kThreads = 256;
 
-template <int OUT> struct TOut;
-template <> struct TOut<SRNG_OUT_U32> { using T = uint32_t; };
-template <> struct TOut<SRNG_OUT_F32> { using T = float; };
-template <> struct TOut<SRNG_OUT_F64> { using T = double; };
-template <> struct TOut<SRNG_OUT_EXP_F32> { using T = float; };
-template <> struct TOut<SRNG_OUT_NORMAL_F32> { using T = float; };
-
-template <int OUT> __device__ __forceinline__ typename TOut<OUT>::T tconv(uint32_t v)
+template <int OUT> __device__ __forceinline__ typename OutType<OUT>::T tconv(uint32_t v)
 {
     if constexpr (OUT == SRNG_OUT_U32) return v;
     else if constexpr (OUT == SRNG_OUT_F32) return srng::to_f32(v);
@@ -83,7 +76,7 @@ __global__ void __launch_bounds__(kThreads)
 template <int OUT>
 __global__ void __launch_bounds__(kThreads) k_tmt_generate(const TmtGenArgs a)
 {
-    using T = typename TOut<OUT>::T;
+    using T = typename OutType<OUT>::T;
     constexpr int EPQ = 32 / sizeof(T);  // values per 32-byte store
     const uint64_t n_items = a.s_count * a.cps;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
