@@ -214,27 +214,59 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
     const uint64_t L = in.length;
     if (a.mode == SRNG_BATCH_FUSED_PI) {
         uint32_t hits = 0;
+        // the four words of 4-word group b (draw index of word 0: k0) and the
+        // next group's word 0 when the pairs straddle (odd start)
+        auto count_group = [&](uint64_t b, const uint32_t *x, auto next_word0) {
+            const int64_t k0 = (int64_t)(b * 4) - al;
+            if ((al & 1) == 0) {
+                // pairs are (word 0, word 1) and (word 2, word 3)
+                if (k0 >= 0 && (uint64_t)k0 + 1 < L) hits += hit_philox(x[0], x[1]);
+                if (k0 + 2 >= 0 && (uint64_t)(k0 + 2) + 1 < L) hits += hit_philox(x[2], x[3]);
+            } else {
+                // odd start: pairs (word 1, word 2) and (word 3, next group's word 0)
+                if (k0 + 1 >= 0 && (uint64_t)(k0 + 1) + 1 < L) hits += hit_philox(x[1], x[2]);
+                if (k0 + 3 >= 0 && (uint64_t)(k0 + 3) + 1 < L) hits += hit_philox(x[3], next_word0());
+            }
+        };
+        if (tf == kCipherThreefry64) {
+            // One Threefry4x64 block holds the 4-word groups 2Q and 2Q + 1: each
+            // lane takes whole blocks and counts the halves inside this item's
+            // groups [b0, b_end), so a block is computed once (once more for the
+            // straddling pair of an odd start at its upper half).
+            const uint64_t b_end = min(b0 + (uint64_t)32 * a.lane_blocks, nb);
+            const uint64_t kk = (uint64_t)in.key1 << 32 | in.key0, sd = (uint64_t)c3 << 32 | c2;
+            for (uint64_t Q = ((q0 + b0) >> 1) + lane; 2 * Q < q0 + b_end; Q += 32) {
+                uint32_t w[8];
+                srng::threefry64::words(Q, kk, sd, w);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint64_t g = 2 * Q + h;  // absolute group
+                    if (g < q0 + b0 || g - q0 >= b_end) continue;
+                    count_group(g - q0, w + 4 * h, [&]() {
+                        if (h == 0) return w[4];
+                        uint32_t v[8];
+                        srng::threefry64::words(Q + 1, kk, sd, v);
+                        return v[0];
+                    });
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) hits += __shfl_down_sync(0xffffffffu, hits, o);
+            if (lane == 0 && hits) atomicAdd(reinterpret_cast<unsigned long long *>(a.out) + ii, (unsigned long long)hits);
+            return;
+        }
         for (uint32_t u = 0; u < a.lane_blocks; ++u) {
             const uint64_t b = b0 + (uint64_t)u * 32 + lane;
             if (b >= nb) break;
             const uint64_t q = q0 + b;
-            uint32_t x0 = (uint32_t)q, x1 = (uint32_t)(q >> 32), x2, x3;
-            item_block(tf, x0, x1, x2, x3, in.key0, in.key1, c2, c3);
-            const int64_t k0 = (int64_t)(b * 4) - al;  // draw index of word 0
-            if ((al & 1) == 0) {
-                // pairs are (word 0, word 1) and (word 2, word 3)
-                if (k0 >= 0 && (uint64_t)k0 + 1 < L) hits += hit_philox(x0, x1);
-                if (k0 + 2 >= 0 && (uint64_t)(k0 + 2) + 1 < L) hits += hit_philox(x2, x3);
-            } else {
-                // odd start: pairs (word 1, word 2) and (word 3, next block's word 0)
-                if (k0 + 1 >= 0 && (uint64_t)(k0 + 1) + 1 < L) hits += hit_philox(x1, x2);
-                if (k0 + 3 >= 0 && (uint64_t)(k0 + 3) + 1 < L) {
-                    const uint64_t qn = q + 1;
-                    uint32_t y0 = (uint32_t)qn, y1 = (uint32_t)(qn >> 32), y2, y3;
-                    item_block(tf, y0, y1, y2, y3, in.key0, in.key1, c2, c3);
-                    hits += hit_philox(x3, y0);
-                }
-            }
+            uint32_t x[4] = {(uint32_t)q, (uint32_t)(q >> 32), 0u, 0u};
+            item_block(tf, x[0], x[1], x[2], x[3], in.key0, in.key1, c2, c3);
+            count_group(b, x, [&]() {
+                const uint64_t qn = q + 1;
+                uint32_t y0 = (uint32_t)qn, y1 = (uint32_t)(qn >> 32), y2, y3;
+                item_block(tf, y0, y1, y2, y3, in.key0, in.key1, c2, c3);
+                return y0;
+            });
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) hits += __shfl_down_sync(0xffffffffu, hits, o);
