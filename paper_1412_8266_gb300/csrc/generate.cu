@@ -442,26 +442,40 @@ template <int DIST> __device__ __forceinline__ float4 variates4(float4 u)
     return v;
 }
 
+constexpr int kTransformU = 2;  // float4 per thread per trip of k_transform (1: slower, 4 without prefetch: slower)
+
 template <int DIST>
 __global__ void __launch_bounds__(256) k_transform(const float *in, uint64_t n, float *out)  // in == out allowed
 {
-    constexpr int U = 4;                      // float4 loads in flight per thread
+    constexpr int U = kTransformU;
     constexpr uint64_t kTile = 256 * U;       // float4 per block per trip, contiguous
     const uint64_t n4 = n / 4;
+    const uint64_t step = (uint64_t)gridDim.x * kTile;
     const float4 *in4 = reinterpret_cast<const float4 *>(in);
     float4 *out4 = reinterpret_cast<float4 *>(out);
-    for (uint64_t base = (uint64_t)blockIdx.x * kTile; base < n4; base += (uint64_t)gridDim.x * kTile) {
-        float4 a[U];
+    // the next trip's loads are issued before this trip's arithmetic (trips
+    // touch disjoint elements, so in == out stays allowed)
+    float4 a[U];
+    uint64_t base = (uint64_t)blockIdx.x * kTile;
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+        const uint64_t i = base + k * 256 + threadIdx.x;
+        if (i < n4) a[k] = in4[i];
+    }
+    for (; base < n4; base += step) {
+        float4 nx[U];
 #pragma unroll
         for (int k = 0; k < U; ++k) {
-            const uint64_t i = base + k * 256 + threadIdx.x;
-            if (i < n4) a[k] = in4[i];
+            const uint64_t i = base + step + k * 256 + threadIdx.x;
+            if (i < n4) nx[k] = in4[i];
         }
 #pragma unroll
         for (int k = 0; k < U; ++k) {
             const uint64_t i = base + k * 256 + threadIdx.x;
             if (i < n4) out4[i] = variates4<DIST>(a[k]);
         }
+#pragma unroll
+        for (int k = 0; k < U; ++k) a[k] = nx[k];
     }
     if (blockIdx.x == 0) {                    // the n mod 4 tail
         const uint64_t t = 4 * n4 + (DIST == SRNG_DIST_EXPONENTIAL ? threadIdx.x : 2 * threadIdx.x);
@@ -675,7 +689,7 @@ cudaError_t launch_transform(int dist, const float *in, uint64_t n, float *out, 
     // normal (more arithmetic to hide); measured on GB300 at 2^30 values
     const uint64_t cap = (uint64_t)dev.sm_count * (dist == SRNG_DIST_NORMAL ? 8 : 4);
     const bool vec = (reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % 16 == 0;
-    uint64_t blocks = vec ? (n / 4 + 1023) / 1024 : (n + 255) / 256;
+    uint64_t blocks = vec ? (n / 4 + 256 * kTransformU - 1) / (256 * kTransformU) : (n + 255) / 256;
     if (blocks > cap) blocks = cap;
     if (blocks == 0) blocks = 1;   // the scalar tail of a short input
     const unsigned g = (unsigned)blocks;
