@@ -191,14 +191,13 @@ __device__ __forceinline__ double to_f64(uint32_t z)
      * most 2^32 - 2, so the sum is below 2^33).  m & 1 = ehi & 1 (zn 2^21 is
      * even), so that carry is known first and enters the sum forming m; as
      * elo is even, elo + (m & 1) = elo | (ehi & 1). */
-    const uint32_t hi0 = (zn >> 11) + ((1021u - lz) << 20);
     uint32_t lo, hi;
     asm("{\n\t.reg .u32 t;\n\t"
         "add.cc.u32 t, %2, 2147483647;\n\t"
         "addc.cc.u32 %0, %3, %4;\n\t"
-        "addc.u32 %1, %5, 0;\n\t}"
+        "addc.u32 %1, %5, %6;\n\t}"
         : "=r"(lo), "=r"(hi)
-        : "r"(elo | (ehi & 1u)), "r"(zn << 21), "r"(ehi), "r"(hi0));
+        : "r"(elo | (ehi & 1u)), "r"(zn << 21), "r"(ehi), "r"(zn >> 11), "r"((1021u - lz) << 20));
     return __hiloint2double((int)hi, (int)lo);
 }
 
