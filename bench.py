@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-extras", action="store_true", help="skip the other workloads")
-    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=4)
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     p.add_argument("--case", choices=sorted(CASES), default=None,
                    help="time one kernel alone on a reduced size (for profiling), print one JSON line")
@@ -317,9 +317,12 @@ def run_ours(args):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
+        each = []
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            e2e_step()
+            t1 = time.perf_counter()
+            e2e_step()  # srng_generate_host synchronises the stream before returning
+            each.append(time.perf_counter() - t1)
         torch.cuda.synchronize()
         e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dev)
         # the host copy must equal the device output of the same step
@@ -332,7 +335,8 @@ def run_ours(args):
         del src, dst
         e2e_gbs = (bytes_u + bytes_f) / e2e_s / 1e9
         e2e = {"value": world * numbers / e2e_s / 1e9, "unit": "Guniforms/s", "h2d_bytes_per_step": 0,
-               "d2h_bytes_per_step": bytes_u + bytes_f, "ms_per_step": e2e_s * 1e3, "matches_device_output": same,
+               "d2h_bytes_per_step": bytes_u + bytes_f, "ms_per_step": e2e_s * 1e3,
+               "ms_each_step": [round(x * 1e3, 2) for x in each], "matches_device_output": same,
                "GB_s": e2e_gbs, "host_link_GB_s": link, "frac_of_host_link": e2e_gbs / link,
                "bound": "host link (device -> pinned host copy measured in this run)"}
         del host_u, host_f
