@@ -177,8 +177,8 @@ int srng_abi_version(void);
  *     words; a block gives eight 32-bit draws, the low then the high half of
  *     each word, draw = 32-bit word position % 8.  Otherwise as Threefry4x32.
  * n_streams: 1 .. 2^40 (MRG32k3a with SRNG_SPACING_STREAM: at most 2^64 by
- * the paper, here limited by device memory: 24 bytes per stream; Philox and
- * Threefry: 8).
+ * the paper, here limited by device memory: 48 bytes per stream, the working
+ * states and the start states srng_reset restores; Philox and Threefry: 8).
  * The set owns its device memory until srng_destroy.  Synchronises
  * cuda_stream before returning (the set is ready to use on any stream). */
 srng_status srng_create(srng_set **out, srng_gen gen, uint64_t seed, uint64_t n_streams,
@@ -327,11 +327,12 @@ srng_status srng_convert(srng_gen gen, srng_out type, const uint32_t *in_dev, ui
  * (the paper's in-kernel constructor + next(), Sec. 5.2).  The pointers stay
  * owned by the set and valid until srng_destroy. */
 typedef struct srng_dev_view {
-    int32_t gen;            /* SRNG_MRG32K3A, SRNG_PHILOX4X32_10 (either layout)
-                             * or SRNG_THREEFRY4X32_20                         */
+    int32_t gen;            /* SRNG_MRG32K3A, SRNG_PHILOX4X32_10 (either layout),
+                             * SRNG_THREEFRY4X32_20, SRNG_THREEFRY4X64_20 or
+                             * SRNG_TINYMT32                                    */
     uint32_t key0, key1;    /* Philox / Threefry: the set's seed words (Philox
-                             * key, or counter words 2-3 when keyed; Threefry
-                             * key words 2-3)                                   */
+                             * key, or counter words 2-3 when keyed; Threefry4x32
+                             * key words 2-3; Threefry4x64 key word 1)          */
     uint32_t flags;         /* bit 0: Philox keyed layout (key = stream)        */
     uint64_t n_streams;
     uint32_t *mrg_state;    /* MRG32k3a, SoA: word j of stream i at

@@ -11,7 +11,7 @@
 // element stores when the output alignment does not allow vectors), so every
 // warp store instruction fills whole 128-byte lines.
 //
-// K3 (Philox4x32-10 and Threefry4x32-20, Sec. 4.3): counter-based, so any
+// K3 (Philox4x32-10, Threefry4x32-20 and Threefry4x64-20, Sec. 4.3): counter-based, so any
 // position is computed directly.  A block of threads covers a contiguous run of Philox blocks of
 // one stream; lane-consecutive blocks are 16 bytes apart in the output, so a
 // warp writes 512 contiguous bytes per store (u32 / f32).
