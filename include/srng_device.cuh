@@ -424,6 +424,13 @@ class Mrg32k3a {
     __device__ __forceinline__ uint32_t next_u32() { return mrg::step(s0, s1, s2, s3, s4, s5); }
     __device__ __forceinline__ float next_f32() { return to_f32(next_u32()); }
     __device__ __forceinline__ double next_f64() { return mrg::to_f64(next_u32()); }
+    /* The next four draws as one vector (x first). */
+    __device__ __forceinline__ uint4 next4()
+    {
+        uint4 r;
+        r.x = next_u32(); r.y = next_u32(); r.z = next_u32(); r.w = next_u32();
+        return r;
+    }
     /* Jump by a precomputed matrix pair (A1^d, A2^d) (srng_jump_matrix). */
     __device__ __forceinline__ void jump(const uint32_t *M18) { mrg::jump(M18, s0, s1, s2, s3, s4, s5); }
     /* Write the current state back (so a later launch continues from here). */
@@ -476,6 +483,13 @@ class Philox4x32_10 {
     }
     __device__ __forceinline__ float next_f32() { return to_f32(next_u32()); }
     __device__ __forceinline__ double next_f64() { return philox::to_f64(next_u32()); }
+    /* The next four draws as one vector (x first). */
+    __device__ __forceinline__ uint4 next4()
+    {
+        uint4 r;
+        r.x = next_u32(); r.y = next_u32(); r.z = next_u32(); r.w = next_u32();
+        return r;
+    }
     __device__ void store(const srng_dev_view &v) const { v.philox_pos[stream_] = pos_; }
     __device__ uint64_t position() const { return pos_; }
 
@@ -521,6 +535,13 @@ class Threefry4x32_20 {
     }
     __device__ __forceinline__ float next_f32() { return to_f32(next_u32()); }
     __device__ __forceinline__ double next_f64() { return philox::to_f64(next_u32()); }
+    /* The next four draws as one vector (x first). */
+    __device__ __forceinline__ uint4 next4()
+    {
+        uint4 r;
+        r.x = next_u32(); r.y = next_u32(); r.z = next_u32(); r.w = next_u32();
+        return r;
+    }
     __device__ void store(const srng_dev_view &v) const { v.philox_pos[stream_] = pos_; }
     __device__ uint64_t position() const { return pos_; }
 
@@ -559,6 +580,13 @@ class Threefry4x64_20 {
     }
     __device__ __forceinline__ float next_f32() { return to_f32(next_u32()); }
     __device__ __forceinline__ double next_f64() { return philox::to_f64(next_u32()); }
+    /* The next four draws as one vector (x first). */
+    __device__ __forceinline__ uint4 next4()
+    {
+        uint4 r;
+        r.x = next_u32(); r.y = next_u32(); r.z = next_u32(); r.w = next_u32();
+        return r;
+    }
     __device__ void store(const srng_dev_view &v) const { v.philox_pos[stream_] = pos_; }
     __device__ uint64_t position() const { return pos_; }
 
@@ -588,6 +616,13 @@ class TinyMT32 {
     }
     __device__ __forceinline__ float next_f32() { return to_f32(next_u32()); }
     __device__ __forceinline__ double next_f64() { return philox::to_f64(next_u32()); }
+    /* The next four draws as one vector (x first). */
+    __device__ __forceinline__ uint4 next4()
+    {
+        uint4 r;
+        r.x = next_u32(); r.y = next_u32(); r.z = next_u32(); r.w = next_u32();
+        return r;
+    }
     __device__ void store(const srng_dev_view &v, uint64_t stream) const
     {
         const uint64_t n = v.n_streams;

@@ -93,3 +93,31 @@ extern "C" int run_listing1(const srng_dev_view *v, void *out, int per_thread)
     if (cudaGetLastError() != cudaSuccess) return 1;
     return cudaDeviceSynchronize() == cudaSuccess ? 0 : 2;
 }
+
+// next4(): four draws per call, `quads` calls per thread, the state stored back.
+template <class Gen>
+__global__ void user_next4(uint4 *ddata, srng_dev_view v, int quads)
+{
+    const uint64_t s = (uint64_t)blockDim.x * blockIdx.x + threadIdx.x;
+    if (s >= v.n_streams) return;
+    Gen rng(v, s);
+    for (int k = 0; k < quads; ++k) ddata[s * quads + k] = rng.next4();
+    if constexpr (std::is_same<Gen, srng::Mrg32k3a>::value || std::is_same<Gen, srng::TinyMT32>::value)
+        rng.store(v, s);
+    else
+        rng.store(v);
+}
+
+extern "C" int run_user_next4(const srng_dev_view *v, uint4 *out, int quads)
+{
+    const unsigned threads = 128, blocks = (unsigned)((v->n_streams + threads - 1) / threads);
+    switch (v->gen) {
+    case SRNG_MRG32K3A: user_next4<srng::Mrg32k3a><<<blocks, threads>>>(out, *v, quads); break;
+    case SRNG_THREEFRY4X32_20: user_next4<srng::Threefry4x32_20><<<blocks, threads>>>(out, *v, quads); break;
+    case SRNG_THREEFRY4X64_20: user_next4<srng::Threefry4x64_20><<<blocks, threads>>>(out, *v, quads); break;
+    case SRNG_TINYMT32: user_next4<srng::TinyMT32><<<blocks, threads>>>(out, *v, quads); break;
+    default: user_next4<srng::Philox4x32_10><<<blocks, threads>>>(out, *v, quads); break;
+    }
+    if (cudaGetLastError() != cudaSuccess) return 1;
+    return cudaDeviceSynchronize() == cudaSuccess ? 0 : 2;
+}

@@ -34,6 +34,8 @@ def user_lib(tmp_path_factory):
     lib.run_user_threefry.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
     lib.run_user_threefry64.restype = ctypes.c_int
     lib.run_user_threefry64.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
+    lib.run_user_next4.restype = ctypes.c_int
+    lib.run_user_next4.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
     lib.run_user_normals.restype = ctypes.c_int
     lib.run_user_normals.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
     return lib
@@ -102,6 +104,49 @@ def test_user_kernel_threefry(user_lib, gen, start):
         srng.srng_generate(h, 0, n_streams, per, srng.SRNG_OUT_U32, nxt)
         torch.cuda.synchronize()
         assert np.array_equal(nxt.cpu().numpy().view(np.uint32).reshape(n_streams, per), ref[:, per:])
+    finally:
+        srng.srng_destroy(h)
+
+
+def _next4_reference(gen, seed, n_streams, start, n):
+    """Oracle draws [start, start + n) of streams 0..n_streams-1 of a set made by srng_create(gen, seed)."""
+    if gen == srng.SRNG_MRG32K3A:
+        st = O.mrg_stream_starts(O.seed_expand(seed), 127, 0, n_streams)
+        return O.mrg_bulk(st, start + n)[0][:, start:]
+    if gen == srng.SRNG_TINYMT32:
+        prm = O.tinymt32_find_params(seed, (n_streams + 255) // 256)
+        st = O.tinymt32_stream_starts(seed & 0xFFFFFFFF, prm, 256, n_streams)
+        return O.tinymt32_bulk(st, prm, 256, start + n)[0][:, start:]
+    if gen == srng.SRNG_PHILOX4X32_10:
+        return O.philox_bulk((seed & 0xFFFFFFFF, seed >> 32), 0, [start] * n_streams, n)[0]
+    if gen == srng.SRNG_THREEFRY4X32_20:
+        return O.threefry_bulk(seed, 0, [start] * n_streams, n)[0]
+    return O.threefry64_bulk(seed, 0, [start] * n_streams, n)[0]
+
+
+@pytest.mark.parametrize("gen", [srng.SRNG_MRG32K3A, srng.SRNG_PHILOX4X32_10, srng.SRNG_THREEFRY4X32_20,
+                                 srng.SRNG_THREEFRY4X64_20, srng.SRNG_TINYMT32])
+def test_user_kernel_next4(user_lib, gen):
+    """next4() of every device class: four draws per call from any start
+    (counter-based streams start 5 draws in, so the vectors straddle blocks),
+    the state stored back so the library continues the streams."""
+    n_streams, quads, seed = 300, 5, 0xC0FFEE
+    start = 0 if gen in (srng.SRNG_MRG32K3A, srng.SRNG_TINYMT32) else 5
+    h = srng.srng_create(gen, seed, n_streams)
+    try:
+        if start:
+            srng.srng_jump(h, 0, n_streams, srng.SRNG_JUMP_DRAWS, start)
+        v = srng.srng_get_device_view(h)
+        out = torch.empty(n_streams * quads * 4, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        assert user_lib.run_user_next4(ctypes.byref(v), out.data_ptr(), quads) == 0
+        ref = _next4_reference(gen, seed, n_streams, start, 4 * quads + 7)
+        got = out.cpu().numpy().view(np.uint32).reshape(n_streams, 4 * quads)
+        assert np.array_equal(got, ref[:, :4 * quads])
+        nxt = torch.empty(n_streams * 7, dtype=torch.int32, device="cuda")
+        srng.srng_generate(h, 0, n_streams, 7, srng.SRNG_OUT_U32, nxt)
+        torch.cuda.synchronize()
+        assert np.array_equal(nxt.cpu().numpy().view(np.uint32).reshape(n_streams, 7), ref[:, 4 * quads:])
     finally:
         srng.srng_destroy(h)
 
