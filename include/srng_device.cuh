@@ -408,6 +408,47 @@ __device__ __forceinline__ float to_f32(uint32_t v)
 
 /* ------------------------------------------------------- generator objects */
 
+namespace mrg {
+/* Jump-ahead by any distance inside a kernel: (A1^n, A2^n) applied by square
+ * and multiply (at most 64 matrix squarings and 64 matrix-vector products per
+ * component), for a stream handle that starts at an offset (Sec. 2.3: the
+ * start of draw n of a stream is A^n y).  The host tables of srng_jump serve
+ * the library's own kernels; this serves user kernels. */
+__device__ __forceinline__ void matmul(const uint32_t *A, const uint32_t *B, uint32_t *C, uint32_t c, uint32_t m)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const uint64_t acc = (uint64_t)reduce64((uint64_t)A[3 * i] * B[j], c, m) +
+                                 (uint64_t)reduce64((uint64_t)A[3 * i + 1] * B[3 + j], c, m) +
+                                 (uint64_t)reduce64((uint64_t)A[3 * i + 2] * B[6 + j], c, m);
+            C[3 * i + j] = reduce64(acc, c, m);
+        }
+}
+
+__device__ inline void skip(uint64_t n, uint32_t &s0, uint32_t &s1, uint32_t &s2, uint32_t &s3, uint32_t &s4,
+                            uint32_t &s5)
+{
+    uint32_t p1[9] = {0, 1, 0, 0, 0, 1, kM1 - kA13, kA12, 0};  /* A1^(2^k) */
+    uint32_t p2[9] = {0, 1, 0, 0, 0, 1, kM2 - kA23, 0, kA21};  /* A2^(2^k) */
+    while (n) {
+        if (n & 1) {
+            matvec(p1, s0, s1, s2, kC1, kM1);
+            matvec(p2, s3, s4, s5, kC2, kM2);
+        }
+        n >>= 1;
+        if (n) {
+            uint32_t t[9];
+            matmul(p1, p1, t, kC1, kM1);
+            for (int k = 0; k < 9; ++k) p1[k] = t[k];
+            matmul(p2, p2, t, kC2, kM2);
+            for (int k = 0; k < 9; ++k) p2[k] = t[k];
+        }
+    }
+}
+}  // namespace mrg (device jump-ahead)
+
 /* MRG32k3a stream handle: the paper's device RNG object with next(). */
 class Mrg32k3a {
   public:
@@ -417,6 +458,11 @@ class Mrg32k3a {
         s0 = v.mrg_state[0 * n + stream]; s1 = v.mrg_state[1 * n + stream];
         s2 = v.mrg_state[2 * n + stream]; s3 = v.mrg_state[3 * n + stream];
         s4 = v.mrg_state[4 * n + stream]; s5 = v.mrg_state[5 * n + stream];
+    }
+    /* Stream `stream` of the view, `offset` draws after its current position. */
+    __device__ Mrg32k3a(const srng_dev_view &v, uint64_t stream, uint64_t offset) : Mrg32k3a(v, stream)
+    {
+        skip(offset);
     }
     __device__ explicit Mrg32k3a(const uint32_t st[6])
         : s0(st[0]), s1(st[1]), s2(st[2]), s3(st[3]), s4(st[4]), s5(st[5]) {}
@@ -433,6 +479,8 @@ class Mrg32k3a {
     }
     /* Jump by a precomputed matrix pair (A1^d, A2^d) (srng_jump_matrix). */
     __device__ __forceinline__ void jump(const uint32_t *M18) { mrg::jump(M18, s0, s1, s2, s3, s4, s5); }
+    /* Move n draws ahead (square and multiply on the device). */
+    __device__ void skip(uint64_t n) { mrg::skip(n, s0, s1, s2, s3, s4, s5); }
     /* Write the current state back (so a later launch continues from here). */
     __device__ void store(const srng_dev_view &v, uint64_t stream) const
     {
@@ -457,6 +505,11 @@ class Philox4x32_10 {
           k1((v.flags & 1u) ? (uint32_t)((v.stream_base + stream) >> 32) : v.key1), stream_(stream),
           ctr_hi_((v.flags & 1u) ? ((uint64_t)v.key1 << 32 | v.key0) : v.stream_base + stream),
           pos_(v.philox_pos[stream]), bq_(~0ull) {}
+    /* Stream `stream` of the view, `offset` draws after its current position. */
+    __device__ Philox4x32_10(const srng_dev_view &v, uint64_t stream, uint64_t offset) : Philox4x32_10(v, stream)
+    {
+        pos_ += offset;
+    }
     __device__ Philox4x32_10(uint32_t key0, uint32_t key1, uint64_t stream, uint64_t position)
         : k0(key0), k1(key1), stream_(stream), ctr_hi_(stream), pos_(position), bq_(~0ull) {}
 
@@ -512,6 +565,10 @@ class Threefry4x32_20 {
     __device__ Threefry4x32_20(const srng_dev_view &v, uint64_t stream)
         : k0((uint32_t)(v.stream_base + stream)), k1((uint32_t)((v.stream_base + stream) >> 32)), k2(v.key0),
           k3(v.key1), stream_(stream), pos_(v.philox_pos[stream]), bq_(~0ull) {}
+    __device__ Threefry4x32_20(const srng_dev_view &v, uint64_t stream, uint64_t offset) : Threefry4x32_20(v, stream)
+    {
+        pos_ += offset;
+    }
     __device__ Threefry4x32_20(uint64_t seed, uint64_t stream, uint64_t position)
         : k0((uint32_t)stream), k1((uint32_t)(stream >> 32)), k2((uint32_t)seed), k3((uint32_t)(seed >> 32)),
           stream_(stream), pos_(position), bq_(~0ull) {}
@@ -560,6 +617,10 @@ class Threefry4x64_20 {
     __device__ Threefry4x64_20(const srng_dev_view &v, uint64_t stream)
         : s_(v.stream_base + stream), seed_((uint64_t)v.key1 << 32 | v.key0), stream_(stream),
           pos_(v.philox_pos[stream]), bq_(~0ull) {}
+    __device__ Threefry4x64_20(const srng_dev_view &v, uint64_t stream, uint64_t offset) : Threefry4x64_20(v, stream)
+    {
+        pos_ += offset;
+    }
     __device__ Threefry4x64_20(uint64_t seed, uint64_t stream, uint64_t position)
         : s_(stream), seed_(seed), stream_(stream), pos_(position), bq_(~0ull) {}
 

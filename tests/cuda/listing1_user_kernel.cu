@@ -121,3 +121,28 @@ extern "C" int run_user_next4(const srng_dev_view *v, uint4 *out, int quads)
     if (cudaGetLastError() != cudaSuccess) return 1;
     return cudaDeviceSynchronize() == cudaSuccess ? 0 : 2;
 }
+
+// Stream handles built at an offset: thread s reads `per` draws starting
+// offsets[s] draws after stream s's position (MRG32k3a by jump-ahead on the
+// device, the counter-based ones by moving the position).
+template <class Gen>
+__global__ void user_offset(uint32_t *ddata, srng_dev_view v, const uint64_t *offsets, int per)
+{
+    const uint64_t s = (uint64_t)blockDim.x * blockIdx.x + threadIdx.x;
+    if (s >= v.n_streams) return;
+    Gen rng(v, s, offsets[s]);
+    for (int k = 0; k < per; ++k) ddata[s * per + k] = rng.next_u32();
+}
+
+extern "C" int run_user_offset(const srng_dev_view *v, uint32_t *out, const uint64_t *offsets, int per)
+{
+    const unsigned threads = 128, blocks = (unsigned)((v->n_streams + threads - 1) / threads);
+    switch (v->gen) {
+    case SRNG_MRG32K3A: user_offset<srng::Mrg32k3a><<<blocks, threads>>>(out, *v, offsets, per); break;
+    case SRNG_THREEFRY4X32_20: user_offset<srng::Threefry4x32_20><<<blocks, threads>>>(out, *v, offsets, per); break;
+    case SRNG_THREEFRY4X64_20: user_offset<srng::Threefry4x64_20><<<blocks, threads>>>(out, *v, offsets, per); break;
+    default: user_offset<srng::Philox4x32_10><<<blocks, threads>>>(out, *v, offsets, per); break;
+    }
+    if (cudaGetLastError() != cudaSuccess) return 1;
+    return cudaDeviceSynchronize() == cudaSuccess ? 0 : 2;
+}

@@ -36,6 +36,8 @@ def user_lib(tmp_path_factory):
     lib.run_user_threefry64.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
     lib.run_user_next4.restype = ctypes.c_int
     lib.run_user_next4.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
+    lib.run_user_offset.restype = ctypes.c_int
+    lib.run_user_offset.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
     lib.run_user_normals.restype = ctypes.c_int
     lib.run_user_normals.argtypes = [ctypes.POINTER(srng.DevView), ctypes.c_void_p, ctypes.c_int]
     return lib
@@ -147,6 +149,39 @@ def test_user_kernel_next4(user_lib, gen):
         srng.srng_generate(h, 0, n_streams, 7, srng.SRNG_OUT_U32, nxt)
         torch.cuda.synchronize()
         assert np.array_equal(nxt.cpu().numpy().view(np.uint32).reshape(n_streams, 7), ref[:, 4 * quads:])
+    finally:
+        srng.srng_destroy(h)
+
+
+@pytest.mark.parametrize("gen", [srng.SRNG_MRG32K3A, srng.SRNG_PHILOX4X32_10, srng.SRNG_THREEFRY4X32_20,
+                                 srng.SRNG_THREEFRY4X64_20])
+def test_user_kernel_at_offset(user_lib, gen):
+    """Stream handles built `offset` draws ahead inside the kernel: MRG32k3a by
+    jump-ahead on the device (square and multiply, offsets up to 2^63 + 5),
+    the counter-based ones by position; draws equal the oracle's."""
+    n_streams, per, seed = 200, 9, 0xC0FFEE
+    rng = np.random.default_rng(4)
+    offs = rng.integers(0, 1 << 40, n_streams, dtype=np.uint64)
+    offs[:6] = [0, 1, 2, 3, 7, 4096]
+    offs[6:9] = [(1 << 63) + 5, (1 << 62) + 1, (1 << 40) + 3]
+    h = srng.srng_create(gen, seed, n_streams)
+    try:
+        v = srng.srng_get_device_view(h)
+        d_offs = torch.from_numpy(offs.view(np.int64)).cuda()
+        out = torch.empty(n_streams * per, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        assert user_lib.run_user_offset(ctypes.byref(v), out.data_ptr(), d_offs.data_ptr(), per) == 0
+        got = out.cpu().numpy().view(np.uint32).reshape(n_streams, per)
+        if gen == srng.SRNG_MRG32K3A:
+            starts = O.mrg_stream_starts(O.seed_expand(seed), 127, 0, n_streams)
+            want = np.stack([O.mrg_generate(O.mrg_jump(starts[i], int(offs[i])), per)[0] for i in range(n_streams)])
+        elif gen == srng.SRNG_PHILOX4X32_10:
+            want = np.stack([O.philox_generate((seed, 0), i, int(offs[i]), per) for i in range(n_streams)])
+        elif gen == srng.SRNG_THREEFRY4X32_20:
+            want = np.stack([O.threefry_generate(seed, i, int(offs[i]), per) for i in range(n_streams)])
+        else:
+            want = np.stack([O.threefry64_generate(seed, i, int(offs[i]), per) for i in range(n_streams)])
+        assert np.array_equal(got, want)
     finally:
         srng.srng_destroy(h)
 
