@@ -6,19 +6,22 @@
 //   - MRG32k3a item: 32 consecutive chunks of `chunk` draws of one instance,
 //     one chunk per lane; a lane reaches its chunk's start by jump-ahead
 //     ((A^chunk)^t applied to the instance's start state, Sec. 2.3);
-//   - Philox / Threefry item: 32 x lane_blocks consecutive counter blocks of
-//     one instance.
+//   - Philox / Threefry item: 32 x lane_blocks consecutive 4-word counter
+//     groups of one instance.
 // A persistent grid (one wave of resident blocks) takes items from a global
 // counter with one atomicAdd per warp and item, so instance lengths spread
-// over five decades still load every SM evenly, and one launch serves them
-// all.  The plan captures {zero counter, zero counts, kernel} in a CUDA graph.
+// over five decades still load every SM evenly.  The plan captures, in one
+// CUDA graph, {zero counters, zero counts} and one persistent kernel per
+// generator family present (MRG32k3a items; counter-based items), the two
+// kernels as independent graph nodes on a forked capture stream.
 //
 // Modes:
 //   WRITE     values go to out[out_offset + k] (staged through shared memory
 //             for MRG32k3a exactly as in the plain kernel);
 //   FUSED_PI  nothing is written: draws stay in registers, pairs
 //             (2k, 2k+1) are tested exactly against the quarter disc and the
-//             per-lane counts are reduced (warp shuffle for Philox items, one
+//             per-lane counts are reduced (warp shuffle for counter-based
+//             items, whose Threefry4x64 lanes take whole 8-word blocks; one
 //             64-bit atomicAdd per lane-chunk for MRG32k3a items).
 #include <cuda_runtime.h>
 #include <stdint.h>
