@@ -6,15 +6,18 @@
 // (Sec. 2.3: chunk t starts at (A^C)^t y), then steps the recurrence in
 // registers.  Because a thread's draws are contiguous in the stream-major
 // output but 32 threads of a warp own 32 different rows, the warp stages a
-// 32-row tile of 128-byte rows in shared memory and writes it back row by row:
-// eight lanes cover one 128-byte row with 16-byte stores (or 32/16 lanes with
-// element stores when the output alignment does not allow vectors), so every
-// warp store instruction fills whole 128-byte lines.
+// 32-row tile of 128-byte rows in shared memory and writes it back row by row
+// (k_mrg_generate_rows: whole 128-byte lines per warp store; k_mrg_generate:
+// 16-byte or element stores for any alignment), or, for whole-row items, each
+// lane writes its own row with 32-byte stores straight from registers
+// (k_mrg_generate_direct: one full sector per lane and store).
 //
-// K3 (Philox4x32-10, Threefry4x32-20 and Threefry4x64-20, Sec. 4.3): counter-based, so any
-// position is computed directly.  A block of threads covers a contiguous run of Philox blocks of
-// one stream; lane-consecutive blocks are 16 bytes apart in the output, so a
-// warp writes 512 contiguous bytes per store (u32 / f32).
+// K3 (Philox4x32-10, Threefry4x32-20 and Threefry4x64-20, Sec. 4.3):
+// counter-based, so any position is computed directly.  A block of threads
+// covers a contiguous run of 4-word groups of one stream (k_philox_generate),
+// or the flat list of (stream, group pair) of many short streams
+// (k_philox_generate_flat); each lane writes its pair of groups -- eight
+// values -- with 32-byte stores, so a warp store covers 1 KiB (u32 / f32).
 //
 // Algorithmic HBM bytes per output value: the value's size (4 or 8); states
 // and positions add 24 and 8 bytes per stream per call.
