@@ -23,17 +23,24 @@ Parity status per function (what pins it is in tests/test_oracle_pins.py):
   threefry4x64_20 / threefry64_* counterparts              parity unpinned: the
       rotation counts and parity constant of Salmon et al. 2011 have no
       independent implementation here; structure pinned (bijection, key and
-      counter use, the block-to-word layout, avalanche)
+      counter use, the block-to-word layout, avalanche, and the round
+      structure by an inverse written in tests/test_oracle_threefry.py that
+      takes every block back to its counter)
   tinymt32_next / charpoly / max_period / jump / find_params  pinned (the
       authors' default parameter set has period 2^127 - 1 under the step,
       checked with sympy; the polynomial annihilates every state bit; jumps
       equal stepping and close the period)
-  tinymt32_init / tinymt32_temper                          parity unpinned (the
-      published TinyMT32 seeding and tempering restated; no implementation
-      here to compare outputs with)
-  seed_expand (SplitMix64)                                structure pinned; the two
-      mixing multipliers are parity unpinned (no implementation in this
-      environment to compare with, and the paper is silent on seeding)
+  tinymt32_init                                            pinned: its mixing
+      function is the MT19937 initialisation's, compared with numpy's MT19937
+      seeding; the seeding rebuilt from that equals the oracle's
+  tinymt32_temper                                          parity unpinned (the
+      published TinyMT32 tempering restated; no implementation here to compare
+      outputs with); structure pinned (the words it reads, the shift of s2,
+      tmat exactly when the sum is odd, inverted to recover s3)
+  splitmix64 / seed_expand (SplitMix64)                    pinned: every output
+      equals pybind11's mix64 (the same finalizer, an independent
+      implementation) of the Weyl sequence, whose step is the odd integer
+      nearest 2^64/phi; the expanded state follows by mod m1 / m2
 """
 from __future__ import annotations
 

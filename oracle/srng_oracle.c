@@ -189,7 +189,8 @@ int oracle_mrg_state_valid(const uint32_t s[6])
 /* random statuses).  Reading: SplitMix64 (Steele, Lea & Flood, OOPSLA      */
 /* 2014) seeded with the 64-bit seed; six successive outputs r0..r5 give    */
 /* x1[i] = r_i mod m1 and x2[i] = r_(i+3) mod m2; a component that comes    */
-/* out all zero is replaced by (12345, 12345, 12345).                       */
+/* out all zero is replaced by (12345, 12345, 12345).  Pinned against an     */
+/* independent implementation of the same output mixer (tests).             */
 /* ---------------------------------------------------------------------- */
 
 uint64_t oracle_splitmix64_next(uint64_t *state)
@@ -609,6 +610,9 @@ void oracle_batch(uint64_t n_inst, const int32_t *gens, const uint32_t *mrg_stat
 /* Jumps use the characteristic polynomial p of the step (degree 127, found */
 /* by Berlekamp-Massey on an output bit of the state): T^J s = r(T) s with  */
 /* r = x^J mod p, evaluated by Horner's rule on states.                     */
+/* Parity: the step is pinned (maximal period of the authors' default set,  */
+/* checked with sympy), the seeding's mixing function against numpy's      */
+/* MT19937 initialisation; the tempering is PARITY UNPINNED (structure only).*/
 /* ---------------------------------------------------------------------- */
 
 #define ORC_TMT_MASK 0x7fffffffU

@@ -59,6 +59,23 @@ MUTATIONS = {
     "tinymt mask": ("uint32_t x = (s[0] & ORC_TMT_MASK) ^ s[1] ^ s[2];", "uint32_t x = s[0] ^ s[1] ^ s[2];"),
     "tinymt horner order": ("    for (int i = 126; i >= 0; --i) {\n        oracle_tinymt32_next(acc",
                             "    for (int i = 0; i <= 126; ++i) {\n        oracle_tinymt32_next(acc"),
+    "splitmix64 shift": ("z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;", "z = (z ^ (z >> 28)) * 0x94D049BB133111EBULL;"),
+    "splitmix64 multiplier": ("0xBF58476D1CE4E5B9ULL", "0xBF58476D1CE4E5B7ULL"),
+    "splitmix64 final shift": ("return z ^ (z >> 31);", "return z ^ (z >> 33);"),
+    "tinymt tempering shift": ("uint32_t t = s[0] + (s[2] >> 8);", "uint32_t t = s[0] + (s[2] >> 9);"),
+    "tinymt tempering word": ("uint32_t t = s[0] + (s[2] >> 8);", "uint32_t t = s[1] + (s[2] >> 8);"),
+    "tinymt seeding shift": ("s[i % 4] ^= i + 1812433253U * (prev ^ (prev >> 30));",
+                             "s[i % 4] ^= i + 1812433253U * (prev ^ (prev >> 27));"),
+    "tinymt seeding multiplier": ("1812433253U", "1812433255U"),
+    "threefry swapped mix pair": ("*b = orc_rotl32(*b, ORC_THREEFRY_ROT[d % 8][pair]) ^ *a;",
+                                  "*b = orc_rotl32(*b, ORC_THREEFRY_ROT[d % 8][1 - pair]) ^ *a;"),
+    "threefry rotation value": ("{10, 26}, {11, 21}", "{10, 25}, {11, 21}"),
+    "threefry parity": ("#define ORC_THREEFRY_PARITY 0x1BD11BDAU", "#define ORC_THREEFRY_PARITY 0x1BD11BDBU"),
+    "threefry injection count": ("            for (int i = 0; i < 4; ++i) v[i] += ks[(j + i) % 5];\n            v[3] += j;",
+                                 "            for (int i = 0; i < 4; ++i) v[i] += ks[(j + i) % 5];\n            v[3] += 0;"),
+    "threefry64 rotation value": ("{14, 16}, {52, 57}", "{14, 17}, {52, 57}"),
+    "threefry64 parity": ("#define ORC_THREEFRY64_PARITY 0x1BD11BDAA9FC1A22ULL",
+                          "#define ORC_THREEFRY64_PARITY 0x1BD11BDAA9FC1A23ULL"),
     "box-muller radius": ("float r = sqrtf(-2.0f * orc_ln(&k, 1.0f - in[2 * j]));",
                           "float r = sqrtf(-2.0f * orc_ln(&k, in[2 * j]));"),
 }
@@ -205,6 +222,33 @@ def _pins_fail(ref):
                 flips[b] += np.unpackbits(O.threefry4x64_20(c2, key).view(np.uint8)) != base
         if np.abs(flips / 32 - 0.5).max() > 0.38:
             return True
+        # SplitMix64 against pybind11's mix64 (when installed)
+        from tests.independent import pybind11_mix64
+        mix = pybind11_mix64()
+        if mix is not None:
+            gamma = 0x9E3779B97F4A7C15
+            for seed in (0, 0x5EED5EED5EED5EED, 2**64 - 1):
+                if O.splitmix64(seed, 4) != [mix((seed + (k + 1) * gamma) % 2**64) for k in range(4)]:
+                    return True
+        # Threefry: the inverse rounds take output blocks back to their counters
+        from tests.test_oracle_threefry import _threefry_inverse
+        rr = np.random.default_rng(3)
+        for bits, f in ((32, O.threefry4x32_20), (64, O.threefry4x64_20)):
+            for _ in range(8):
+                ctr = [int(x) for x in rr.integers(0, 2**31, 4)]
+                key = [int(x) for x in rr.integers(0, 2**31, 4)]
+                if _threefry_inverse(f(ctr, key), key, bits) != ctr:
+                    return True
+        # TinyMT32: seeding through numpy's MT19937 mixer; tempering structure
+        from tests.test_oracle_tinymt import _seed_from_mt19937_mixer
+        dflt = (0x8F7011EE, 0xFC78FF1F, 0x3793FDFF)
+        for seed in (1, 12345, 0xFFFFFFFF):
+            if not np.array_equal(O.tinymt32_init(seed, dflt), _seed_from_mt19937_mixer(seed, dflt)):
+                return True
+        for st in ([5, 6, 7 << 9, 8], [0xFFFFFFFF, 3, 0x12345678, 0x9ABCDEF0]):
+            t = (st[0] + (st[2] >> 8)) & 0xFFFFFFFF
+            if O.tinymt32_temper(st, dflt[2]) != st[3] ^ t ^ (dflt[2] if t & 1 else 0):
+                return True
         # TinyMT32: the authors' default parameter set has period 2^127 - 1
         # under the step; jumps equal stepping
         if not O.tinymt32_max_period(0x8F7011EE, 0xFC78FF1F):

@@ -342,7 +342,7 @@ def test_pi_counts_match_brute_force_and_pi():
 def test_seed_expansion_structure():
     """SplitMix64 steps its state by the odd integer nearest 2^64/phi, and
     the expanded state obeys the range invariant (0 <= x < m, no all-zero
-    component).  The two mixing multipliers themselves are parity unpinned."""
+    component).  The mixer itself is pinned by the next test."""
     st = (ctypes.c_uint64 * 1)(0)
     lib = O._load()
     lib.oracle_splitmix64_next(ctypes.cast(st, ctypes.POINTER(ctypes.c_uint64)))
@@ -358,6 +358,34 @@ def test_seed_expansion_structure():
         r = O.splitmix64(seed, 6)
         assert [int(x) for x in s[:3]] == [x % M1 for x in r[:3]]
         assert [int(x) for x in s[3:]] == [x % M2 for x in r[3:]]
+
+
+def test_splitmix64_equals_an_independent_implementation():
+    """Seed expansion (reading of Sec. 2.3, SplitMix64): output k of the
+    oracle's SplitMix64 from seed x is mix64(x + (k + 1) gamma) with
+    pybind11's own mix64 (the same finalizer, an independent implementation
+    run as a library), for edge and random seeds; and the expanded MRG32k3a
+    start state of every seed follows from those outputs reduced mod m1 / m2,
+    so the bulk workload's start state is pinned end to end."""
+    from tests.independent import pybind11_mix64
+    mix = pybind11_mix64()
+    if mix is None:
+        pytest.skip("pybind11 headers (or g++ / Python.h) not available")
+    g = sympy.floor(sympy.Integer(2**64) * 2 / (1 + sympy.sqrt(5)))
+    gamma = int(g) | 1  # the odd integer nearest 2^64 / phi (pinned above)
+    rng = random.Random(20141226)
+    seeds = [0, 1, 2**63, 2**64 - 1, 0xC0FFEE, 0x5EED5EED5EED5EED] + [rng.getrandbits(64) for _ in range(200)]
+    for seed in seeds:
+        want = [mix((seed + (k + 1) * gamma) % 2**64) for k in range(8)]
+        assert O.splitmix64(seed, 8) == want, hex(seed)
+        s = O.seed_expand(seed)
+        w3 = [x % M1 for x in want[:3]]
+        w3 += [x % M2 for x in want[3:6]]
+        if w3[:3] == [0, 0, 0]:
+            w3[:3] = [12345] * 3
+        if w3[3:] == [0, 0, 0]:
+            w3[3:] = [12345] * 3
+        assert [int(x) for x in s] == w3, hex(seed)
 
 
 # ------------------------------------------------------------------ statistics

@@ -1,14 +1,68 @@
-"""Structure pins of the oracle's Threefry4x32-20 (Sec. 4.3 names Threefry
-beside Philox).  Its rotation counts and key-schedule parity constant come
-from Salmon et al. 2011 and no independent implementation is available to
-compare with, so their values are parity unpinned; what is pinned here holds
-for the construction whatever the constants: the stream layout, diffusion of
-every counter and key bit into every output bit, uniform bytes, and distinct
-blocks for distinct counters (the block function is a permutation)."""
+"""Structure pins of the oracle's Threefry4x32-20 and Threefry4x64-20 (Sec. 4.3
+names Threefry beside Philox).  Their rotation counts and key-schedule parity
+constants come from Salmon et al. 2011 and no independent implementation is
+available to compare with, so their values are parity unpinned; what is
+pinned here holds for the construction whatever the constants: the stream
+layout, diffusion of every counter and key bit into every output bit, uniform
+bytes, distinct blocks for distinct counters (the block function is a
+permutation), and -- the round structure -- an inverse written here from the
+definition (undo the key injection, the word permutation and each MIX, round
+by round, from the last) that takes every output block back to its counter,
+which fails for a wrong rotation, a swapped MIX pair, a missing injection
+count or a wrong parity constant in either the oracle or this inverse."""
+import random
+
 import numpy as np
 import pytest
 
 from oracle import oracle as O
+
+# Rotation pairs and parity constants of the two Threefry forms (Salmon et al.
+# 2011; the 64-bit ones are Threefish-256's), written out again for the inverse.
+R32 = [(10, 26), (11, 21), (13, 27), (23, 5), (6, 20), (17, 11), (25, 10), (18, 20)]
+R64 = [(14, 16), (52, 57), (23, 40), (5, 37), (25, 33), (46, 12), (58, 22), (32, 32)]
+PARITY = {32: 0x1BD11BDA, 64: 0x1BD11BDAA9FC1A22}
+
+
+def _threefry_inverse(out, key, bits):
+    """Counter of the Threefry-4xbits-20 block `out` under `key`, by running the
+    twenty rounds backwards: subtract the injected subkey (and its count), undo
+    the (0, 3, 2, 1) permutation, then each MIX (b = rotr(b ^ a), a -= b)."""
+    mask = (1 << bits) - 1
+    rot = R32 if bits == 32 else R64
+    ks = [int(k) for k in key]
+    par = PARITY[bits]
+    for k in ks:
+        par ^= k
+    ks.append(par)
+    v = [int(x) for x in out]
+    for d in range(19, -1, -1):
+        if d % 4 == 3:
+            j = (d + 1) // 4
+            v = [(v[i] - ks[(j + i) % 5]) & mask for i in range(4)]
+            v[3] = (v[3] - j) & mask
+        v[1], v[3] = v[3], v[1]
+        for pair in (0, 1):
+            a, b = v[2 * pair], v[2 * pair + 1]
+            r = rot[d % 8][pair]
+            b ^= a
+            b = ((b >> r) | (b << (bits - r))) & mask
+            a = (a - b) & mask
+            v[2 * pair], v[2 * pair + 1] = a, b
+    return [(v[i] - ks[i]) & mask for i in range(4)]
+
+
+@pytest.mark.parametrize("bits", [32, 64])
+def test_inverse_rounds_recover_the_counter(bits):
+    rng = random.Random(bits)
+    f = O.threefry4x32_20 if bits == 32 else O.threefry4x64_20
+    for t in range(300):
+        ctr = [rng.getrandbits(bits) for _ in range(4)]
+        key = [rng.getrandbits(bits) for _ in range(4)]
+        if t < 4:  # edge blocks: zero and all-ones counters and keys
+            ctr = [0 if t % 2 == 0 else (1 << bits) - 1] * 4
+            key = [0 if t < 2 else (1 << bits) - 1] * 4
+        assert _threefry_inverse(f(ctr, key), key, bits) == ctr
 
 
 def test_word_layout():

@@ -10,13 +10,22 @@ the threads of a block, sequence splitting between the threads).
 - Jumps equal brute-force stepping, compose additively, and T^(2^127 - 1)
   is the identity.
 - Parameter search: every set found has period 2^127 - 1 (sympy).
-The seeding procedure and the tempering are the published TinyMT32 ones,
-restated; no independent implementation is available to compare their
-outputs with, so they are parity unpinned beyond the properties below."""
+- Seeding: its mixing function x -> 1812433253 (x ^ (x >> 30)) is the MT19937
+  initialisation's, taken here from numpy's MT19937 (an independent
+  implementation run as a library); the seeding rebuilt from it (seven
+  xor-mixing passes over (seed, mat1, mat2, tmat), the all-zero guard, eight
+  steps) equals the oracle's for many seeds and parameter sets.
+- Tempering: structure only -- it is a function of (s0, s2, s3) that does not
+  read s1, reduces to s3 when s0 = s2 = 0 and tmat = 0, adds s2 >> 8 to s0
+  and xors tmat exactly when that sum is odd; inverted here to recover s3.
+  Its shift and the published form are restated from the publication, with
+  no implementation here to compare outputs with, so the tempering stays
+  parity unpinned beyond these properties."""
 import numpy as np
 import pytest
 
 from oracle import oracle as O
+from tests.independent import mt19937_init_mix
 
 DEFAULT = (0x8F7011EE, 0xFC78FF1F, 0x3793FDFF)
 
@@ -135,3 +144,49 @@ def test_output_bytes_uniform_and_streams_distinct():
     assert ((counts - e) ** 2 / e).sum() < 400
     rows = {bytes(r[:64].tobytes()) for r in out}
     assert len(rows) == 4
+
+
+def _seed_from_mt19937_mixer(seed32, prm):
+    """TinyMT32 seeding with its multiply-xorshift taken from numpy's MT19937."""
+    s = [seed32 & 0xFFFFFFFF, int(prm[0]), int(prm[1]), int(prm[2])]
+    for i in range(1, 8):
+        s[i % 4] ^= (i + mt19937_init_mix(s[(i - 1) % 4])) & 0xFFFFFFFF
+    if (s[0] & 0x7FFFFFFF) == 0 and s[1] == s[2] == s[3] == 0:
+        s = [ord("T"), ord("I"), ord("N"), ord("Y")]
+    st = np.array(s, dtype=np.uint32)
+    for _ in range(8):
+        st = O.tinymt32_next(st, int(prm[0]), int(prm[1]))
+    return st
+
+
+def test_seeding_uses_the_mt19937_initialisation_mixer():
+    rng = np.random.default_rng(42)
+    sets = [DEFAULT] + [tuple(int(x) for x in r) for r in O.tinymt32_find_params(0x5EED, 3)]
+    seeds = [0, 1, 12345, 0xFFFFFFFF, 0x80000000] + [int(x) for x in rng.integers(0, 2**32, 40)]
+    for prm in sets:
+        for seed in seeds:
+            assert np.array_equal(O.tinymt32_init(seed, prm), _seed_from_mt19937_mixer(seed, prm)), (prm, seed)
+
+
+def test_tempering_structure_and_inverse():
+    rng = np.random.default_rng(7)
+    tmat = DEFAULT[2]
+    for _ in range(2000):
+        s = [int(x) for x in rng.integers(0, 2**32, 4)]
+        v = O.tinymt32_temper(s, tmat)
+        # s1 is not read
+        s_other = list(s)
+        s_other[1] ^= 0xDEADBEEF
+        assert O.tinymt32_temper(s_other, tmat) == v
+        # recover s3 from the output: t = s0 + (s2 >> 8); v = s3 ^ t ^ (tmat if t odd)
+        t = (s[0] + (s[2] >> 8)) & 0xFFFFFFFF
+        assert v ^ t ^ (tmat if t & 1 else 0) == s[3]
+        # tmat enters exactly when t is odd
+        assert (O.tinymt32_temper(s, 0) ^ v) == (tmat if t & 1 else 0)
+    for s3 in (0, 1, 0x12345678, 0xFFFFFFFF):
+        assert O.tinymt32_temper([0, 77, 0, s3], 0) == s3
+    # the shift of s2: bit k of s2 reaches bit k - 8 of t
+    for k in range(8, 32):
+        assert O.tinymt32_temper([0, 0, 1 << k, 0], 0) == 1 << (k - 8)
+    for k in range(8):
+        assert O.tinymt32_temper([0, 0, 1 << k, 0], 0) == 0
