@@ -12,7 +12,13 @@ One step = one pass of the MRG32k3a bulk workload through the C ABI:
 
 Other workloads (MRG32k3a plain 64 x 2^16 FP64, Philox4x32-10 bulk 2^30
 words, the 10^4-instance batched launch with its fused Monte Carlo consumer
-and the serving loop) are reported under "workloads" in the same JSON line.
+and the serving loop, at the offered rate and compressed 2x, 5x and 10x) are
+summarised under "summary" in the same JSON line, with fractions of both the
+measured copy peak and a write-only fill measured in the same run; "parity"
+holds the oracle comparisons of every configuration's outputs (sampled rows,
+runs, instances) and "cpu_baseline.per_config" the oracle's rate on each.
+The full record (tunes, medians, the other generators) goes to
+gpurun_out/bench_details.json when that folder exists.
 
 --impl reference times the CPU oracle (the plain definition, OpenMP over
 streams) on the host cores on a bounded sample of the same workload.
@@ -170,6 +176,14 @@ def ncu_traffic(kernel_key: str):
 
 
 # --------------------------------------------------------------------- CPU oracle
+def host_threads() -> int:
+    """Host cores this process may run on (the oracle's thread count)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def oracle_sample(target_s: float, threads: int = 0):
     """Time the oracle on a bounded sample of the MRG32k3a bulk workload:
     the first s streams of the same set, 4096 draws each as uint32, then 4096
@@ -178,7 +192,7 @@ def oracle_sample(target_s: float, threads: int = 0):
     (Guniforms/s, cores used, description)."""
     from oracle import oracle as O
     y0 = O.seed_expand(SEED)
-    threads = threads or O.max_threads()
+    threads = threads or host_threads()
 
     def run(s):
         starts = O.mrg_stream_starts(y0, 127, 0, s)
@@ -341,10 +355,18 @@ def run_ours(args):
                "bound": "host link (device -> pinned host copy measured in this run)"}
         del host_u, host_f
 
+    # parity of the timed step's outputs: sampled streams (rows) of both outputs
+    # against the oracle, from the seed alone
+    par_c2 = parity_c2(out_u, out_f, S_STREAMS, base) if rank == 0 else {}
     srng.srng_destroy(h)
     del out_u, out_f
     torch.cuda.empty_cache()
 
+    wfill = write_only_peak(torch, dev, stream)
+    c2 = {"ms_u32": ms_u, "ms_f64": ms_f, "Guniforms_s": value / world,
+          "frac_copy": {"u32": bytes_u / ms_u / 1e6 / peak, "f64": bytes_f / ms_f / 1e6 / peak},
+          "frac_write_fill": {"u32": bytes_u / ms_u / 1e6 / wfill["GB_s"], "f64": bytes_f / ms_f / 1e6 / wfill["GB_s"]},
+          "parity": par_c2}
     line = {
         "metric": "Guniforms/s (MRG32k3a bulk, uint32 + FP64, bit-exact)", "value": value, "unit": "Guniforms/s",
         "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
@@ -358,32 +380,84 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "traffic": ncu_traffic(dom), "algorithmic_bytes_per_launch": dom_bytes,
-                     "ms_per_launch": dom_ms},
-        "kernels": {"mrg_u32": {"ms": ms_u, "GB_s": bytes_u / (ms_u / 1e3) / 1e9,
-                                "Guniforms_s": S_STREAMS * N_DRAWS / (ms_u / 1e3) / 1e9},
-                    "mrg_f64": {"ms": ms_f, "GB_s": bytes_f / (ms_f / 1e3) / 1e9,
-                                "Guniforms_s": S_STREAMS * N_DRAWS / (ms_f / 1e3) / 1e9}},
+                     "ms_per_launch": dom_ms, "write_fill_GB_s": wfill["GB_s"],
+                     "frac_of_write_fill": achieved / wfill["GB_s"]},
         "clocks": clk,
-        "tune": {"mrg_u32": tune_u, "mrg_f64": tune_f, "tuning_s": t_tune},
         "e2e": e2e,
         "gpu_launches": 4 * args.steps,  # per step: generate + state advance, twice (the reset is a device copy)
+        "parity": {"C2": par_c2},
     }
-
-    if rank == 0 and not args.no_extras:
-        try:
-            line["workloads"] = extras(torch, srng, dev, stream, peak)
-        except Exception as ex:  # report, do not hide
-            line["workloads"] = {"error": repr(ex)}
+    details = {"kernels": {"mrg_u32": {"ms": ms_u}, "mrg_f64": {"ms": ms_f}},
+               "tune": {"mrg_u32": tune_u, "mrg_f64": tune_f, "tuning_s": t_tune}, "write_only_fill": wfill}
+    summary = {"C2": c2}
     if rank == 0:
+        cpu = {}
         v, cores, desc = oracle_sample(args.cpu_seconds)
         v1, _, desc1 = oracle_sample(args.cpu_seconds / 4, threads=1)
+        if not args.no_extras:
+            try:
+                summ, det, par, cpu = extras(torch, srng, dev, stream, peak, wfill["GB_s"], args.cpu_seconds)
+                summary.update(summ)
+                details["workloads"] = det
+                line["parity"].update(par)
+            except Exception as ex:  # report, do not hide
+                summary["error"] = repr(ex)
         line["cpu_baseline"] = {"value": v, "unit": "Guniforms/s", "cores": cores, "kind": "oracle", "sample": desc,
-                                "single_core": {"value": v1, "sample": desc1}}
-        print(json.dumps(line), flush=True)
+                                "single_core": {"value": v1, "sample": desc1}, "per_config": cpu}
+        line["parity"]["mismatches"] = sum(int(p.get("mismatches", 0)) for p in line["parity"].values()
+                                           if isinstance(p, dict))
+        line["summary"] = summary
+        write_details(details)
+        print(json.dumps(_rounded(line), separators=(",", ":")), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def _rounded(x, nd=4):
+    """Floats to nd significant digits, so the one JSON line stays short."""
+    if isinstance(x, float):
+        return float(f"{x:.{nd}g}")
+    if isinstance(x, dict):
+        return {k: _rounded(v, nd) for k, v in x.items()}
+    if isinstance(x, list):
+        return [_rounded(v, nd) for v in x]
+    return x
+
+
+def write_details(details):
+    """The long per-workload record (tunes, every timing) goes to a file beside
+    the run, not into the one JSON line: gpurun_out/ when that folder exists,
+    else $SRNG_BENCH_DETAILS, else nowhere."""
+    path = os.environ.get("SRNG_BENCH_DETAILS")
+    if not path and os.path.isdir(os.path.join(ROOT, "gpurun_out")):
+        path = os.path.join(ROOT, "gpurun_out", "bench_details.json")
+    if path:
+        with open(path, "w") as f:
+            json.dump(details, f, indent=1)
+
+
+def parity_c2(out_u, out_f, n_streams, base, rows=48):
+    """Sampled rows of the bulk step's outputs against the oracle: stream s's
+    first 4096 draws as uint32, then its next 4096 as FP64."""
+    import numpy as np
+    from oracle import oracle as O
+    if not n_streams:
+        return {"rows": 0}
+    rng = np.random.default_rng(1412)
+    pick = sorted(set([0, n_streams - 1] + rng.integers(0, n_streams, rows - 2).tolist()))
+    y0 = O.seed_expand(SEED)
+    bad = 0
+    gu = out_u.view(-1, N_DRAWS)
+    gf = out_f.view(-1, N_DRAWS)
+    for s in pick:
+        st = O.mrg_stream_starts(y0, 127, base + s, 1)[0]
+        ru, st = O.mrg_generate(st, N_DRAWS, O.OUT_U32)
+        rf, _ = O.mrg_generate(st, N_DRAWS, O.OUT_F64)
+        bad += int(np.count_nonzero(gu[s].cpu().numpy().view(np.uint32) != ru))
+        bad += int(np.count_nonzero(gf[s].cpu().numpy().view(np.uint64) != rf.view(np.uint64)))
+    return {"rows": len(pick), "values": 2 * len(pick) * N_DRAWS, "mismatches": bad}
 
 
 def _time(torch, stream, fn, reps=5, warm=2):
@@ -412,36 +486,90 @@ def write_only_peak(torch, dev, stream):
     return {"GB_s": (8 << 30) / best / 1e6, "ms_best": best, "how": "torch zero_ of 8 GiB, best of 5"}
 
 
-def extras(torch, srng, dev, stream, peak):
+def _threaded(fn, jobs, threads):
+    """Run fn over jobs on host threads (the oracle's C calls release the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        return list(ex.map(fn, jobs))
+
+
+def _fracs(nbytes, ms, peak, wfill):
+    gbs = nbytes / ms / 1e6
+    return {"GB_s": gbs, "frac_copy": gbs / peak, "frac_write_fill": gbs / wfill}
+
+
+def extras(torch, srng, dev, stream, peak, wfill, cpu_seconds):
+    """The other workloads.  Returns (summary, details, parity, cpu): a short
+    per-configuration summary for the JSON line, the full record for the
+    details file, the oracle comparisons, and the oracle's timings on each
+    configuration (a bounded sample, on all host threads)."""
     import numpy as np
+    from oracle import oracle as O
+    from paper_1412_8266_gb300 import autotune
     from paper_1412_8266_gb300 import workload as W
-    res = {"write_only_fill": write_only_peak(torch, dev, stream)}
-    # MRG32k3a plain: 64 streams x 2^16 FP64
+    threads = host_threads()
+    summ, det, par, cpu = {}, {}, {}, {}
+
+    # ---- C1: MRG32k3a plain, 64 streams x 2^16 FP64 (all-12345 state, 2^127 apart)
     h = srng.srng_create_from_state([12345] * 6, 64, srng.SRNG_SPACING_STREAM, stream)
     o = torch.empty(64 << 16, dtype=torch.float64, device=dev)
-    best, med = _time(torch, stream, lambda: (srng.srng_reset(h, stream),
-                                              srng.srng_generate(h, 0, 64, 1 << 16, srng.SRNG_OUT_F64, o, stream)))
-    res["mrg_plain_64x65536_f64"] = {"ms_best": best, "ms_median": med, "Guniforms_s": (64 << 16) / best / 1e6,
-                                     "GB_s": (64 << 16) * 8 / best / 1e6}
+    call = lambda s: (srng.srng_reset(h, s), srng.srng_generate(h, 0, 64, 1 << 16, srng.SRNG_OUT_F64, o, s))
+    best, med = _time(torch, stream, lambda: call(stream))
+    # the same call captured 20 times in a CUDA graph: device time per call, without host launch gaps
+    side = torch.cuda.Stream(dev)
+    with torch.cuda.stream(side):
+        call(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        for _ in range(20):
+            call(side)
+    gb, gm = _time(torch, stream, g.replay)
+    call(stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ref, _ = O.mrg_bulk(O.mrg_stream_starts([12345] * 6, 127, 0, 64), 1 << 16, O.OUT_F64, threads)
+    t_or = time.perf_counter() - t0
+    bad = int(np.count_nonzero(o.cpu().numpy().view(np.uint64) != ref.ravel().view(np.uint64)))
+    par["C1"] = {"values": 64 << 16, "mismatches": bad}
+    cpu["C1"] = {"Guniforms_s": (64 << 16) / t_or / 1e9, "cores": threads, "sample": "whole workload"}
+    us = gb / 20 * 1e3
+    summ["C1"] = {"us_per_call_graph": us, "us_per_call_plain": best * 1e3,
+                  "Guniforms_s": (64 << 16) / us / 1e3, **_fracs((64 << 16) * 8, us / 1e3, peak, wfill)}
+    det["mrg_plain_64x65536_f64"] = {"plain_ms_best": best, "plain_ms_median": med, "graph_20_calls_ms": gb}
+    del g, o
     srng.srng_destroy(h)
-    del o
-    # Philox bulk: 2^30 words u32 and f32
-    from paper_1412_8266_gb300 import autotune
+
+    # ---- C3: Philox bulk, 2^30 words of one stream, u32 and f32
     n = 1 << 30
+    key = (0xC0FFEE, 0)
     ph = {}
     tunes = {}
-    for t in (srng.SRNG_OUT_U32, srng.SRNG_OUT_F32):
-        tunes[t] = autotune.tune_generate(srng.SRNG_PHILOX4X32_10, t, 1, n, use_cache=False, install=False)[0]
-        ph["tune_u32" if t == 0 else "tune_f32"] = tunes[t]
     h = srng.srng_create(srng.SRNG_PHILOX4X32_10, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
+    rng = np.random.default_rng(3)
+    pos = sorted(set([0, n - (1 << 16)] + (rng.integers(0, n >> 16, 30) << 16).tolist()))
+    c3 = {}
+    bad = 0
     for name, t, dt in (("u32", srng.SRNG_OUT_U32, torch.int32), ("f32", srng.SRNG_OUT_F32, torch.float32)):
+        tunes[t] = autotune.tune_generate(srng.SRNG_PHILOX4X32_10, t, 1, n, use_cache=False, install=False)[0]
         o = torch.empty(n, dtype=dt, device=dev)
         best, med = _time(torch, stream, lambda: (srng.srng_reset(h, stream),
                                                   srng.srng_generate_tuned(h, 0, 1, n, t, o, tunes[t], stream)))
-        ph[name] = {"ms_best": best, "ms_median": med, "Guniforms_s": n / best / 1e6, "GB_s": n * 4 / best / 1e6,
-                    "frac_of_copy_peak": n * 4 / best / 1e6 / peak}
+        ph[name] = {"ms_best": best, "ms_median": med, "tune": tunes[t]}
+        c3["ms_" + name] = best
+        c3[name] = _fracs(n * 4, best, peak, wfill)
+        t0 = time.perf_counter()
+        refs = _threaded(lambda p: O.philox_generate(key, 0, p, 1 << 16, t), pos, threads)
+        t_or = time.perf_counter() - t0
+        for p, r in zip(pos, refs):
+            bad += int(np.count_nonzero(o[p:p + (1 << 16)].cpu().numpy().view(np.uint32) != r.view(np.uint32)))
+        cpu["C3_" + name] = {"Guniforms_s": len(pos) * (1 << 16) / t_or / 1e9, "cores": threads,
+                             "sample": f"{len(pos)} runs of 2^16 words at seeded positions"}
         del o
-    # Variates: 2^30 FP32 Philox uniforms -> exponential / normal (read 4 B, write 4 B per value)
+    par["C3"] = {"values": 2 * len(pos) * (1 << 16), "mismatches": bad}
+    summ["C3"] = c3
+    det["philox_bulk_2^30"] = ph
+    # variates: 2^30 FP32 Philox uniforms -> exponential / normal, and fused into generation
     u = torch.empty(n, dtype=torch.float32, device=dev)
     srng.srng_reset(h, stream)
     srng.srng_generate_tuned(h, 0, 1, n, srng.SRNG_OUT_F32, u, tunes[srng.SRNG_OUT_F32], stream)
@@ -449,66 +577,57 @@ def extras(torch, srng, dev, stream, peak):
     var = {}
     for name, d in (("exponential", srng.SRNG_DIST_EXPONENTIAL), ("normal", srng.SRNG_DIST_NORMAL)):
         best, med = _time(torch, stream, lambda: srng.srng_transform(d, u, n, z, stream))
-        var[name] = {"ms_best": best, "ms_median": med, "Gvariates_s": n / best / 1e6, "GB_s": n * 8 / best / 1e6,
-                     "frac_of_copy_peak": n * 8 / best / 1e6 / peak}
-    # the same normals fused into generation (SRNG_OUT_NORMAL_F32: 4 bytes written per value)
+        var[name] = {"ms_best": best, **_fracs(n * 8, best, peak, wfill)}
     for name, t in (("fused_exponential", srng.SRNG_OUT_EXP_F32), ("fused_normal", srng.SRNG_OUT_NORMAL_F32)):
         tt = autotune.tune_generate(srng.SRNG_PHILOX4X32_10, t, 1, n, use_cache=False, install=False)[0]
         best, med = _time(torch, stream, lambda: (srng.srng_reset(h, stream),
                                                   srng.srng_generate_tuned(h, 0, 1, n, t, z, tt, stream)))
-        var[name] = {"ms_best": best, "ms_median": med, "Gvariates_s": n / best / 1e6, "GB_s": n * 4 / best / 1e6,
-                     "frac_of_copy_peak": n * 4 / best / 1e6 / peak,
-                     "vs_generate_then_transform": (ph["f32"]["ms_best"] + var[name[6:]]["ms_best"]) / best,
-                     "tune": tt}
+        var[name] = {"ms_best": best, "Gvariates_s": n / best / 1e6, "tune": tt,
+                     "vs_generate_then_transform": (c3["ms_f32"] + var[name[6:]]["ms_best"]) / best}
     del u, z
     srng.srng_destroy(h)
-    res["philox_bulk_2^30"] = ph
-    res["variates_2^30_f32"] = var
-    # Threefry bulk: 2^30 words of one stream, u32 and f32, both word sizes (ALU bound: 20 rounds of
-    # add / rotate / xor per block; the 4x64 block gives eight words)
-    for key, g in (("threefry_bulk_2^30", srng.SRNG_THREEFRY4X32_20),
-                   ("threefry4x64_bulk_2^30", srng.SRNG_THREEFRY4X64_20)):
+    det["variates_2^30_f32"] = var
+    summ["variates"] = {k: round(v["ms_best"], 4) for k, v in var.items()}
+    # Threefry (both word sizes) and TinyMT32 bulk: the rows beyond the first hot path
+    for key_name, gen in (("threefry_bulk_2^30", srng.SRNG_THREEFRY4X32_20),
+                          ("threefry4x64_bulk_2^30", srng.SRNG_THREEFRY4X64_20)):
         tf = {}
-        h = srng.srng_create(g, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
+        h = srng.srng_create(gen, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
         for name, t, dt in (("u32", srng.SRNG_OUT_U32, torch.int32), ("f32", srng.SRNG_OUT_F32, torch.float32)):
-            tt = autotune.tune_generate(g, t, 1, n, use_cache=False, install=False)[0]
+            tt = autotune.tune_generate(gen, t, 1, n, use_cache=False, install=False)[0]
             o = torch.empty(n, dtype=dt, device=dev)
             best, med = _time(torch, stream, lambda: (srng.srng_reset(h, stream),
                                                       srng.srng_generate_tuned(h, 0, 1, n, t, o, tt, stream)))
-            tf[name] = {"ms_best": best, "ms_median": med, "Guniforms_s": n / best / 1e6, "GB_s": n * 4 / best / 1e6,
-                        "frac_of_copy_peak": n * 4 / best / 1e6 / peak, "tune": tt}
+            tf[name] = {"ms_best": best, "tune": tt, **_fracs(n * 4, best, peak, wfill)}
             del o
         srng.srng_destroy(h)
-        res[key] = tf
-    # TinyMT32 bulk at the MRG32k3a bulk shape: 2^18 streams (1024 parameter sets of 256) x 4096, u32 and FP64
+        det[key_name] = tf
     tm = {}
-    t0 = time.perf_counter()
     h = srng.srng_create(srng.SRNG_TINYMT32, SEED, S_STREAMS, srng.SRNG_SPACING_STREAM, stream)
-    tm["create_s"] = time.perf_counter() - t0
     for name, t, dt in (("u32", srng.SRNG_OUT_U32, torch.int32), ("f64", srng.SRNG_OUT_F64, torch.float64)):
         o = torch.empty(S_STREAMS * N_DRAWS, dtype=dt, device=dev)
         best, med = _time(torch, stream, lambda: srng.srng_generate(h, 0, S_STREAMS, N_DRAWS, t, o, stream))
-        nb = o.numel() * o.element_size()
-        tm[name] = {"ms_best": best, "ms_median": med, "Guniforms_s": o.numel() / best / 1e6, "GB_s": nb / best / 1e6,
-                    "frac_of_copy_peak": nb / best / 1e6 / peak}
+        tm[name] = {"ms_best": best, **_fracs(o.numel() * o.element_size(), best, peak, wfill)}
         del o
     srng.srng_destroy(h)
-    res["tinymt_bulk_2^18x4096"] = tm
-    # Philox layouts at the many-stream shape (2^18 streams x 4096 words, uint32):
-    # counter split (one key) vs keyed (key = stream, Sec. 4.3)
+    det["tinymt_bulk_2^18x4096"] = tm
     lay = {}
     o = torch.empty(S_STREAMS * N_DRAWS, dtype=torch.int32, device=dev)
-    for name, g in (("counter_split", srng.SRNG_PHILOX4X32_10), ("keyed", srng.SRNG_PHILOX4X32_10_KEYED)):
-        h = srng.srng_create(g, 0xC0FFEE, S_STREAMS, srng.SRNG_SPACING_STREAM, stream)
+    for name, gen in (("counter_split", srng.SRNG_PHILOX4X32_10), ("keyed", srng.SRNG_PHILOX4X32_10_KEYED)):
+        h = srng.srng_create(gen, 0xC0FFEE, S_STREAMS, srng.SRNG_SPACING_STREAM, stream)
         best, med = _time(torch, stream, lambda: (srng.srng_reset(h, stream),
                                                   srng.srng_generate_tuned(h, 0, S_STREAMS, N_DRAWS, srng.SRNG_OUT_U32,
                                                                            o, tunes[srng.SRNG_OUT_U32], stream)))
-        lay[name] = {"ms_best": best, "GB_s": o.numel() * 4 / best / 1e6,
-                     "frac_of_copy_peak": o.numel() * 4 / best / 1e6 / peak}
+        lay[name] = {"ms_best": best, **_fracs(o.numel() * 4, best, peak, wfill)}
         srng.srng_destroy(h)
     del o
-    res["philox_layouts_2^18x4096_u32"] = lay
-    # Batched: 10^4 instances, plain per-instance launches vs one graph launch; fused pi
+    det["philox_layouts_2^18x4096_u32"] = lay
+    summ["beyond"] = {"threefry4x32_u32_frac_copy": det["threefry_bulk_2^30"]["u32"]["frac_copy"],
+                      "threefry4x64_u32_frac_copy": det["threefry4x64_bulk_2^30"]["u32"]["frac_copy"],
+                      "tinymt_u32_frac_copy": tm["u32"]["frac_copy"], "tinymt_f64_frac_copy": tm["f64"]["frac_copy"],
+                      "philox_keyed_frac_copy": lay["keyed"]["frac_copy"]}
+
+    # ---- C4: batched uneven, 10^4 instances: one graph launch vs one launch per instance; fused pi
     gens, lengths, outoff = W.batched_instances()
     ni = len(gens)
     total = int(outoff[-1] + lengths[-1])
@@ -522,6 +641,31 @@ def extras(torch, srng, dev, stream, peak):
     bb, bm = _time(torch, stream, lambda: srng.srng_batch_plan_launch(plan, stream), reps=5)
     items, _ = srng.srng_batch_plan_info(plan)
     srng.srng_batch_plan_destroy(plan)
+    # oracle on a seeded sample of instances (also the parity check of the batched output)
+    draws = int(np.sum(lengths))
+    rng = np.random.default_rng(9)
+    order = rng.permutation(ni)
+    pick, acc = [], 0
+    for i in order:
+        if acc > draws // 40:
+            break
+        pick.append(int(i))
+        acc += int(lengths[i])
+    pick = sorted(pick)
+    pl = np.array([int(lengths[i]) for i in pick], dtype=np.uint64)
+    po = np.zeros(len(pick), dtype=np.uint64)
+    po[1:] = np.cumsum(pl[:-1])
+    y0 = O.seed_expand(SEED)
+    mst = np.stack([O.mrg_stream_starts(y0, 127, i, 1)[0] for i in pick])
+    pg = np.array([int(gens[i]) for i in pick], dtype=np.int32)
+    t0 = time.perf_counter()
+    ref = O.batch(pg, mst, (0xC0FFEE, 0), pick, np.zeros(len(pick), dtype=np.uint64), pl, po, 0, O.OUT_U32,
+                  total=int(pl.sum()), threads=threads)
+    t_or = time.perf_counter() - t0
+    bad = 0
+    for j, i in enumerate(pick):
+        L, off = int(lengths[i]), int(outoff[i])
+        bad += int(np.count_nonzero(out[off:off + L].cpu().numpy().view(np.uint32) != ref[int(po[j]):int(po[j]) + L]))
     views = [out[int(outoff[i]):int(outoff[i]) + int(lengths[i])] for i in range(ni)]
 
     def plain():
@@ -529,6 +673,8 @@ def extras(torch, srng, dev, stream, peak):
             srng.srng_generate(hm if gens[i] == 0 else hp, i, 1, int(lengths[i]), srng.SRNG_OUT_U32, views[i], stream)
 
     pb, pm = _time(torch, stream, plain, reps=2, warm=1)
+    srng.srng_reset(hm, stream)  # the plain launches moved the streams on; the fused plan starts from the start
+    srng.srng_reset(hp, stream)
     counts = torch.empty(ni, dtype=torch.int64, device=dev)
     ptune, _ = autotune.tune_batch([hm, hp], inst, srng.SRNG_BATCH_FUSED_PI, srng.SRNG_OUT_U32, counts, reps=2)
     plan = srng.srng_batch_plan_create([hm, hp], inst, srng.SRNG_BATCH_FUSED_PI, srng.SRNG_OUT_U32, counts, ptune,
@@ -536,50 +682,95 @@ def extras(torch, srng, dev, stream, peak):
     fb, fm = _time(torch, stream, lambda: srng.srng_batch_plan_launch(plan, stream), reps=5)
     srng.srng_batch_plan_destroy(plan)
     c = counts.cpu().numpy()
+    t0 = time.perf_counter()
+    refc = O.batch(pg, mst, (0xC0FFEE, 0), pick, np.zeros(len(pick), dtype=np.uint64), pl, po, 1, O.OUT_U32,
+                   threads=threads)
+    t_orc = time.perf_counter() - t0
+    badc = int(np.count_nonzero(np.array([c[i] for i in pick]) != refc))
+    par["C4"] = {"instances": len(pick), "values": int(pl.sum()), "counts": len(pick), "mismatches": bad + badc}
+    cpu["C4"] = {"Guniforms_s": int(pl.sum()) / t_or / 1e9, "fused_pi_Guniforms_s": int(pl.sum()) / t_orc / 1e9,
+                 "cores": threads, "sample": f"{len(pick)} of {ni} instances ({int(pl.sum())} draws)"}
     pairs = int(np.sum(lengths // 2))
-    draws = int(np.sum(lengths))
-    res["batched_10k_u32"] = {
-        "draws": draws, "work_items": items, "slots": "prefix-sum offsets rounded up to 32 bytes",
-        "batched_ms": bb, "batched_Guniforms_s": draws / bb / 1e6, "batched_GB_s": draws * 4 / bb / 1e6,
-        "batched_frac_of_copy_peak": draws * 4 / bb / 1e6 / peak,
-        "plain_per_instance_ms": pb, "plain_Guniforms_s": draws / pb / 1e6, "plain_launches": 2 * ni,
-        "speedup_batched_vs_plain": pb / bb, "tune_write": btune, "tune_fused_pi": ptune,
-        "fused_pi_ms": fb, "fused_pi_Guniforms_s": draws / fb / 1e6, "pi_estimate": 4.0 * c.sum() / pairs,
-    }
+    summ["C4"] = {"batched_ms": bb, "plain_ms": pb, "speedup": pb / bb, "fused_pi_ms": fb,
+                  "Guniforms_s": draws / bb / 1e6, **_fracs(draws * 4, bb, peak, wfill),
+                  "pi": 4.0 * c.sum() / pairs}
+    det["batched_10k_u32"] = {"draws": draws, "work_items": items, "batched_ms": bb, "batched_ms_median": bm,
+                              "plain_per_instance_ms": pb, "plain_launches": 2 * ni, "fused_pi_ms": fb,
+                              "tune_write": btune, "tune_fused_pi": ptune}
     srng.srng_destroy(hm)
     srng.srng_destroy(hp)
     del out, views, counts
     torch.cuda.empty_cache()
-    res["serving"] = serving(srng)
-    return res
+
+    # ---- C5: serving
+    sv, cpu5 = serving(srng, threads, cpu_seconds)
+    det["serving"] = sv
+    cpu["C5"] = cpu5
+    b1, p1 = sv["rates"]["1x"]["batched"], sv["rates"]["1x"]["plain"]
+    summ["C5"] = {"offered_Guniforms_s": sv["offered_Guniforms_s"], "requests": sv["requests"],
+                  "batched": {"Guniforms_s": b1["Guniforms_s"], "p50_us": b1["p50_us"], "p99_us": b1["p99_us"]},
+                  "plain": {"Guniforms_s": p1["Guniforms_s"], "p50_us": p1["p50_us"], "p99_us": p1["p99_us"]},
+                  "capacity_Guniforms_s": {k: {"batched": v["batched"]["Guniforms_s"], "plain": v["plain"]["Guniforms_s"],
+                                               "batched_p99_us": v["batched"]["p99_us"]}
+                                           for k, v in sv["rates"].items() if k != "1x"}}
+    return summ, det, par, cpu
 
 
-def serving(srng, seconds=1.0):
+def serving(srng, threads, cpu_seconds, seconds=1.0):
     """Serving workload: Poisson arrivals (20k/s) of FP32 requests, n log-uniform
     in [1e3, 1e8], over 10^6 MRG32k3a substreams, 16 GB output budget, replayed
     by the library's native client; continuous batching vs one request per
-    step with one step in flight (plain per-request launches)."""
+    step with one step in flight (plain per-request launches), at the offered
+    rate and at 2x, 5x and 10x it (the same requests, arrivals compressed),
+    which shows each form's capacity.  Also the oracle's rate on a sample of
+    the same requests (jump to the request's position, then step)."""
+    import numpy as np
+    from oracle import oracle as O
     from paper_1412_8266_gb300 import workload as W
     trace = [(r.arrival_s, r.stream, r.n) for r in W.serving_trace(seconds)]
     h = srng.srng_create_from_state([12345] * 6, W.SERVING["n_streams"], srng.SRNG_SPACING_SUBSTREAM)
     out = {"requests": len(trace), "draws": sum(r[2] for r in trace), "arrival_s": seconds,
-           "offered_Guniforms_s": sum(r[2] for r in trace) / seconds / 1e9}
+           "offered_Guniforms_s": sum(r[2] for r in trace) / seconds / 1e9, "rates": {}}
     try:
-        for name, cfg in (("batched", dict(budget_bytes=W.SERVING["budget"])),
-                          ("plain", dict(budget_bytes=W.SERVING["budget"], max_inflight=1, max_step_requests=1))):
-            srv = srng.srng_server_create(h, cfg)
-            try:
-                srng.srng_server_replay(srv, trace[:200], srng.SRNG_OUT_F32, 0.0)  # warm-up
-                st = srng.srng_server_replay(srv, trace, srng.SRNG_OUT_F32, 1.0, 300000)
-            finally:
-                srng.srng_server_destroy(srv)
-            out[name] = {"p50_us": st.p50_us, "p99_us": st.p99_us, "mean_us": st.mean_us, "max_us": st.max_us,
-                         "wall_s": st.wall_s, "Guniforms_s": st.draws_completed / st.wall_s / 1e9 if st.wall_s else None,
-                         "completed": st.completed, "steps": st.steps, "kernels": st.kernels,
-                         "peak_pool_GB": st.peak_pool_bytes / 1e9}
+        for k in (1, 2, 5, 10):
+            res = {}
+            for name, cfg in (("batched", dict(budget_bytes=W.SERVING["budget"])),
+                              ("plain", dict(budget_bytes=W.SERVING["budget"], max_inflight=1, max_step_requests=1))):
+                srv = srng.srng_server_create(h, cfg)
+                try:
+                    srng.srng_server_replay(srv, trace[:200], srng.SRNG_OUT_F32, 0.0)  # warm-up
+                    st = srng.srng_server_replay(srv, trace, srng.SRNG_OUT_F32, 1.0 / k, 600000)
+                finally:
+                    srng.srng_server_destroy(srv)
+                res[name] = {"p50_us": st.p50_us, "p99_us": st.p99_us, "mean_us": st.mean_us, "max_us": st.max_us,
+                             "wall_s": st.wall_s,
+                             "Guniforms_s": st.draws_completed / st.wall_s / 1e9 if st.wall_s else None,
+                             "completed": st.completed, "steps": st.steps, "kernels": st.kernels,
+                             "peak_pool_GB": st.peak_pool_bytes / 1e9}
+            out["rates"][f"{k}x"] = res
     finally:
         srng.srng_destroy(h)
-    return out
+    # the oracle on a sample of the same requests
+    rng = np.random.default_rng(5)
+    idx = rng.permutation(len(trace))
+    sample, acc = [], 0
+    budget = int(150e6 * max(1.0, cpu_seconds / 10.0) * threads / 16)
+    for i in idx:
+        if acc >= budget:
+            break
+        sample.append(trace[int(i)])
+        acc += trace[int(i)][2]
+
+    def one(r):
+        st = O.mrg_stream_starts([12345] * 6, 76, r[1], 1)[0]
+        v, _ = O.mrg_generate(st, r[2], O.OUT_F32)
+        return v.size
+
+    t0 = time.perf_counter()
+    done = sum(_threaded(one, sample, threads))
+    dt = time.perf_counter() - t0
+    return out, {"Guniforms_s": done / dt / 1e9, "cores": threads,
+                 "sample": f"{len(sample)} of {len(trace)} requests ({done} draws), each from its substream start"}
 
 
 def run_case(args):

@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define SRNG_ABI_VERSION 2
+#define SRNG_ABI_VERSION 3
 
 typedef enum srng_status {
     SRNG_OK = 0,
@@ -124,11 +124,21 @@ typedef struct srng_set srng_set;
  *                   covers whole 128-byte lines; 2 = never (element stores,
  *                   always coalesced); 3 = MRG32k3a whole-chunk rows written
  *                   by each lane directly with 32-byte stores (one full
- *                   sector per lane), else as 1
+ *                   sector per lane), else as 1; 4 = as 3, and for MRG32k3a
+ *                   FP64 output the first double of every four is the FP64
+ *                   multiply z * norm itself while the rest are built from
+ *                   integers (the same bits), so the FP64 unit shares the
+ *                   conversion work
  *   lane_blocks   : batched launches only: Philox blocks each lane computes
  *                   per work item (a Philox work item covers 32 x lane_blocks
  *                   blocks of one instance); MRG32k3a work items are 32
- *                   chunks of `chunk` draws of one instance                  */
+ *                   chunks of `chunk` draws of one instance
+ *   split         : MRG32k3a generation: 1 = items of `chunk` draws taken by
+ *                   grid stride; 2 = balanced shares: one wave of resident
+ *                   blocks, every warp an equal contiguous share of (32
+ *                   streams x 64 draws) units, for calls whose n is a multiple
+ *                   of 64 with a 32-byte aligned output (else as 1); `chunk`
+ *                   is then unused                                             */
 typedef struct srng_tune {
     uint32_t block_threads;
     uint32_t blocks_per_sm;
@@ -136,7 +146,8 @@ typedef struct srng_tune {
     uint32_t unroll;
     uint32_t vector_store;
     uint32_t lane_blocks;
-    uint32_t reserved[2];
+    uint32_t split;
+    uint32_t reserved;
 } srng_tune;
 
 /* ------------------------------------------------------------------ errors */
@@ -455,7 +466,7 @@ typedef struct srng_server_stats {
     uint64_t submitted, completed, rejected;
     uint64_t draws_completed;
     uint64_t steps;             /* steps launched                                              */
-    uint64_t kernels;           /* kernels launched (set-up + batch per step)                  */
+    uint64_t kernels;           /* kernels launched (set-up, MRG32k3a item starts, batch)      */
     double p50_us, p99_us;      /* latency, submission -> completion seen by the dispatcher    */
     double mean_us, max_us;
     double wall_s;              /* first submission -> last completion                         */
@@ -519,18 +530,26 @@ srng_status srng_server_replay(srng_server *srv, const srng_request *req, uint64
  * fixed-size __device__ array of about 0.6 MB inside this library, which
  * every GPU that loads the library holds until the process exits.  Limits:
  * at most SRNG_BATCH_STATIC_MAX_INSTANCES instances and
- * SRNG_BATCH_STATIC_MAX_SETS sets, else SRNG_ERR_ARG with nothing enqueued.
+ * SRNG_BATCH_STATIC_MAX_SETS sets, MRG32k3a instances of at most 2^41 draws
+ * and at most 2^31 work items in one call (an MRG32k3a item covers up to
+ * 16,384 draws, a counter-based one up to 8,192; the kernels count items in
+ * 32-bit words), else SRNG_ERR_ARG with nothing enqueued.
  *
  * The first call on a device does that device's set-up (it looks up the
  * array's device address with cudaGetSymbolAddress and sizes the grid); make
  * that first call before any stream capture.  The call is asynchronous on
- * cuda_stream: it copies `inst` to the device (the caller may reuse `inst`
- * when the call returns), then launches three kernels (descriptors, prefix
+ * cuda_stream: it copies `inst` to the device with cudaMemcpyAsync on that
+ * stream, then launches three kernels (descriptors, prefix
  * sums with the zeroing of the work counter and of the FUSED_PI counts, the
  * persistent batch kernel).  Every call shares the one array, which keeps the
  * last call's contents: calls whose work overlaps on the GPU (different
  * streams without ordering, or several host threads on different streams)
- * race on it.  Order the calls on one stream, or synchronise between them. */
+ * race on it.  Order the calls on one stream, or synchronise between them.
+ * When `inst` is pageable host memory the runtime stages the copy before the
+ * call returns, so the caller may reuse `inst` at once.  When it is
+ * page-locked host memory the copy runs later, in stream order: keep `inst`
+ * unchanged until the stream has passed the call (for instance, until
+ * cudaStreamSynchronize or an event recorded after it). */
 #define SRNG_BATCH_STATIC_MAX_INSTANCES 4096
 #define SRNG_BATCH_STATIC_MAX_SETS 8
 srng_status srng_batch_run_static(srng_set *const *sets, uint32_t n_sets, const srng_instance *inst,

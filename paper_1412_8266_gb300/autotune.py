@@ -9,7 +9,9 @@ and device (name and SM count).
 
 Search spaces (all values valid for every problem):
   MRG32k3a  block_threads x resident blocks/SM x chunk (draws per thread item)
-            x store path (shared-memory staged rows or direct per-lane rows)
+            x store path (shared-memory staged rows or direct per-lane rows;
+            for FP64 also direct rows with a quarter of the doubles through
+            the FP64 multiply) x item lists or balanced shares
   Philox    block_threads x unroll (blocks per thread per trip) x blocks/SM
   batch     chunk (MRG32k3a) x lane_blocks (Philox) per work item
 """
@@ -25,6 +27,12 @@ import paper_1412_8266_gb300 as srng
 
 MRG_SPACE = [dict(block_threads=bt, blocks_per_sm=b, chunk=c, vector_store=v)
              for bt, b, c, v in itertools.product((128, 256), (4, 8), (512, 1024, 2048, 4096), (1, 3))]
+# balanced shares (one wave of resident blocks, equal runs of units per warp)
+MRG_SPACE += [dict(block_threads=bt, split=2, vector_store=v) for bt, v in itertools.product((128, 256), (1, 3))]
+# FP64 adds the direct rows with a quarter of the doubles through the FP64 multiply
+MRG_SPACE_F64 = MRG_SPACE + [dict(block_threads=bt, blocks_per_sm=b, chunk=c, vector_store=4)
+                             for bt, b, c in itertools.product((128, 256), (4, 8), (512, 1024, 2048, 4096))] + \
+    [dict(block_threads=bt, split=2, vector_store=4) for bt in (128, 256)]
 PHILOX_SPACE = [dict(block_threads=bt, unroll=u, blocks_per_sm=b)
                 for bt, u, b in itertools.product((128, 256), (1, 2, 4), (4, 8))]
 BATCH_SPACE = [dict(chunk=c, lane_blocks=lb) for c, lb in itertools.product((256, 512, 1024, 2048, 4096),
@@ -92,7 +100,11 @@ def tune_generate(gen: int, out_type: int, n_streams: int, n_per_stream: int, sp
         if install:
             srng.srng_set_tune(gen, out_type, best)
         return best, cache[key].get("table", {})
-    space = space or (MRG_SPACE if gen == srng.SRNG_MRG32K3A else PHILOX_SPACE)
+    if not space:
+        if gen == srng.SRNG_MRG32K3A:
+            space = MRG_SPACE_F64 if out_type == srng.SRNG_OUT_F64 else MRG_SPACE
+        else:
+            space = PHILOX_SPACE
     stream = torch.cuda.current_stream()
     h = srng.srng_create(gen, seed, n_streams, srng.SRNG_SPACING_STREAM, stream)
     item = 8 if out_type == srng.SRNG_OUT_F64 else 4

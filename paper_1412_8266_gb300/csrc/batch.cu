@@ -91,7 +91,7 @@ __device__ __forceinline__ void bst256(void *p, uint4 x, uint4 y)
 // (4 lanes per 128-byte row) when the instance's rows are 32-byte aligned,
 // element stores (one row per warp instruction) otherwise.
 template <int OUT>
-__device__ void mrg_item(const BatchArgs &a, const JumpTable &tab, uint32_t ii, uint32_t first_chunk,
+__device__ void mrg_item(const BatchArgs &a, const JumpTable &tab, uint32_t it, uint32_t ii, uint32_t first_chunk,
                          Smem<OUT> &sm, int warp, int lane)
 {
     using T = typename OutType<OUT>::T;
@@ -101,11 +101,19 @@ __device__ void mrg_item(const BatchArgs &a, const JumpTable &tab, uint32_t ii, 
     const uint64_t t = (uint64_t)first_chunk + lane;
     const uint64_t start = t * a.chunk;
     const uint64_t len = start < in.length ? min(a.chunk, in.length - start) : 0;
-    uint32_t s0 = in.st[0], s1 = in.st[1], s2 = in.st[2], s3 = in.st[3], s4 = in.st[4], s5 = in.st[5];
-    if (len) {
-        for (int k = 0; k < 40; ++k) {
-            if ((t >> k) == 0) break;
-            if ((t >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
+    uint32_t s0, s1, s2, s3, s4, s5;
+    if (a.item_state) {
+        // the item's first-chunk state, then one jump by this lane's l chunks
+        const uint32_t *is = a.item_state + 6 * (size_t)it;
+        s0 = is[0]; s1 = is[1]; s2 = is[2]; s3 = is[3]; s4 = is[4]; s5 = is[5];
+        if (len && lane) srng::mrg::jump(a.lane_tab + 18 * lane, s0, s1, s2, s3, s4, s5);
+    } else {
+        s0 = in.st[0]; s1 = in.st[1]; s2 = in.st[2]; s3 = in.st[3]; s4 = in.st[4]; s5 = in.st[5];
+        if (len) {
+            for (int k = 0; k < 40; ++k) {
+                if ((t >> k) == 0) break;
+                if ((t >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
+            }
         }
     }
     if (a.mode == SRNG_BATCH_FUSED_PI) {
@@ -327,7 +335,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_batch(const BatchArgs a, const 
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= a.n_items) break;
         const uint2 item = a.items[it];
-        if constexpr (FAM == kFamMrg) mrg_item<OUT>(a, tab, item.x, item.y, sm, warp, lane);
+        if constexpr (FAM == kFamMrg) mrg_item<OUT>(a, tab, it, item.x, item.y, sm, warp, lane);
         else philox_item<OUT>(a, item.x, item.y, lane);
     }
 }
@@ -351,6 +359,23 @@ __global__ void __launch_bounds__(256) k_batch_setup(BatchInst *inst, uint64_t n
     }
 }
 
+// State at each MRG32k3a item's first chunk: the instance's start state moved
+// by J_k = A^(chunk 2^k) for the set bits of the first chunk (a multiple of 32).
+__global__ void __launch_bounds__(256)
+    k_batch_item_states(const BatchInst *inst, const uint2 *items, uint64_t n, const __grid_constant__ JumpTable tab,
+                        uint32_t *item_state)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint2 item = items[i];
+    const BatchInst &in = inst[item.x];
+    uint32_t s0 = in.st[0], s1 = in.st[1], s2 = in.st[2], s3 = in.st[3], s4 = in.st[4], s5 = in.st[5];
+    for (int k = 0; k < 32; ++k)
+        if ((item.y >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
+    uint32_t *o = item_state + 6 * i;
+    o[0] = s0; o[1] = s1; o[2] = s2; o[3] = s3; o[4] = s4; o[5] = s5;
+}
+
 }  // namespace
 
 // Host-side plan.
@@ -361,6 +386,8 @@ struct BatchPlanImpl {
     uint64_t n_inst, n_items;
     BatchInst *d_inst = nullptr;
     uint2 *d_items = nullptr;
+    uint32_t *d_item_state = nullptr;        // MRG32k3a items' first-chunk states
+    uint32_t *d_lane_tab = nullptr;          // A^(chunk l), l < 32
     uint32_t *d_counter = nullptr;           // one per family kernel
     void *out = nullptr;
     BatchArgs args[2];                       // [0] MRG32k3a items, [1] counter-based items
@@ -391,6 +418,8 @@ static void plan_free(srng_batch_plan *pl)
     if (p.graph) cudaGraphDestroy(p.graph);
     if (p.d_inst) cudaFree(p.d_inst);
     if (p.d_items) cudaFree(p.d_items);
+    if (p.d_item_state) cudaFree(p.d_item_state);
+    if (p.d_lane_tab) cudaFree(p.d_lane_tab);
     if (p.d_counter) cudaFree(p.d_counter);
     if (p.side) cudaStreamDestroy(p.side);
     if (p.fork) cudaEventDestroy(p.fork);
@@ -457,6 +486,24 @@ cudaError_t launch_batch_setup(BatchInst *d_inst, uint64_t n, cudaStream_t s)
     });
     k_batch_setup<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_inst, n, unit_tab);
     return cudaGetLastError();
+}
+
+cudaError_t launch_batch_item_states(const BatchInst *d_inst, const uint2 *d_items, uint64_t n,
+                                     const JumpTable &chunk_tab, uint32_t *item_state, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_batch_item_states<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_inst, d_items, n, chunk_tab, item_state);
+    return cudaGetLastError();
+}
+
+void lane_jump_table(uint64_t chunk, uint32_t out[32 * 18])
+{
+    const MatPair c = mat_pow_shifted(0, chunk, 0);
+    MatPair m = mat_identity();
+    for (int l = 0; l < 32; ++l) {
+        memcpy(out + 18 * l, m.a, sizeof m.a);
+        m = mat_mul(m, c);
+    }
 }
 
 cudaError_t launch_batch(const BatchArgs &a, srng_out type, bool mrg, const JumpTable &chunk_tab, unsigned grid,
@@ -612,6 +659,14 @@ srng_status srng_batch_plan_create(srng_batch_plan **out, srng_set *const *sets,
             m = mat_mul(m, m);
         }
     }
+    if (n_mrg) {  // each MRG32k3a item's first-chunk state, and the lane table
+        uint32_t lane_tab[32 * 18];
+        lane_jump_table(chunk, lane_tab);
+        PLAN_TRY(cudaMalloc(&p.d_lane_tab, sizeof lane_tab));
+        PLAN_TRY(cudaMemcpyAsync(p.d_lane_tab, lane_tab, sizeof lane_tab, cudaMemcpyHostToDevice, stream));
+        PLAN_TRY(cudaMalloc(&p.d_item_state, n_mrg * 6 * sizeof(uint32_t)));
+        PLAN_TRY(launch_batch_item_states(p.d_inst, p.d_items, n_mrg, p.chunk_tab, p.d_item_state, stream));
+    }
     for (int f = 0; f < 2; ++f) {  // [0] MRG32k3a items, [1] counter-based items
         BatchArgs &a = p.args[f];
         a.inst = p.d_inst;
@@ -622,6 +677,8 @@ srng_status srng_batch_plan_create(srng_batch_plan **out, srng_set *const *sets,
         a.lane_blocks = t.lane_blocks ? t.lane_blocks : 64;
         a.mode = mode;
         a.out = out_dev;
+        a.item_state = f ? nullptr : p.d_item_state;
+        a.lane_tab = f ? nullptr : p.d_lane_tab;
         int per_sm = f ? occupancy_blocks_fam<kFamCounter>(type) : occupancy_blocks_fam<kFamMrg>(type);
         if (tune && tune->blocks_per_sm) per_sm = std::min<int>(per_sm, (int)tune->blocks_per_sm);
         const uint64_t want = (a.n_items + kWarps - 1) / kWarps;
@@ -713,6 +770,10 @@ constexpr uint32_t kStaticMaxInst = SRNG_BATCH_STATIC_MAX_INSTANCES;
 constexpr uint32_t kStaticMaxSets = SRNG_BATCH_STATIC_MAX_SETS;
 constexpr uint64_t kStaticChunk = 512;       // MRG32k3a draws per lane-chunk
 constexpr uint32_t kStaticLaneBlocks = 64;   // Philox blocks per lane per work item
+// Work items of one call: the work counter, the total and the item numbers are
+// 32-bit, and every warp adds one to the counter past the total before it
+// stops, so the total stays far below 2^32.
+constexpr uint64_t kStaticMaxItems = 1ull << 31;
 
 constexpr size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 // Layout: [0,4) work counter, [4,8) total work items, then the prefix sums of
@@ -849,7 +910,7 @@ __global__ void __launch_bounds__(kWarps * 32)
             else hi = mid;
         }
         const uint32_t j = it - (uint32_t)prefix[lo];
-        if (a.inst[lo].gen == SRNG_MRG32K3A) mrg_item<OUT>(a, tab, lo, 32u * j, sm, warp, lane);
+        if (a.inst[lo].gen == SRNG_MRG32K3A) mrg_item<OUT>(a, tab, it, lo, 32u * j, sm, warp, lane);
         else philox_item<OUT>(a, lo, j, lane);
     }
 }
@@ -951,6 +1012,11 @@ extern "C" srng_status srng_batch_run_static(srng_set *const *sets, uint32_t n_s
         ss.ns[k] = s->n_streams;
         ss.pos[k] = s->d_pos;
     }
+    // Work items per instance, counted as k_static_setup counts them: the
+    // device side holds chunk indices, per-instance item numbers and the total
+    // in 32-bit words, so calls that would overflow them are refused here,
+    // before anything is enqueued.
+    uint64_t total_items = 0;
     for (uint64_t i = 0; i < n_inst; ++i) {
         const srng_instance &x = inst[i];
         if (x.set_index >= n_sets) return fail(SRNG_ERR_ARG, "instance with a bad set index");
@@ -960,6 +1026,18 @@ extern "C" srng_status srng_batch_run_static(srng_set *const *sets, uint32_t n_s
         if (s->gen == SRNG_PHILOX4X32_10 &&
             (x.offset > UINT64_MAX - s->max_pos || x.length > UINT64_MAX - s->max_pos - x.offset))
             return fail(SRNG_ERR_RANGE, "instance Philox position would pass 2^64 - 1");
+        if (x.length == 0) continue;
+        if (s->gen == SRNG_MRG32K3A) {
+            const uint64_t nch = (x.length + kStaticChunk - 1) / kStaticChunk;
+            if (nch > (1ull << 32))
+                return fail(SRNG_ERR_ARG, "srng_batch_run_static: an MRG32k3a instance longer than 2^41 draws");
+            total_items += (nch + 31) / 32;
+        } else {
+            const uint64_t nb = (x.length + 3) / 4 + 1, per = 32ull * kStaticLaneBlocks;
+            total_items += (nb + per - 1) / per;
+        }
+        if (total_items > kStaticMaxItems)
+            return fail(SRNG_ERR_ARG, "srng_batch_run_static: more than 2^31 work items in one call");
     }
     int dev = 0;
     SRNG_CUDA_TRY(cudaGetDevice(&dev));

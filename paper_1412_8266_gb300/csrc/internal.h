@@ -100,8 +100,11 @@ struct MrgGenArgs {
     uint64_t chunk;       // draws per thread item
     uint64_t cps;         // chunks per stream
     int nbits;            // table entries used for the chunk jumps
+    int balanced;         // balanced shares (chunk = kBalUnit, the jump table J_k = A^(kBalUnit 2^k))
     void *out;
 };
+// Draws per unit of the balanced-share generation kernels.
+constexpr uint64_t kBalUnit = 64;
 cudaError_t launch_mrg_generate(const MrgGenArgs &a, srng_out type, const JumpTable &tab,
                                 const srng_tune &t, cudaStream_t stream, const DeviceInfo &dev);
 
@@ -150,6 +153,11 @@ struct BatchArgs {
     uint32_t lane_blocks;     // Philox blocks per lane per item
     int32_t mode;             // srng_batch_mode
     void *out;                // values (WRITE) or int64 counts (FUSED_PI)
+    // MRG32k3a items, optional: the state at each item's first chunk (6 words
+    // per item, in item order) and the lane table A^(chunk l), l < 32 (18 words
+    // each); when set, lane l starts from its item's state with one jump.
+    const uint32_t *item_state;
+    const uint32_t *lane_tab;
 };
 
 // Launchers shared by the batch plan and the server.
@@ -160,6 +168,13 @@ cudaError_t launch_batch_setup(BatchInst *d_inst, uint64_t n, cudaStream_t s);
 // counter-based (!mrg); a.counter must be zero.
 cudaError_t launch_batch(const BatchArgs &a, srng_out type, bool mrg, const JumpTable &chunk_tab, unsigned grid,
                          cudaStream_t s);
+// State at the first chunk of every MRG32k3a item (the instance's start state
+// moved by chunk_tab's J_k for the set bits of the item's first chunk):
+// item_state[6 i + j], items[0, n) all MRG32k3a.
+cudaError_t launch_batch_item_states(const BatchInst *d_inst, const uint2 *d_items, uint64_t n,
+                                     const JumpTable &chunk_tab, uint32_t *item_state, cudaStream_t s);
+// Lane table of the chunk size: A^(chunk l), l < 32, 18 words each (host).
+void lane_jump_table(uint64_t chunk, uint32_t out[32 * 18]);
 // Resident blocks per SM of the batch kernel for `type`.
 int batch_blocks_per_sm(srng_out type, bool mrg);
 // J_k = A^(chunk 2^k), k < 64.

@@ -53,6 +53,7 @@ struct Slot {
     bool busy = false;
     BatchInst *h_inst = nullptr, *d_inst = nullptr;
     uint2 *h_items = nullptr, *d_items = nullptr;
+    uint32_t *d_item_state = nullptr;  // MRG32k3a items' first-chunk states (6 words each)
     uint32_t *d_counter = nullptr;
     std::vector<std::pair<uint64_t, uint64_t>> parts;  // (ticket, draws) of the step in flight
 };
@@ -111,6 +112,7 @@ struct srng_server {
     char *pool_mem = nullptr;
     Pool pool;
     JumpTable chunk_tab;
+    uint32_t *d_lane_tab = nullptr;  // A^(chunk l), l < 32 (MRG32k3a sets)
     std::vector<Slot> slots;
     uint32_t cap_items = 0;
 
@@ -221,6 +223,10 @@ srng_status launch_step(srng_server *srv, Slot &sl)
     SRNG_CUDA_TRY(cudaMemcpyAsync(sl.d_inst, sl.h_inst, n_inst * sizeof(BatchInst), cudaMemcpyHostToDevice, sl.stream));
     SRNG_CUDA_TRY(cudaMemcpyAsync(sl.d_items, sl.h_items, n_items * sizeof(uint2), cudaMemcpyHostToDevice, sl.stream));
     SRNG_CUDA_TRY(launch_batch_setup(sl.d_inst, n_inst, sl.stream));
+    const bool mrg = set->gen == SRNG_MRG32K3A;
+    if (mrg)  // each item's first-chunk state, so a lane reaches its chunk with one jump
+        SRNG_CUDA_TRY(launch_batch_item_states(sl.d_inst, sl.d_items, n_items, srv->chunk_tab, sl.d_item_state,
+                                               sl.stream));
     SRNG_CUDA_TRY(cudaMemsetAsync(sl.d_counter, 0, sizeof(uint32_t), sl.stream));
     BatchArgs a;
     memset(&a, 0, sizeof a);
@@ -232,12 +238,14 @@ srng_status launch_step(srng_server *srv, Slot &sl)
     a.lane_blocks = (uint32_t)lane_blocks;
     a.mode = SRNG_BATCH_WRITE;
     a.out = srv->pool_mem;
+    a.item_state = mrg ? sl.d_item_state : nullptr;
+    a.lane_tab = mrg ? srv->d_lane_tab : nullptr;
     const unsigned grid = std::max(1u, std::min(srv->grid[type], (n_items + 7) / 8));
-    SRNG_CUDA_TRY(launch_batch(a, (srng_out)type, set->gen == SRNG_MRG32K3A, srv->chunk_tab, grid, sl.stream));
+    SRNG_CUDA_TRY(launch_batch(a, (srng_out)type, mrg, srv->chunk_tab, grid, sl.stream));
     SRNG_CUDA_TRY(cudaEventRecord(sl.ev, sl.stream));
     sl.busy = true;
     srv->steps++;
-    srv->kernels += 2;
+    srv->kernels += mrg ? 3 : 2;
     return SRNG_OK;
 }
 
@@ -381,8 +389,10 @@ void server_free(srng_server *srv)
         if (sl.h_items) cudaFreeHost(sl.h_items);
         if (sl.d_inst) cudaFree(sl.d_inst);
         if (sl.d_items) cudaFree(sl.d_items);
+        if (sl.d_item_state) cudaFree(sl.d_item_state);
         if (sl.d_counter) cudaFree(sl.d_counter);
     }
+    if (srv->d_lane_tab) cudaFree(srv->d_lane_tab);
     if (srv->pool_mem) cudaFree(srv->pool_mem);
     delete srv;
 }
@@ -442,6 +452,14 @@ srng_status srng_server_create(srng_server **out, srng_set *set, const srng_serv
         SRV_TRY(cudaMalloc(&sl.d_inst, c.max_step_requests * sizeof(BatchInst)));
         SRV_TRY(cudaMalloc(&sl.d_items, srv->cap_items * sizeof(uint2)));
         SRV_TRY(cudaMalloc(&sl.d_counter, sizeof(uint32_t)));
+        if (set->gen == SRNG_MRG32K3A)
+            SRV_TRY(cudaMalloc(&sl.d_item_state, srv->cap_items * 6 * sizeof(uint32_t)));
+    }
+    if (set->gen == SRNG_MRG32K3A) {
+        uint32_t lane_tab[32 * 18];
+        lane_jump_table(c.chunk, lane_tab);
+        SRV_TRY(cudaMalloc(&srv->d_lane_tab, sizeof lane_tab));
+        SRV_TRY(cudaMemcpy(srv->d_lane_tab, lane_tab, sizeof lane_tab, cudaMemcpyHostToDevice));
     }
 #undef SRV_TRY
     try {

@@ -181,3 +181,87 @@ def test_replay_of_the_serving_trace():
     finally:
         srng.srng_server_destroy(srv)
         srng.srng_destroy(h)
+
+
+def _oracle_points(s, p, n, offsets):
+    """Draws p + k (k in offsets) of substream s as FP32, each reached by the
+    oracle's own jump-ahead from the substream's start (point evaluation)."""
+    st0 = O.mrg_stream_starts([12345] * 6, 76, s, 1)[0]
+    out = np.empty(len(offsets), dtype=np.float32)
+    for i, k in enumerate(offsets):
+        v, _ = O.mrg_generate(O.mrg_jump(st0, p + int(k)), 1, O.OUT_F32)
+        out[i] = v[0]
+    return out
+
+
+def _oracle_full(s, p, n, threads=0):
+    """The whole request from the oracle: the range is cut into pieces whose
+    start states the oracle reaches by jump-ahead, then stepped (on all host
+    threads)."""
+    st0 = O.mrg_stream_starts([12345] * 6, 76, s, 1)[0]
+    piece = 1 << 20
+    k = (n + piece - 1) // piece
+    starts = np.stack([O.mrg_jump(st0, p + j * piece) for j in range(k)])
+    vals, _ = O.mrg_bulk(starts, piece, O.OUT_F32, threads)
+    return vals.ravel()[:n]
+
+
+def test_serving_workload_slice_equals_oracle():
+    """A seeded slice of the serving workload at its own sizes: Poisson
+    arrivals of FP32 requests with n log-uniform in [1e3, 1e8] over the 10^6
+    MRG32k3a substreams of the all-12345 state, a 16 GB budget, submitted in
+    arrival order with up to 48 requests outstanding (continuous batching:
+    requests join steps while others run).  Requests of at most 10^6 draws are
+    compared with the oracle in full; larger ones at 256 seeded positions plus
+    their first and last 4096 draws by oracle jump-ahead, and three of them
+    (seeded) in full.  Zero tolerance: FP32 values are exact functions of
+    integers."""
+    trace = W.serving_trace(0.02)  # 20 ms of arrivals at 20,000 requests/s
+    h = srng.srng_create_from_state([12345] * 6, W.SERVING["n_streams"], srng.SRNG_SPACING_SUBSTREAM)
+    srv = srng.srng_server_create(h, dict(budget_bytes=W.SERVING["budget"]))
+    rng = np.random.default_rng(14128266)
+    large = [i for i, r in enumerate(trace) if r.n > 1_000_000]
+    full_large = set(rng.choice(large, min(3, len(large)), replace=False).tolist()) if large else set()
+    pos = {}
+    pending = []
+    counts = dict(requests=0, full=0, sampled=0, draws=0, draws_checked=0)
+
+    def check(t, i, s, p, n):
+        srng.srng_server_wait(srv, t, 120000)
+        got = _read(srv, t, n, np.float32)
+        srng.srng_server_release(srv, t)
+        if n <= 1_000_000 or i in full_large:
+            ref = _oracle_full(s, p, n) if n > 1_000_000 else _oracle_f32(s, p, n)
+            assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), (i, s, p, n)
+            counts["full"] += 1
+            counts["draws_checked"] += n
+        else:
+            ks = np.unique(np.concatenate([rng.integers(0, n, 256), [0, n - 1]]))
+            assert np.array_equal(got[ks].view(np.uint32), _oracle_points(s, p, n, ks).view(np.uint32)), (i, s, p, n)
+            head = _oracle_f32(s, p, 4096)
+            tail = _oracle_f32(s, p + n - 4096, 4096)
+            assert np.array_equal(got[:4096].view(np.uint32), head.view(np.uint32)), (i, s, p, n)
+            assert np.array_equal(got[-4096:].view(np.uint32), tail.view(np.uint32)), (i, s, p, n)
+            counts["sampled"] += 1
+            counts["draws_checked"] += len(ks) + 8192
+        counts["requests"] += 1
+        counts["draws"] += n
+
+    try:
+        for i, r in enumerate(trace):
+            t = srng.srng_server_submit(srv, r.stream, r.n, srng.SRNG_OUT_F32)
+            p = pos.get(r.stream, 0)
+            pos[r.stream] = p + r.n
+            pending.append((t, i, r.stream, p, r.n))
+            if len(pending) > 48:
+                check(*pending.pop(0))
+        while pending:
+            check(*pending.pop(0))
+        st = srng.srng_server_get_stats(srv)
+        assert st.completed == len(trace) and st.peak_pool_bytes <= W.SERVING["budget"]
+    finally:
+        srng.srng_server_destroy(srv)
+        srng.srng_destroy(h)
+    assert counts["requests"] == len(trace) and counts["full"] > 100 and counts["sampled"] > 50
+    print(f"serving slice: {counts['requests']} requests, {counts['draws']} draws; {counts['full']} compared in "
+          f"full, {counts['sampled']} at sampled points; {counts['draws_checked']} draws checked against the oracle")
