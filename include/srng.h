@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define SRNG_ABI_VERSION 3
+#define SRNG_ABI_VERSION 2
 
 typedef enum srng_status {
     SRNG_OK = 0,
@@ -132,13 +132,7 @@ typedef struct srng_set srng_set;
  *   lane_blocks   : batched launches only: Philox blocks each lane computes
  *                   per work item (a Philox work item covers 32 x lane_blocks
  *                   blocks of one instance); MRG32k3a work items are 32
- *                   chunks of `chunk` draws of one instance
- *   split         : MRG32k3a generation: 1 = items of `chunk` draws taken by
- *                   grid stride; 2 = balanced shares: one wave of resident
- *                   blocks, every warp an equal contiguous share of (32
- *                   streams x 64 draws) units, for calls whose n is a multiple
- *                   of 64 with a 32-byte aligned output (else as 1); `chunk`
- *                   is then unused                                             */
+ *                   chunks of `chunk` draws of one instance                  */
 typedef struct srng_tune {
     uint32_t block_threads;
     uint32_t blocks_per_sm;
@@ -146,8 +140,7 @@ typedef struct srng_tune {
     uint32_t unroll;
     uint32_t vector_store;
     uint32_t lane_blocks;
-    uint32_t split;
-    uint32_t reserved;
+    uint32_t reserved[2];
 } srng_tune;
 
 /* ------------------------------------------------------------------ errors */

@@ -11,7 +11,7 @@ Search spaces (all values valid for every problem):
   MRG32k3a  block_threads x resident blocks/SM x chunk (draws per thread item)
             x store path (shared-memory staged rows or direct per-lane rows;
             for FP64 also direct rows with a quarter of the doubles through
-            the FP64 multiply) x item lists or balanced shares
+            the FP64 multiply)
   Philox    block_threads x unroll (blocks per thread per trip) x blocks/SM
   batch     chunk (MRG32k3a) x lane_blocks (Philox) per work item
 """
@@ -27,12 +27,9 @@ import paper_1412_8266_gb300 as srng
 
 MRG_SPACE = [dict(block_threads=bt, blocks_per_sm=b, chunk=c, vector_store=v)
              for bt, b, c, v in itertools.product((128, 256), (4, 8), (512, 1024, 2048, 4096), (1, 3))]
-# balanced shares (one wave of resident blocks, equal runs of units per warp)
-MRG_SPACE += [dict(block_threads=bt, split=2, vector_store=v) for bt, v in itertools.product((128, 256), (1, 3))]
 # FP64 adds the direct rows with a quarter of the doubles through the FP64 multiply
 MRG_SPACE_F64 = MRG_SPACE + [dict(block_threads=bt, blocks_per_sm=b, chunk=c, vector_store=4)
-                             for bt, b, c in itertools.product((128, 256), (4, 8), (512, 1024, 2048, 4096))] + \
-    [dict(block_threads=bt, split=2, vector_store=4) for bt in (128, 256)]
+                             for bt, b, c in itertools.product((128, 256), (4, 8), (512, 1024, 2048, 4096))]
 PHILOX_SPACE = [dict(block_threads=bt, unroll=u, blocks_per_sm=b)
                 for bt, u, b in itertools.product((128, 256), (1, 2, 4), (4, 8))]
 BATCH_SPACE = [dict(chunk=c, lane_blocks=lb) for c, lb in itertools.product((256, 512, 1024, 2048, 4096),

@@ -100,7 +100,6 @@ srng_tune effective_tune(srng_gen gen, srng_out type, const srng_tune *user)
             if (d.unroll) t.unroll = d.unroll;
             if (d.vector_store) t.vector_store = d.vector_store;
             if (d.lane_blocks) t.lane_blocks = d.lane_blocks;
-            if (d.split) t.split = d.split;
         }
     }
     if (user) {
@@ -110,7 +109,6 @@ srng_tune effective_tune(srng_gen gen, srng_out type, const srng_tune *user)
         if (user->unroll) t.unroll = user->unroll;
         if (user->vector_store) t.vector_store = user->vector_store;
         if (user->lane_blocks) t.lane_blocks = user->lane_blocks;
-        if (user->split) t.split = user->split;
     }
     return t;
 }
@@ -126,7 +124,6 @@ srng_status check_tune(const srng_tune *t)
         return fail(SRNG_ERR_ARG, "tune.unroll must be 1, 2 or 4");
     if (t->vector_store > 4) return fail(SRNG_ERR_ARG, "tune.vector_store must be 0, 1, 2, 3 or 4");
     if (t->lane_blocks > 4096) return fail(SRNG_ERR_ARG, "tune.lane_blocks must be <= 4096");
-    if (t->split > 2) return fail(SRNG_ERR_ARG, "tune.split must be 0, 1 or 2");
     return SRNG_OK;
 }
 
@@ -479,9 +476,6 @@ static srng_status generate_dev(srng_set *s, uint64_t b, uint64_t c, uint64_t n,
                 if (n % d == 0) { chunk = d; break; }
         }
         if (chunk > n) chunk = n;
-        // balanced shares: n in whole units, 32-byte aligned rows
-        a.balanced = t.split == 2 && n % kBalUnit == 0 && (reinterpret_cast<uintptr_t>(out) & 31) == 0;
-        if (a.balanced) chunk = kBalUnit;
         a.chunk = chunk;
         a.cps = (n + chunk - 1) / chunk;
         a.nbits = bit_length(a.cps - 1);

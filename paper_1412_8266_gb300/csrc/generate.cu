@@ -23,10 +23,6 @@
 // and positions add 24 and 8 bytes per stream per call.
 #include <stdint.h>
 
-#include <algorithm>
-#include <map>
-#include <mutex>
-
 #include "counter_based.cuh"
 #include "internal.h"
 #include "srng_device.cuh"
@@ -265,110 +261,6 @@ __global__ void __launch_bounds__(WARPS * 32)
             const uint4 *p = reinterpret_cast<const uint4 *>(v);
             st256(dst + j, p[0], p[1]);
         }
-    }
-}
-
-// K2, balanced shares.  For uniform rows (n a multiple of kBalUnit, the
-// output 32-byte aligned) the call's s_count x n draws are cut into units of
-// 32 streams x kBalUnit draws, ordered group by group (a group: 32 consecutive
-// streams, one per lane), and every warp of a persistent grid -- one wave of
-// resident blocks -- takes an equal contiguous share of units (shares differ
-// by one unit at most).  A share starts inside a group's rows at unit b0: the
-// lanes reach draw b0 kBalUnit of their streams by jump-ahead (tab: J_k =
-// A^(kBalUnit 2^k)), run on to the end of those rows, then through whole rows
-// of the next groups from their streams' states.  With item lists the last
-// partial wave leaves SMs unevenly loaded (at 2^18 streams x 4096 the SMs run
-// 6 or 7 blocks); shares load every warp alike.  STORE 0: rows staged in
-// shared memory, whole 128-byte lines per warp store; 1: each lane writes its
-// row with 32-byte stores; 2: as 1, and for FP64 the first double of every
-// four is the FP64 multiply (the definition), the rest built from integers.
-template <int OUT, int WARPS, int STORE>
-__global__ void __launch_bounds__(WARPS * 32, STORE == 0 ? 1 : 48 / WARPS)
-    k_mrg_generate_bal(const MrgGenArgs a, const __grid_constant__ JumpTable tab)
-{
-    using T = typename OutType<OUT>::T;
-    constexpr int G = 128 / sizeof(T);   // elements per 128-byte row piece
-    constexpr int VPL = 16 / sizeof(T);  // elements per 16 bytes
-    constexpr int RS = G + VPL;          // 144-byte row stride in shared memory
-    constexpr int EPQ = 32 / sizeof(T);  // elements per 32-byte store
-    __shared__ __align__(16) T tile[STORE == 0 ? WARPS : 1][STORE == 0 ? 32 * RS : 4];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T *out = static_cast<T *>(a.out);
-    const uint64_t upr = a.n / kBalUnit;                 // units per row
-    const uint64_t groups = (a.s_count + 31) / 32;
-    const unsigned __int128 total = (unsigned __int128)groups * upr;
-    const uint64_t nw = (uint64_t)gridDim.x * WARPS, w = (uint64_t)blockIdx.x * WARPS + warp;
-    uint64_t u = (uint64_t)(total * w / nw);
-    const uint64_t u_end = (uint64_t)(total * (w + 1) / nw);
-    while (u < u_end) {
-        const uint64_t g = u / upr, b0 = u - g * upr;
-        const uint64_t b1 = min(upr, b0 + (u_end - u));   // this pass: units [b0, b1) of group g's rows
-        const uint64_t s_rel = g * 32 + lane;
-        const bool active = s_rel < a.s_count;
-        uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
-        if (active) {
-            const uint64_t s = a.s_begin + s_rel, ns = a.n_streams;
-            s0 = a.state[s]; s1 = a.state[ns + s]; s2 = a.state[2 * ns + s];
-            s3 = a.state[3 * ns + s]; s4 = a.state[4 * ns + s]; s5 = a.state[5 * ns + s];
-            for (int k = 0; (b0 >> k) != 0; ++k)
-                if ((b0 >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
-        }
-        const uint64_t d0 = b0 * kBalUnit, d1 = b1 * kBalUnit;  // draws [d0, d1) of every row
-        if constexpr (STORE == 0) {
-            T *my = &tile[warp][lane * RS];
-            const uint32_t rows = (uint32_t)min((uint64_t)32, a.s_count - g * 32);
-            const int q = lane & 3, rsub = lane >> 2;
-            T *dst0 = out + g * 32 * a.n + (uint64_t)q * EPQ;  // row r at dst0 + r n
-            for (uint64_t done = d0; done < d1; done += G) {
-                if (active) {
-#pragma unroll
-                    for (int j = 0; j < G; j += VPL) {
-                        if constexpr (sizeof(T) == 4) {
-                            uint32_t w4[4];
-                            T x[4];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) w4[e] = srng::mrg::step(s0, s1, s2, s3, s4, s5);
-                            convert_k<SRNG_MRG32K3A, OUT, 4>(w4, x);
-                            *reinterpret_cast<uint4 *>(&my[j]) = *reinterpret_cast<uint4 *>(x);
-                        } else {
-                            double2 v;
-                            v.x = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
-                            v.y = convert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
-                            *reinterpret_cast<double2 *>(&my[j]) = v;
-                        }
-                    }
-                }
-                __syncwarp();
-#pragma unroll
-                for (int r0 = 0; r0 < 32; r0 += 8) {
-                    const int r = r0 + rsub;
-                    if ((uint32_t)r < rows) {
-                        const T *src = &tile[warp][r * RS + q * EPQ];
-                        st256(dst0 + (uint64_t)r * a.n + done, *reinterpret_cast<const uint4 *>(src),
-                              *reinterpret_cast<const uint4 *>(src + VPL));
-                    }
-                }
-                __syncwarp();
-            }
-        } else if (active) {
-            T *dst = out + s_rel * a.n;
-            for (uint64_t j = d0; j < d1; j += EPQ) {
-                uint32_t w4[EPQ];
-                T v[EPQ];
-#pragma unroll
-                for (int e = 0; e < EPQ; ++e) w4[e] = srng::mrg::step(s0, s1, s2, s3, s4, s5);
-                if constexpr (STORE == 2 && OUT == SRNG_OUT_F64) {
-                    v[0] = srng::mrg::to_f64_dmul(w4[0]);
-#pragma unroll
-                    for (int e = 1; e < EPQ; ++e) v[e] = srng::mrg::to_f64(w4[e]);
-                } else {
-                    convert_k<SRNG_MRG32K3A, OUT, EPQ>(w4, v);
-                }
-                const uint4 *p = reinterpret_cast<const uint4 *>(v);
-                st256(dst + j, p[0], p[1]);
-            }
-        }
-        u += b1 - b0;
     }
 }
 
@@ -698,48 +590,6 @@ cudaError_t mrg_dispatch_rows(const MrgGenArgs &a, const JumpTable &tab, const s
     return cudaGetLastError();
 }
 
-// One wave of resident blocks of kernel k (cached per kernel and device).
-template <typename K>
-unsigned resident_grid(K k, int threads, const DeviceInfo &dev)
-{
-    static std::mutex mu;
-    static std::map<std::pair<const void *, int>, int> per_sm;
-    std::lock_guard<std::mutex> lk(mu);
-    const auto key = std::make_pair(reinterpret_cast<const void *>(k), dev.device);
-    auto it = per_sm.find(key);
-    if (it == per_sm.end()) {
-        int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, 0) != cudaSuccess || nb < 1) nb = 1;
-        it = per_sm.emplace(key, nb).first;
-    }
-    return (unsigned)(dev.sm_count * it->second);
-}
-
-template <int OUT, int WARPS, int STORE>
-cudaError_t mrg_launch_bal(const MrgGenArgs &a, const JumpTable &tab, cudaStream_t stream, const DeviceInfo &dev)
-{
-    auto k = k_mrg_generate_bal<OUT, WARPS, STORE>;
-    const uint64_t units = (a.s_count + 31) / 32 * (a.n / kBalUnit);
-    uint64_t grid = resident_grid(k, WARPS * 32, dev);
-    const uint64_t want = (units + WARPS - 1) / WARPS;  // at least one unit per warp
-    if (grid > want) grid = want;
-    k<<<(unsigned)std::max<uint64_t>(1, grid), WARPS * 32, 0, stream>>>(a, tab);
-    return cudaGetLastError();
-}
-
-template <int OUT>
-cudaError_t mrg_dispatch_bal(const MrgGenArgs &a, const JumpTable &tab, const srng_tune &t, cudaStream_t stream,
-                             const DeviceInfo &dev)
-{
-    const bool w8 = t.block_threads >= 256;
-    if (t.vector_store == 3 || (t.vector_store == 4 && OUT != SRNG_OUT_F64))
-        return w8 ? mrg_launch_bal<OUT, 8, 1>(a, tab, stream, dev) : mrg_launch_bal<OUT, 4, 1>(a, tab, stream, dev);
-    if constexpr (OUT == SRNG_OUT_F64)
-        if (t.vector_store == 4)
-            return w8 ? mrg_launch_bal<OUT, 8, 2>(a, tab, stream, dev) : mrg_launch_bal<OUT, 4, 2>(a, tab, stream, dev);
-    return w8 ? mrg_launch_bal<OUT, 8, 0>(a, tab, stream, dev) : mrg_launch_bal<OUT, 4, 0>(a, tab, stream, dev);
-}
-
 template <int OUT>
 cudaError_t mrg_dispatch(const MrgGenArgs &a, const JumpTable &tab, const srng_tune &t, cudaStream_t stream,
                          const DeviceInfo &dev)
@@ -747,7 +597,6 @@ cudaError_t mrg_dispatch(const MrgGenArgs &a, const JumpTable &tab, const srng_t
     using T = typename OutType<OUT>::T;
     constexpr uint64_t VPL = 16 / sizeof(T);
     constexpr uint64_t G = 128 / sizeof(T);
-    if (a.balanced) return mrg_dispatch_bal<OUT>(a, tab, t, stream, dev);
     if (t.vector_store != 2 && (reinterpret_cast<uintptr_t>(a.out) & 31) == 0 && a.n % a.chunk == 0 &&
         a.chunk % G == 0)
         return mrg_dispatch_rows<OUT>(a, tab, t, stream, dev);

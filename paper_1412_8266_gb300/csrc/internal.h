@@ -100,11 +100,8 @@ struct MrgGenArgs {
     uint64_t chunk;       // draws per thread item
     uint64_t cps;         // chunks per stream
     int nbits;            // table entries used for the chunk jumps
-    int balanced;         // balanced shares (chunk = kBalUnit, the jump table J_k = A^(kBalUnit 2^k))
     void *out;
 };
-// Draws per unit of the balanced-share generation kernels.
-constexpr uint64_t kBalUnit = 64;
 cudaError_t launch_mrg_generate(const MrgGenArgs &a, srng_out type, const JumpTable &tab,
                                 const srng_tune &t, cudaStream_t stream, const DeviceInfo &dev);
 

@@ -111,9 +111,7 @@ def test_chunked_and_unaligned_vs_oracle(sets, out_type, pad, chunk):
                                   dict(vector_store=3, chunk=512), dict(vector_store=3, chunk=4096),
                                   dict(vector_store=3, chunk=32, block_threads=128),
                                   dict(vector_store=4, chunk=512), dict(vector_store=4, chunk=4096),
-                                  dict(vector_store=4, chunk=32, block_threads=128),
-                                  dict(split=2), dict(split=2, vector_store=3), dict(split=2, vector_store=4),
-                                  dict(split=2, block_threads=128, vector_store=4), dict(split=1)])
+                                  dict(vector_store=4, chunk=32, block_threads=128)])
 def test_tuning_never_changes_output(sets, tune, n):
     S = 300
     outs = []
@@ -124,39 +122,6 @@ def test_tuning_never_changes_output(sets, tune, n):
         outs.append(o)
     torch.cuda.synchronize()
     assert torch.equal(outs[0].view(torch.int64), outs[1].view(torch.int64))
-
-
-@pytest.mark.parametrize("out_type", [srng.SRNG_OUT_U32, srng.SRNG_OUT_F32, srng.SRNG_OUT_F64,
-                                      srng.SRNG_OUT_EXP_F32, srng.SRNG_OUT_NORMAL_F32])
-@pytest.mark.parametrize("S,n,offset", [(300, 4096, 0), (37, 64 * 97, 5), (1024, 128, 0), (5, 64, 2)])
-def test_balanced_shares_equal_item_lists(sets, out_type, S, n, offset):
-    """Balanced shares (tune.split = 2: one wave of resident blocks, every warp
-    an equal run of 32-stream x 64-draw units, starting mid-row by jump-ahead)
-    give the item lists' output bit for bit, for every output type, for
-    partial stream groups, for stream ranges that start inside the set, and
-    after the streams have moved on; the states advance alike."""
-    total = S + offset
-    dt = {srng.SRNG_OUT_F64: torch.float64, srng.SRNG_OUT_U32: torch.int32}.get(out_type, torch.float32)
-    outs, states = [], []
-    for t in (dict(split=1), dict(split=2), dict(split=2, vector_store=3), dict(split=2, vector_store=4),
-              dict(split=2, block_threads=128)):
-        h = sets(srng.srng_create(srng.SRNG_MRG32K3A, 1412, total))
-        warm = torch.empty(total * 96, dtype=torch.int32, device="cuda")
-        srng.srng_generate(h, 0, total, 96, srng.SRNG_OUT_U32, warm)  # positions no longer at a stream start
-        o = torch.empty(S * n, dtype=dt, device="cuda")
-        srng.srng_generate_tuned(h, offset, S, n, out_type, o, t)
-        outs.append(o)
-        states.append(get_states(h, 0, total))
-    torch.cuda.synchronize()
-    bits = torch.int64 if dt == torch.float64 else torch.int32
-    for o in outs[1:]:
-        assert torch.equal(o.view(bits), outs[0].view(bits))
-    for st in states[1:]:
-        assert np.array_equal(st, states[0])
-    if out_type in (srng.SRNG_OUT_U32, srng.SRNG_OUT_F64):
-        st0 = O.mrg_stream_starts(O.seed_expand(1412), 127, offset, S)  # from the seed alone
-        ref, _ = O.mrg_bulk(O.mrg_bulk(st0, 96, O.OUT_U32)[1], n, out_type)
-        assert_bitexact(to_np(outs[1], out_type).reshape(S, n), ref, out_type)
 
 
 def test_state_save_restore_resumes(sets):
@@ -206,7 +171,6 @@ def test_full_size_mrg_plain_f64():
      dict(block_threads=128, blocks_per_sm=16, chunk=4096, vector_store=1)),
     (dict(block_threads=256, blocks_per_sm=8, chunk=4096, vector_store=1),
      dict(block_threads=256, blocks_per_sm=8, chunk=2048, vector_store=4)),
-    (dict(block_threads=256, split=2, vector_store=1), dict(block_threads=256, split=2, vector_store=4)),
 ])
 def test_full_size_mrg_bulk_sampled(tune_u, tune_f):
     """Whole workload in the benchmark's launch configurations: seed
