@@ -406,6 +406,15 @@ __device__ __forceinline__ float to_f32(uint32_t v)
     return __fadd_rn(one_k, minus);
 }
 
+/* The same value as to_f32 through the integer-to-float conversion unit:
+ * v >> 8 has at most 24 significant bits, so the conversion and the scaling
+ * by 2^-24 are both exact.  Kernels whose integer pipes are the busy ones
+ * (the counter-based rounds) take this form. */
+__device__ __forceinline__ float to_f32_cvt(uint32_t v)
+{
+    return __fmul_rn(__uint2float_rn(v >> 8), 0x1p-24f);
+}
+
 /* ------------------------------------------------------- generator objects */
 
 namespace mrg {

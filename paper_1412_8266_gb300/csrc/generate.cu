@@ -322,6 +322,12 @@ __device__ __forceinline__ void store8(typename OutType<OUT>::T *row, int64_t k0
 // host's quotient / remainder of gridDim.x by tps.  Each lane computes U pairs
 // of adjacent blocks (2U independent blocks in flight) and writes each pair's
 // eight values with 32-byte stores: a warp store covers 1 KiB (u32 / f32).
+// A tile lies wholly inside its stream's run when the stream's position is a
+// multiple of the words per cipher block (no offset inside the first block)
+// and the tile ends before the last whole block; such tiles of a 32-byte
+// aligned row take a lean path (no bounds or alignment tests, FP32 through the
+// conversion unit).  Every other tile takes the general path one pair at a
+// time: partial pairs and misaligned runs with element stores.
 template <int OUT, int U, bool VEC, int CIPHER>
 __global__ void __launch_bounds__(256)
     k_philox_generate(const PhiloxGenArgs a, uint64_t tps, uint64_t q_grid, uint64_t r_grid)
@@ -329,11 +335,13 @@ __global__ void __launch_bounds__(256)
     using T = typename OutType<OUT>::T;
     const uint64_t tb = 2ull * blockDim.x * U;
     const uint64_t n_tiles = a.s_count * tps;
+    const uint64_t full = a.n / (4 * tb);  // whole tiles of a run that starts at a block boundary
     uint64_t s_rel = blockIdx.x / tps;
     uint64_t tt = blockIdx.x - s_rel * tps;
     uint64_t cur = ~0ull;  // stream whose position is loaded
     uint32_t al = 0, c2 = 0, c3 = 0, kk0 = a.k0, kk1 = a.k1;
     uint64_t q0 = 0, nb = 0;
+    bool lean = false;
     T *row = nullptr;
     for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         if (s_rel != cur) {  // a block's tiles stay in one stream for long runs
@@ -345,22 +353,43 @@ __global__ void __launch_bounds__(256)
             q0 = (p0 - al) >> 2;
             nb = (al + a.n + 3) >> 2;
             row = static_cast<T *>(a.out) + s_rel * a.n;
+            lean = VEC && al == 0 && (reinterpret_cast<uintptr_t>(row) & 31) == 0;
             if (a.keyed) {  // key = the stream, counter words 2-3 = the seed
                 kk0 = (uint32_t)s; kk1 = (uint32_t)(s >> 32); c2 = a.k0; c3 = a.k1;
             } else {
                 c2 = (uint32_t)s; c3 = (uint32_t)(s >> 32);
             }
         }
-        uint32_t x[U][8];
+        if (lean && tt < full) {
+            uint32_t x[U][8];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint64_t b = tt * tb + (uint64_t)u * 2 * blockDim.x + 2 * threadIdx.x;
-            cb_pair<CIPHER, true>(q0 + b, x[u], kk0, kk1, c2, c3);
-        }
+            for (int u = 0; u < U; ++u) {
+                const uint64_t b = tt * tb + (uint64_t)u * 2 * blockDim.x + 2 * threadIdx.x;
+                cb_pair<CIPHER, true>(q0 + b, x[u], kk0, kk1, c2, c3);
+            }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint64_t b = tt * tb + (uint64_t)u * 2 * blockDim.x + 2 * threadIdx.x;
-            if (b < nb) store8<SRNG_PHILOX4X32_10, OUT, VEC>(row, (int64_t)(b * 4) - al, a.n, x[u]);
+            for (int u = 0; u < U; ++u) {
+                const uint64_t b = tt * tb + (uint64_t)u * 2 * blockDim.x + 2 * threadIdx.x;
+                T v[8];
+                if constexpr (OUT == SRNG_OUT_F32) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j] = srng::to_f32_cvt(x[u][j]);
+                } else {
+                    convert_k<SRNG_PHILOX4X32_10, OUT, 8>(x[u], v);
+                }
+                const uint4 *p = reinterpret_cast<const uint4 *>(v);
+                st256(row + 4 * b, p[0], p[1]);
+                if constexpr (sizeof(T) == 8) st256(row + 4 * b + 4, p[2], p[3]);
+            }
+        } else {
+#pragma unroll 1
+            for (int u = 0; u < U; ++u) {
+                const uint64_t b = tt * tb + (uint64_t)u * 2 * blockDim.x + 2 * threadIdx.x;
+                if (b >= nb) break;
+                uint32_t w[8];
+                cb_pair<CIPHER, true>(q0 + b, w, kk0, kk1, c2, c3);
+                store8<SRNG_PHILOX4X32_10, OUT, VEC>(row, (int64_t)(b * 4) - al, a.n, w);
+            }
         }
         tt += r_grid;
         s_rel += q_grid;
