@@ -525,6 +525,13 @@ def extras(torch, srng, dev, stream, peak, wfill, cpu_seconds):
         for _ in range(20):
             call(side)
     gb, gm = _time(torch, stream, g.replay)
+    # the generation call alone (kernel + state advance), 20 calls per graph: the streams move on
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2, stream=side):
+        for _ in range(20):
+            srng.srng_generate(h, 0, 64, 1 << 16, srng.SRNG_OUT_F64, o, side)
+    gg, _ = _time(torch, stream, g2.replay)
+    del g2
     call(stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -534,7 +541,7 @@ def extras(torch, srng, dev, stream, peak, wfill, cpu_seconds):
     par["C1"] = {"values": 64 << 16, "mismatches": bad}
     cpu["C1"] = {"Guniforms_s": (64 << 16) / t_or / 1e9, "cores": threads, "sample": "whole workload"}
     us = gb / 20 * 1e3
-    summ["C1"] = {"us_per_call_graph": us, "us_per_call_plain": best * 1e3,
+    summ["C1"] = {"us_per_call_graph": us, "us_per_call_plain": best * 1e3, "us_per_generate_graph": gg / 20 * 1e3,
                   "Guniforms_s": (64 << 16) / us / 1e3, **_fracs((64 << 16) * 8, us / 1e3, peak, wfill)}
     det["mrg_plain_64x65536_f64"] = {"plain_ms_best": best, "plain_ms_median": med, "graph_20_calls_ms": gb}
     del g, o
@@ -785,7 +792,7 @@ def run_case(args):
     c = args.case
     k = max(1, args.case_scale)
     res = {"case": c, "scale": k, "tune": args.case_tune}
-    if c.startswith("mrg"):
+    if c.startswith("mrg") and c != "mrg_plain":
         S = S_STREAMS // k
         t = srng.SRNG_OUT_U32 if c == "mrg_u32" else srng.SRNG_OUT_F64
         h = srng.srng_create(srng.SRNG_MRG32K3A, SEED, S, srng.SRNG_SPACING_STREAM, stream)
@@ -810,8 +817,16 @@ def run_case(args):
         h = srng.srng_create(g, 0xC0FFEE, 1, srng.SRNG_SPACING_STREAM, stream)
         dt = torch.int32 if t == 0 else torch.float64 if t == srng.SRNG_OUT_F64 else torch.float32
         o = torch.empty(n, dtype=dt, device=dev)
-        fn = lambda: srng.srng_generate(h, 0, 1, n, t, o, stream)
+        tune = json.loads(args.case_tune) if args.case_tune else None
+        fn = lambda: srng.srng_generate_tuned(h, 0, 1, n, t, o, tune, stream)
         nbytes, nvals = n * o.element_size(), n
+    elif c == "mrg_plain":
+        # 64 streams x 2^16 FP64 from the all-12345 state, 2^127 apart (the whole workload; no scaling)
+        h = srng.srng_create_from_state([12345] * 6, 64, srng.SRNG_SPACING_STREAM, stream)
+        o = torch.empty(64 << 16, dtype=torch.float64, device=dev)
+        tune = json.loads(args.case_tune) if args.case_tune else None
+        fn = lambda: srng.srng_generate_tuned(h, 0, 64, 1 << 16, srng.SRNG_OUT_F64, o, tune, stream)
+        nbytes, nvals = o.numel() * 8, o.numel()
     elif c.startswith("tinymt"):
         S = S_STREAMS // k
         t = srng.SRNG_OUT_U32 if c == "tinymt_u32" else srng.SRNG_OUT_F64
@@ -850,7 +865,7 @@ def run_case(args):
     return 0
 
 
-CASES = {"mrg_u32", "mrg_f64", "philox_u32", "philox_f32", "philox_f64", "philox_normal", "philox_many_u32", "philox_keyed_many_u32",
+CASES = {"mrg_u32", "mrg_f64", "mrg_plain", "philox_u32", "philox_f32", "philox_f64", "philox_normal", "philox_many_u32", "philox_keyed_many_u32",
          "threefry_u32", "threefry_f32", "threefry64_u32", "threefry64_f32",
          "tinymt_u32", "tinymt_f64",
          "batch_write", "batch_pi", "transform_exponential", "transform_normal"}
