@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define SRNG_ABI_VERSION 2
+#define SRNG_ABI_VERSION 3
 
 typedef enum srng_status {
     SRNG_OK = 0,
@@ -132,7 +132,11 @@ typedef struct srng_set srng_set;
  *   lane_blocks   : batched launches only: Philox blocks each lane computes
  *                   per work item (a Philox work item covers 32 x lane_blocks
  *                   blocks of one instance); MRG32k3a work items are 32
- *                   chunks of `chunk` draws of one instance                  */
+ *                   chunks of `chunk` draws of one instance
+ *   resident      : MRG32k3a generation: at most this many blocks resident on
+ *                   an SM at once, held by reserving shared memory (0: the
+ *                   default, 6 for FP64 output and no limit otherwise; 32: as
+ *                   many as the kernel's registers allow)                     */
 typedef struct srng_tune {
     uint32_t block_threads;
     uint32_t blocks_per_sm;
@@ -140,7 +144,8 @@ typedef struct srng_tune {
     uint32_t unroll;
     uint32_t vector_store;
     uint32_t lane_blocks;
-    uint32_t reserved[2];
+    uint32_t resident;
+    uint32_t reserved;
 } srng_tune;
 
 /* ------------------------------------------------------------------ errors */

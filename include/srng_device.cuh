@@ -125,20 +125,39 @@ __device__ __forceinline__ uint32_t reduce64(uint64_t x, uint32_t c, uint32_t m)
     return min(r, r - m);
 }
 
+/* a 64-bit x folded once by 2^32 = c (mod 2^32 - c): hi c + lo, the same
+ * residue, below 2^47 + 2^32 for c < 2^15 */
+__device__ __forceinline__ uint64_t fold64(uint64_t x, uint32_t c)
+{
+    return (uint64_t)(uint32_t)(x >> 32) * c + (uint32_t)x;
+}
+
+/* (a M0 + b M1 + d M2) mod (2^32 - c) for entries and arguments below 2^32:
+ * each product folded once (< 2^48), the three summed (< 2^50), the sum folded
+ * once more -- its high word is below 2^18, so the result is below 2^34 --
+ * then by its high word (below 4) into 32 bits with one carry correction,
+ * and one conditional subtraction.  Seven 32x32 -> 64-bit products per dot
+ * product where reducing every product in full took fifteen. */
+__device__ __forceinline__ uint32_t dot3(uint32_t M0, uint32_t a, uint32_t M1, uint32_t b, uint32_t M2, uint32_t d,
+                                         uint32_t c, uint32_t m)
+{
+    const uint64_t s = fold64((uint64_t)M0 * a, c) + fold64((uint64_t)M1 * b, c) + fold64((uint64_t)M2 * d, c);
+    const uint64_t g = fold64(s, c);                                   /* < 2^18 c + 2^32 < 2^34 */
+    const uint32_t gh = (uint32_t)(g >> 32), gl = (uint32_t)g;        /* gh < 4                 */
+    uint32_t r = gl + gh * c;
+    r += r < gl ? c : 0u;  /* a carry out of 32 bits is 2^32 = c: then r < gh c < 2^17, r + c < 2^32 */
+    return min(r, r - m);
+}
+
 /* (y0, y1, y2) <- M (y0, y1, y2) mod m for a row-major 3x3 matrix M with
- * entries below m.  Each product is reduced before the three are summed. */
+ * entries below m (m = 2^32 - c). */
 __device__ __forceinline__ void matvec(const uint32_t *M, uint32_t &y0, uint32_t &y1, uint32_t &y2,
                                        uint32_t c, uint32_t m)
 {
-    uint32_t r[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        uint64_t acc = (uint64_t)reduce64((uint64_t)M[3 * i] * y0, c, m) +
-                       (uint64_t)reduce64((uint64_t)M[3 * i + 1] * y1, c, m) +
-                       (uint64_t)reduce64((uint64_t)M[3 * i + 2] * y2, c, m);
-        r[i] = reduce64(acc, c, m);
-    }
-    y0 = r[0]; y1 = r[1]; y2 = r[2];
+    const uint32_t r0 = dot3(M[0], y0, M[1], y1, M[2], y2, c, m);
+    const uint32_t r1 = dot3(M[3], y0, M[4], y1, M[5], y2, c, m);
+    const uint32_t r2 = dot3(M[6], y0, M[7], y1, M[8], y2, c, m);
+    y0 = r0; y1 = r1; y2 = r2;
 }
 
 /* Apply a pair of jump matrices (A1^d, A2^d), 18 words: 9 for m1 then 9 for m2. */
@@ -429,10 +448,7 @@ __device__ __forceinline__ void matmul(const uint32_t *A, const uint32_t *B, uin
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            const uint64_t acc = (uint64_t)reduce64((uint64_t)A[3 * i] * B[j], c, m) +
-                                 (uint64_t)reduce64((uint64_t)A[3 * i + 1] * B[3 + j], c, m) +
-                                 (uint64_t)reduce64((uint64_t)A[3 * i + 2] * B[6 + j], c, m);
-            C[3 * i + j] = reduce64(acc, c, m);
+            C[3 * i + j] = dot3(A[3 * i], B[j], A[3 * i + 1], B[3 + j], A[3 * i + 2], B[6 + j], c, m);
         }
 }
 

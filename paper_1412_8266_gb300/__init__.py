@@ -27,7 +27,7 @@ __all__ = [
     "SRNG_JUMP_STREAMS", "SRNG_BATCH_WRITE", "SRNG_BATCH_FUSED_PI", "SRNG_DIST_EXPONENTIAL", "SRNG_DIST_NORMAL",
 ]
 
-SRNG_ABI_VERSION = 2  # the struct layouts below follow this version of include/srng.h
+SRNG_ABI_VERSION = 3  # the struct layouts below follow this version of include/srng.h
 SRNG_MRG32K3A, SRNG_PHILOX4X32_10, SRNG_PHILOX4X32_10_KEYED, SRNG_THREEFRY4X32_20, SRNG_TINYMT32 = 0, 1, 2, 3, 4
 SRNG_THREEFRY4X64_20 = 5
 SRNG_OUT_U32, SRNG_OUT_F32, SRNG_OUT_F64 = 0, 1, 2
@@ -57,7 +57,7 @@ class SrngError(RuntimeError):
 class Tune(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
                 ("chunk", ctypes.c_uint32), ("unroll", ctypes.c_uint32), ("vector_store", ctypes.c_uint32),
-                ("lane_blocks", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
+                ("lane_blocks", ctypes.c_uint32), ("resident", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class Instance(ctypes.Structure):

@@ -28,8 +28,10 @@ import paper_1412_8266_gb300 as srng
 MRG_SPACE = [dict(block_threads=bt, blocks_per_sm=b, chunk=c, vector_store=v)
              for bt, b, c, v in itertools.product((128, 256), (4, 8), (512, 1024, 2048, 4096), (1, 3))]
 # FP64 adds the direct rows with a quarter of the doubles through the FP64 multiply
-MRG_SPACE_F64 = MRG_SPACE + [dict(block_threads=bt, blocks_per_sm=b, chunk=c, vector_store=4)
-                             for bt, b, c in itertools.product((128, 256), (4, 8), (512, 1024, 2048, 4096))]
+# (with at most 6 resident blocks per SM, the FP64 default, or as many as fit: 32)
+MRG_SPACE_F64 = MRG_SPACE + [dict(block_threads=bt, blocks_per_sm=b, chunk=c, vector_store=4, resident=r)
+                             for bt, b, c, r in itertools.product((128, 256), (4, 8), (512, 1024, 2048, 4096),
+                                                                  (6, 32))]
 PHILOX_SPACE = [dict(block_threads=bt, unroll=u, blocks_per_sm=b)
                 for bt, u, b in itertools.product((128, 256), (1, 2, 4), (4, 8))]
 BATCH_SPACE = [dict(chunk=c, lane_blocks=lb) for c, lb in itertools.product((256, 512, 1024, 2048, 4096),

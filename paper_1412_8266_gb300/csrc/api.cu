@@ -76,9 +76,12 @@ srng_tune builtin_tune(srng_gen gen, srng_out type)
     // per lane keeps the registers (and the resident warps) of the uniforms
     t.unroll = type == SRNG_OUT_EXP_F32 || type == SRNG_OUT_NORMAL_F32 ? 1 : 4;
     // MRG32k3a whole-row items: doubles from each lane's registers with 32-byte
-    // stores, 4-byte values through the shared-memory row stage (the measured
-    // best of each at 2^18 streams x 4096)
-    t.vector_store = gen == SRNG_MRG32K3A && type == SRNG_OUT_F64 ? 3 : 1;
+    // stores, a quarter of them through the FP64 multiply, 4-byte values through
+    // the shared-memory row stage (the measured best of each at 2^18 x 4096)
+    t.vector_store = gen == SRNG_MRG32K3A && type == SRNG_OUT_F64 ? 4 : 1;
+    // the FP64 direct rows run best with 6 or 7 resident blocks of 256 per SM
+    // (2^18 x 4096: 1.75 ms, against 1.88 with the 8 its registers allow)
+    t.resident = gen == SRNG_MRG32K3A && type == SRNG_OUT_F64 ? 6 : 0;
     t.lane_blocks = 64;
     return t;
 }
@@ -100,6 +103,7 @@ srng_tune effective_tune(srng_gen gen, srng_out type, const srng_tune *user)
             if (d.unroll) t.unroll = d.unroll;
             if (d.vector_store) t.vector_store = d.vector_store;
             if (d.lane_blocks) t.lane_blocks = d.lane_blocks;
+            if (d.resident) t.resident = d.resident;
         }
     }
     if (user) {
@@ -109,6 +113,7 @@ srng_tune effective_tune(srng_gen gen, srng_out type, const srng_tune *user)
         if (user->unroll) t.unroll = user->unroll;
         if (user->vector_store) t.vector_store = user->vector_store;
         if (user->lane_blocks) t.lane_blocks = user->lane_blocks;
+        if (user->resident) t.resident = user->resident;
     }
     return t;
 }
@@ -124,6 +129,7 @@ srng_status check_tune(const srng_tune *t)
         return fail(SRNG_ERR_ARG, "tune.unroll must be 1, 2 or 4");
     if (t->vector_store > 4) return fail(SRNG_ERR_ARG, "tune.vector_store must be 0, 1, 2, 3 or 4");
     if (t->lane_blocks > 4096) return fail(SRNG_ERR_ARG, "tune.lane_blocks must be <= 4096");
+    if (t->resident > 32) return fail(SRNG_ERR_ARG, "tune.resident must be <= 32");
     return SRNG_OK;
 }
 

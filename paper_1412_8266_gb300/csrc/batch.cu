@@ -131,6 +131,38 @@ __device__ void mrg_item(const BatchArgs &a, const JumpTable &tab, uint32_t it, 
     const uint64_t row0 = in.out_offset + (uint64_t)first_chunk * a.chunk;  // row r starts at row0 + r * chunk
     const uint64_t first_start = (uint64_t)first_chunk * a.chunk;             // draw index of row 0
     const bool vec = ((reinterpret_cast<uintptr_t>(out + row0) & 31) == 0) && (a.chunk % EPQ == 0);
+    if (vec && a.chunk % G == 0 && first_start + 32 * a.chunk <= in.length) {
+        // all 32 rows whole (every item of an instance but its last): full tiles,
+        // 32-byte stores at fixed strides, no per-row tests
+        const int q = lane & 3, rsub = lane >> 2;
+        T *dst0 = out + row0 + (uint64_t)q * EPQ;  // row r at dst0 + r chunk
+        for (uint64_t done = 0; done < a.chunk; done += G) {
+#pragma unroll
+            for (int j = 0; j < G; j += VPL) {
+                if constexpr (sizeof(T) == 4) {
+                    T x[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) x[e] = bconvert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+                    *reinterpret_cast<uint4 *>(&my[j]) = *reinterpret_cast<uint4 *>(x);
+                } else {
+                    double2 v;
+                    v.x = bconvert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+                    v.y = bconvert<SRNG_MRG32K3A, OUT>(srng::mrg::step(s0, s1, s2, s3, s4, s5));
+                    *reinterpret_cast<double2 *>(&my[j]) = v;
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r0 = 0; r0 < 32; r0 += 8) {
+                const int r = r0 + rsub;
+                const T *src = &sm.tile[warp][r * RS + q * EPQ];
+                bst256(dst0 + (uint64_t)r * a.chunk + done, *reinterpret_cast<const uint4 *>(src),
+                       *reinterpret_cast<const uint4 *>(src + VPL));
+            }
+            __syncwarp();
+        }
+        return;
+    }
     const uint32_t max_tiles = (uint32_t)((min(a.chunk, in.length - first_start) + G - 1) / G);  // row 0 is the longest
     for (uint32_t g = 0; g < max_tiles; ++g) {
         const uint64_t done = (uint64_t)g * G;
@@ -325,7 +357,8 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
 enum { kFamMrg = 1, kFamCounter = 2 };
 
 template <int OUT, int FAM>
-__global__ void __launch_bounds__(kWarps * 32) k_batch(const BatchArgs a, const __grid_constant__ JumpTable tab)
+__global__ void __launch_bounds__(kWarps * 32, FAM == kFamMrg ? (OUT == SRNG_OUT_F64 ? 2 : 4) : 5)
+    k_batch(const BatchArgs a, const __grid_constant__ JumpTable tab)
 {
     __shared__ __align__(16) Smem<OUT> sm;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

@@ -23,6 +23,10 @@
 // and positions add 24 and 8 bytes per stream per call.
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "counter_based.cuh"
 #include "internal.h"
 #include "srng_device.cuh"
@@ -574,6 +578,60 @@ cudaError_t mrg_dispatch_warps(const MrgGenArgs &a, const JumpTable &tab, const 
     return cudaGetLastError();
 }
 
+// Dynamic shared memory that holds kernel k to at most `resident` blocks per SM
+// (0: no limit, or none needed), found from the SM's shared memory and checked
+// with the occupancy calculator; cached per (kernel, threads, limit, device).
+template <typename K>
+size_t residency_smem(K k, int threads, uint32_t resident)
+{
+    if (!resident) return 0;
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, uint32_t, int>, size_t> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(reinterpret_cast<const void *>(k), threads, resident, dev);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    size_t dyn = 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, 0) == cudaSuccess && nb > (int)resident) {
+        int per_sm = 0, reserved = 0;
+        cudaFuncAttributes fa;
+        if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess &&
+            cudaFuncGetAttributes(&fa, k) == cudaSuccess) {
+            const long want = (long)per_sm / (long)resident - reserved - (long)fa.sharedSizeBytes;
+            if (want > 0) {
+                dyn = (size_t)want;
+                // static + dynamic above 48 KiB needs the kernel's opt-in
+                auto allow = [&]() {
+                    if (fa.sharedSizeBytes + dyn > 48 * 1024)
+                        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+                };
+                allow();
+                // never more than `resident`: grow the reservation until the calculator agrees
+                for (int step = 0; step < 64; ++step) {
+                    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, dyn) != cudaSuccess) break;
+                    if (nb <= (int)resident) break;
+                    dyn += 256;
+                    allow();
+                }
+            }
+        }
+        cudaGetLastError();  // a refused attribute leaves no error behind; the launch then runs unlimited
+    }
+    cache.emplace(key, dyn);
+    return dyn;
+}
+
+template <typename K>
+void launch_limited(K k, unsigned grid, int threads, const srng_tune &t, cudaStream_t stream, const MrgGenArgs &a,
+                    const JumpTable &tab)
+{
+    k<<<grid, threads, residency_smem(k, threads, t.resident), stream>>>(a, tab);
+}
+
 template <int OUT>
 cudaError_t mrg_dispatch_rows(const MrgGenArgs &a, const JumpTable &tab, const srng_tune &t, cudaStream_t stream,
                               const DeviceInfo &dev)
@@ -590,30 +648,30 @@ cudaError_t mrg_dispatch_rows(const MrgGenArgs &a, const JumpTable &tab, const s
     if constexpr (OUT == SRNG_OUT_F64) {
         if (t.vector_store == 4) {  // direct rows, a quarter of the doubles through the FP64 multiply
             if (warps == 8) {
-                if (jump) k_mrg_generate_direct<OUT, 8, true, true><<<g, 256, 0, stream>>>(a, tab);
-                else k_mrg_generate_direct<OUT, 8, false, true><<<g, 256, 0, stream>>>(a, tab);
+                if (jump) launch_limited(k_mrg_generate_direct<OUT, 8, true, true>, g, 256, t, stream, a, tab);
+                else launch_limited(k_mrg_generate_direct<OUT, 8, false, true>, g, 256, t, stream, a, tab);
             } else {
-                if (jump) k_mrg_generate_direct<OUT, 4, true, true><<<g, 128, 0, stream>>>(a, tab);
-                else k_mrg_generate_direct<OUT, 4, false, true><<<g, 128, 0, stream>>>(a, tab);
+                if (jump) launch_limited(k_mrg_generate_direct<OUT, 4, true, true>, g, 128, t, stream, a, tab);
+                else launch_limited(k_mrg_generate_direct<OUT, 4, false, true>, g, 128, t, stream, a, tab);
             }
             return cudaGetLastError();
         }
     }
     if (t.vector_store == 3 || t.vector_store == 4) {
         if (warps == 8) {
-            if (jump) k_mrg_generate_direct<OUT, 8, true><<<g, 256, 0, stream>>>(a, tab);
-            else k_mrg_generate_direct<OUT, 8, false><<<g, 256, 0, stream>>>(a, tab);
+            if (jump) launch_limited(k_mrg_generate_direct<OUT, 8, true>, g, 256, t, stream, a, tab);
+            else launch_limited(k_mrg_generate_direct<OUT, 8, false>, g, 256, t, stream, a, tab);
         } else {
-            if (jump) k_mrg_generate_direct<OUT, 4, true><<<g, 128, 0, stream>>>(a, tab);
-            else k_mrg_generate_direct<OUT, 4, false><<<g, 128, 0, stream>>>(a, tab);
+            if (jump) launch_limited(k_mrg_generate_direct<OUT, 4, true>, g, 128, t, stream, a, tab);
+            else launch_limited(k_mrg_generate_direct<OUT, 4, false>, g, 128, t, stream, a, tab);
         }
     } else {
         if (warps == 8) {
-            if (jump) k_mrg_generate_rows<OUT, 8, true><<<g, 256, 0, stream>>>(a, tab);
-            else k_mrg_generate_rows<OUT, 8, false><<<g, 256, 0, stream>>>(a, tab);
+            if (jump) launch_limited(k_mrg_generate_rows<OUT, 8, true>, g, 256, t, stream, a, tab);
+            else launch_limited(k_mrg_generate_rows<OUT, 8, false>, g, 256, t, stream, a, tab);
         } else {
-            if (jump) k_mrg_generate_rows<OUT, 4, true><<<g, 128, 0, stream>>>(a, tab);
-            else k_mrg_generate_rows<OUT, 4, false><<<g, 128, 0, stream>>>(a, tab);
+            if (jump) launch_limited(k_mrg_generate_rows<OUT, 4, true>, g, 128, t, stream, a, tab);
+            else launch_limited(k_mrg_generate_rows<OUT, 4, false>, g, 128, t, stream, a, tab);
         }
     }
     return cudaGetLastError();

@@ -50,7 +50,7 @@ def test_python_binding_covers_every_entry_point(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert srng.srng_abi_version() == srng.SRNG_ABI_VERSION == 2
+    assert srng.srng_abi_version() == srng.SRNG_ABI_VERSION == 3
     assert srng.srng_status_string(0) == "SRNG_OK"
     assert srng.srng_status_string(3) == "SRNG_ERR_STATE"
 

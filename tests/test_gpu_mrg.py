@@ -111,7 +111,9 @@ def test_chunked_and_unaligned_vs_oracle(sets, out_type, pad, chunk):
                                   dict(vector_store=3, chunk=512), dict(vector_store=3, chunk=4096),
                                   dict(vector_store=3, chunk=32, block_threads=128),
                                   dict(vector_store=4, chunk=512), dict(vector_store=4, chunk=4096),
-                                  dict(vector_store=4, chunk=32, block_threads=128)])
+                                  dict(vector_store=4, chunk=32, block_threads=128),
+                                  dict(vector_store=4, resident=3), dict(vector_store=1, resident=3),
+                                  dict(vector_store=3, resident=32)])
 def test_tuning_never_changes_output(sets, tune, n):
     S = 300
     outs = []
