@@ -337,16 +337,18 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
             }
         }
     };
-    // two pairs per lane in flight (four independent blocks); the second pair is
-    // computed even past the end of the item and then not stored
-    for (uint32_t u = 0; u < a.lane_blocks; u += 4) {
-        const uint64_t b = b0 + (uint64_t)u * 32 + 2 * lane;  // this lane's pairs: b, b + 1 and b + 64, b + 65
+    // PP pairs per lane in flight (2 PP independent blocks); pairs past the end
+    // of the item are computed and then not stored
+    constexpr int PP = 4;
+    for (uint32_t u = 0; u < a.lane_blocks; u += 2 * PP) {
+        const uint64_t b = b0 + (uint64_t)u * 32 + 2 * lane;  // this lane's pairs: b + 64 p, b + 64 p + 1
         if (b >= nb) break;
-        uint32_t w[2][8];
+        uint32_t w[PP][8];
 #pragma unroll
-        for (int p = 0; p < 2; ++p) item_pair(tf, q0 + b + 64 * p, w[p], in.key0, in.key1, c2, c3);
-        store_pair(b, w[0]);
-        if (u + 2 < a.lane_blocks && b + 64 < nb) store_pair(b + 64, w[1]);
+        for (int p = 0; p < PP; ++p) item_pair(tf, q0 + b + 64 * p, w[p], in.key0, in.key1, c2, c3);
+#pragma unroll
+        for (int p = 0; p < PP; ++p)
+            if (u + 2 * p < a.lane_blocks && b + 64 * p < nb) store_pair(b + 64 * p, w[p]);
     }
 }
 
@@ -357,7 +359,7 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
 enum { kFamMrg = 1, kFamCounter = 2 };
 
 template <int OUT, int FAM>
-__global__ void __launch_bounds__(kWarps * 32, FAM == kFamMrg ? (OUT == SRNG_OUT_F64 ? 2 : 4) : 5)
+__global__ void __launch_bounds__(kWarps * 32, FAM == kFamMrg ? (OUT == SRNG_OUT_F64 ? 2 : 4) : 4)
     k_batch(const BatchArgs a, const __grid_constant__ JumpTable tab)
 {
     __shared__ __align__(16) Smem<OUT> sm;
