@@ -241,7 +241,7 @@ __device__ __forceinline__ void item_pair(int cipher, uint64_t q, uint32_t *w, u
 
 // Lane l computes pairs of adjacent blocks; eight values per pair go out as
 // 32-byte stores when inside the instance and aligned, else element stores.
-template <int OUT>
+template <int OUT, bool PHILOX_ONLY = false>
 __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int lane)
 {
     using T = typename OutType<OUT>::T;
@@ -252,7 +252,8 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
     const uint64_t nb = (al + in.length + 3) >> 2;
     const uint64_t b0 = (uint64_t)seg * 32 * a.lane_blocks;
     const uint32_t c2 = (uint32_t)in.ctr_hi, c3 = (uint32_t)(in.ctr_hi >> 32);
-    const int tf = in.gen == SRNG_THREEFRY4X32_20 ? kCipherThreefry
+    const int tf = PHILOX_ONLY ? kCipherPhilox  // a kernel for Philox items alone holds no Threefry code
+                 : in.gen == SRNG_THREEFRY4X32_20 ? kCipherThreefry
                  : in.gen == SRNG_THREEFRY4X64_20 ? kCipherThreefry64 : kCipherPhilox;  // uniform over the warp
     const uint64_t L = in.length;
     if (a.mode == SRNG_BATCH_FUSED_PI) {
@@ -356,10 +357,10 @@ __device__ void philox_item(const BatchArgs &a, uint32_t ii, uint32_t seg, int l
 // counter-based (Philox, Threefry) items.  A plan launches one kernel per family
 // present: each carries half the code, so fewer instruction-cache misses, and
 // its own register count and occupancy.
-enum { kFamMrg = 1, kFamCounter = 2 };
+enum { kFamMrg = 1, kFamCounter = 2, kFamPhilox = 3 };
 
 template <int OUT, int FAM>
-__global__ void __launch_bounds__(kWarps * 32, FAM == kFamMrg ? (OUT == SRNG_OUT_F64 ? 2 : 4) : 4)
+__global__ void __launch_bounds__(kWarps * 32, FAM == kFamMrg ? (OUT == SRNG_OUT_F64 ? 2 : 4) : FAM == kFamPhilox ? 3 : 4)
     k_batch(const BatchArgs a, const __grid_constant__ JumpTable tab)
 {
     __shared__ __align__(16) Smem<OUT> sm;
@@ -371,7 +372,7 @@ __global__ void __launch_bounds__(kWarps * 32, FAM == kFamMrg ? (OUT == SRNG_OUT
         if (it >= a.n_items) break;
         const uint2 item = a.items[it];
         if constexpr (FAM == kFamMrg) mrg_item<OUT>(a, tab, it, item.x, item.y, sm, warp, lane);
-        else philox_item<OUT>(a, item.x, item.y, lane);
+        else philox_item<OUT, FAM == kFamPhilox>(a, item.x, item.y, lane);
     }
 }
 
@@ -428,6 +429,7 @@ struct BatchPlanImpl {
     BatchArgs args[2];                       // [0] MRG32k3a items, [1] counter-based items
     JumpTable chunk_tab;
     unsigned grid[2] = {0, 0};
+    int cfam = 2;                            // kernel family of the counter-based items (kFamCounter / kFamPhilox)
     cudaStream_t side = nullptr;             // capture fork for the second kernel
     cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraph_t graph = nullptr;
@@ -488,13 +490,17 @@ static cudaError_t enqueue_batch(const BatchPlanImpl &p, cudaStream_t s)
         if ((e = cudaEventRecord(p.fork, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(p.side, p.fork, 0)) != cudaSuccess) return e;
         launch_fam<kFamMrg>(p.type, p.grid[0], p.args[0], p.chunk_tab, s);
-        launch_fam<kFamCounter>(p.type, p.grid[1], p.args[1], p.chunk_tab, p.side);
+        if (p.cfam == kFamPhilox) launch_fam<kFamPhilox>(p.type, p.grid[1], p.args[1], p.chunk_tab, p.side);
+        else launch_fam<kFamCounter>(p.type, p.grid[1], p.args[1], p.chunk_tab, p.side);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = cudaEventRecord(p.join, p.side)) != cudaSuccess) return e;
         return cudaStreamWaitEvent(s, p.join, 0);
     }
     if (m) launch_fam<kFamMrg>(p.type, p.grid[0], p.args[0], p.chunk_tab, s);
-    if (c) launch_fam<kFamCounter>(p.type, p.grid[1], p.args[1], p.chunk_tab, s);
+    if (c) {
+        if (p.cfam == kFamPhilox) launch_fam<kFamPhilox>(p.type, p.grid[1], p.args[1], p.chunk_tab, s);
+        else launch_fam<kFamCounter>(p.type, p.grid[1], p.args[1], p.chunk_tab, s);
+    }
     return cudaGetLastError();
 }
 
@@ -541,18 +547,20 @@ void lane_jump_table(uint64_t chunk, uint32_t out[32 * 18])
     }
 }
 
-cudaError_t launch_batch(const BatchArgs &a, srng_out type, bool mrg, const JumpTable &chunk_tab, unsigned grid,
+cudaError_t launch_batch(const BatchArgs &a, srng_out type, BatchFamily fam, const JumpTable &chunk_tab, unsigned grid,
                          cudaStream_t s)
 {
     if (a.n_items == 0) return cudaSuccess;
-    if (mrg) launch_fam<kFamMrg>(type, grid, a, chunk_tab, s);
+    if (fam == kBatchMrg) launch_fam<kFamMrg>(type, grid, a, chunk_tab, s);
+    else if (fam == kBatchPhilox) launch_fam<kFamPhilox>(type, grid, a, chunk_tab, s);
     else launch_fam<kFamCounter>(type, grid, a, chunk_tab, s);
     return cudaGetLastError();
 }
 
-int batch_blocks_per_sm(srng_out type, bool mrg)
+int batch_blocks_per_sm(srng_out type, BatchFamily fam)
 {
-    return mrg ? occupancy_blocks_fam<kFamMrg>(type) : occupancy_blocks_fam<kFamCounter>(type);
+    return fam == kBatchMrg ? occupancy_blocks_fam<kFamMrg>(type)
+         : fam == kBatchPhilox ? occupancy_blocks_fam<kFamPhilox>(type) : occupancy_blocks_fam<kFamCounter>(type);
 }
 
 void chunk_jump_table(uint64_t chunk, JumpTable *out)
@@ -660,6 +668,9 @@ srng_status srng_batch_plan_create(srng_batch_plan **out, srng_set *const *sets,
     p.n_inst = n_inst;
     p.n_items = items.size();
     p.out = out_dev;
+    p.cfam = kFamPhilox;  // a kernel with Philox code alone, unless a Threefry instance is present
+    for (const BatchInst &b : hin)
+        if (b.length && (b.gen == SRNG_THREEFRY4X32_20 || b.gen == SRNG_THREEFRY4X64_20)) p.cfam = kFamCounter;
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
     cudaStream_t cap = nullptr;
     cudaError_t e;
@@ -714,7 +725,8 @@ srng_status srng_batch_plan_create(srng_batch_plan **out, srng_set *const *sets,
         a.out = out_dev;
         a.item_state = f ? nullptr : p.d_item_state;
         a.lane_tab = f ? nullptr : p.d_lane_tab;
-        int per_sm = f ? occupancy_blocks_fam<kFamCounter>(type) : occupancy_blocks_fam<kFamMrg>(type);
+        int per_sm = !f ? occupancy_blocks_fam<kFamMrg>(type)
+                   : p.cfam == kFamPhilox ? occupancy_blocks_fam<kFamPhilox>(type) : occupancy_blocks_fam<kFamCounter>(type);
         if (tune && tune->blocks_per_sm) per_sm = std::min<int>(per_sm, (int)tune->blocks_per_sm);
         const uint64_t want = (a.n_items + kWarps - 1) / kWarps;
         uint64_t g = (uint64_t)dev.sm_count * per_sm;

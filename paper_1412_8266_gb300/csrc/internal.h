@@ -163,7 +163,9 @@ struct BatchArgs {
 cudaError_t launch_batch_setup(BatchInst *d_inst, uint64_t n, cudaStream_t s);
 // The persistent batch kernel over a.n_items items, all MRG32k3a (mrg) or all
 // counter-based (!mrg); a.counter must be zero.
-cudaError_t launch_batch(const BatchArgs &a, srng_out type, bool mrg, const JumpTable &chunk_tab, unsigned grid,
+// Work-item families of the batch kernels: each kernel holds code for one.
+enum BatchFamily { kBatchMrg = 0, kBatchCounter = 1, kBatchPhilox = 2 };  // counter: Philox and Threefry
+cudaError_t launch_batch(const BatchArgs &a, srng_out type, BatchFamily fam, const JumpTable &chunk_tab, unsigned grid,
                          cudaStream_t s);
 // State at the first chunk of every MRG32k3a item (the instance's start state
 // moved by chunk_tab's J_k for the set bits of the item's first chunk):
@@ -173,7 +175,9 @@ cudaError_t launch_batch_item_states(const BatchInst *d_inst, const uint2 *d_ite
 // Lane table of the chunk size: A^(chunk l), l < 32, 18 words each (host).
 void lane_jump_table(uint64_t chunk, uint32_t out[32 * 18]);
 // Resident blocks per SM of the batch kernel for `type`.
-int batch_blocks_per_sm(srng_out type, bool mrg);
+int batch_blocks_per_sm(srng_out type, BatchFamily fam);
+// The batch kernel family of a set's work items.
+inline BatchFamily batch_family(const srng_set *s);
 // J_k = A^(chunk 2^k), k < 64.
 void chunk_jump_table(uint64_t chunk, JumpTable *out);
 constexpr int kBatchThreads = 256;
@@ -264,6 +268,11 @@ struct srng_set {
 
 namespace srng_impl {
 // Generator value of a set's work descriptors: the kernels' choice of block function.
+inline BatchFamily batch_family(const srng_set *s)
+{
+    return s->gen == SRNG_MRG32K3A ? kBatchMrg : s->threefry ? kBatchCounter : kBatchPhilox;
+}
+
 inline uint32_t inst_gen(const srng_set *s)
 {
     return s->threefry64 ? SRNG_THREEFRY4X64_20 : s->threefry ? SRNG_THREEFRY4X32_20 : (uint32_t)s->gen;

@@ -241,7 +241,7 @@ srng_status launch_step(srng_server *srv, Slot &sl)
     a.item_state = mrg ? sl.d_item_state : nullptr;
     a.lane_tab = mrg ? srv->d_lane_tab : nullptr;
     const unsigned grid = std::max(1u, std::min(srv->grid[type], (n_items + 7) / 8));
-    SRNG_CUDA_TRY(launch_batch(a, (srng_out)type, mrg, srv->chunk_tab, grid, sl.stream));
+    SRNG_CUDA_TRY(launch_batch(a, (srng_out)type, batch_family(set), srv->chunk_tab, grid, sl.stream));
     SRNG_CUDA_TRY(cudaEventRecord(sl.ev, sl.stream));
     sl.busy = true;
     srv->steps++;
@@ -435,7 +435,7 @@ srng_status srng_server_create(srng_server **out, srng_set *set, const srng_serv
     } while (0)
     SRV_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, srv->device));
     for (int t = 0; t < 3; ++t)
-        srv->grid[t] = (unsigned)(sms * batch_blocks_per_sm((srng_out)t, set->gen == SRNG_MRG32K3A));
+        srv->grid[t] = (unsigned)(sms * batch_blocks_per_sm((srng_out)t, batch_family(set)));
     SRV_TRY(cudaMalloc(&srv->pool_mem, c.budget_bytes));
     srv->pool.init(c.budget_bytes / 256 * 256);
     chunk_jump_table(c.chunk, &srv->chunk_tab);
