@@ -128,7 +128,10 @@ typedef struct srng_set srng_set;
  *                   FP64 output the first double of every four is the FP64
  *                   multiply z * norm itself while the rest are built from
  *                   integers (the same bits), so the FP64 unit shares the
- *                   conversion work
+ *                   conversion work.  Default: 1 for the counter-based
+ *                   generators and TinyMT32; for MRG32k3a 4 for FP64, and
+ *                   for 4-byte values 3 when every stream of the call is cut
+ *                   into a multiple of 32 chunks, else 1
  *   lane_blocks   : batched launches only: Philox blocks each lane computes
  *                   per work item (a Philox work item covers 32 x lane_blocks
  *                   blocks of one instance); MRG32k3a work items are 32

@@ -77,9 +77,12 @@ srng_tune builtin_tune(srng_gen gen, srng_out type)
     // doubles: two pairs (2^30 Philox doubles 1.20 ms, against 1.28 with four)
     t.unroll = type == SRNG_OUT_EXP_F32 || type == SRNG_OUT_NORMAL_F32 ? 1 : type == SRNG_OUT_F64 ? 2 : 4;
     // MRG32k3a whole-row items: doubles from each lane's registers with 32-byte
-    // stores, a quarter of them through the FP64 multiply, 4-byte values through
-    // the shared-memory row stage (the measured best of each at 2^18 x 4096)
-    t.vector_store = gen == SRNG_MRG32K3A && type == SRNG_OUT_F64 ? 4 : 1;
+    // stores, a quarter of them through the FP64 multiply; 4-byte values through
+    // the shared-memory row stage (the measured best of each at 2^18 x 4096),
+    // or, for streams cut into a multiple of 32 chunks (radix-32 chunk starts),
+    // from each lane's registers (0: decided by the call's shape; 64 x 2^16
+    // uint32 11.3 us per call against 13.4 staged)
+    t.vector_store = gen == SRNG_MRG32K3A ? (type == SRNG_OUT_F64 ? 4 : 0) : 1;
     // the FP64 direct rows run best with 6 or 7 resident blocks of 256 per SM
     // (2^18 x 4096: 1.75 ms, against 1.88 with the 8 its registers allow)
     t.resident = gen == SRNG_MRG32K3A && type == SRNG_OUT_F64 ? 6 : 0;
@@ -153,6 +156,29 @@ const JumpTable &jump_table(int shift, uint64_t base)
         m = mat_mul(m, m);
     }
     return g_tabs.emplace(key, t).first->second;
+}
+
+std::map<uint64_t, RadixTable> g_radix;  // chunk -> A^(chunk l), A^(32 chunk g)
+
+const RadixTable &radix_table(uint64_t chunk)
+{
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    auto it = g_radix.find(chunk);
+    if (it != g_radix.end()) return it->second;
+    RadixTable r;
+    const MatPair c = mat_pow_shifted(0, chunk, 0);
+    MatPair m = mat_identity();
+    for (int l = 0; l < 32; ++l) {
+        memcpy(r.lane[l], m.a, sizeof m.a);
+        m = mat_mul(m, c);
+    }
+    const MatPair w = m;  // A^(32 chunk)
+    m = mat_identity();
+    for (int g = 0; g < 32; ++g) {
+        memcpy(r.warp[g], m.a, sizeof m.a);
+        m = mat_mul(m, w);
+    }
+    return g_radix.emplace(chunk, r).first->second;
 }
 
 int bit_length(uint64_t x)
@@ -474,10 +500,9 @@ static srng_status generate_dev(srng_set *s, uint64_t b, uint64_t c, uint64_t n,
             const uint64_t splits = 4 * c >= 3 * resident || c >= want ? 1 : (want + c - 1) / c;
             chunk = (n + splits - 1) / splits;
             chunk = ((chunk + 31) / 32) * 32;
-            // a floor of 128 draws: a few long streams (64 x 2^16 FP64 draws)
-            // then run as 32,768 items, 23 us per call under graph replay
-            // against 36 us with 256-draw items and 25 us with 64-draw ones
-            if (chunk < 128) chunk = 128;
+            // a floor of 64 draws: a few long streams (64 x 2^16 FP64 draws)
+            // then run as 65,536 items with radix-32 chunk starts
+            if (chunk < 64) chunk = 64;
             // prefer a chunk that divides n (whole-row items, the fast kernel)
             for (uint64_t d = chunk; d <= 2 * chunk && d <= n; d += 32)
                 if (n % d == 0) { chunk = d; break; }
@@ -488,8 +513,11 @@ static srng_status generate_dev(srng_set *s, uint64_t b, uint64_t c, uint64_t n,
         a.nbits = bit_length(a.cps - 1);
         a.out = out;
         const JumpTable &tab = jump_table(0, chunk);
-        SRNG_CUDA_TRY(launch_mrg_generate(a, type, tab, t, stream, dev));
-        SRNG_CUDA_TRY(launch_mrg_apply(s->d_state, s->n_streams, b, c, mat_pow_shifted(0, n, 0), stream, dev));
+        const RadixTable *rt = a.cps >= 32 && a.cps % 32 == 0 ? &radix_table(chunk) : nullptr;
+        srng_tune tt = t;
+        if (!tt.vector_store) tt.vector_store = rt ? 3 : 1;
+        SRNG_CUDA_TRY(launch_mrg_generate(a, type, tab, tt, stream, dev, rt));
+        SRNG_CUDA_TRY(launch_mrg_apply(s->d_state, s->n_streams, b, c, mat_pow_shifted(0, n, 0), stream, dev, true));
     } else if (s->gen == SRNG_TINYMT32) {
         const uint64_t gs = s->tmt_group_size;
         TmtGenArgs a;

@@ -62,11 +62,21 @@ __device__ __forceinline__ void convert_k(const uint32_t *w, typename OutType<OU
     }
 }
 
+// The state advance that follows an MRG32k3a generation launch is launched
+// as its programmatic dependent: it may be scheduled once every block of the
+// generation kernel has started, and it waits for the whole kernel to finish
+// (and its memory to be visible) before it touches a state.
+__device__ __forceinline__ void allow_dependent_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ K2
 template <int OUT, bool VEC, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
     k_mrg_generate(const MrgGenArgs a, const __grid_constant__ JumpTable tab)
 {
+    allow_dependent_launch();
     using T = typename OutType<OUT>::T;
     constexpr int G = 128 / sizeof(T);    // elements per 128-byte row (32 or 16)
     constexpr int VPL = 16 / sizeof(T);   // elements per 16-byte vector (4 or 2)
@@ -158,6 +168,7 @@ template <int OUT, int WARPS, bool JUMP>
 __global__ void __launch_bounds__(WARPS * 32)
     k_mrg_generate_rows(const MrgGenArgs a, const __grid_constant__ JumpTable tab)
 {
+    allow_dependent_launch();
     using T = typename OutType<OUT>::T;
     constexpr int G = 128 / sizeof(T);    // elements per 128-byte row
     constexpr int VPL = 16 / sizeof(T);   // elements per 16 bytes
@@ -234,6 +245,7 @@ template <int OUT, int WARPS, bool JUMP, bool MIX = false>
 __global__ void __launch_bounds__(WARPS * 32)
     k_mrg_generate_direct(const MrgGenArgs a, const __grid_constant__ JumpTable tab)
 {
+    allow_dependent_launch();
     using T = typename OutType<OUT>::T;
     constexpr int EPQ = 32 / sizeof(T);  // values per 32-byte store
     T *out = static_cast<T *>(a.out);
@@ -249,6 +261,69 @@ __global__ void __launch_bounds__(WARPS * 32)
         if (JUMP)
             for (int k = 0; k < a.nbits; ++k)
                 if ((t >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
+        T *dst = out + item * a.chunk;
+        for (uint64_t j = 0; j < a.chunk; j += EPQ) {
+            uint32_t w[EPQ];
+            T v[EPQ];
+#pragma unroll
+            for (int e = 0; e < EPQ; ++e) w[e] = srng::mrg::step(s0, s1, s2, s3, s4, s5);
+            if constexpr (MIX && OUT == SRNG_OUT_F64) {
+                v[0] = srng::mrg::to_f64_dmul(w[0]);
+#pragma unroll
+                for (int e = 1; e < EPQ; ++e) v[e] = srng::mrg::to_f64(w[e]);
+            } else {
+                convert_k<SRNG_MRG32K3A, OUT, EPQ>(w, v);
+            }
+            const uint4 *p = reinterpret_cast<const uint4 *>(v);
+            st256(dst + j, p[0], p[1]);
+        }
+    }
+}
+
+// Direct rows with radix-32 chunk starts, for streams cut into a multiple of
+// 32 chunks: the 32 lanes of a warp take chunks t = 32 g + l (l the lane) of
+// one stream, so that A^(C t) splits into A^(32 C (g mod 32)) -- the same
+// matrix for the whole warp, read from the table in the parameters --,
+// A^(C 2^k) for each set bit k >= 10 of t (also warp-uniform), and the lane's
+// own A^(C l), read from a copy of the table in shared memory: at most two
+// products for up to 1024 chunks per stream, where the bitwise jumps take one
+// product per set bit of t and the warp waits for the slowest lane.
+template <int OUT, int WARPS, bool MIX = false>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_mrg_generate_radix(const MrgGenArgs a, const __grid_constant__ JumpTable tab,
+                         const __grid_constant__ RadixTable rt)
+{
+    allow_dependent_launch();
+    using T = typename OutType<OUT>::T;
+    constexpr int EPQ = 32 / sizeof(T);
+    __shared__ __align__(16) uint32_t lane_m[32][20];  // 80-byte rows: conflict-free 16-byte reads
+    for (int i = threadIdx.x; i < 32 * 18; i += WARPS * 32) lane_m[i / 18][i % 18] = rt.lane[i / 18][i % 18];
+    __syncthreads();
+    T *out = static_cast<T *>(a.out);
+    const int lane = threadIdx.x & 31;
+    const uint64_t n_items = a.s_count * a.cps;
+    const uint64_t stride = (uint64_t)gridDim.x * WARPS * 32;
+    for (uint64_t item = (uint64_t)blockIdx.x * WARPS * 32 + threadIdx.x; item < n_items; item += stride) {
+        const uint64_t s_rel = item / a.cps;
+        const uint64_t t = item - s_rel * a.cps;
+        const uint64_t s = a.s_begin + s_rel;
+        const uint64_t ns = a.n_streams;
+        uint32_t s0 = a.state[s], s1 = a.state[ns + s], s2 = a.state[2 * ns + s];
+        uint32_t s3 = a.state[3 * ns + s], s4 = a.state[4 * ns + s], s5 = a.state[5 * ns + s];
+        const uint32_t g = (uint32_t)(t >> 5) & 31u;
+        if (g) srng::mrg::jump(rt.warp[g], s0, s1, s2, s3, s4, s5);
+        for (int k = 10; k < a.nbits; ++k)
+            if ((t >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
+        if (lane) {
+            uint32_t m[20];
+            const uint4 *row = reinterpret_cast<const uint4 *>(lane_m[lane]);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const uint4 v = row[q];
+                m[4 * q] = v.x; m[4 * q + 1] = v.y; m[4 * q + 2] = v.z; m[4 * q + 3] = v.w;
+            }
+            srng::mrg::jump(m, s0, s1, s2, s3, s4, s5);
+        }
         T *dst = out + item * a.chunk;
         for (uint64_t j = 0; j < a.chunk; j += EPQ) {
             uint32_t w[EPQ];
@@ -632,9 +707,16 @@ void launch_limited(K k, unsigned grid, int threads, const srng_tune &t, cudaStr
     k<<<grid, threads, residency_smem(k, threads, t.resident), stream>>>(a, tab);
 }
 
+template <typename K>
+void launch_limited(K k, unsigned grid, int threads, const srng_tune &t, cudaStream_t stream, const MrgGenArgs &a,
+                    const JumpTable &tab, const RadixTable &rt)
+{
+    k<<<grid, threads, residency_smem(k, threads, t.resident), stream>>>(a, tab, rt);
+}
+
 template <int OUT>
 cudaError_t mrg_dispatch_rows(const MrgGenArgs &a, const JumpTable &tab, const srng_tune &t, cudaStream_t stream,
-                              const DeviceInfo &dev)
+                              const DeviceInfo &dev, const RadixTable *rt)
 {
     const uint64_t items = a.s_count * a.cps;
     const int warps = t.block_threads >= 256 ? 8 : 4;
@@ -645,6 +727,18 @@ cudaError_t mrg_dispatch_rows(const MrgGenArgs &a, const JumpTable &tab, const s
     // one item per stream (no chunk starts to reach): kernels without the jump code
     const bool jump = a.cps > 1;
     const unsigned g = (unsigned)blocks;
+    if (rt && jump && a.cps % 32 == 0 && (t.vector_store == 3 || t.vector_store == 4)) {
+        constexpr bool F64 = OUT == SRNG_OUT_F64;  // the mixed conversion exists for doubles only
+        const bool mix = F64 && t.vector_store == 4;
+        if (warps == 8) {
+            if (mix) launch_limited(k_mrg_generate_radix<OUT, 8, F64>, g, 256, t, stream, a, tab, *rt);
+            else launch_limited(k_mrg_generate_radix<OUT, 8, false>, g, 256, t, stream, a, tab, *rt);
+        } else {
+            if (mix) launch_limited(k_mrg_generate_radix<OUT, 4, F64>, g, 128, t, stream, a, tab, *rt);
+            else launch_limited(k_mrg_generate_radix<OUT, 4, false>, g, 128, t, stream, a, tab, *rt);
+        }
+        return cudaGetLastError();
+    }
     if constexpr (OUT == SRNG_OUT_F64) {
         if (t.vector_store == 4) {  // direct rows, a quarter of the doubles through the FP64 multiply
             if (warps == 8) {
@@ -679,14 +773,14 @@ cudaError_t mrg_dispatch_rows(const MrgGenArgs &a, const JumpTable &tab, const s
 
 template <int OUT>
 cudaError_t mrg_dispatch(const MrgGenArgs &a, const JumpTable &tab, const srng_tune &t, cudaStream_t stream,
-                         const DeviceInfo &dev)
+                         const DeviceInfo &dev, const RadixTable *rt)
 {
     using T = typename OutType<OUT>::T;
     constexpr uint64_t VPL = 16 / sizeof(T);
     constexpr uint64_t G = 128 / sizeof(T);
     if (t.vector_store != 2 && (reinterpret_cast<uintptr_t>(a.out) & 31) == 0 && a.n % a.chunk == 0 &&
         a.chunk % G == 0)
-        return mrg_dispatch_rows<OUT>(a, tab, t, stream, dev);
+        return mrg_dispatch_rows<OUT>(a, tab, t, stream, dev, rt);
     const bool vec_ok = t.vector_store != 2 && (reinterpret_cast<uintptr_t>(a.out) & 15) == 0 &&
                         a.n % VPL == 0 && a.chunk % VPL == 0;
     return vec_ok ? mrg_dispatch_warps<OUT, true>(a, tab, t, stream, dev)
@@ -751,14 +845,14 @@ cudaError_t philox_dispatch(const PhiloxGenArgs &a, const srng_tune &t, cudaStre
 }  // namespace
 
 cudaError_t launch_mrg_generate(const MrgGenArgs &a, srng_out type, const JumpTable &tab, const srng_tune &t,
-                                cudaStream_t stream, const DeviceInfo &dev)
+                                cudaStream_t stream, const DeviceInfo &dev, const RadixTable *rt)
 {
     switch (type) {
-    case SRNG_OUT_U32: return mrg_dispatch<SRNG_OUT_U32>(a, tab, t, stream, dev);
-    case SRNG_OUT_F32: return mrg_dispatch<SRNG_OUT_F32>(a, tab, t, stream, dev);
-    case SRNG_OUT_EXP_F32: return mrg_dispatch<SRNG_OUT_EXP_F32>(a, tab, t, stream, dev);
-    case SRNG_OUT_NORMAL_F32: return mrg_dispatch<SRNG_OUT_NORMAL_F32>(a, tab, t, stream, dev);
-    default: return mrg_dispatch<SRNG_OUT_F64>(a, tab, t, stream, dev);
+    case SRNG_OUT_U32: return mrg_dispatch<SRNG_OUT_U32>(a, tab, t, stream, dev, rt);
+    case SRNG_OUT_F32: return mrg_dispatch<SRNG_OUT_F32>(a, tab, t, stream, dev, rt);
+    case SRNG_OUT_EXP_F32: return mrg_dispatch<SRNG_OUT_EXP_F32>(a, tab, t, stream, dev, rt);
+    case SRNG_OUT_NORMAL_F32: return mrg_dispatch<SRNG_OUT_NORMAL_F32>(a, tab, t, stream, dev, rt);
+    default: return mrg_dispatch<SRNG_OUT_F64>(a, tab, t, stream, dev, rt);
     }
 }
 

@@ -80,6 +80,13 @@ struct JumpTable {
     uint32_t m[64][18];
 };
 
+// Radix-32 chunk starts: lane[l] = A^(C l) and warp[g] = A^(32 C g), l, g < 32,
+// for chunks of C draws (both components, 18 words each).
+struct RadixTable {
+    uint32_t lane[32][18];
+    uint32_t warp[32][18];
+};
+
 // ------------------------------------------------------------ kernels
 // K1: stream placement and jumps (jump.cu).
 // Slots [first, first + count) get streams index_base + slot: y0 times J_k for
@@ -87,8 +94,11 @@ struct JumpTable {
 cudaError_t launch_mrg_place(uint32_t *state, uint64_t n_streams, uint64_t first, uint64_t count,
                              uint64_t index_base, const uint32_t y0[6], const JumpTable &tab, int nbits,
                              cudaStream_t stream, const DeviceInfo &dev);
+// dependent: launched right after an MRG32k3a generation kernel on the same
+// stream, as its programmatic dependent (scheduled early, waits for it).
 cudaError_t launch_mrg_apply(uint32_t *state, uint64_t n_streams, uint64_t first, uint64_t count,
-                             const MatPair &m, cudaStream_t stream, const DeviceInfo &dev);
+                             const MatPair &m, cudaStream_t stream, const DeviceInfo &dev,
+                             bool dependent = false);
 cudaError_t launch_philox_advance(uint64_t *pos, uint64_t first, uint64_t count, uint64_t n,
                                   cudaStream_t stream, const DeviceInfo &dev);
 
@@ -102,8 +112,11 @@ struct MrgGenArgs {
     int nbits;            // table entries used for the chunk jumps
     void *out;
 };
+// rt: radix-32 chunk starts (used by the direct-row kernels when the chunk
+// count per stream is a multiple of 32), or null.
 cudaError_t launch_mrg_generate(const MrgGenArgs &a, srng_out type, const JumpTable &tab,
-                                const srng_tune &t, cudaStream_t stream, const DeviceInfo &dev);
+                                const srng_tune &t, cudaStream_t stream, const DeviceInfo &dev,
+                                const RadixTable *rt = nullptr);
 
 struct PhiloxGenArgs {
     uint64_t stream_base; // stream number of the set's slot 0

@@ -38,6 +38,9 @@ __global__ void __launch_bounds__(kThreads)
 __global__ void __launch_bounds__(kThreads)
     k_mrg_apply(uint32_t *__restrict__ st, uint64_t ns, uint64_t first, uint64_t count, const MatPair m)
 {
+    // launched as a programmatic dependent of a generation kernel: wait until
+    // that kernel has finished reading the states (no-op otherwise)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
         const uint64_t idx = first + i;
@@ -79,11 +82,24 @@ cudaError_t launch_mrg_place(uint32_t *state, uint64_t n_streams, uint64_t first
 }
 
 cudaError_t launch_mrg_apply(uint32_t *state, uint64_t n_streams, uint64_t first, uint64_t count,
-                             const MatPair &m, cudaStream_t stream, const DeviceInfo &dev)
+                             const MatPair &m, cudaStream_t stream, const DeviceInfo &dev, bool dependent)
 {
     if (count == 0) return cudaSuccess;
-    k_mrg_apply<<<grid_for(count, dev), kThreads, 0, stream>>>(state, n_streams, first, count, m);
-    return cudaGetLastError();
+    if (!dependent) {
+        k_mrg_apply<<<grid_for(count, dev), kThreads, 0, stream>>>(state, n_streams, first, count, m);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid_for(count, dev));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_mrg_apply, state, n_streams, first, count, m);
 }
 
 cudaError_t launch_philox_advance(uint64_t *pos, uint64_t first, uint64_t count, uint64_t n,

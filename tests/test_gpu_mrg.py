@@ -126,6 +126,31 @@ def test_tuning_never_changes_output(sets, tune, n):
     assert torch.equal(outs[0].view(torch.int64), outs[1].view(torch.int64))
 
 
+@pytest.mark.parametrize("out_type,vs", [(srng.SRNG_OUT_U32, 3), (srng.SRNG_OUT_F32, 3), (srng.SRNG_OUT_F64, 3),
+                                         (srng.SRNG_OUT_F64, 4)])
+@pytest.mark.parametrize("S,n,chunk,extra", [
+    (3, 1024, 32, {}),                          # 32 chunks per stream: lane products only
+    (5, 6144, 64, dict(block_threads=128)),     # 96 chunks: warp digits 0-2, 4-warp blocks
+    (7, 131072, 128, {}),                       # 1024 chunks: warp digits up to 31
+    (2, 65536, 32, {}),                         # 2048 chunks: bit 10 of the chunk index
+    (1, 131072, 32, {}),                        # 4096 chunks: bits 10 and 11
+    (64, 65536, 64, dict(blocks_per_sm=1)),     # more items than threads: grid-stride passes
+])
+def test_radix_chunk_starts_vs_oracle(sets, out_type, vs, S, n, chunk, extra):
+    """Direct rows with radix-32 chunk starts (chunk count a multiple of 32),
+    from the third stream of the set on, against the oracle in full."""
+    h = sets(srng.srng_create(srng.SRNG_MRG32K3A, 0xABCDEF, S + 2, srng.SRNG_SPACING_STREAM))
+    starts = get_states(h, 0, S + 2)
+    _, out = empty(S * n, out_type)
+    srng.srng_generate_tuned(h, 2, S, n, out_type, out, dict(chunk=chunk, vector_store=vs, **extra))
+    torch.cuda.synchronize()
+    ref, final = O.mrg_bulk(starts[2:], n, out_type)
+    assert_bitexact(to_np(out, out_type).reshape(S, n), ref, out_type)
+    after = get_states(h, 0, S + 2)
+    assert np.array_equal(after[2:], final)
+    assert np.array_equal(after[:2], starts[:2])
+
+
 def test_state_save_restore_resumes(sets):
     """Checkpoint mid-stream, continue, restore, continue again: same draws."""
     h = sets(srng.srng_create(srng.SRNG_MRG32K3A, 5, 10))
