@@ -532,6 +532,13 @@ def extras(torch, srng, dev, stream, peak, wfill, cpu_seconds):
             srng.srng_generate(h, 0, 64, 1 << 16, srng.SRNG_OUT_F64, o, side)
     gg, _ = _time(torch, stream, g2.replay)
     del g2
+    # the state advance alone (the call's second, dependent launch), 20 per graph
+    g3 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g3, stream=side):
+        for _ in range(20):
+            srng.srng_jump(h, 0, 64, srng.SRNG_JUMP_DRAWS, 1 << 16, side)
+    ga, _ = _time(torch, stream, g3.replay)
+    del g3
     call(stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -542,6 +549,7 @@ def extras(torch, srng, dev, stream, peak, wfill, cpu_seconds):
     cpu["C1"] = {"Guniforms_s": (64 << 16) / t_or / 1e9, "cores": threads, "sample": "whole workload"}
     us = gb / 20 * 1e3
     summ["C1"] = {"us_per_call_graph": us, "us_per_call_plain": best * 1e3, "us_per_generate_graph": gg / 20 * 1e3,
+                  "us_per_advance_graph": ga / 20 * 1e3,
                   "Guniforms_s": (64 << 16) / us / 1e3, **_fracs((64 << 16) * 8, us / 1e3, peak, wfill)}
     det["mrg_plain_64x65536_f64"] = {"plain_ms_best": best, "plain_ms_median": med, "graph_20_calls_ms": gb}
     del g, o

@@ -151,6 +151,37 @@ def test_radix_chunk_starts_vs_oracle(sets, out_type, vs, S, n, chunk, extra):
     assert np.array_equal(after[:2], starts[:2])
 
 
+@pytest.mark.parametrize("out_type,tune", [(srng.SRNG_OUT_F64, dict(chunk=64)),   # radix-32 chunk starts
+                                           (srng.SRNG_OUT_U32, dict(chunk=64)),
+                                           (srng.SRNG_OUT_F64, dict(chunk=4096))])  # one item per stream
+def test_graph_replay_of_generate_calls(sets, out_type, tune):
+    """Three generation calls captured in one CUDA graph (each a generation
+    kernel and its dependent state advance), replayed twice: the buffers hold
+    the second replay's draws and the states moved by six calls, as the oracle
+    says."""
+    S, n, K = 8, 4096, 3
+    h = sets(srng.srng_create(srng.SRNG_MRG32K3A, 99, S, srng.SRNG_SPACING_STREAM))
+    starts = get_states(h, 0, S)
+    bufs = [empty(S * n, out_type)[1] for _ in range(K)]
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        srng.srng_generate_tuned(h, 0, S, n, out_type, bufs[0], tune, side)  # warm-up outside the capture
+        srng.srng_reset(h, side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        for k in range(K):
+            srng.srng_generate_tuned(h, 0, S, n, out_type, bufs[k], tune, side)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    ref, final = O.mrg_bulk(starts, 2 * K * n, out_type)
+    for k in range(K):
+        want = ref[:, (K + k) * n:(K + k + 1) * n]
+        assert_bitexact(to_np(bufs[k], out_type).reshape(S, n), want, out_type)
+    assert np.array_equal(get_states(h, 0, S), final)
+
+
 def test_state_save_restore_resumes(sets):
     """Checkpoint mid-stream, continue, restore, continue again: same draws."""
     h = sets(srng.srng_create(srng.SRNG_MRG32K3A, 5, 10))
