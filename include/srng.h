@@ -125,10 +125,10 @@ typedef struct srng_set srng_set;
  *                   always coalesced); 3 = MRG32k3a whole-chunk rows written
  *                   by each lane directly with 32-byte stores (one full
  *                   sector per lane), else as 1; 4 = as 3, and for MRG32k3a
- *                   FP64 output the first double of every four is the FP64
- *                   multiply z * norm itself while the rest are built from
- *                   integers (the same bits), so the FP64 unit shares the
- *                   conversion work.  Default: 1 for the counter-based
+ *                   FP64 output three of every eight doubles (the 1st, 5th
+ *                   and 7th) are the FP64 multiply z * norm itself while the
+ *                   rest are built from integers (the same bits), so the FP64
+ *                   unit shares the conversion work.  Default: 1 for the counter-based
  *                   generators and TinyMT32; for MRG32k3a 4 for FP64, and
  *                   for 4-byte values 3 when every stream of the call is cut
  *                   into a multiple of 32 chunks, else 1

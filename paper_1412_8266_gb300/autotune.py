@@ -10,7 +10,7 @@ and device (name and SM count).
 Search spaces (all values valid for every problem):
   MRG32k3a  block_threads x resident blocks/SM x chunk (draws per thread item)
             x store path (shared-memory staged rows or direct per-lane rows;
-            for FP64 also direct rows with a quarter of the doubles through
+            for FP64 also direct rows with three in eight doubles through
             the FP64 multiply)
   Philox    block_threads x unroll (blocks per thread per trip) x blocks/SM
   batch     chunk (MRG32k3a) x lane_blocks (Philox) per work item
@@ -27,7 +27,7 @@ import paper_1412_8266_gb300 as srng
 
 MRG_SPACE = [dict(block_threads=bt, blocks_per_sm=b, chunk=c, vector_store=v)
              for bt, b, c, v in itertools.product((128, 256), (4, 8), (512, 1024, 2048, 4096), (1, 3))]
-# FP64 adds the direct rows with a quarter of the doubles through the FP64 multiply
+# FP64 adds the direct rows with three in eight doubles through the FP64 multiply
 # (with at most 6 resident blocks per SM, the FP64 default, or as many as fit: 32)
 MRG_SPACE_F64 = MRG_SPACE + [dict(block_threads=bt, blocks_per_sm=b, chunk=c, vector_store=4, resident=r)
                              for bt, b, c, r in itertools.product((128, 256), (4, 8), (512, 1024, 2048, 4096),

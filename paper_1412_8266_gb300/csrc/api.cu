@@ -77,7 +77,7 @@ srng_tune builtin_tune(srng_gen gen, srng_out type)
     // doubles: two pairs (2^30 Philox doubles 1.20 ms, against 1.28 with four)
     t.unroll = type == SRNG_OUT_EXP_F32 || type == SRNG_OUT_NORMAL_F32 ? 1 : type == SRNG_OUT_F64 ? 2 : 4;
     // MRG32k3a whole-row items: doubles from each lane's registers with 32-byte
-    // stores, a quarter of them through the FP64 multiply; 4-byte values through
+    // stores, three in eight through the FP64 multiply; 4-byte values through
     // the shared-memory row stage (the measured best of each at 2^18 x 4096),
     // or, for streams cut into a multiple of 32 chunks (radix-32 chunk starts),
     // from each lane's registers (0: decided by the call's shape; 64 x 2^16

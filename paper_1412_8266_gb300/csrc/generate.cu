@@ -234,20 +234,61 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
 }
 
+// One lane's row of `chunk` values (a multiple of 8) from its registers, with
+// 32-byte stores.  DMUL (FP64 only, a mask over each eight doubles): the doubles
+// at its set positions are the FP64 multiply z * norm itself (the definition)
+// and the others are built from integers -- the same bits -- so the FP64 unit,
+// otherwise idle, takes part of the conversions off the integer pipes.  The
+// throughput-bound bulk rows take three in eight (0x51: the 1st, 5th and 7th;
+// one half makes the FP64 unit the bottleneck), the latency-bound rows of a few
+// long streams one in four (0x11: the multiply's latency sits in each lane's
+// chain there).
+constexpr uint32_t kDmulBulk = 0x51, kDmulLatency = 0x11;
+
+template <int OUT, uint32_t DMUL>
+__device__ __forceinline__ void lane_row(typename OutType<OUT>::T *dst, uint64_t chunk, uint32_t &s0, uint32_t &s1,
+                                         uint32_t &s2, uint32_t &s3, uint32_t &s4, uint32_t &s5)
+{
+    using T = typename OutType<OUT>::T;
+    constexpr int EPQ = 32 / sizeof(T);  // values per 32-byte store
+    if constexpr (DMUL != 0 && OUT == SRNG_OUT_F64) {
+        constexpr uint32_t kDmul = DMUL;
+        for (uint64_t j = 0; j < chunk; j += 2 * EPQ) {
+            uint32_t w[2 * EPQ];
+            T v[2 * EPQ];
+#pragma unroll
+            for (int e = 0; e < 2 * EPQ; ++e) w[e] = srng::mrg::step(s0, s1, s2, s3, s4, s5);
+#pragma unroll
+            for (int e = 0; e < 2 * EPQ; ++e)
+                v[e] = ((kDmul >> e) & 1) ? srng::mrg::to_f64_dmul(w[e]) : srng::mrg::to_f64(w[e]);
+            const uint4 *p = reinterpret_cast<const uint4 *>(v);
+            st256(dst + j, p[0], p[1]);
+            st256(dst + j + EPQ, p[2], p[3]);
+        }
+    } else {
+        for (uint64_t j = 0; j < chunk; j += EPQ) {
+            uint32_t w[EPQ];
+            T v[EPQ];
+#pragma unroll
+            for (int e = 0; e < EPQ; ++e) w[e] = srng::mrg::step(s0, s1, s2, s3, s4, s5);
+            convert_k<SRNG_MRG32K3A, OUT, EPQ>(w, v);
+            const uint4 *p = reinterpret_cast<const uint4 *>(v);
+            st256(dst + j, p[0], p[1]);
+        }
+    }
+}
+
 // K2, uniform rows, direct: each lane writes its own row with 32-byte stores
 // straight from registers -- every store fills one whole 32-byte sector, 32
 // sectors per warp instruction, no shared-memory transpose.  Same preconditions
-// as k_mrg_generate_rows.  MIX (FP64 only): the first double of each group of
-// four is the FP64 multiply z * norm itself (the definition), the other three
-// are built from integers -- the same bits -- so the FP64 unit, otherwise
-// idle, takes a quarter of the conversions off the integer pipes.
+// as k_mrg_generate_rows.  MIX: three in eight FP64 conversions on the FP64 unit
+// (lane_row).
 template <int OUT, int WARPS, bool JUMP, bool MIX = false>
 __global__ void __launch_bounds__(WARPS * 32)
     k_mrg_generate_direct(const MrgGenArgs a, const __grid_constant__ JumpTable tab)
 {
     allow_dependent_launch();
     using T = typename OutType<OUT>::T;
-    constexpr int EPQ = 32 / sizeof(T);  // values per 32-byte store
     T *out = static_cast<T *>(a.out);
     const uint64_t n_items = a.s_count * a.cps;
     const uint64_t stride = (uint64_t)gridDim.x * WARPS * 32;
@@ -261,22 +302,7 @@ __global__ void __launch_bounds__(WARPS * 32)
         if (JUMP)
             for (int k = 0; k < a.nbits; ++k)
                 if ((t >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
-        T *dst = out + item * a.chunk;
-        for (uint64_t j = 0; j < a.chunk; j += EPQ) {
-            uint32_t w[EPQ];
-            T v[EPQ];
-#pragma unroll
-            for (int e = 0; e < EPQ; ++e) w[e] = srng::mrg::step(s0, s1, s2, s3, s4, s5);
-            if constexpr (MIX && OUT == SRNG_OUT_F64) {
-                v[0] = srng::mrg::to_f64_dmul(w[0]);
-#pragma unroll
-                for (int e = 1; e < EPQ; ++e) v[e] = srng::mrg::to_f64(w[e]);
-            } else {
-                convert_k<SRNG_MRG32K3A, OUT, EPQ>(w, v);
-            }
-            const uint4 *p = reinterpret_cast<const uint4 *>(v);
-            st256(dst + j, p[0], p[1]);
-        }
+        lane_row<OUT, MIX ? kDmulBulk : 0u>(out + item * a.chunk, a.chunk, s0, s1, s2, s3, s4, s5);
     }
 }
 
@@ -287,7 +313,8 @@ __global__ void __launch_bounds__(WARPS * 32)
 // A^(C 2^k) for each set bit k >= 10 of t (also warp-uniform), and the lane's
 // own A^(C l), read from a copy of the table in shared memory: at most two
 // products for up to 1024 chunks per stream, where the bitwise jumps take one
-// product per set bit of t and the warp waits for the slowest lane.
+// product per set bit of t and the warp waits for the slowest lane.  MIX: one in
+// four FP64 conversions on the FP64 unit (lane_row).
 template <int OUT, int WARPS, bool MIX = false>
 __global__ void __launch_bounds__(WARPS * 32)
     k_mrg_generate_radix(const MrgGenArgs a, const __grid_constant__ JumpTable tab,
@@ -295,7 +322,6 @@ __global__ void __launch_bounds__(WARPS * 32)
 {
     allow_dependent_launch();
     using T = typename OutType<OUT>::T;
-    constexpr int EPQ = 32 / sizeof(T);
     __shared__ __align__(16) uint32_t lane_m[32][20];  // 80-byte rows: conflict-free 16-byte reads
     for (int i = threadIdx.x; i < 32 * 18; i += WARPS * 32) lane_m[i / 18][i % 18] = rt.lane[i / 18][i % 18];
     __syncthreads();
@@ -324,22 +350,7 @@ __global__ void __launch_bounds__(WARPS * 32)
             }
             srng::mrg::jump(m, s0, s1, s2, s3, s4, s5);
         }
-        T *dst = out + item * a.chunk;
-        for (uint64_t j = 0; j < a.chunk; j += EPQ) {
-            uint32_t w[EPQ];
-            T v[EPQ];
-#pragma unroll
-            for (int e = 0; e < EPQ; ++e) w[e] = srng::mrg::step(s0, s1, s2, s3, s4, s5);
-            if constexpr (MIX && OUT == SRNG_OUT_F64) {
-                v[0] = srng::mrg::to_f64_dmul(w[0]);
-#pragma unroll
-                for (int e = 1; e < EPQ; ++e) v[e] = srng::mrg::to_f64(w[e]);
-            } else {
-                convert_k<SRNG_MRG32K3A, OUT, EPQ>(w, v);
-            }
-            const uint4 *p = reinterpret_cast<const uint4 *>(v);
-            st256(dst + j, p[0], p[1]);
-        }
+        lane_row<OUT, MIX ? kDmulLatency : 0u>(out + item * a.chunk, a.chunk, s0, s1, s2, s3, s4, s5);
     }
 }
 
@@ -740,7 +751,7 @@ cudaError_t mrg_dispatch_rows(const MrgGenArgs &a, const JumpTable &tab, const s
         return cudaGetLastError();
     }
     if constexpr (OUT == SRNG_OUT_F64) {
-        if (t.vector_store == 4) {  // direct rows, a quarter of the doubles through the FP64 multiply
+        if (t.vector_store == 4) {  // direct rows, three in eight doubles through the FP64 multiply
             if (warps == 8) {
                 if (jump) launch_limited(k_mrg_generate_direct<OUT, 8, true, true>, g, 256, t, stream, a, tab);
                 else launch_limited(k_mrg_generate_direct<OUT, 8, false, true>, g, 256, t, stream, a, tab);
