@@ -225,6 +225,16 @@ __device__ __forceinline__ double to_f64_dmul(uint32_t z)
 {
     return __dmul_rn((double)z, 0x1.000000d00000bp-32);
 }
+
+/* The same value through one FP64 fused multiply-add and no conversion: the
+ * double with high word 0x43300000 and low word z is 2^52 + z exactly, and
+ * (2^52 + z) norm - 2^52 norm is z norm exactly (2^52 norm is a double), so the
+ * FMA's single rounding gives RN(z norm), the definition. */
+__device__ __forceinline__ double to_f64_fma(uint32_t z)
+{
+    constexpr double kNorm = 0x1.000000d00000bp-32;
+    return __fma_rn(__hiloint2double(0x43300000, (int)z), kNorm, -0x1p52 * kNorm);
+}
 }  // namespace mrg
 
 /* ------------------------------------------------------ Philox4x32-10 maths */

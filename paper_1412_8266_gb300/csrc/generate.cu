@@ -236,16 +236,17 @@ __global__ void __launch_bounds__(WARPS * 32)
 
 // One lane's row of `chunk` values (a multiple of 8) from its registers, with
 // 32-byte stores.  DMUL (FP64 only, a mask over each eight doubles): the doubles
-// at its set positions are the FP64 multiply z * norm itself (the definition)
-// and the others are built from integers -- the same bits -- so the FP64 unit,
-// otherwise idle, takes part of the conversions off the integer pipes.  The
-// throughput-bound bulk rows take three in eight (0x51: the 1st, 5th and 7th;
-// one half makes the FP64 unit the bottleneck), the latency-bound rows of a few
-// long streams one in four (0x11: the multiply's latency sits in each lane's
-// chain there).
-constexpr uint32_t kDmulBulk = 0x51, kDmulLatency = 0x11;
+// at its set positions come from the FP64 unit -- the multiply z * norm itself
+// (the definition), or with FMA its one-instruction form (2^52 + z) norm -
+// 2^52 norm -- and the others are built from integers, all the same bits, so
+// the FP64 unit, otherwise idle, takes part of the conversions off the integer
+// pipes.  The throughput-bound bulk rows take three in eight through the
+// multiply (0x51: the 1st, 5th and 7th; one half makes the FP64 unit the
+// bottleneck, and the FMA form measured slower there), the latency-bound rows
+// of a few long streams one half through the FMA form (0x55).
+constexpr uint32_t kDmulBulk = 0x51, kDmulLatency = 0x55;
 
-template <int OUT, uint32_t DMUL>
+template <int OUT, uint32_t DMUL, bool FMA = false>
 __device__ __forceinline__ void lane_row(typename OutType<OUT>::T *dst, uint64_t chunk, uint32_t &s0, uint32_t &s1,
                                          uint32_t &s2, uint32_t &s3, uint32_t &s4, uint32_t &s5)
 {
@@ -260,7 +261,9 @@ __device__ __forceinline__ void lane_row(typename OutType<OUT>::T *dst, uint64_t
             for (int e = 0; e < 2 * EPQ; ++e) w[e] = srng::mrg::step(s0, s1, s2, s3, s4, s5);
 #pragma unroll
             for (int e = 0; e < 2 * EPQ; ++e)
-                v[e] = ((kDmul >> e) & 1) ? srng::mrg::to_f64_dmul(w[e]) : srng::mrg::to_f64(w[e]);
+                v[e] = !((kDmul >> e) & 1) ? srng::mrg::to_f64(w[e])
+                       : FMA                   ? srng::mrg::to_f64_fma(w[e])
+                                               : srng::mrg::to_f64_dmul(w[e]);
             const uint4 *p = reinterpret_cast<const uint4 *>(v);
             st256(dst + j, p[0], p[1]);
             st256(dst + j + EPQ, p[2], p[3]);
@@ -313,8 +316,8 @@ __global__ void __launch_bounds__(WARPS * 32)
 // A^(C 2^k) for each set bit k >= 10 of t (also warp-uniform), and the lane's
 // own A^(C l), read from a copy of the table in shared memory: at most two
 // products for up to 1024 chunks per stream, where the bitwise jumps take one
-// product per set bit of t and the warp waits for the slowest lane.  MIX: one in
-// four FP64 conversions on the FP64 unit (lane_row).
+// product per set bit of t and the warp waits for the slowest lane.  MIX: one
+// half of the FP64 conversions as one FMA each on the FP64 unit (lane_row).
 template <int OUT, int WARPS, bool MIX = false>
 __global__ void __launch_bounds__(WARPS * 32)
     k_mrg_generate_radix(const MrgGenArgs a, const __grid_constant__ JumpTable tab,
@@ -350,7 +353,7 @@ __global__ void __launch_bounds__(WARPS * 32)
             }
             srng::mrg::jump(m, s0, s1, s2, s3, s4, s5);
         }
-        lane_row<OUT, MIX ? kDmulLatency : 0u>(out + item * a.chunk, a.chunk, s0, s1, s2, s3, s4, s5);
+        lane_row<OUT, MIX ? kDmulLatency : 0u, true>(out + item * a.chunk, a.chunk, s0, s1, s2, s3, s4, s5);
     }
 }
 

@@ -283,3 +283,25 @@ def test_paper_form_tinymt(paper_form_lib):
     st = O.tinymt32_stream_starts(seed & 0xFFFFFFFF, prm, 256, n)
     ref, _ = O.tinymt32_bulk(st, prm, 256, 2, O.OUT_F32)
     assert np.array_equal(out.cpu().numpy().view(np.uint32).reshape(n, 2), ref.view(np.uint32))
+
+
+def test_mrg_f64_forms_agree_exhaustively(tmp_path):
+    """The three forms of the MRG32k3a double the generation kernels mix -- built
+    from integers, the FP64 multiply, and the one-FMA form -- agree bit for bit
+    for every z in [1, m1] (the integer-built form is compared with the IEEE
+    product in the conversion tests)."""
+    nvcc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    if not os.path.exists(nvcc):
+        nvcc = shutil.which("nvcc")
+    assert nvcc, "nvcc is needed to build the check"
+    out = str(tmp_path / "libforms.so")
+    subprocess.run([nvcc, "-shared", "-Xcompiler", "-fPIC", "-O2", "-gencode", "arch=compute_103a,code=sm_103a",
+                    "-I", os.path.join(ROOT, "include"), os.path.join(HERE, "cuda", "mrg_f64_forms.cu"),
+                    "-o", out], check=True)
+    lib = ctypes.CDLL(out)
+    lib.run_mrg_f64_forms.restype = ctypes.c_int
+    lib.run_mrg_f64_forms.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_ulonglong),
+                                      ctypes.POINTER(ctypes.c_ulonglong)]
+    bad, first = ctypes.c_ulonglong(0), ctypes.c_ulonglong(0)
+    assert lib.run_mrg_f64_forms(1, O.M1, ctypes.byref(bad), ctypes.byref(first)) == 0
+    assert bad.value == 0, f"{bad.value} values differ, the first at z = {first.value}"
