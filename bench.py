@@ -17,8 +17,8 @@ summarised under "summary" in the same JSON line, with fractions of both the
 measured copy peak and a write-only fill measured in the same run; "parity"
 holds the oracle comparisons of every configuration's outputs (sampled rows,
 runs, instances) and "cpu_baseline.per_config" the oracle's rate on each.
-The full record (tunes, medians, the other generators) goes to
-gpurun_out/bench_details.json when that folder exists.
+The full record (tunes, medians, the other generators) goes to the file
+named by $SRNG_BENCH_DETAILS, when that is set.
 
 --impl reference times the CPU oracle (the plain definition, OpenMP over
 streams) on the host cores on a bounded sample of the same workload.
@@ -427,12 +427,9 @@ def _rounded(x, nd=4):
 
 
 def write_details(details):
-    """The long per-workload record (tunes, every timing) goes to a file beside
-    the run, not into the one JSON line: gpurun_out/ when that folder exists,
-    else $SRNG_BENCH_DETAILS, else nowhere."""
+    """The long per-workload record (tunes, every timing) goes to a file, not
+    into the one JSON line: the one $SRNG_BENCH_DETAILS names, else nowhere."""
     path = os.environ.get("SRNG_BENCH_DETAILS")
-    if not path and os.path.isdir(os.path.join(ROOT, "gpurun_out")):
-        path = os.path.join(ROOT, "gpurun_out", "bench_details.json")
     if path:
         with open(path, "w") as f:
             json.dump(details, f, indent=1)
