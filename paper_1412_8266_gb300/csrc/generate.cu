@@ -14,10 +14,11 @@
 //
 // K3 (Philox4x32-10, Threefry4x32-20 and Threefry4x64-20, Sec. 4.3):
 // counter-based, so any position is computed directly.  A block of threads
-// covers a contiguous run of 4-word groups of one stream (k_philox_generate),
-// or the flat list of (stream, group pair) of many short streams
-// (k_philox_generate_flat); each lane writes its pair of groups -- eight
-// values -- with 32-byte stores, so a warp store covers 1 KiB (u32 / f32).
+// covers a contiguous run of 4-word groups of one stream (k_philox_generate):
+// each lane writes its pair of groups -- eight values -- with 32-byte stores,
+// so a warp store covers 1 KiB (u32 / f32); or the flat list of (stream, run
+// of U block pairs) of many short streams (k_philox_generate_flat), each lane
+// writing its run with 32-byte stores.
 //
 // Algorithmic HBM bytes per output value: the value's size (4 or 8); states
 // and positions add 24 and 8 bytes per stream per call.
@@ -517,43 +518,36 @@ __device__ __forceinline__ uint32_t divide(uint32_t n, const Divider &v)
 }
 
 // Flat Philox generation for many short streams: the work is the flat list of
-// (stream, block pair) with pps pairs per stream; consecutive lanes take
-// consecutive pairs, so a warp's 32-byte stores stay contiguous within a
-// stream and no lane idles at a stream's end beyond one pair.
+// (stream, group) with gps groups per stream, a group being U consecutive block
+// pairs of one stream, so that the division of the group index, the stream's
+// position load and its key or counter words are paid once per U pairs (the
+// key-per-stream layout gains most); no lane idles at a stream's end beyond
+// its last group.  Every store is a full 32-byte sector.
 template <int OUT, int U, bool VEC, int CIPHER>
 __global__ void __launch_bounds__(256)
-    k_philox_generate_flat(const PhiloxGenArgs a, uint32_t total_pairs, const Divider pps)
+    k_philox_generate_flat(const PhiloxGenArgs a, uint32_t total_groups, const Divider gps)
 {
     using T = typename OutType<OUT>::T;
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t p0 = blockIdx.x * blockDim.x + threadIdx.x; p0 < total_pairs; p0 += U * stride) {
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total_groups; g += stride) {
+        const uint32_t s_rel = divide(g, gps);
+        const uint64_t b0 = 2ull * U * (g - s_rel * gps.d);  // first block of the group
+        const uint64_t slot = a.s_begin + s_rel;
+        const uint64_t pos = a.pos[slot];
+        const uint32_t al = (uint32_t)pos & cb_align_mask<CIPHER>();
+        const uint64_t nb = (al + a.n + 3) >> 2;
+        const uint64_t s = a.stream_base + slot;
+        uint32_t kk0 = a.k0, kk1 = a.k1, c2, c3;
+        if (a.keyed) { kk0 = (uint32_t)s; kk1 = (uint32_t)(s >> 32); c2 = a.k0; c3 = a.k1; }
+        else { c2 = (uint32_t)s; c3 = (uint32_t)(s >> 32); }
+        const uint64_t q0 = (pos - al) >> 2;
+        T *row = static_cast<T *>(a.out) + (uint64_t)s_rel * a.n;
         uint32_t x[U][8];
-        uint64_t bb[U];
-        uint32_t srel[U], al[U];
-        bool ok[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {  // U independent pairs (2U Philox blocks) in flight
-            const uint32_t p = p0 + u * stride;
-            const uint32_t s_rel = p < total_pairs ? divide(p, pps) : 0u;
-            const uint64_t b = 2ull * (p - s_rel * pps.d);  // first block of the pair
-            const uint64_t slot = a.s_begin + s_rel;
-            const uint64_t pos = a.pos[slot];
-            al[u] = (uint32_t)pos & cb_align_mask<CIPHER>();
-            ok[u] = p < total_pairs && b < ((al[u] + a.n + 3) >> 2);
-            srel[u] = s_rel;
-            bb[u] = b;
-            const uint64_t s = a.stream_base + slot;
-            uint32_t kk0 = a.k0, kk1 = a.k1, c2, c3;
-            if (a.keyed) { kk0 = (uint32_t)s; kk1 = (uint32_t)(s >> 32); c2 = a.k0; c3 = a.k1; }
-            else { c2 = (uint32_t)s; c3 = (uint32_t)(s >> 32); }
-            cb_pair<CIPHER, true>(((pos - al[u]) >> 2) + b, x[u], kk0, kk1, c2, c3);
-        }
+        for (int u = 0; u < U; ++u) cb_pair<CIPHER, true>(q0 + b0 + 2 * u, x[u], kk0, kk1, c2, c3);
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (!ok[u]) continue;
-            T *row = static_cast<T *>(a.out) + (uint64_t)srel[u] * a.n;
-            store8<SRNG_PHILOX4X32_10, OUT, VEC>(row, (int64_t)(bb[u] * 4) - al[u], a.n, x[u]);
-        }
+        for (int u = 0; u < U; ++u)
+            if (b0 + 2 * u < nb) store8<SRNG_PHILOX4X32_10, OUT, VEC>(row, (int64_t)((b0 + 2 * u) * 4) - al, a.n, x[u]);
     }
 }
 
@@ -831,11 +825,13 @@ cudaError_t philox_dispatch(const PhiloxGenArgs &a, const srng_tune &t, cudaStre
     const uint32_t threads = t.block_threads ? t.block_threads : 256;
     const uint64_t tile_pairs = (uint64_t)threads * (t.unroll ? t.unroll : 4);
     if (a.s_count > 1 && pps < tile_pairs && a.s_count * pps < (1ull << 32)) {
-        const uint32_t total = (uint32_t)(a.s_count * pps);
+        const uint32_t uu = t.unroll == 1 ? 1u : t.unroll == 4 ? 4u : 2u;  // pairs per group (the kernel's U)
+        const uint64_t gps = (pps + uu - 1) / uu;                             // groups per stream
+        const uint32_t total = (uint32_t)(a.s_count * gps);
         uint64_t blocks = (total + threads - 1) / threads;
         const uint64_t cap = (uint64_t)dev.sm_count * (t.blocks_per_sm ? t.blocks_per_sm : 2048 / threads);
         if (blocks > cap) blocks = cap;
-        const Divider dv = make_divider((uint32_t)pps);
+        const Divider dv = make_divider((uint32_t)gps);
         const bool vec = t.vector_store != 2;
         if (t.unroll == 1) {
             if (vec) k_philox_generate_flat<OUT, 1, true, CIPHER><<<(unsigned)blocks, threads, 0, stream>>>(a, total, dv);
