@@ -820,11 +820,13 @@ template <int OUT, int CIPHER>
 cudaError_t philox_dispatch(const PhiloxGenArgs &a, const srng_tune &t, cudaStream_t stream, const DeviceInfo &dev)
 {
     // Many short streams: the flat kernel (no idle lanes at stream ends), when
-    // the pair count fits 32 bits and a stream is shorter than one tile.
+    // a stream is shorter than one tile and the pair count stays below 2^31 (so
+    // the kernel's 32-bit group index plus its grid stride, below 2^22, cannot
+    // wrap).
     const uint64_t pps = ((a.n + cb_align_mask<CIPHER>() + 3) / 4 + 1) / 2;  // block pairs per stream, any start offset
     const uint32_t threads = t.block_threads ? t.block_threads : 256;
     const uint64_t tile_pairs = (uint64_t)threads * (t.unroll ? t.unroll : 4);
-    if (a.s_count > 1 && pps < tile_pairs && a.s_count * pps < (1ull << 32)) {
+    if (a.s_count > 1 && pps < tile_pairs && a.s_count * pps < (1ull << 31)) {
         const uint32_t uu = t.unroll == 1 ? 1u : t.unroll == 4 ? 4u : 2u;  // pairs per group (the kernel's U)
         const uint64_t gps = (pps + uu - 1) / uu;                             // groups per stream
         const uint32_t total = (uint32_t)(a.s_count * gps);
