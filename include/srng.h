@@ -291,7 +291,11 @@ srng_status srng_jump(srng_set *set, uint64_t stream_begin, uint64_t count, srng
  * [stream_begin, stream_begin + stream_count) into out_dev (stream-major, see
  * above; needs stream_count * n_per_stream * sizeof(type) bytes, any
  * alignment of the element size; 16-byte alignment is fastest) and move the
- * streams forward by n_per_stream draws.  Asynchronous on cuda_stream. */
+ * streams forward by n_per_stream draws.  Asynchronous on cuda_stream.
+ * MRG32k3a: the call's state advance is launched as a programmatic dependent
+ * of its generation kernel (scheduled while the last blocks run, it waits for
+ * the kernel to finish); the advance itself allows no early launch, so work
+ * the caller enqueues after the call starts only when both have finished. */
 srng_status srng_generate(srng_set *set, uint64_t stream_begin, uint64_t stream_count,
                           uint64_t n_per_stream, srng_out type, void *out_dev, void *cuda_stream);
 
