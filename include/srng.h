@@ -461,7 +461,7 @@ typedef struct srng_server_config {
     uint64_t budget_bytes;      /* output pool allocated at create (0: 16 GiB)                 */
     uint32_t max_inflight;      /* steps on the device at once, 1..8 (0: 4)                    */
     uint32_t max_step_requests; /* request parts per step, 1..65536 (0: 4096)                  */
-    uint64_t max_step_draws;    /* draws per step (0: 2^25); larger requests span steps        */
+    uint64_t max_step_draws;    /* draws per step (0: 2^30); larger requests span steps        */
     uint32_t chunk;             /* MRG32k3a draws per lane chunk, multiple of 32 (0: 512)      */
     uint32_t lane_blocks;       /* Philox blocks per lane per work item (0: 64)                */
     uint32_t reserved[4];

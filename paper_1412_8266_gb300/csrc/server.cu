@@ -414,7 +414,10 @@ srng_status srng_server_create(srng_server **out, srng_set *set, const srng_serv
     if (!c.budget_bytes) c.budget_bytes = 16ull << 30;
     if (!c.max_inflight) c.max_inflight = 4;
     if (!c.max_step_requests) c.max_step_requests = 4096;
-    if (!c.max_step_draws) c.max_step_draws = 1ull << 25;
+    // steps of up to 2^30 draws: the serving workload's saturation throughput
+    // grows with the step (2^25: 535 Guniforms/s, 2^27: 723, 2^30: 806) and
+    // its latency at the offered load does not suffer (p99 356 -> 285 us)
+    if (!c.max_step_draws) c.max_step_draws = 1ull << 30;
     if (!c.chunk) c.chunk = 512;
     if (!c.lane_blocks) c.lane_blocks = 64;
     if (c.max_inflight > 8 || c.max_step_requests > 65536 || c.chunk % 32 || c.lane_blocks > 4096 ||
