@@ -117,6 +117,39 @@ def test_full_size_philox_bulk_sampled():
         srng.srng_destroy(h)
 
 
+@pytest.mark.parametrize("gen", [srng.SRNG_PHILOX4X32_10, srng.SRNG_PHILOX4X32_10_KEYED])
+@pytest.mark.parametrize("tune", [None, dict(unroll=2)])
+def test_full_size_many_streams_sampled(gen, tune):
+    """The many-short-streams workload at full size: 2^18 streams x 4096 words
+    (the flat kernel, a run of block pairs per lane), then every stream moved 3
+    draws on and 4096 more words from there (unaligned starts).  Sampled
+    streams and both ends are compared with the oracle in full; every
+    position moved by 4096 + 3 + 4096."""
+    seed, S, n = 0xC0FFEE, 1 << 18, 4096
+    h = srng.srng_create(gen, seed, S)
+    try:
+        out = torch.empty(S * n, dtype=torch.int32, device="cuda")
+        rng = np.random.default_rng(8)
+        pick = np.unique(np.concatenate([[0, 1, S - 1], rng.integers(0, S, 253)]))
+        sel = torch.from_numpy(pick).cuda()
+        for start in (0, n + 3):
+            if start:
+                srng.srng_jump(h, 0, S, srng.SRNG_JUMP_DRAWS, 3)
+            srng.srng_generate_tuned(h, 0, S, n, srng.SRNG_OUT_U32, out, tune)
+            torch.cuda.synchronize()
+            got = out.view(S, n)[sel].cpu().numpy().view(np.uint32)
+            if gen == srng.SRNG_PHILOX4X32_10:
+                ref = np.stack([O.philox_generate(key_of(seed), int(s), start, n) for s in pick])
+            else:
+                ref = np.stack([O.philox_keyed_generate(seed, int(s), start, n) for s in pick])
+            assert np.array_equal(got, ref), start
+        pos = np.zeros(S, dtype=np.uint64)
+        srng.srng_get_state(h, 0, S, pos)
+        assert np.all(pos == 2 * n + 3)
+    finally:
+        srng.srng_destroy(h)
+
+
 def test_position_overflow_is_rejected(philox_set):
     h = philox_set(1, 1)
     srng.srng_jump(h, 0, 1, srng.SRNG_JUMP_DRAWS, 2**64 - 10)
