@@ -377,10 +377,13 @@ __global__ void __launch_bounds__(kWarps * 32, FAM == kFamMrg ? (OUT == SRNG_OUT
 }
 
 // Instance start states: MRG32k3a = A^offset applied to the stream's state
-// (J_k = A^(2^k)); Philox = stream position + offset.
-__global__ void __launch_bounds__(256) k_batch_setup(BatchInst *inst, uint64_t n, const __grid_constant__ JumpTable tab)
+// (J_k = A^(2^k)); Philox = stream position + offset.  `zero`, if given, is a
+// work counter set to 0 here (one stream operation less than a memset).
+__global__ void __launch_bounds__(256)
+    k_batch_setup(BatchInst *inst, uint64_t n, const __grid_constant__ JumpTable tab, uint32_t *zero)
 {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && zero) *zero = 0u;
     if (i >= n) return;
     BatchInst &in = inst[i];
     if (in.gen == SRNG_MRG32K3A) {
@@ -517,7 +520,7 @@ static int occupancy_blocks_fam(srng_out type)
 }
 
 
-cudaError_t launch_batch_setup(BatchInst *d_inst, uint64_t n, cudaStream_t s)
+cudaError_t launch_batch_setup(BatchInst *d_inst, uint64_t n, cudaStream_t s, uint32_t *zero)
 {
     if (n == 0) return cudaSuccess;
     static std::once_flag once;
@@ -525,7 +528,7 @@ cudaError_t launch_batch_setup(BatchInst *d_inst, uint64_t n, cudaStream_t s)
     std::call_once(once, [] {
         for (int k = 0; k < 64; ++k) memcpy(unit_tab.m[k], mat_pow2(k).a, sizeof unit_tab.m[k]);
     });
-    k_batch_setup<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_inst, n, unit_tab);
+    k_batch_setup<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_inst, n, unit_tab, zero);
     return cudaGetLastError();
 }
 
@@ -690,7 +693,7 @@ srng_status srng_batch_plan_create(srng_batch_plan **out, srng_set *const *sets,
             JumpTable unit_tab;  // J_k = A^(2^k)
             for (int k = 0; k < 64; ++k) memcpy(unit_tab.m[k], mat_pow2(k).a, sizeof unit_tab.m[k]);
             const unsigned g = (unsigned)((n_inst + 255) / 256);
-            k_batch_setup<<<g, 256, 0, stream>>>(p.d_inst, n_inst, unit_tab);
+            k_batch_setup<<<g, 256, 0, stream>>>(p.d_inst, n_inst, unit_tab, nullptr);
             PLAN_TRY(cudaGetLastError());
         }
     }

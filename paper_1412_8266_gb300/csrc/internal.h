@@ -173,7 +173,8 @@ struct BatchArgs {
 // Launchers shared by the batch plan and the server.
 // Instance start states: MRG32k3a = A^offset applied to the stream state;
 // Philox = stream position + offset (reads src_* fields, writes st / pos).
-cudaError_t launch_batch_setup(BatchInst *d_inst, uint64_t n, cudaStream_t s);
+// zero: a work counter the kernel sets to 0 (or null)
+cudaError_t launch_batch_setup(BatchInst *d_inst, uint64_t n, cudaStream_t s, uint32_t *zero = nullptr);
 // The persistent batch kernel over a.n_items items, all MRG32k3a (mrg) or all
 // counter-based (!mrg); a.counter must be zero.
 // Work-item families of the batch kernels: each kernel holds code for one.

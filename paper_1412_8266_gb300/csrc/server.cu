@@ -223,12 +223,11 @@ srng_status launch_step(srng_server *srv, Slot &sl)
     if (n_inst == 0) return SRNG_OK;
     SRNG_CUDA_TRY(cudaMemcpyAsync(sl.d_inst, sl.h_inst, n_inst * sizeof(BatchInst), cudaMemcpyHostToDevice, sl.stream));
     SRNG_CUDA_TRY(cudaMemcpyAsync(sl.d_items, sl.h_items, n_items * sizeof(uint2), cudaMemcpyHostToDevice, sl.stream));
-    SRNG_CUDA_TRY(launch_batch_setup(sl.d_inst, n_inst, sl.stream));
+    SRNG_CUDA_TRY(launch_batch_setup(sl.d_inst, n_inst, sl.stream, sl.d_counter));  // also zeroes the work counter
     const bool mrg = set->gen == SRNG_MRG32K3A;
     if (mrg)  // each item's first-chunk state, so a lane reaches its chunk with one jump
         SRNG_CUDA_TRY(launch_batch_item_states(sl.d_inst, sl.d_items, n_items, srv->chunk_tab, sl.d_item_state,
                                                sl.stream));
-    SRNG_CUDA_TRY(cudaMemsetAsync(sl.d_counter, 0, sizeof(uint32_t), sl.stream));
     BatchArgs a;
     memset(&a, 0, sizeof a);
     a.inst = sl.d_inst;
