@@ -105,6 +105,20 @@ struct Pool {
 
 using namespace srng_impl;
 
+// MRG32k3a lane chunks of a step: its jump table (A^(chunk 2^k)) and lane table
+// (A^(chunk l), l < 32, on the device).
+struct ChunkCfg {
+    uint64_t chunk = 0;
+    JumpTable tab;
+    uint32_t *d_lane_tab = nullptr;
+};
+// Default chunks: steps of fewer than kSmallStepDraws draws take 256-draw
+// chunks (more lanes for a small step: lower latency), larger steps 1024
+// (fewer work items: higher throughput).  Serving workload, 20k req/s:
+// 512 everywhere p50 83 us / saturation 805 Guniforms/s; 256: 67 us / 790;
+// 1024: 120 us / 810.
+constexpr uint64_t kSmallChunk = 256, kLargeChunk = 1024, kSmallStepDraws = 1ull << 27;
+
 struct srng_server {
     srng_set *set = nullptr;
     srng_server_config cfg;
@@ -112,8 +126,8 @@ struct srng_server {
     unsigned grid[3] = {0, 0, 0};
     char *pool_mem = nullptr;
     Pool pool;
-    JumpTable chunk_tab;
-    uint32_t *d_lane_tab = nullptr;  // A^(chunk l), l < 32 (MRG32k3a sets)
+    ChunkCfg ck[2];                  // [0]: the small (or only) chunk, [1]: the large one
+    int n_ck = 1;
     std::vector<Slot> slots;
     uint32_t cap_items = 0;
 
@@ -173,7 +187,24 @@ srng_status launch_step(srng_server *srv, Slot &sl)
     uint64_t budget = srv->cfg.max_step_draws;
     uint32_t n_inst = 0, n_items = 0;
     int type = -1;
-    const uint64_t chunk = srv->cfg.chunk, lane_blocks = srv->cfg.lane_blocks;
+    // the step's chunk: the large one once the draws it can take reach kSmallStepDraws
+    int ci = 0;
+    if (srv->n_ck == 2) {
+        uint64_t want = 0;
+        uint32_t parts = 0;
+        int t0 = -1;
+        for (uint64_t id : srv->active) {
+            if (want >= kSmallStepDraws || parts >= srv->cfg.max_step_requests) break;
+            const Req &r = srv->reqs[id];
+            if (t0 < 0) t0 = r.type;
+            if ((int)r.type != t0) continue;
+            want += r.n - r.scheduled;
+            ++parts;
+        }
+        ci = std::min(want, srv->cfg.max_step_draws) >= kSmallStepDraws ? 1 : 0;
+    }
+    const ChunkCfg &ck = srv->ck[ci];
+    const uint64_t chunk = ck.chunk, lane_blocks = srv->cfg.lane_blocks;
     for (auto it = srv->active.begin(); it != srv->active.end() && budget && n_inst < srv->cfg.max_step_requests;) {
         Req &r = srv->reqs[*it];
         if (type < 0) type = r.type;
@@ -226,7 +257,7 @@ srng_status launch_step(srng_server *srv, Slot &sl)
     SRNG_CUDA_TRY(launch_batch_setup(sl.d_inst, n_inst, sl.stream, sl.d_counter));  // also zeroes the work counter
     const bool mrg = set->gen == SRNG_MRG32K3A;
     if (mrg)  // each item's first-chunk state, so a lane reaches its chunk with one jump
-        SRNG_CUDA_TRY(launch_batch_item_states(sl.d_inst, sl.d_items, n_items, srv->chunk_tab, sl.d_item_state,
+        SRNG_CUDA_TRY(launch_batch_item_states(sl.d_inst, sl.d_items, n_items, ck.tab, sl.d_item_state,
                                                sl.stream));
     BatchArgs a;
     memset(&a, 0, sizeof a);
@@ -239,9 +270,9 @@ srng_status launch_step(srng_server *srv, Slot &sl)
     a.mode = SRNG_BATCH_WRITE;
     a.out = srv->pool_mem;
     a.item_state = mrg ? sl.d_item_state : nullptr;
-    a.lane_tab = mrg ? srv->d_lane_tab : nullptr;
+    a.lane_tab = mrg ? ck.d_lane_tab : nullptr;
     const unsigned grid = std::max(1u, std::min(srv->grid[type], (n_items + 7) / 8));
-    SRNG_CUDA_TRY(launch_batch(a, (srng_out)type, batch_family(set), srv->chunk_tab, grid, sl.stream));
+    SRNG_CUDA_TRY(launch_batch(a, (srng_out)type, batch_family(set), ck.tab, grid, sl.stream));
     SRNG_CUDA_TRY(cudaEventRecord(sl.ev, sl.stream));
     sl.busy = true;
     srv->steps++;
@@ -397,7 +428,8 @@ void server_free(srng_server *srv)
         if (sl.d_item_state) cudaFree(sl.d_item_state);
         if (sl.d_counter) cudaFree(sl.d_counter);
     }
-    if (srv->d_lane_tab) cudaFree(srv->d_lane_tab);
+    for (ChunkCfg &k : srv->ck)
+        if (k.d_lane_tab) cudaFree(k.d_lane_tab);
     if (srv->pool_mem) cudaFree(srv->pool_mem);
     delete srv;
 }
@@ -423,7 +455,6 @@ srng_status srng_server_create(srng_server **out, srng_set *set, const srng_serv
     // grows with the step (2^25: 535 Guniforms/s, 2^27: 723, 2^30: 806) and
     // its latency at the offered load does not suffer (p99 356 -> 285 us)
     if (!c.max_step_draws) c.max_step_draws = 1ull << 30;
-    if (!c.chunk) c.chunk = 512;
     if (!c.lane_blocks) c.lane_blocks = 64;
     if (c.max_inflight > 8 || c.max_step_requests > 65536 || c.chunk % 32 || c.lane_blocks > 4096 ||
         c.max_step_draws > (1ull << 34))
@@ -446,9 +477,13 @@ srng_status srng_server_create(srng_server **out, srng_set *set, const srng_serv
         srv->grid[t] = (unsigned)(sms * batch_blocks_per_sm((srng_out)t, batch_family(set)));
     SRV_TRY(cudaMalloc(&srv->pool_mem, c.budget_bytes));
     srv->pool.init(c.budget_bytes / 256 * 256);
-    chunk_jump_table(c.chunk, &srv->chunk_tab);
+    srv->n_ck = c.chunk ? 1 : 2;
+    srv->ck[0].chunk = c.chunk ? c.chunk : kSmallChunk;
+    srv->ck[1].chunk = kLargeChunk;
+    for (int k = 0; k < srv->n_ck; ++k) chunk_jump_table(srv->ck[k].chunk, &srv->ck[k].tab);
     {
-        const uint64_t per_item = set->gen == SRNG_MRG32K3A ? 32ull * c.chunk : 32ull * c.lane_blocks * 4;
+        // item buffers sized for the smallest chunk over a whole step
+        const uint64_t per_item = set->gen == SRNG_MRG32K3A ? 32ull * srv->ck[0].chunk : 32ull * c.lane_blocks * 4;
         srv->cap_items = (uint32_t)(c.max_step_draws / per_item + 2ull * c.max_step_requests + 2);
     }
     srv->slots.resize(c.max_inflight);
@@ -464,10 +499,12 @@ srng_status srng_server_create(srng_server **out, srng_set *set, const srng_serv
             SRV_TRY(cudaMalloc(&sl.d_item_state, srv->cap_items * 6 * sizeof(uint32_t)));
     }
     if (set->gen == SRNG_MRG32K3A) {
-        uint32_t lane_tab[32 * 18];
-        lane_jump_table(c.chunk, lane_tab);
-        SRV_TRY(cudaMalloc(&srv->d_lane_tab, sizeof lane_tab));
-        SRV_TRY(cudaMemcpy(srv->d_lane_tab, lane_tab, sizeof lane_tab, cudaMemcpyHostToDevice));
+        for (int k = 0; k < srv->n_ck; ++k) {
+            uint32_t lane_tab[32 * 18];
+            lane_jump_table(srv->ck[k].chunk, lane_tab);
+            SRV_TRY(cudaMalloc(&srv->ck[k].d_lane_tab, sizeof lane_tab));
+            SRV_TRY(cudaMemcpy(srv->ck[k].d_lane_tab, lane_tab, sizeof lane_tab, cudaMemcpyHostToDevice));
+        }
     }
 #undef SRV_TRY
     try {

@@ -41,9 +41,11 @@ def _alone(set_h, stream, pos, n, out_type, dtype):
     return out.cpu().numpy()
 
 
-def test_mixed_requests_equal_oracle_and_alone(mrg_set):
+@pytest.mark.parametrize("extra", [{}, dict(chunk=96), dict(chunk=1024)])
+def test_mixed_requests_equal_oracle_and_alone(mrg_set, extra):
+    """Default per-step chunks and fixed ones give the same outputs."""
     rng = np.random.default_rng(2)
-    srv = srng.srng_server_create(mrg_set, dict(budget_bytes=64 << 20, max_step_draws=1 << 18, max_inflight=4))
+    srv = srng.srng_server_create(mrg_set, dict(budget_bytes=64 << 20, max_step_draws=1 << 18, max_inflight=4, **extra))
     try:
         reqs = []
         pos = {}
