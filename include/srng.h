@@ -463,7 +463,7 @@ typedef struct srng_server_config {
     uint32_t max_step_requests; /* request parts per step, 1..65536 (0: 4096)                  */
     uint64_t max_step_draws;    /* draws per step (0: 2^30); larger requests span steps        */
     uint32_t chunk;             /* MRG32k3a draws per lane chunk, multiple of 32 (0: by step:  */
-                                /* 256 below 2^27 draws, else 1024)                           */
+                                /* 128 below 2^23 draws, 256 below 2^27, else 1024)            */
     uint32_t lane_blocks;       /* Philox blocks per lane per work item (0: 64)                */
     uint32_t reserved[4];
 } srng_server_config;

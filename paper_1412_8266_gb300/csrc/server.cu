@@ -112,12 +112,15 @@ struct ChunkCfg {
     JumpTable tab;
     uint32_t *d_lane_tab = nullptr;
 };
-// Default chunks: steps of fewer than kSmallStepDraws draws take 256-draw
-// chunks (more lanes for a small step: lower latency), larger steps 1024
-// (fewer work items: higher throughput).  Serving workload, 20k req/s:
-// 512 everywhere p50 83 us / saturation 805 Guniforms/s; 256: 67 us / 790;
-// 1024: 120 us / 810.
-constexpr uint64_t kSmallChunk = 256, kLargeChunk = 1024, kSmallStepDraws = 1ull << 27;
+// Default chunks by the draws a step can take: below kStepDraws[0] 128-draw
+// chunks, below kStepDraws[1] 256, else 1024 -- more lanes for a small step
+// (lower latency), fewer work items for a large one (higher throughput).
+// Serving workload, 20k req/s, one chunk for every step: 128 p50 62 us /
+// saturation 763 Guniforms/s; 256: 67 us / 790; 512: 83 us / 805; 1024:
+// 120 us / 810.
+constexpr int kChunks = 3;
+constexpr uint64_t kDefaultChunk[kChunks] = {128, 256, 1024};
+constexpr uint64_t kStepDraws[kChunks - 1] = {1ull << 23, 1ull << 27};
 
 struct srng_server {
     srng_set *set = nullptr;
@@ -126,7 +129,7 @@ struct srng_server {
     unsigned grid[3] = {0, 0, 0};
     char *pool_mem = nullptr;
     Pool pool;
-    ChunkCfg ck[2];                  // [0]: the small (or only) chunk, [1]: the large one
+    ChunkCfg ck[kChunks];            // by step size, smallest first ([0] only: a configured chunk)
     int n_ck = 1;
     std::vector<Slot> slots;
     uint32_t cap_items = 0;
@@ -187,21 +190,22 @@ srng_status launch_step(srng_server *srv, Slot &sl)
     uint64_t budget = srv->cfg.max_step_draws;
     uint32_t n_inst = 0, n_items = 0;
     int type = -1;
-    // the step's chunk: the large one once the draws it can take reach kSmallStepDraws
+    // the step's chunk, by the draws it can take (capped once past the last threshold)
     int ci = 0;
-    if (srv->n_ck == 2) {
+    if (srv->n_ck > 1) {
         uint64_t want = 0;
         uint32_t parts = 0;
         int t0 = -1;
         for (uint64_t id : srv->active) {
-            if (want >= kSmallStepDraws || parts >= srv->cfg.max_step_requests) break;
+            if (want >= kStepDraws[kChunks - 2] || parts >= srv->cfg.max_step_requests) break;
             const Req &r = srv->reqs[id];
             if (t0 < 0) t0 = r.type;
             if ((int)r.type != t0) continue;
             want += r.n - r.scheduled;
             ++parts;
         }
-        ci = std::min(want, srv->cfg.max_step_draws) >= kSmallStepDraws ? 1 : 0;
+        want = std::min(want, srv->cfg.max_step_draws);
+        while (ci < srv->n_ck - 1 && want >= kStepDraws[ci]) ++ci;
     }
     const ChunkCfg &ck = srv->ck[ci];
     const uint64_t chunk = ck.chunk, lane_blocks = srv->cfg.lane_blocks;
@@ -477,9 +481,8 @@ srng_status srng_server_create(srng_server **out, srng_set *set, const srng_serv
         srv->grid[t] = (unsigned)(sms * batch_blocks_per_sm((srng_out)t, batch_family(set)));
     SRV_TRY(cudaMalloc(&srv->pool_mem, c.budget_bytes));
     srv->pool.init(c.budget_bytes / 256 * 256);
-    srv->n_ck = c.chunk ? 1 : 2;
-    srv->ck[0].chunk = c.chunk ? c.chunk : kSmallChunk;
-    srv->ck[1].chunk = kLargeChunk;
+    srv->n_ck = c.chunk ? 1 : kChunks;
+    for (int k = 0; k < kChunks; ++k) srv->ck[k].chunk = c.chunk ? c.chunk : kDefaultChunk[k];
     for (int k = 0; k < srv->n_ck; ++k) chunk_jump_table(srv->ck[k].chunk, &srv->ck[k].tab);
     {
         // item buffers sized for the smallest chunk over a whole step
