@@ -52,8 +52,10 @@ struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     bool busy = false;
+    // one host-to-device copy per step: the step's descriptors, then (16-byte
+    // aligned) its work items, in one page-locked buffer and its device twin
     BatchInst *h_inst = nullptr, *d_inst = nullptr;
-    uint2 *h_items = nullptr, *d_items = nullptr;
+    uint2 *h_items = nullptr;  // work items as the step is gathered
     uint32_t *d_item_state = nullptr;  // MRG32k3a items' first-chunk states (6 words each)
     uint32_t *d_counter = nullptr;
     std::vector<std::pair<uint64_t, uint64_t>> parts;  // (ticket, draws) of the step in flight
@@ -256,17 +258,20 @@ srng_status launch_step(srng_server *srv, Slot &sl)
         else ++it;
     }
     if (n_inst == 0) return SRNG_OK;
-    SRNG_CUDA_TRY(cudaMemcpyAsync(sl.d_inst, sl.h_inst, n_inst * sizeof(BatchInst), cudaMemcpyHostToDevice, sl.stream));
-    SRNG_CUDA_TRY(cudaMemcpyAsync(sl.d_items, sl.h_items, n_items * sizeof(uint2), cudaMemcpyHostToDevice, sl.stream));
+    const size_t items_off = (n_inst * sizeof(BatchInst) + 15) / 16 * 16;
+    memcpy(reinterpret_cast<char *>(sl.h_inst) + items_off, sl.h_items, n_items * sizeof(uint2));
+    SRNG_CUDA_TRY(cudaMemcpyAsync(sl.d_inst, sl.h_inst, items_off + n_items * sizeof(uint2), cudaMemcpyHostToDevice,
+                                  sl.stream));
+    uint2 *const d_items = reinterpret_cast<uint2 *>(reinterpret_cast<char *>(sl.d_inst) + items_off);
     SRNG_CUDA_TRY(launch_batch_setup(sl.d_inst, n_inst, sl.stream, sl.d_counter));  // also zeroes the work counter
     const bool mrg = set->gen == SRNG_MRG32K3A;
     if (mrg)  // each item's first-chunk state, so a lane reaches its chunk with one jump
-        SRNG_CUDA_TRY(launch_batch_item_states(sl.d_inst, sl.d_items, n_items, ck.tab, sl.d_item_state,
+        SRNG_CUDA_TRY(launch_batch_item_states(sl.d_inst, d_items, n_items, ck.tab, sl.d_item_state,
                                                sl.stream));
     BatchArgs a;
     memset(&a, 0, sizeof a);
     a.inst = sl.d_inst;
-    a.items = sl.d_items;
+    a.items = d_items;
     a.counter = sl.d_counter;
     a.n_items = n_items;
     a.chunk = chunk;
@@ -428,7 +433,6 @@ void server_free(srng_server *srv)
         if (sl.h_inst) cudaFreeHost(sl.h_inst);
         if (sl.h_items) cudaFreeHost(sl.h_items);
         if (sl.d_inst) cudaFree(sl.d_inst);
-        if (sl.d_items) cudaFree(sl.d_items);
         if (sl.d_item_state) cudaFree(sl.d_item_state);
         if (sl.d_counter) cudaFree(sl.d_counter);
     }
@@ -493,10 +497,11 @@ srng_status srng_server_create(srng_server **out, srng_set *set, const srng_serv
     for (Slot &sl : srv->slots) {
         SRV_TRY(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
         SRV_TRY(cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming));
-        SRV_TRY(cudaMallocHost(&sl.h_inst, c.max_step_requests * sizeof(BatchInst)));
+        const size_t desc_bytes = (c.max_step_requests * sizeof(BatchInst) + 15) / 16 * 16 +
+                                  srv->cap_items * sizeof(uint2);
+        SRV_TRY(cudaMallocHost(&sl.h_inst, desc_bytes));
         SRV_TRY(cudaMallocHost(&sl.h_items, srv->cap_items * sizeof(uint2)));
-        SRV_TRY(cudaMalloc(&sl.d_inst, c.max_step_requests * sizeof(BatchInst)));
-        SRV_TRY(cudaMalloc(&sl.d_items, srv->cap_items * sizeof(uint2)));
+        SRV_TRY(cudaMalloc(&sl.d_inst, desc_bytes));
         SRV_TRY(cudaMalloc(&sl.d_counter, sizeof(uint32_t)));
         if (set->gen == SRNG_MRG32K3A)
             SRV_TRY(cudaMalloc(&sl.d_item_state, srv->cap_items * 6 * sizeof(uint32_t)));
