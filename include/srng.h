@@ -472,7 +472,8 @@ typedef struct srng_server_stats {
     uint64_t submitted, completed, rejected;
     uint64_t draws_completed;
     uint64_t steps;             /* steps launched                                              */
-    uint64_t kernels;           /* kernels launched (set-up, MRG32k3a item starts, batch)      */
+    uint64_t kernels;           /* kernels launched: set-up, MRG32k3a item starts (one kernel  */
+                                /* for both in a small MRG32k3a step), batch                   */
     double p50_us, p99_us;      /* latency, submission -> completion seen by the dispatcher    */
     double mean_us, max_us;
     double wall_s;              /* first submission -> last completion                         */

@@ -415,6 +415,42 @@ __global__ void __launch_bounds__(256)
     o[0] = s0; o[1] = s1; o[2] = s2; o[3] = s3; o[4] = s4; o[5] = s5;
 }
 
+// The same state straight from the stream's state, for small steps of the
+// server: A^offset (J_k = A^(2^k), `unit`) then A^(chunk first) (`tab`) per
+// item, so no set-up kernel runs before it (each item repeats its instance's
+// offset jump); `zero` is the step's work counter, set to 0 here.
+__global__ void __launch_bounds__(256)
+    k_batch_item_states_direct(const BatchInst *inst, const uint2 *items, uint64_t n,
+                               const __grid_constant__ JumpTable unit, const __grid_constant__ JumpTable tab,
+                               uint32_t *item_state, uint32_t *zero)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && zero) *zero = 0u;
+    if (i >= n) return;
+    const uint2 item = items[i];
+    const BatchInst &in = inst[item.x];
+    const uint64_t ns = in.src_ns, s = in.stream;
+    uint32_t s0 = in.src_state[s], s1 = in.src_state[ns + s], s2 = in.src_state[2 * ns + s];
+    uint32_t s3 = in.src_state[3 * ns + s], s4 = in.src_state[4 * ns + s], s5 = in.src_state[5 * ns + s];
+    for (int k = 0; k < 64; ++k)
+        if ((in.offset >> k) & 1) srng::mrg::jump(unit.m[k], s0, s1, s2, s3, s4, s5);
+    for (int k = 0; k < 32; ++k)
+        if ((item.y >> k) & 1) srng::mrg::jump(tab.m[k], s0, s1, s2, s3, s4, s5);
+    uint32_t *o = item_state + 6 * i;
+    o[0] = s0; o[1] = s1; o[2] = s2; o[3] = s3; o[4] = s4; o[5] = s5;
+}
+
+// J_k = A^(2^k), k < 64 (built once).
+const JumpTable &unit_jump_table()
+{
+    static std::once_flag once;
+    static JumpTable unit_tab;
+    std::call_once(once, [] {
+        for (int k = 0; k < 64; ++k) memcpy(unit_tab.m[k], mat_pow2(k).a, sizeof unit_tab.m[k]);
+    });
+    return unit_tab;
+}
+
 }  // namespace
 
 // Host-side plan.
@@ -523,12 +559,17 @@ static int occupancy_blocks_fam(srng_out type)
 cudaError_t launch_batch_setup(BatchInst *d_inst, uint64_t n, cudaStream_t s, uint32_t *zero)
 {
     if (n == 0) return cudaSuccess;
-    static std::once_flag once;
-    static JumpTable unit_tab;  // J_k = A^(2^k)
-    std::call_once(once, [] {
-        for (int k = 0; k < 64; ++k) memcpy(unit_tab.m[k], mat_pow2(k).a, sizeof unit_tab.m[k]);
-    });
-    k_batch_setup<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_inst, n, unit_tab, zero);
+    k_batch_setup<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_inst, n, unit_jump_table(), zero);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_item_states_direct(const BatchInst *d_inst, const uint2 *d_items, uint64_t n,
+                                            const JumpTable &chunk_tab, uint32_t *item_state, uint32_t *zero,
+                                            cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_batch_item_states_direct<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_inst, d_items, n, unit_jump_table(),
+                                                                          chunk_tab, item_state, zero);
     return cudaGetLastError();
 }
 

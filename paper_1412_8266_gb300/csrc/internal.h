@@ -186,6 +186,11 @@ cudaError_t launch_batch(const BatchArgs &a, srng_out type, BatchFamily fam, con
 // item_state[6 i + j], items[0, n) all MRG32k3a.
 cudaError_t launch_batch_item_states(const BatchInst *d_inst, const uint2 *d_items, uint64_t n,
                                      const JumpTable &chunk_tab, uint32_t *item_state, cudaStream_t s);
+// The same from the stream states directly (no set-up kernel needed before it);
+// zero: the step's work counter, set to 0.
+cudaError_t launch_batch_item_states_direct(const BatchInst *d_inst, const uint2 *d_items, uint64_t n,
+                                            const JumpTable &chunk_tab, uint32_t *item_state, uint32_t *zero,
+                                            cudaStream_t s);
 // Lane table of the chunk size: A^(chunk l), l < 32, 18 words each (host).
 void lane_jump_table(uint64_t chunk, uint32_t out[32 * 18]);
 // Resident blocks per SM of the batch kernel for `type`.

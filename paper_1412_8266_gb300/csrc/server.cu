@@ -121,6 +121,9 @@ struct ChunkCfg {
 // saturation 763 Guniforms/s; 256: 67 us / 790; 512: 83 us / 805; 1024:
 // 120 us / 810.
 constexpr int kChunks = 3;
+// MRG32k3a steps of at most this many work items set up their item states in
+// one kernel straight from the stream states
+constexpr uint32_t kDirectItemStates = 4096;
 constexpr uint64_t kDefaultChunk[kChunks] = {128, 256, 1024};
 constexpr uint64_t kStepDraws[kChunks - 1] = {1ull << 23, 1ull << 27};
 
@@ -263,11 +266,21 @@ srng_status launch_step(srng_server *srv, Slot &sl)
     SRNG_CUDA_TRY(cudaMemcpyAsync(sl.d_inst, sl.h_inst, items_off + n_items * sizeof(uint2), cudaMemcpyHostToDevice,
                                   sl.stream));
     uint2 *const d_items = reinterpret_cast<uint2 *>(reinterpret_cast<char *>(sl.d_inst) + items_off);
-    SRNG_CUDA_TRY(launch_batch_setup(sl.d_inst, n_inst, sl.stream, sl.d_counter));  // also zeroes the work counter
     const bool mrg = set->gen == SRNG_MRG32K3A;
-    if (mrg)  // each item's first-chunk state, so a lane reaches its chunk with one jump
-        SRNG_CUDA_TRY(launch_batch_item_states(sl.d_inst, d_items, n_items, ck.tab, sl.d_item_state,
-                                               sl.stream));
+    // each MRG32k3a item's first-chunk state, so a lane reaches its chunk with one
+    // jump: for a small step straight from the stream states in one kernel (the
+    // set-up kernel's launch saved), else after a set-up kernel per instance
+    // (each instance's offset jump done once); both zero the work counter
+    const bool direct = mrg && n_items <= kDirectItemStates;
+    if (direct) {
+        SRNG_CUDA_TRY(launch_batch_item_states_direct(sl.d_inst, d_items, n_items, ck.tab, sl.d_item_state,
+                                                      sl.d_counter, sl.stream));
+    } else {
+        SRNG_CUDA_TRY(launch_batch_setup(sl.d_inst, n_inst, sl.stream, sl.d_counter));
+        if (mrg)
+            SRNG_CUDA_TRY(launch_batch_item_states(sl.d_inst, d_items, n_items, ck.tab, sl.d_item_state,
+                                                   sl.stream));
+    }
     BatchArgs a;
     memset(&a, 0, sizeof a);
     a.inst = sl.d_inst;
@@ -285,7 +298,7 @@ srng_status launch_step(srng_server *srv, Slot &sl)
     SRNG_CUDA_TRY(cudaEventRecord(sl.ev, sl.stream));
     sl.busy = true;
     srv->steps++;
-    srv->kernels += mrg ? 3 : 2;
+    srv->kernels += mrg && !direct ? 3 : 2;
     return SRNG_OK;
 }
 
