@@ -841,6 +841,22 @@ def run_case(args):
         tune = json.loads(args.case_tune) if args.case_tune else None
         fn = lambda: srng.srng_generate_tuned(h, 0, S, N_DRAWS, t, o, tune, stream)
         nbytes, nvals = o.numel() * o.element_size(), o.numel()
+    elif c == "serving":
+        # the serving trace replayed once at its offered rate through the default server
+        from paper_1412_8266_gb300 import workload as W
+        trace = [(r.arrival_s, r.stream, r.n) for r in W.serving_trace(1.0)]
+        h = srng.srng_create_from_state([12345] * 6, W.SERVING["n_streams"], srng.SRNG_SPACING_SUBSTREAM, stream)
+        srv = srng.srng_server_create(h, dict(budget_bytes=W.SERVING["budget"]))
+        try:
+            srng.srng_server_replay(srv, trace[:200], srng.SRNG_OUT_F32, 0.0)  # warm-up
+            st = srng.srng_server_replay(srv, trace, srng.SRNG_OUT_F32, 1.0, 600000)
+        finally:
+            srng.srng_server_destroy(srv)
+            srng.srng_destroy(h)
+        res.update({"requests": len(trace), "steps": st.steps, "kernels": st.kernels, "p50_us": st.p50_us,
+                    "p99_us": st.p99_us, "Guniforms_s": st.draws_completed / st.wall_s / 1e9})
+        print(json.dumps(res), flush=True)
+        return 0
     elif c.startswith("transform"):
         n = (1 << 30) // k
         d = srng.SRNG_DIST_NORMAL if c == "transform_normal" else srng.SRNG_DIST_EXPONENTIAL
@@ -874,7 +890,7 @@ def run_case(args):
 CASES = {"mrg_u32", "mrg_f64", "mrg_plain", "philox_u32", "philox_f32", "philox_f64", "philox_normal", "philox_many_u32", "philox_keyed_many_u32",
          "threefry_u32", "threefry_f32", "threefry64_u32", "threefry64_f32",
          "tinymt_u32", "tinymt_f64",
-         "batch_write", "batch_pi", "transform_exponential", "transform_normal"}
+         "batch_write", "batch_pi", "transform_exponential", "transform_normal", "serving"}
 
 
 def main():
