@@ -136,6 +136,7 @@ def test_tuning_never_changes_output(sets, tune, n):
     (1, 131072, 32, {}),                        # 4096 chunks: bits 10 and 11
     (64, 65536, 64, dict(blocks_per_sm=1)),     # more items than threads: grid-stride passes
     (9, 8192, 128, dict(resident=3)),           # shared memory reserved beside the lane table
+    (5000, 2048, 64, {}),                       # 160,000 items: many grid-stride passes
 ])
 def test_radix_chunk_starts_vs_oracle(sets, out_type, vs, S, n, chunk, extra):
     """Direct rows with radix-32 chunk starts (chunk count a multiple of 32),
