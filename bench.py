@@ -31,6 +31,7 @@ its own; no data-path collective).
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import math
@@ -83,10 +84,14 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms, each sample
+    with its timestamp; started before the warm-up so that it runs through the
+    whole timed region, whose samples mark() selects (all samples when the
+    region is shorter than the sampling interval)."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,timestamp")
+    window = None
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
@@ -98,10 +103,14 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def mark(self, t0: float, t1: float):
+        """The timed region in host time (time.time())."""
+        self.window = (t0, t1)
 
     def stop(self):
         if self.proc is None:
@@ -120,13 +129,27 @@ class ClockSampler:
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def when(r):
+            try:
+                return datetime.datetime.strptime(r[9], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except Exception:
+                return None
+        in_region = len(rows)
+        if self.window:
+            a, b = self.window
+            sel = [r for r in rows if when(r) is not None and a - 0.02 <= when(r) <= b + 0.02]
+            in_region = len(sel)
+            if sel:
+                rows = sel
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+                "reasons": reasons, "samples": len(rows), "samples_in_region": in_region,
+                "power_w_max": max(pw) if pw else None}
 
 
 def source_hash(parts):
@@ -286,14 +309,15 @@ def run_ours(args):
         if k is not None:
             ev[k][3].record(stream)
 
+    clocks = ClockSampler(local)
+    clocks.start()  # running before the timed region starts
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
+    host_t0 = time.time()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
@@ -304,6 +328,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    clocks.mark(host_t0, time.time())
     clk = clocks.stop()
     ms_total = max_over_ranks(t_start.elapsed_time(t_end), dev)
     ms_step = ms_total / args.steps

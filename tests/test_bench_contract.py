@@ -42,3 +42,37 @@ def test_traffic_lookup_reads_the_committed_counters():
         assert e["bytes_per_launch"] > 0 and len(e["source_hash"]) == 16 and e["captured"]
         # reported only while the kernel sources are the captured ones
         assert bench.ncu_traffic(key) == (e["bytes_per_launch"] if e["source_hash"] == h else None)
+
+
+def test_clock_sampler_keeps_the_timed_window(tmp_path):
+    """The clock record keeps the samples inside the timed region (a fake
+    nvidia-smi log: one sample before, two inside, one after)."""
+    import datetime
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    cs = bench.ClockSampler(0)
+    log = tmp_path / "clocks.csv"
+    log.write_text("\n".join([
+        "0, 1000, 2070, 500.0, 0x0, Not Active, Not Active, Not Active, Not Active, 2026/12/04 10:00:00.000",
+        "0, 2070, 2070, 900.0, 0x4, Not Active, Not Active, Not Active, Active, 2026/12/04 10:00:00.100",
+        "0, 2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active, 2026/12/04 10:00:00.120",
+        "0, 900, 2070, 300.0, 0x8, Active, Not Active, Not Active, Not Active, 2026/12/04 10:00:01.000",
+    ]) + "\n")
+    cs.path = str(log)
+
+    class FakeProc:  # stands in for the sampling process
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    cs.proc = FakeProc()
+    t = lambda s: datetime.datetime.strptime(s, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+    cs.mark(t("2026/12/04 10:00:00.090"), t("2026/12/04 10:00:00.130"))
+    clk = cs.stop()
+    assert clk["samples"] == 2 and clk["samples_in_region"] == 2
+    assert clk["sm_mhz"] == 2070.0 and clk["sm_max_mhz"] == 2070.0
+    assert clk["reasons"] == ["sw_power_cap"] and clk["power_w_max"] == 950.0
