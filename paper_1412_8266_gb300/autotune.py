@@ -28,14 +28,19 @@ import paper_1412_8266_gb300 as srng
 MRG_SPACE = [dict(block_threads=bt, blocks_per_sm=b, chunk=c, vector_store=v)
              for bt, b, c, v in itertools.product((128, 256), (4, 8), (512, 1024, 2048, 4096), (1, 3))]
 # 4-byte values add the direct rows held to 6 resident blocks per SM (2^18 x 4096
-# uint32 in items of 2048: 1.150 ms, against 1.229 with no limit)
+# uint32 in items of 2048: 1.150 ms, against 1.229 with no limit), also with
+# grids of 16 and 32 blocks per SM: more blocks than fit at once, which the
+# block scheduler hands out as others finish, so no SM waits through a partial
+# last grid-stride pass (items of 1024: 1.107 ms, against 1.173 with 8)
 MRG_SPACE_4B = MRG_SPACE + [dict(block_threads=bt, blocks_per_sm=b, chunk=c, vector_store=3, resident=6)
-                            for bt, b, c in itertools.product((128, 256), (4, 8), (512, 1024, 2048, 4096))]
+                            for bt, b, c in itertools.product((128, 256), (4, 8, 16, 32), (512, 1024, 2048, 4096))]
 # FP64 adds the direct rows with three in eight doubles through the FP64 multiply
-# (with at most 6 resident blocks per SM, the FP64 default, or as many as fit: 32)
+# (with at most 6 resident blocks per SM, the FP64 default, or as many as fit:
+# 32), on grids of 4 to 32 blocks per SM (items of 1024, 16 per SM: 1.621 ms,
+# against 1.686 for the best with 8)
 MRG_SPACE_F64 = MRG_SPACE + [dict(block_threads=bt, blocks_per_sm=b, chunk=c, vector_store=4, resident=r)
-                             for bt, b, c, r in itertools.product((128, 256), (4, 8), (512, 1024, 2048, 4096),
-                                                                  (6, 32))]
+                             for bt, b, c, r in itertools.product((128, 256), (4, 8, 16, 32),
+                                                                  (512, 1024, 2048, 4096), (6, 32))]
 PHILOX_SPACE = [dict(block_threads=bt, unroll=u, blocks_per_sm=b)
                 for bt, u, b in itertools.product((128, 256), (1, 2, 4), (4, 8))]
 BATCH_SPACE = [dict(chunk=c, lane_blocks=lb) for c, lb in itertools.product((256, 512, 1024, 2048, 4096),

@@ -233,6 +233,8 @@ def test_full_size_mrg_plain_f64():
      dict(block_threads=256, blocks_per_sm=8, chunk=2048, vector_store=4)),
     (dict(block_threads=256, blocks_per_sm=8, chunk=2048, vector_store=3, resident=6),
      dict(block_threads=256, blocks_per_sm=8, chunk=2048, vector_store=4, resident=6)),
+    (dict(block_threads=256, blocks_per_sm=32, chunk=1024, vector_store=3, resident=6),
+     dict(block_threads=256, blocks_per_sm=16, chunk=1024, vector_store=4, resident=6)),
 ])
 def test_full_size_mrg_bulk_sampled(tune_u, tune_f):
     """Whole workload in the benchmark's launch configurations: seed
