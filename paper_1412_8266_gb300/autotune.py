@@ -42,7 +42,7 @@ MRG_SPACE_F64 = MRG_SPACE + [dict(block_threads=bt, blocks_per_sm=b, chunk=c, ve
                              for bt, b, c, r in itertools.product((128, 256), (4, 8, 16, 32),
                                                                   (512, 1024, 2048, 4096), (6, 32))]
 PHILOX_SPACE = [dict(block_threads=bt, unroll=u, blocks_per_sm=b)
-                for bt, u, b in itertools.product((128, 256), (1, 2, 4), (4, 8))]
+                for bt, u, b in itertools.product((128, 256), (1, 2, 4), (4, 8, 16, 32))]
 BATCH_SPACE = [dict(chunk=c, lane_blocks=lb) for c, lb in itertools.product((256, 512, 1024, 2048, 4096),
                                                                               (32, 64, 128, 256))]
 
